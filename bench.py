@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 EN-PT2 + CIPSI selection sweep.
+
+One step = one complete sweep (validation, generator order, coarse and fine
+filters, Slater-Condon accumulation, e_alpha, E_PT2 reduction, top-k
+selection) over the stored Psi0 of the mid-size workload: 64 orbitals,
+10 alpha + 10 beta electrons, 10^4 determinants grown by three CIPSI
+doublings, k = 2 * 10^4 selected determinants, FP64.
+
+Prints ONE JSON line.  ``value`` is perturbers/s with inputs resident in HBM
+(CUDA-event time of the C-ABI call, L2 flushed between steps); ``e2e`` is the
+same metric through the C-ABI call with pinned host buffers.  With N > 1
+ranks (torchrun) each rank sweeps its share of the generators
+(rank r mod N) and the partial results are merged with one all-reduce and one
+all-gather inside the timed region.
+
+``--impl reference`` times the CPU oracle instead (the reference arm): each
+step is a bounded sample of the same workload (a few generators of the
+canonical per-generator definition), on all host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "cfg2"
+METRIC = "EN-PT2 perturbers/s and generators/s on 1 GB300 vs plain FP64 GPU sweep"
+UNIT = "perturbers/s"
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic work model of the sweep kernel (lane-operations), see the
+# roofline section of the design notes: per connection (J, alpha) one
+# excitation/phase evaluation, one or two packed-integral gathers and one
+# FMA; per perturber one incremental diagonal, one division, the digest hash
+# and the selection compare; per coarse-filter pair test 2*nint XOR+POPC.
+OPS_PER_CONNECTION = 24
+OPS_PER_PERTURBER = 64
+# ALU issue peak: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz
+ALU_PEAK_GOPS = 152 * 4 * 32 * 2.07
+
+
+def load_workload(name=WORKLOAD):
+    from paper_1902_08154_gb300 import synthetic as S
+
+    P = np.load(os.path.join(ROOT, "tests", "golden", f"{name}_psi0.npz"))
+    meta = json.loads(str(P["meta"]))
+    h, eri = S.hamiltonian(meta["norb"], meta["rank"], meta["seed"])
+    return meta, h, eri, np.ascontiguousarray(P["dets"]), np.ascontiguousarray(P["coefs"]), float(P["e0"])
+
+
+def workload_config(meta, n):
+    return {
+        "workload": f"{WORKLOAD}: norb={meta['norb']}, {meta['nalpha']}a+{meta['nbeta']}b electrons, "
+                    f"ndet={meta['ndet']} (3 CIPSI doublings), k={meta['k']}, Cholesky rank {meta['rank']}, "
+                    f"seed {meta['seed']}",
+        "ndet": meta["ndet"],
+        "k_select": meta["k"],
+        "norb": meta["norb"],
+        "precision": "fp64",
+        "l2": "flushed between timed steps (256 MiB device write)",
+        "parallelism": f"generator shards x{n}" if n > 1 else "single GPU",
+    }
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(meta, h, eri, dets, coefs, e0, budget_s=15.0, stride=97):
+    """The oracle's per-generator definition on a bounded sample of
+    generators (ranks 0, stride, 2*stride, ...), all host cores."""
+    import oracle
+
+    ham = oracle.Hamiltonian(meta["norb"], meta["nalpha"], meta["nbeta"], h, eri)
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    ranks, npert, ncon = [], 0, 0
+    g = 0
+    while g < len(dets) and (time.perf_counter() - t0) < budget_s:
+        r = ham.generator(dets, coefs, e0, g, nthreads=threads)
+        npert += r["n_perturbers"]
+        ncon += r["n_connections"]
+        ranks.append(g)
+        g += stride
+    dt = time.perf_counter() - t0
+    return {"value": npert / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"per-generator oracle on {len(ranks)} of {len(dets)} generators (ranks 0, {stride}, "
+                      f"{2 * stride}, ...): {npert} perturbers in {dt:.2f} s",
+            "generators_per_s": len(ranks) / dt, "seconds": dt}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    meta, h, eri, dets, coefs, e0 = load_workload()
+    import oracle
+
+    ham = oracle.Hamiltonian(meta["norb"], meta["nalpha"], meta["nbeta"], h, eri)
+    threads = oracle.max_threads()
+    per_step = 2  # generators per step (a bounded sample of the workload)
+    stride = 97
+    g = 0
+    times, perts = [], []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        n = 0
+        for _ in range(per_step):
+            n += ham.generator(dets, coefs, e0, g % len(dets), nthreads=threads)["n_perturbers"]
+            g += stride
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+            perts.append(n)
+    T = sum(times)
+    value = sum(perts) / T
+    sample = (f"per-generator oracle, {per_step} generators per step (ranks stepping by {stride}), "
+              f"{sum(perts)} perturbers over {args.steps} steps")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(meta, 1),
+            "generators_per_s": per_step * args.steps / T,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gb300(args):
+    import torch
+
+    import paper_1902_08154_gb300 as qp
+    from paper_1902_08154_gb300.shard import distributed_merge
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    device = torch.device("cuda", torch.cuda.current_device())
+    qp.load()
+    meta, h, eri, dets, coefs, e0 = load_workload()
+    k = meta["k"]
+    stream = torch.cuda.Stream(device=device)
+    pt2 = qp.PT2(meta["norb"], meta["nalpha"], meta["nbeta"], h, eri, stream=stream.cuda_stream,
+                 shard_index=rank if world > 1 else 0, shard_count=world if world > 1 else 0)
+    nint = pt2.nint
+    d_dets = torch.from_numpy(dets.view(np.int64)).to(device)
+    d_coefs = torch.from_numpy(coefs).to(device)
+    sel = torch.zeros((k, 2, nint), dtype=torch.int64, device=device)
+    sel_e = torch.zeros(k, dtype=torch.float64, device=device)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    ndet = len(dets)
+
+    def step():
+        res = qp.qp_pt2_eval(pt2.ctx, ndet, d_dets, d_coefs, e0, k, sel, sel_e).as_dict()
+        return res
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            res = step()
+            if dist:
+                distributed_merge(dist, res, sel_e[: res["n_selected"]], sel[: res["n_selected"]], k, device)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    evs = []
+    sweep_ms, launches, units = [], 0, 0
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()
+            e0v, e1v = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0v.record(stream)
+            res = step()
+            if dist:
+                tot, _, _ = distributed_merge(dist, res, sel_e[: res["n_selected"]], sel[: res["n_selected"]],
+                                              k, device)
+                units = int(tot["n_perturbers"])
+            else:
+                units = res["n_perturbers"]
+            e1v.record(stream)
+            evs.append((e0v, e1v))
+            sweep_ms.append(qp.qp_pt2_last_timings(pt2.ctx)[0])
+            launches += qp.qp_pt2_last_launches(pt2.ctx)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    T = sum(step_ms)
+    if dist:
+        tt = torch.tensor([T], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        T = float(tt.item())
+    ms_step = T / args.steps
+    value = units / (ms_step * 1e-3)
+    gens_per_s = ndet / (ms_step * 1e-3)
+
+    # end to end through the C ABI with pinned host buffers
+    h_dets = torch.from_numpy(dets.view(np.int64)).pin_memory()
+    h_coefs = torch.from_numpy(coefs).pin_memory()
+    h_sel = torch.zeros((k, 2, nint), dtype=torch.int64).pin_memory()
+    h_sel_e = torch.zeros(k, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    with torch.cuda.stream(stream):
+        for it in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res2 = qp.qp_pt2_eval(pt2.ctx, ndet, h_dets, h_coefs, e0, k, h_sel, h_sel_e).as_dict()
+            if dist:
+                distributed_merge(dist, res2, h_sel_e[: res2["n_selected"]].to(device),
+                                  h_sel[: res2["n_selected"]].to(device), k, device)
+            t1 = time.perf_counter()
+            if it >= args.warmup:
+                e2e_times.append(t1 - t0)
+    e2e_T = sum(e2e_times)
+    if dist:
+        tt = torch.tensor([e2e_T], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_T = float(tt.item())
+    e2e_val = units / (e2e_T / args.steps)
+    h2d = dets.nbytes + coefs.nbytes
+    d2h = res2["n_selected"] * (2 * nint * 8 + 8) + 88
+
+    # roofline of the dominant kernel (the persistent sweep)
+    ms_sweep = statistics.mean(sweep_ms)
+    ops = (OPS_PER_CONNECTION * res["n_connections"] + OPS_PER_PERTURBER * res["n_perturbers"]
+           + 4 * nint * ndet * ndet // max(world, 1))
+    achieved = ops / (ms_sweep * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_GOPS, "unit": "Gop/s",
+            "frac": achieved / ALU_PEAK_GOPS, "traffic": None, "kernel": "qp::sweep_kernel<1>",
+            "kernel_ms": ms_sweep, "peak_source": "derived: 152 SMs x 128 lanes/clk x 2.07 GHz",
+            "ops_model": f"{OPS_PER_CONNECTION}/connection + {OPS_PER_PERTURBER}/perturber + 4*nint/pair test"}
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(meta, world),
+            "generators_per_s": gens_per_s, "n_perturbers": units, "e_pt2": res["e_pt2"],
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roof, "clocks": ck}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(meta, h, eri, dets, coefs, e0)
+    print(json.dumps(line), flush=True)
+    pt2.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

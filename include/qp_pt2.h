@@ -1,0 +1,155 @@
+/*
+ * qp_pt2.h -- C ABI of the GB300 (sm_103a) Epstein-Nesbet PT2 + CIPSI
+ * selection sweep (Quantum Package 2.0, arXiv:1902.08154).
+ *
+ * The library evaluates, for a zeroth-order wave function
+ * Psi0 = sum_I c_I |I> given as packed bitstring determinants,
+ *
+ *   e_alpha = <Psi0|H|alpha>^2 / (E0 - <alpha|H|alpha>)        (Eq. e2)
+ *   E_PT2   = sum over external alpha of e_alpha                 (Eq. PT2)
+ *
+ * over every external determinant alpha that is a single or double
+ * substitution of some internal determinant, together with the k external
+ * determinants of largest |e_alpha| (the CIPSI selection, Sec. "The basic
+ * algorithm", step 4).  The sweep follows the paper's determinant-driven
+ * scheme (Appendix "CIPSI selection and PT2 energy"): generators sorted by
+ * decreasing c_I^2, each alpha counted once under the first generator it is
+ * connected to (Eqs. calpha, edetstoch), a coarse filter of Psi0 per
+ * generator and batches of alpha sharing the holes of the generator, with
+ * matrix elements from the Slater-Condon rules (Eqs. Hij).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * Orbitals are 0-based, 1 <= norb <= 128; nint = (norb-1)/64 + 1.
+ * A determinant is uint64_t[2][nint]: word [0][w] holds spin-up orbitals
+ * 64w..64w+63 (orbital p in bit p%64), word [1][w] the spin-down ones
+ * (Sec. "Internal representation of determinants").  The determinant KEY
+ * orders determinants by these 2*nint words compared as unsigned integers,
+ * spin-up words first.
+ * h is double[norb*norb], row-major, symmetric: (p|h|q).
+ * eri is the 8-fold packed chemists' integral array, double[P] with
+ * P = M(M+1)/2, M = norb(norb+1)/2: (pq|rs) is stored at
+ * tri(tri(p,q), tri(r,s)), tri(a,b) = max(a,b)(max(a,b)+1)/2 + min(a,b)
+ * (the compound index of Algorithm hash, 0-based).
+ * Spin orbitals are ordered spin-up before spin-down, increasing index
+ * inside a spin; phases follow that ordering.
+ *
+ * Readings of points the paper leaves open:
+ *  - "connected" is structural: alpha is a perturber when it is not internal
+ *    and differs from some internal determinant by one or two spin orbitals,
+ *    whatever the value of the matrix element;
+ *  - generators are ranked by decreasing c_I^2 (the IEEE product c_I*c_I),
+ *    ties by increasing input index;
+ *  - the selection is ordered by decreasing |e_alpha|, ties by increasing
+ *    key; k is a parameter;
+ *  - E0 is an input and the coefficients are used as given (no
+ *    normalisation).
+ *
+ * Pointers: every array argument may be host memory or device memory of the
+ * current device; the library detects which (cudaPointerGetAttributes) and
+ * copies host arrays through its own device workspace.  The library never
+ * frees or retains caller memory.  Calls run on the stream of the context's
+ * configuration and return after the stream has finished the call's work.
+ *
+ * Errors: every entry point returns QP_OK (0) or a negative code; no call
+ * aborts, traps or throws.  qp_pt2_strerror() names a code;
+ * qp_pt2_last_error() gives the message of the last failing call of this
+ * thread.
+ */
+#ifndef QP_PT2_H
+#define QP_PT2_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QP_OK 0
+#define QP_EINVAL (-1)     /* bad size, occupation, bit beyond norb, k < 0 */
+#define QP_EDUP (-2)       /* duplicate determinant in Psi0 */
+#define QP_ESYM (-3)       /* h not symmetric to 1e-12 */
+#define QP_ESINGULAR (-4)  /* some |E0 - H_aa| < 1e-12; results still filled */
+#define QP_ENOMEM (-5)     /* device allocation failed */
+#define QP_ECUDA (-6)      /* CUDA runtime error */
+#define QP_ENOTSUP (-8)    /* configuration not supported by this build */
+
+#define QP_FP64 0          /* every step in FP64 */
+
+typedef struct qp_pt2_ctx qp_pt2_ctx; /* opaque, library-owned */
+
+typedef struct {
+    int precision;      /* QP_FP64 */
+    void *stream;       /* cudaStream_t; NULL = legacy default stream */
+    int blocks_per_sm;  /* persistent CTAs per SM; 0 = as many as fit */
+    int threads;        /* threads per CTA; 0 = 256 */
+    int shard_index;    /* generator sharding across processes: this call   */
+    int shard_count;    /* sweeps the generators of rank r with              */
+                        /* r % shard_count == shard_index (0, 0: all of them) */
+} qp_pt2_config;
+
+typedef struct {
+    double e_pt2;               /* E_PT2 (Eq. PT2) */
+    double sum_e_over_d;        /* sum_alpha A^2/D^2 = -dSigma/dE at E0 (Sec. rPT2) */
+    double min_abs_denominator; /* min |E0 - H_aa| over perturbers (inf if none) */
+    int64_t n_perturbers;       /* |A|: external determinants connected to Psi0 */
+    int64_t n_connections;      /* pairs (J, alpha), alpha in A, deg(J,alpha) <= 2 */
+    int64_t n_selected;         /* min(k, n_perturbers) */
+    int64_t n_tiny;             /* perturbers with |A_alpha| < 1e-14 */
+    uint64_t perturber_digest[2]; /* order-free digest of the perturber set: the
+                                    sum (mod 2^64) and the xor of
+                                    splitmix64(hk ^ 0x243F6A8885A308D3) over the
+                                    key hashes hk, hk = fold of splitmix64 over
+                                    the 2*nint key words starting from 0 */
+} qp_pt2_result;
+
+/* Create a context for norb orbitals and n_alpha + n_beta electrons.
+ * Copies h and eri to the device (context-owned).  cfg may be NULL.
+ * Returns QP_EINVAL for sizes out of range, QP_ESYM if h is not symmetric. */
+int qp_pt2_create(qp_pt2_ctx **out, int norb, int n_alpha, int n_beta, const double *h,
+                  const double *eri, const qp_pt2_config *cfg);
+
+/* One sweep over Psi0 (ndet determinants, layout above; coefs[ndet]).
+ * Writes the best min(k, |A|) external determinants, best first, to
+ * sel_dets[k][2][nint] and their e_alpha to sel_e[k] (either may be NULL when
+ * k = 0).  Fills *res.  Validates Psi0: QP_EINVAL for a wrong popcount or a
+ * bit at or beyond norb, QP_EDUP for a repeated determinant. */
+int qp_pt2_eval(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, const double *coefs, double e0,
+                int64_t k, uint64_t *sel_dets, double *sel_e, qp_pt2_result *res);
+
+/* With sharding (shard_count > 1) the call covers only its share of the
+ * generators: e_pt2, sums, counts and digest are partial (they add up over
+ * the shards; the digests add modulo 2^64 and xor), the selection is the best
+ * min(k, |A| of the shard) of the shard, and per-generator outputs of other
+ * shards' generators are zero.
+ *
+ * qp_pt2_eval plus optional outputs (each may be NULL):
+ *   sel_num[k]        A_alpha = <Psi0|H|alpha> of each selected determinant;
+ *   eps_by_rank[ndet] eps_I of the generator of rank r (Eq. edetstoch);
+ *   na_by_rank[ndet]  |A_I|;  ncon_by_rank[ndet]  connections of A_I;
+ *   rank_of[ndet]     rank of each input determinant in the generator order. */
+int qp_pt2_eval_ex(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, const double *coefs,
+                   double e0, int64_t k, uint64_t *sel_dets, double *sel_e, double *sel_num,
+                   double *eps_by_rank, int64_t *na_by_rank, int64_t *ncon_by_rank,
+                   int32_t *rank_of, qp_pt2_result *res);
+
+/* Number of device kernel launches made by the last qp_pt2_eval* call of ctx
+ * (the library's own kernels; the radix sorts' kernels are not counted). */
+int64_t qp_pt2_last_launches(const qp_pt2_ctx *ctx);
+
+/* Device time of the last qp_pt2_eval* call of ctx, from CUDA events recorded
+ * on the context's stream: ms[0] = the persistent sweep kernel alone,
+ * ms[1] = from the first to the last device operation of the call.
+ * Returns QP_EINVAL if no call has completed yet. */
+int qp_pt2_last_timings(const qp_pt2_ctx *ctx, double *ms);
+
+/* Release the context and its device memory.  NULL is accepted. */
+void qp_pt2_destroy(qp_pt2_ctx *ctx);
+
+const char *qp_pt2_strerror(int code);
+const char *qp_pt2_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,217 @@
+"""GB300 (sm_103a) EN-PT2 + CIPSI selection sweep: Python binding.
+
+Thin ctypes binding over the C ABI of ``include/qp_pt2.h`` with the same
+entry-point names.  It only marshals arguments (numpy arrays for host memory,
+torch CUDA tensors for device memory); every step of the sweep runs in the
+CUDA library ``_build/libqp_pt2.so``.  If that library is missing or cannot
+be loaded, ``load()`` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SO = os.path.join(HERE, "_build", "libqp_pt2.so")
+
+QP_OK, QP_EINVAL, QP_EDUP, QP_ESYM, QP_ESINGULAR, QP_ENOMEM, QP_ECUDA, QP_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -8
+QP_FP64 = 0
+
+EXPORTS = (
+    "qp_pt2_create",
+    "qp_pt2_eval",
+    "qp_pt2_eval_ex",
+    "qp_pt2_last_launches",
+    "qp_pt2_last_timings",
+    "qp_pt2_destroy",
+    "qp_pt2_strerror",
+    "qp_pt2_last_error",
+)
+
+
+class Config(C.Structure):
+    _fields_ = [("precision", C.c_int), ("stream", C.c_void_p), ("blocks_per_sm", C.c_int), ("threads", C.c_int),
+                ("shard_index", C.c_int), ("shard_count", C.c_int)]
+
+
+class Result(C.Structure):
+    _fields_ = [
+        ("e_pt2", C.c_double),
+        ("sum_e_over_d", C.c_double),
+        ("min_abs_denominator", C.c_double),
+        ("n_perturbers", C.c_int64),
+        ("n_connections", C.c_int64),
+        ("n_selected", C.c_int64),
+        ("n_tiny", C.c_int64),
+        ("perturber_digest", C.c_uint64 * 2),
+    ]
+
+    def as_dict(self):
+        return {
+            "e_pt2": self.e_pt2,
+            "sum_e_over_d": self.sum_e_over_d,
+            "min_abs_den": self.min_abs_denominator,
+            "n_perturbers": self.n_perturbers,
+            "n_connections": self.n_connections,
+            "n_selected": self.n_selected,
+            "n_tiny": self.n_tiny,
+            "digest": (int(self.perturber_digest[0]), int(self.perturber_digest[1])),
+        }
+
+
+class QPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = SO):
+    """Load the CUDA library (raises if it is absent: no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = C.CDLL(path)
+    vp, i64, dbl = C.c_void_p, C.c_int64, C.c_double
+    L.qp_pt2_create.restype = C.c_int
+    L.qp_pt2_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, vp, vp, C.POINTER(Config)]
+    L.qp_pt2_eval.restype = C.c_int
+    L.qp_pt2_eval.argtypes = [vp, i64, vp, vp, dbl, i64, vp, vp, C.POINTER(Result)]
+    L.qp_pt2_eval_ex.restype = C.c_int
+    L.qp_pt2_eval_ex.argtypes = [vp, i64, vp, vp, dbl, i64, vp, vp, vp, vp, vp, vp, vp, C.POINTER(Result)]
+    L.qp_pt2_last_launches.restype = i64
+    L.qp_pt2_last_launches.argtypes = [vp]
+    L.qp_pt2_last_timings.restype = C.c_int
+    L.qp_pt2_last_timings.argtypes = [vp, C.POINTER(C.c_double)]
+    L.qp_pt2_destroy.restype = None
+    L.qp_pt2_destroy.argtypes = [vp]
+    L.qp_pt2_strerror.restype = C.c_char_p
+    L.qp_pt2_strerror.argtypes = [C.c_int]
+    L.qp_pt2_last_error.restype = C.c_char_p
+    L.qp_pt2_last_error.argtypes = []
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or torch tensor (None stays NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def _check(rc):
+    if rc != QP_OK:
+        L = load()
+        raise QPError(rc, f"{L.qp_pt2_strerror(rc).decode()}: {L.qp_pt2_last_error().decode()}")
+
+
+def qp_pt2_create(norb, n_alpha, n_beta, h, eri, stream=None, blocks_per_sm=0, precision=QP_FP64,
+                  shard_index=0, shard_count=0):
+    """Create a context; h and eri are float64 numpy arrays or CUDA tensors."""
+    L = load()
+    cfg = Config(precision, stream or None, blocks_per_sm, 0, shard_index, shard_count)
+    out = C.c_void_p()
+    _check(L.qp_pt2_create(C.byref(out), norb, n_alpha, n_beta, _ptr(h), _ptr(eri), C.byref(cfg)))
+    return out
+
+
+def qp_pt2_destroy(ctx):
+    load().qp_pt2_destroy(ctx)
+
+
+def qp_pt2_eval(ctx, ndet, dets, coefs, e0, k, sel_dets=None, sel_e=None):
+    res = Result()
+    _check(load().qp_pt2_eval(ctx, ndet, _ptr(dets), _ptr(coefs), float(e0), k, _ptr(sel_dets), _ptr(sel_e),
+                              C.byref(res)))
+    return res
+
+
+def qp_pt2_eval_ex(ctx, ndet, dets, coefs, e0, k, sel_dets=None, sel_e=None, sel_num=None, eps_by_rank=None,
+                   na_by_rank=None, ncon_by_rank=None, rank_of=None, check=True):
+    res = Result()
+    rc = load().qp_pt2_eval_ex(ctx, ndet, _ptr(dets), _ptr(coefs), float(e0), k, _ptr(sel_dets), _ptr(sel_e),
+                               _ptr(sel_num), _ptr(eps_by_rank), _ptr(na_by_rank), _ptr(ncon_by_rank),
+                               _ptr(rank_of), C.byref(res))
+    if check:
+        _check(rc)
+    return rc, res
+
+
+def qp_pt2_last_launches(ctx):
+    return int(load().qp_pt2_last_launches(ctx))
+
+
+def qp_pt2_last_timings(ctx):
+    """(sweep kernel ms, whole call ms) of the last call, from CUDA events."""
+    ms = (C.c_double * 2)()
+    _check(load().qp_pt2_last_timings(ctx, ms))
+    return float(ms[0]), float(ms[1])
+
+
+class PT2:
+    """Owning wrapper: one context per (Hamiltonian, electron count)."""
+
+    def __init__(self, norb, n_alpha, n_beta, h, eri, stream=None, blocks_per_sm=0, shard_index=0,
+                 shard_count=0):
+        self.norb, self.n_alpha, self.n_beta = norb, n_alpha, n_beta
+        self.nint = (norb - 1) // 64 + 1
+        self.ctx = qp_pt2_create(norb, n_alpha, n_beta, h, eri, stream, blocks_per_sm,
+                                 shard_index=shard_index, shard_count=shard_count)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and _lib is not None:
+            qp_pt2_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        self.close()
+
+    def eval(self, dets, coefs, e0, k, per_generator=False, check=True):
+        """Sweep with host (numpy) or device (torch CUDA) inputs; outputs are
+        allocated in the same kind of memory as ``dets``."""
+        ndet = len(dets)
+        on_device = not isinstance(dets, np.ndarray)
+        if on_device:
+            import torch
+
+            dev = dets.device
+            sel = torch.zeros((max(k, 1), 2, self.nint), dtype=torch.int64, device=dev)
+            se = torch.zeros(max(k, 1), dtype=torch.float64, device=dev)
+            sn = torch.zeros(max(k, 1), dtype=torch.float64, device=dev)
+            if per_generator:
+                eps = torch.zeros(max(ndet, 1), dtype=torch.float64, device=dev)
+                na = torch.zeros(max(ndet, 1), dtype=torch.int64, device=dev)
+                nc = torch.zeros(max(ndet, 1), dtype=torch.int64, device=dev)
+                rk = torch.zeros(max(ndet, 1), dtype=torch.int32, device=dev)
+        else:
+            sel = np.zeros((max(k, 1), 2, self.nint), dtype=np.uint64)
+            se = np.zeros(max(k, 1))
+            sn = np.zeros(max(k, 1))
+            if per_generator:
+                eps = np.zeros(max(ndet, 1))
+                na = np.zeros(max(ndet, 1), dtype=np.int64)
+                nc = np.zeros(max(ndet, 1), dtype=np.int64)
+                rk = np.zeros(max(ndet, 1), dtype=np.int32)
+        if not per_generator:
+            eps = na = nc = rk = None
+        rc, res = qp_pt2_eval_ex(self.ctx, ndet, dets, coefs, e0, k, sel if k else None, se if k else None,
+                                 sn if k else None, eps, na, nc, rk, check=check)
+        out = res.as_dict()
+        out["rc"] = rc
+        m = res.n_selected
+        out.update(sel_dets=sel[:m], sel_e=se[:m], sel_num=sn[:m])
+        if per_generator:
+            out.update(eps_by_rank=eps[:ndet], na_by_rank=na[:ndet], ncon_by_rank=nc[:ndet], rank_of=rk[:ndet])
+        out["launches"] = qp_pt2_last_launches(self.ctx)
+        return out

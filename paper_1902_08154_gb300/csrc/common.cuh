@@ -1,0 +1,96 @@
+// common.cuh -- device helpers and launch parameters of the sm_103a EN-PT2
+// sweep (Quantum Package 2.0, arXiv:1902.08154).  Internal to the library.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qp {
+
+constexpr int kMaxOrb = 128;
+constexpr int kMaxElec = 64;  // per determinant (both spins); hole masks are uint64
+
+// Fold of splitmix64 over the key words: the digest hash of a determinant.
+// splitmix64 is the generator of Steele, Lea & Flood (2014); its finaliser
+// constants are those of Vigna's public reference implementation.
+__host__ __device__ inline uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// Compound triangular index of Algorithm hash (0-based).
+__device__ __forceinline__ int tri(int a, int b) {
+  int hi = a > b ? a : b, lo = a > b ? b : a;
+  return hi * (hi + 1) / 2 + lo;
+}
+
+__device__ __forceinline__ int eri_index(int p, int q, int r, int s) {
+  return tri(tri(p, q), tri(r, s));
+}
+
+// Number of set bits of the spin string sw (NINT words) strictly between
+// orbitals lo < hi: the masked popcount that gives a single substitution's
+// phase (Sec. "Internal representation of determinants").
+template <int NINT>
+__device__ __forceinline__ int count_between(const uint64_t* sw, int lo, int hi) {
+  int a = lo + 1, b = hi, n = 0;
+#pragma unroll
+  for (int w = 0; w < NINT; w++) {
+    int l = a - 64 * w, u = b - 64 * w;
+    l = l < 0 ? 0 : l;
+    u = u > 64 ? 64 : u;
+    if (l < u) {
+      uint64_t m = (u == 64 ? ~0ull : ((1ull << u) - 1)) & ~((1ull << l) - 1);
+      n += __popcll(sw[w] & m);
+    }
+  }
+  return n;
+}
+
+struct SweepParams {
+  int norb, nalpha, nbeta, nel;
+  int64_t ndet;
+  const uint64_t* dets;   // [ndet][2][NINT]
+  const double* coefs;    // [ndet]
+  const int32_t* order;   // det index by rank
+  const int32_t* rank_of; // rank by det index
+  const double* h;        // [norb*norb]
+  const double* eri;      // packed
+  const double* Jm;       // [norb*norb] (pp|qq)
+  const double* Km;       // [norb*norb] (pq|qp)
+  double e0;
+
+  // per-generator outputs, by rank
+  double* eps;
+  double* s2;
+  long long* na;
+  long long* ncon;
+  // global accumulators
+  unsigned long long* digest;       // [2]
+  unsigned long long* min_den_bits; // bits of min |D| (non-negative double)
+  unsigned long long* n_tiny;
+  int* queue;                       // next generator rank to take
+  int shard_index, shard_count;     // this call sweeps ranks r = shard_index + t * shard_count
+
+  // per-CTA coarse-filter records (capacity ndet each), structure of arrays
+  uint64_t* f_words;   // [grid][ndet][2*NINT]
+  double* f_coef;      // [grid][ndet]
+  uint64_t* f_hmask;   // [grid][ndet]  holes of I missing from J, by occupied index
+  uint64_t* f_part;    // [grid][ndet]  up to 4 particle spin-orbital codes, 16 bits each (0xFFFF = none)
+  uint32_t* f_flag;    // [grid][ndet]  bit 0: rank(J) < rank(I)
+
+  // selection
+  int64_t k;
+  int64_t cap;                   // per-CTA candidate capacity (>= k + max cells)
+  double* tk_e;                  // [grid][cap]
+  double* tk_a;                  // [grid][cap]
+  uint64_t* tk_key;              // [grid][cap][2*NINT]
+  int* tk_cnt;                   // [grid]
+  unsigned long long* tau_bits;  // global selection threshold (bits of |e|)
+
+  int max_cells;
+  int* err;                      // device error flags (0 = fine)
+};
+
+}  // namespace qp

@@ -1,0 +1,657 @@
+// qp_pt2.cu -- C ABI of the EN-PT2 + selection sweep (include/qp_pt2.h):
+// context set-up, input validation, generator ranking, the persistent sweep
+// launch, the fixed-order E_PT2 reduction and the merge of the selection.
+#include <cuda_runtime.h>
+
+#include <cub/device/device_radix_sort.cuh>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/qp_pt2.h"
+#include "common.cuh"
+
+namespace qp {
+cudaError_t launch_sweep(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
+int sweep_blocks_per_sm(int nint, size_t smem);
+int sweep_threads();
+}  // namespace qp
+
+using namespace qp;
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(e_ == cudaErrorMemoryAllocation ? QP_ENOMEM : QP_ECUDA,                  \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+// device error flags
+enum : int { kErrOcc = 1, kErrDup = 2, kErrCoef = 4 };
+
+// ---------------------------------------------------------------------------
+// Small kernels
+// ---------------------------------------------------------------------------
+__global__ void jk_kernel(int norb, const double* eri, double* Jm, double* Km) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= norb * norb) return;
+  int p = x / norb, q = x % norb;
+  Jm[x] = eri[eri_index(p, p, q, q)];
+  Km[x] = eri[eri_index(p, q, q, p)];
+}
+
+// Occupation counts, bits beyond norb, finite coefficients; key hashes for
+// the duplicate check; generator sort keys.
+__global__ void prep_kernel(int64_t ndet, int nint, int norb, int na, int nb, const uint64_t* dets,
+                            const double* coefs, unsigned long long* hkey, int32_t* hidx,
+                            unsigned long long* rkey, int32_t* ridx, int* err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ndet) return;
+  const int nw = 2 * nint;
+  const uint64_t* d = dets + i * nw;
+  int bad = 0;
+  uint64_t hk = 0;
+  for (int s = 0; s < 2; s++) {
+    int n = 0;
+    for (int w = 0; w < nint; w++) {
+      uint64_t x = d[s * nint + w];
+      n += __popcll(x);
+      int lo = norb - 64 * w;  // bits >= lo of this word are beyond norb
+      if (lo < 64) {
+        uint64_t beyond = lo <= 0 ? ~0ull : ~((1ull << lo) - 1);
+        if (x & beyond) bad = 1;
+      }
+    }
+    if (n != (s == 0 ? na : nb)) bad = 1;
+  }
+  for (int w = 0; w < nw; w++) hk = splitmix64(hk ^ d[w]);
+  if (bad) atomicOr(err, kErrOcc);
+  const double c = coefs[i];
+  if (!isfinite(c)) atomicOr(err, kErrCoef);
+  hkey[i] = hk;
+  hidx[i] = (int32_t)i;
+  // decreasing c^2 == increasing ~bits(c*c); the radix sort is stable, so
+  // ties keep increasing input index
+  const double c2 = c * c;
+  rkey[i] = ~(unsigned long long)__double_as_longlong(c2);
+  ridx[i] = (int32_t)i;
+}
+
+__global__ void dup_kernel(int64_t ndet, int nint, const uint64_t* dets, const unsigned long long* hs,
+                           const int32_t* hi, int* err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ndet) return;
+  const int nw = 2 * nint;
+  for (int64_t j = i + 1; j < ndet && hs[j] == hs[i]; j++) {
+    bool same = true;
+    for (int w = 0; w < nw; w++) same &= dets[(int64_t)hi[i] * nw + w] == dets[(int64_t)hi[j] * nw + w];
+    if (same) atomicOr(err, kErrDup);
+  }
+}
+
+__global__ void rank_kernel(int64_t ndet, const int32_t* order, int32_t* rank_of) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < ndet) rank_of[order[g]] = (int32_t)g;
+}
+
+struct DevResult {
+  double e_pt2, s2;
+  long long na, ncon;
+};
+
+// One block: fixed-order sums over generators (rank order), each thread a
+// contiguous slice with Neumaier compensation, then a fixed tree.
+__global__ void finalize_kernel(int64_t ndet, const double* eps, const double* s2, const long long* na,
+                                const long long* nc, DevResult* out) {
+  __shared__ double se[1024], ce[1024], ss[1024];
+  __shared__ long long sa[1024], sc[1024];
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int64_t per = (ndet + nt - 1) / nt;
+  const int64_t b = t * per, e = (b + per < ndet) ? b + per : ndet;
+  double s = 0, c = 0, q = 0;
+  long long x = 0, y = 0;
+  for (int64_t i = b; i < e; i++) {
+    double v = eps[i], tt = s + v;
+    if (fabs(s) >= fabs(v)) c += (s - tt) + v;
+    else c += (v - tt) + s;
+    s = tt;
+    q += s2[i];
+    x += na[i];
+    y += nc[i];
+  }
+  se[t] = s;
+  ce[t] = c;
+  ss[t] = q;
+  sa[t] = x;
+  sc[t] = y;
+  __syncthreads();
+  for (int o = nt / 2; o > 0; o >>= 1) {
+    if (t < o) {
+      se[t] += se[t + o];
+      ce[t] += ce[t + o];
+      ss[t] += ss[t + o];
+      sa[t] += sa[t + o];
+      sc[t] += sc[t + o];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    out->e_pt2 = se[0] + ce[0];
+    out->s2 = ss[0];
+    out->na = sa[0];
+    out->ncon = sc[0];
+  }
+}
+
+// Gather the CTAs' selection buffers, dropping entries below the global
+// threshold (they cannot be among the k best).
+__global__ void gather_kernel(int grid, int nint, int64_t cap, const int* tk_cnt, const double* tk_e,
+                              const double* tk_a, const uint64_t* tk_key, const unsigned long long* tau,
+                              double* ce, double* ca, uint64_t* ck, int* ncand) {
+  const int b = blockIdx.x;
+  const int nw = 2 * nint;
+  const int n = tk_cnt[b];
+  const unsigned long long t = *tau;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const size_t src = (size_t)b * cap + i;
+    const double e = tk_e[src];
+    if ((unsigned long long)__double_as_longlong(fabs(e)) < t) continue;
+    const int o = atomicAdd(ncand, 1);
+    ce[o] = e;
+    ca[o] = tk_a[src];
+    for (int w = 0; w < nw; w++) ck[(size_t)o * nw + w] = tk_key[src * nw + w];
+  }
+}
+
+// sort key of pass w: w < nw: key word w; w == nw: ~bits(|e|)
+__global__ void sortkey_kernel(int n, int nint, int w, const double* ce, const uint64_t* ck,
+                               const int32_t* perm, unsigned long long* keys) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int nw = 2 * nint, j = perm[i];
+  keys[i] = (w < nw) ? ck[(size_t)j * nw + w] : ~(unsigned long long)__double_as_longlong(fabs(ce[j]));
+}
+
+__global__ void iota_kernel(int n, int32_t* v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = i;
+}
+
+__global__ void select_out_kernel(int n, int nint, const int32_t* perm, const double* ce, const double* ca,
+                                  const uint64_t* ck, uint64_t* sel, double* se, double* sn) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int nw = 2 * nint, j = perm[i];
+  if (sel)
+    for (int w = 0; w < nw; w++) sel[(size_t)i * nw + w] = ck[(size_t)j * nw + w];
+  if (se) se[i] = ce[j];
+  if (sn) sn[i] = ca[j];
+}
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct Buf {
+  void* p = nullptr;
+  size_t n = 0;
+  int grow(size_t bytes) {
+    if (bytes <= n) return QP_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    size_t want = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return fail(e == cudaErrorMemoryAllocation ? QP_ENOMEM : QP_ECUDA,
+                  std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    n = want;
+    return QP_OK;
+  }
+  template <typename T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+struct qp_pt2_ctx {
+  int norb, nalpha, nbeta, nint, nel;
+  int64_t P;
+  qp_pt2_config cfg;
+  cudaStream_t st;
+  int device, nsm;
+  int max_cells, bps, grid;
+  size_t smem;
+  double *d_h = nullptr, *d_eri = nullptr, *d_J = nullptr, *d_K = nullptr;
+  // workspace
+  Buf in_dets, in_coefs, hkey, hkey2, hidx, hidx2, rkey, rkey2, order, rank_of, cub_tmp;
+  Buf eps, s2, na, ncon, acc, res;
+  Buf f_words, f_coef, f_hmask, f_part, f_flag;
+  Buf tk_e, tk_a, tk_key, tk_cnt;
+  Buf cand_e, cand_a, cand_key, skey, skey2, perm, perm2, cub_tmp2;
+  Buf out_sel, out_e, out_num, out_eps, out_na, out_ncon, out_rank;
+  int64_t launches = 0;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // call start, sweep start, sweep end
+  cudaEvent_t ev_end = nullptr;
+  bool timed = false;
+};
+
+// accumulator block layout (unsigned long long words)
+enum { kAccDigest0 = 0, kAccDigest1, kAccMinDen, kAccTiny, kAccTau, kAccQueue, kAccErr, kAccNcand, kAccWords };
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int cells_max(int norb, int na, int nb) {
+  const int va = norb - na, vb = norb - nb;
+  int m = va > vb ? va : vb;
+  int t = va * (va - 1) / 2;
+  m = t > m ? t : m;
+  t = vb * (vb - 1) / 2;
+  m = t > m ? t : m;
+  t = va * vb;
+  m = t > m ? t : m;
+  return m;
+}
+
+extern "C" int qp_pt2_create(qp_pt2_ctx** out, int norb, int n_alpha, int n_beta, const double* h,
+                             const double* eri, const qp_pt2_config* cfg) {
+  if (!out) return fail(QP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (norb < 1 || norb > kMaxOrb) return fail(QP_EINVAL, "norb must be in [1, 128]");
+  if (n_alpha < 0 || n_beta < 0 || n_alpha > norb || n_beta > norb)
+    return fail(QP_EINVAL, "electron counts out of range");
+  if (n_alpha + n_beta > kMaxElec) return fail(QP_EINVAL, "more than 64 electrons");
+  if (!h || !eri) return fail(QP_EINVAL, "h or eri is NULL");
+  qp_pt2_config c{};
+  if (cfg) c = *cfg;
+  if (c.precision != QP_FP64) return fail(QP_ENOTSUP, "only QP_FP64 is implemented");
+  if (c.threads != 0 && c.threads != sweep_threads())
+    return fail(QP_ENOTSUP, "threads per CTA is fixed at 256 in this build");
+  const int64_t M = (int64_t)norb * (norb + 1) / 2, P = M * (M + 1) / 2;
+  // symmetry of h (host copy either way)
+  std::vector<double> hh((size_t)norb * norb);
+  if (is_device_ptr(h)) {
+    if (cudaMemcpy(hh.data(), h, sizeof(double) * norb * norb, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(QP_ECUDA, "copy of h failed");
+  } else {
+    memcpy(hh.data(), h, sizeof(double) * norb * norb);
+  }
+  for (int p = 0; p < norb; p++)
+    for (int q = 0; q < p; q++)
+      if (!(fabs(hh[(size_t)p * norb + q] - hh[(size_t)q * norb + p]) <= 1e-12))
+        return fail(QP_ESYM, "h is not symmetric");
+  qp_pt2_ctx* x = new (std::nothrow) qp_pt2_ctx();
+  if (!x) return fail(QP_ENOMEM, "host allocation failed");
+  x->norb = norb;
+  x->nalpha = n_alpha;
+  x->nbeta = n_beta;
+  x->nint = (norb - 1) / 64 + 1;
+  x->nel = n_alpha + n_beta;
+  x->P = P;
+  x->cfg = c;
+  x->st = (cudaStream_t)c.stream;
+  auto bail = [&](int code, const char* what) {
+    qp_pt2_destroy(x);
+    return fail(code, what);
+  };
+  if (c.shard_count < 0 || c.shard_index < 0 || (c.shard_count > 0 && c.shard_index >= c.shard_count))
+    return bail(QP_EINVAL, "shard_index must lie in [0, shard_count)");
+  if (c.shard_count == 0) {
+    x->cfg.shard_count = 1;
+    x->cfg.shard_index = 0;
+  }
+  if (cudaGetDevice(&x->device) != cudaSuccess) return bail(QP_ECUDA, "no CUDA device");
+  for (int i = 0; i < 3; i++)
+    if (cudaEventCreate(&x->ev[i]) != cudaSuccess) return bail(QP_ECUDA, "cudaEventCreate failed");
+  if (cudaEventCreate(&x->ev_end) != cudaSuccess) return bail(QP_ECUDA, "cudaEventCreate failed");
+  cudaDeviceGetAttribute(&x->nsm, cudaDevAttrMultiProcessorCount, x->device);
+  if (cudaMalloc(&x->d_h, sizeof(double) * norb * norb) != cudaSuccess ||
+      cudaMalloc(&x->d_eri, sizeof(double) * P) != cudaSuccess ||
+      cudaMalloc(&x->d_J, sizeof(double) * norb * norb) != cudaSuccess ||
+      cudaMalloc(&x->d_K, sizeof(double) * norb * norb) != cudaSuccess)
+    return bail(QP_ENOMEM, "device allocation of the integrals failed");
+  if (cudaMemcpyAsync(x->d_h, hh.data(), sizeof(double) * norb * norb, cudaMemcpyHostToDevice, x->st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(x->d_eri, eri, sizeof(double) * P, cudaMemcpyDefault, x->st) != cudaSuccess)
+    return bail(QP_ECUDA, "copy of the integrals failed");
+  jk_kernel<<<(norb * norb + 255) / 256, 256, 0, x->st>>>(norb, x->d_eri, x->d_J, x->d_K);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(x->st) != cudaSuccess)
+    return bail(QP_ECUDA, "integral tables failed");
+  x->max_cells = cells_max(norb, n_alpha, n_beta);
+  if (x->max_cells < 1) x->max_cells = 1;
+  x->smem = sizeof(double) * x->max_cells + sizeof(uint32_t) * ((x->max_cells + 31) / 32);
+  int bps = sweep_blocks_per_sm(x->nint, x->smem);
+  if (bps < 1) return bail(QP_ENOTSUP, "the batch accumulator does not fit in shared memory");
+  if (c.blocks_per_sm > 0 && c.blocks_per_sm < bps) bps = c.blocks_per_sm;
+  x->bps = bps;
+  x->grid = bps * x->nsm;
+  *out = x;
+  return QP_OK;
+}
+
+extern "C" void qp_pt2_destroy(qp_pt2_ctx* x) {
+  if (!x) return;
+  for (int i = 0; i < 3; i++)
+    if (x->ev[i]) cudaEventDestroy(x->ev[i]);
+  if (x->ev_end) cudaEventDestroy(x->ev_end);
+  cudaFree(x->d_h);
+  cudaFree(x->d_eri);
+  cudaFree(x->d_J);
+  cudaFree(x->d_K);
+  Buf* all[] = {&x->in_dets, &x->in_coefs, &x->hkey, &x->hkey2, &x->hidx, &x->hidx2, &x->rkey, &x->rkey2,
+                &x->order, &x->rank_of, &x->cub_tmp, &x->eps, &x->s2, &x->na, &x->ncon, &x->acc,
+                &x->res, &x->f_words, &x->f_coef, &x->f_hmask, &x->f_part, &x->f_flag, &x->tk_e,
+                &x->tk_a, &x->tk_key, &x->tk_cnt, &x->cand_e, &x->cand_a, &x->cand_key, &x->skey,
+                &x->skey2, &x->perm, &x->perm2, &x->cub_tmp2, &x->out_sel, &x->out_e, &x->out_num,
+                &x->out_eps, &x->out_na, &x->out_ncon, &x->out_rank};
+  for (Buf* b : all) b->release();
+  delete x;
+}
+
+extern "C" int64_t qp_pt2_last_launches(const qp_pt2_ctx* x) { return x ? x->launches : 0; }
+
+extern "C" int qp_pt2_last_timings(const qp_pt2_ctx* x, double* ms) {
+  if (!x || !ms) return fail(QP_EINVAL, "ctx or ms is NULL");
+  if (!x->timed) return fail(QP_EINVAL, "no completed call to time");
+  float a = 0.f, b = 0.f;
+  if (cudaEventElapsedTime(&a, x->ev[1], x->ev[2]) != cudaSuccess ||
+      cudaEventElapsedTime(&b, x->ev[0], x->ev_end) != cudaSuccess)
+    return fail(QP_ECUDA, "cudaEventElapsedTime failed");
+  ms[0] = a;
+  ms[1] = b;
+  return QP_OK;
+}
+
+extern "C" const char* qp_pt2_strerror(int code) {
+  switch (code) {
+    case QP_OK: return "ok";
+    case QP_EINVAL: return "invalid argument";
+    case QP_EDUP: return "duplicate determinant";
+    case QP_ESYM: return "h is not symmetric";
+    case QP_ESINGULAR: return "a denominator E0 - H_aa is below 1e-12 in magnitude";
+    case QP_ENOMEM: return "device memory allocation failed";
+    case QP_ECUDA: return "CUDA runtime error";
+    case QP_ENOTSUP: return "not supported by this build";
+    default: return "unknown error";
+  }
+}
+
+extern "C" const char* qp_pt2_last_error(void) { return g_last_error.c_str(); }
+
+// Stage a caller array on the device: returns the device pointer to use.
+template <typename T>
+static int stage_in(qp_pt2_ctx* x, Buf& b, const T* src, size_t count, const T** dst) {
+  if (is_device_ptr(src)) {
+    *dst = src;
+    return QP_OK;
+  }
+  int rc = b.grow(sizeof(T) * count);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(b.p, src, sizeof(T) * count, cudaMemcpyHostToDevice, x->st));
+  *dst = b.as<T>();
+  return QP_OK;
+}
+
+template <typename T>
+static int out_target(Buf& b, T* user, size_t count, T** dst, bool* copy_back) {
+  *copy_back = false;
+  *dst = nullptr;
+  if (!user) return QP_OK;
+  if (is_device_ptr(user)) {
+    *dst = user;
+    return QP_OK;
+  }
+  int rc = b.grow(sizeof(T) * (count ? count : 1));
+  if (rc) return rc;
+  *dst = b.as<T>();
+  *copy_back = true;
+  return QP_OK;
+}
+
+extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const double* coefs,
+                              double e0, int64_t k, uint64_t* sel_dets, double* sel_e, double* sel_num,
+                              double* eps_by_rank, int64_t* na_by_rank, int64_t* ncon_by_rank,
+                              int32_t* rank_of_out, qp_pt2_result* res) {
+  if (!x || !res) return fail(QP_EINVAL, "ctx or res is NULL");
+  if (ndet < 0 || k < 0) return fail(QP_EINVAL, "ndet and k must be non-negative");
+  if (ndet > 0 && (!dets || !coefs)) return fail(QP_EINVAL, "dets or coefs is NULL");
+  if (ndet >= (1ll << 31)) return fail(QP_EINVAL, "ndet must be below 2^31");
+  if (!std::isfinite(e0)) return fail(QP_EINVAL, "E0 is not finite");
+  memset(res, 0, sizeof(*res));
+  res->min_abs_denominator = INFINITY;
+  x->launches = 0;
+  x->timed = false;
+  if (ndet == 0) return QP_OK;
+  const int nint = x->nint, nw = 2 * nint;
+  cudaStream_t st = x->st;
+  int rc;
+  const uint64_t* d_dets;
+  const double* d_coefs;
+  CUDA_TRY(cudaEventRecord(x->ev[0], st));
+  if ((rc = stage_in(x, x->in_dets, dets, (size_t)ndet * nw, &d_dets))) return rc;
+  if ((rc = stage_in(x, x->in_coefs, coefs, (size_t)ndet, &d_coefs))) return rc;
+
+  // ---- validation and generator order ----
+  const size_t nd = (size_t)ndet;
+  if ((rc = x->hkey.grow(8 * nd)) || (rc = x->hkey2.grow(8 * nd)) || (rc = x->hidx.grow(4 * nd)) ||
+      (rc = x->hidx2.grow(4 * nd)) || (rc = x->rkey.grow(8 * nd)) || (rc = x->rkey2.grow(8 * nd)) ||
+      (rc = x->order.grow(4 * nd)) || (rc = x->rank_of.grow(4 * nd)) || (rc = x->acc.grow(8 * kAccWords)))
+    return rc;
+  unsigned long long* acc = x->acc.as<unsigned long long>();
+  {
+    unsigned long long init[kAccWords] = {0};
+    init[kAccMinDen] = 0x7FF0000000000000ull;  // +inf
+    CUDA_TRY(cudaMemcpyAsync(acc, init, sizeof(init), cudaMemcpyHostToDevice, st));
+  }
+  int* d_err = reinterpret_cast<int*>(acc + kAccErr);
+  const int tb = 256;
+  const int nb = (int)((ndet + tb - 1) / tb);
+  prep_kernel<<<nb, tb, 0, st>>>(ndet, nint, x->norb, x->nalpha, x->nbeta, d_dets, d_coefs,
+                                 x->hkey.as<unsigned long long>(), x->hidx.as<int32_t>(),
+                                 x->rkey.as<unsigned long long>(), x->rank_of.as<int32_t>(), d_err);
+  x->launches++;
+  CUDA_TRY(cudaGetLastError());
+  size_t tmp1 = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, tmp1, x->hkey.as<unsigned long long>(),
+                                  x->hkey2.as<unsigned long long>(), x->hidx.as<int32_t>(),
+                                  x->hidx2.as<int32_t>(), (int)ndet, 0, 64, st);
+  if ((rc = x->cub_tmp.grow(tmp1))) return rc;
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(x->cub_tmp.p, tmp1, x->hkey.as<unsigned long long>(),
+                                           x->hkey2.as<unsigned long long>(), x->hidx.as<int32_t>(),
+                                           x->hidx2.as<int32_t>(), (int)ndet, 0, 64, st));
+  dup_kernel<<<nb, tb, 0, st>>>(ndet, nint, d_dets, x->hkey2.as<unsigned long long>(), x->hidx2.as<int32_t>(),
+                                d_err);
+  x->launches++;
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(x->cub_tmp.p, tmp1, x->rkey.as<unsigned long long>(),
+                                           x->rkey2.as<unsigned long long>(), x->rank_of.as<int32_t>(),
+                                           x->order.as<int32_t>(), (int)ndet, 0, 64, st));
+  rank_kernel<<<nb, tb, 0, st>>>(ndet, x->order.as<int32_t>(), x->rank_of.as<int32_t>());
+  x->launches++;
+  int herr = 0;
+  CUDA_TRY(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (herr & kErrOcc) return fail(QP_EINVAL, "a determinant has the wrong occupation or bits beyond norb");
+  if (herr & kErrCoef) return fail(QP_EINVAL, "a coefficient is not finite");
+  if (herr & kErrDup) return fail(QP_EDUP, "duplicate determinant in Psi0");
+
+  // ---- sweep ----
+  const int grid = x->grid;
+  const int64_t cap = k > 0 ? k + x->max_cells : 1;
+  if ((rc = x->eps.grow(8 * nd)) || (rc = x->s2.grow(8 * nd)) || (rc = x->na.grow(8 * nd)) ||
+      (rc = x->ncon.grow(8 * nd)) || (rc = x->f_words.grow(8 * nd * nw * grid)) ||
+      (rc = x->f_coef.grow(8 * nd * grid)) || (rc = x->f_hmask.grow(8 * nd * grid)) ||
+      (rc = x->f_part.grow(8 * nd * grid)) || (rc = x->f_flag.grow(4 * nd * grid)) ||
+      (rc = x->tk_e.grow(8 * (size_t)cap * grid)) || (rc = x->tk_a.grow(8 * (size_t)cap * grid)) ||
+      (rc = x->tk_key.grow(8 * (size_t)cap * grid * nw)) || (rc = x->tk_cnt.grow(4 * (size_t)grid)) ||
+      (rc = x->res.grow(sizeof(DevResult))))
+    return rc;
+  SweepParams p{};
+  p.norb = x->norb;
+  p.nalpha = x->nalpha;
+  p.nbeta = x->nbeta;
+  p.nel = x->nel;
+  p.ndet = ndet;
+  p.dets = d_dets;
+  p.coefs = d_coefs;
+  p.order = x->order.as<int32_t>();
+  p.rank_of = x->rank_of.as<int32_t>();
+  p.h = x->d_h;
+  p.eri = x->d_eri;
+  p.Jm = x->d_J;
+  p.Km = x->d_K;
+  p.e0 = e0;
+  p.eps = x->eps.as<double>();
+  p.s2 = x->s2.as<double>();
+  p.na = x->na.as<long long>();
+  p.ncon = x->ncon.as<long long>();
+  p.digest = acc + kAccDigest0;
+  p.min_den_bits = acc + kAccMinDen;
+  p.n_tiny = acc + kAccTiny;
+  p.queue = reinterpret_cast<int*>(acc + kAccQueue);
+  p.f_words = x->f_words.as<uint64_t>();
+  p.f_coef = x->f_coef.as<double>();
+  p.f_hmask = x->f_hmask.as<uint64_t>();
+  p.f_part = x->f_part.as<uint64_t>();
+  p.f_flag = x->f_flag.as<uint32_t>();
+  p.k = k;
+  p.cap = cap;
+  p.tk_e = x->tk_e.as<double>();
+  p.tk_a = x->tk_a.as<double>();
+  p.tk_key = x->tk_key.as<uint64_t>();
+  p.tk_cnt = x->tk_cnt.as<int>();
+  p.tau_bits = acc + kAccTau;
+  p.max_cells = x->max_cells;
+  p.err = d_err;
+  p.shard_index = x->cfg.shard_index;
+  p.shard_count = x->cfg.shard_count;
+  if (x->cfg.shard_count > 1) {
+    CUDA_TRY(cudaMemsetAsync(p.eps, 0, 8 * nd, st));
+    CUDA_TRY(cudaMemsetAsync(p.s2, 0, 8 * nd, st));
+    CUDA_TRY(cudaMemsetAsync(p.na, 0, 8 * nd, st));
+    CUDA_TRY(cudaMemsetAsync(p.ncon, 0, 8 * nd, st));
+  }
+  CUDA_TRY(cudaEventRecord(x->ev[1], st));
+  CUDA_TRY(launch_sweep(nint, p, grid, x->smem, st));
+  CUDA_TRY(cudaEventRecord(x->ev[2], st));
+  x->launches++;
+  DevResult* dres = x->res.as<DevResult>();
+  finalize_kernel<<<1, 1024, 0, st>>>(ndet, p.eps, p.s2, p.na, p.ncon, dres);
+  x->launches++;
+  CUDA_TRY(cudaGetLastError());
+
+  // ---- selection merge ----
+  int64_t nsel = 0;
+  if (k > 0) {
+    const size_t maxc = (size_t)grid * (size_t)k;
+    if ((rc = x->cand_e.grow(8 * maxc)) || (rc = x->cand_a.grow(8 * maxc)) ||
+        (rc = x->cand_key.grow(8 * maxc * nw)) || (rc = x->skey.grow(8 * maxc)) ||
+        (rc = x->skey2.grow(8 * maxc)) || (rc = x->perm.grow(4 * maxc)) || (rc = x->perm2.grow(4 * maxc)))
+      return rc;
+    int* d_ncand = reinterpret_cast<int*>(acc + kAccNcand);
+    gather_kernel<<<grid, 256, 0, st>>>(grid, nint, cap, p.tk_cnt, p.tk_e, p.tk_a, p.tk_key, p.tau_bits,
+                                        x->cand_e.as<double>(), x->cand_a.as<double>(),
+                                        x->cand_key.as<uint64_t>(), d_ncand);
+    x->launches++;
+    int ncand = 0;
+    CUDA_TRY(cudaMemcpyAsync(&ncand, d_ncand, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (ncand > 0) {
+      size_t tmp2 = 0;
+      cub::DeviceRadixSort::SortPairs(nullptr, tmp2, x->skey.as<unsigned long long>(),
+                                      x->skey2.as<unsigned long long>(), x->perm.as<int32_t>(),
+                                      x->perm2.as<int32_t>(), ncand, 0, 64, st);
+      if ((rc = x->cub_tmp2.grow(tmp2))) return rc;
+      const int sb = (ncand + 255) / 256;
+      iota_kernel<<<sb, 256, 0, st>>>(ncand, x->perm.as<int32_t>());
+      x->launches++;
+      // least significant first: key words from last to first, then |e|
+      for (int pass = 0; pass <= nw; pass++) {
+        const int word = (pass < nw) ? (nw - 1 - pass) : nw;  // nw means |e|
+        sortkey_kernel<<<sb, 256, 0, st>>>(ncand, nint, word, x->cand_e.as<double>(),
+                                           x->cand_key.as<uint64_t>(), x->perm.as<int32_t>(),
+                                           x->skey.as<unsigned long long>());
+        x->launches++;
+        CUDA_TRY(cub::DeviceRadixSort::SortPairs(x->cub_tmp2.p, tmp2, x->skey.as<unsigned long long>(),
+                                                 x->skey2.as<unsigned long long>(), x->perm.as<int32_t>(),
+                                                 x->perm2.as<int32_t>(), ncand, 0, 64, st));
+        std::swap(x->perm, x->perm2);
+      }
+      nsel = ncand < k ? ncand : k;
+      uint64_t* d_sel;
+      double *d_se, *d_sn;
+      bool cb1, cb2, cb3;
+      if ((rc = out_target(x->out_sel, sel_dets, (size_t)k * nw, &d_sel, &cb1)) ||
+          (rc = out_target(x->out_e, sel_e, (size_t)k, &d_se, &cb2)) ||
+          (rc = out_target(x->out_num, sel_num, (size_t)k, &d_sn, &cb3)))
+        return rc;
+      select_out_kernel<<<(int)((nsel + 255) / 256), 256, 0, st>>>((int)nsel, nint, x->perm.as<int32_t>(),
+                                                                 x->cand_e.as<double>(), x->cand_a.as<double>(),
+                                                                 x->cand_key.as<uint64_t>(), d_sel, d_se, d_sn);
+      x->launches++;
+      CUDA_TRY(cudaGetLastError());
+      if (cb1) CUDA_TRY(cudaMemcpyAsync(sel_dets, d_sel, 8 * nsel * nw, cudaMemcpyDeviceToHost, st));
+      if (cb2) CUDA_TRY(cudaMemcpyAsync(sel_e, d_se, 8 * nsel, cudaMemcpyDeviceToHost, st));
+      if (cb3) CUDA_TRY(cudaMemcpyAsync(sel_num, d_sn, 8 * nsel, cudaMemcpyDeviceToHost, st));
+    }
+  }
+
+  // ---- per-generator outputs ----
+  auto copy_out = [&](void* user, const void* dev, size_t bytes) -> int {
+    if (!user) return QP_OK;
+    CUDA_TRY(cudaMemcpyAsync(user, dev, bytes, cudaMemcpyDefault, st));
+    return QP_OK;
+  };
+  if ((rc = copy_out(eps_by_rank, p.eps, 8 * nd)) || (rc = copy_out(na_by_rank, p.na, 8 * nd)) ||
+      (rc = copy_out(ncon_by_rank, p.ncon, 8 * nd)) || (rc = copy_out(rank_of_out, p.rank_of, 4 * nd)))
+    return rc;
+
+  DevResult hres;
+  unsigned long long hacc[kAccWords];
+  CUDA_TRY(cudaMemcpyAsync(&hres, dres, sizeof(hres), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaEventRecord(x->ev_end, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  x->timed = true;
+  res->e_pt2 = hres.e_pt2;
+  res->sum_e_over_d = hres.s2;
+  res->n_perturbers = hres.na;
+  res->n_connections = hres.ncon;
+  res->n_selected = nsel;
+  res->n_tiny = (int64_t)hacc[kAccTiny];
+  res->perturber_digest[0] = hacc[kAccDigest0];
+  res->perturber_digest[1] = hacc[kAccDigest1];
+  double md;
+  memcpy(&md, &hacc[kAccMinDen], sizeof(md));
+  res->min_abs_denominator = md;
+  if (hres.na > 0 && md < 1e-12) return fail(QP_ESINGULAR, "a denominator E0 - H_aa is below 1e-12");
+  return QP_OK;
+}
+
+extern "C" int qp_pt2_eval(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const double* coefs, double e0,
+                           int64_t k, uint64_t* sel_dets, double* sel_e, qp_pt2_result* res) {
+  return qp_pt2_eval_ex(x, ndet, dets, coefs, e0, k, sel_dets, sel_e, nullptr, nullptr, nullptr, nullptr,
+                        nullptr, res);
+}

@@ -1,0 +1,79 @@
+"""Write the stored workloads and their expected sweep results.
+
+Calls only the CPU oracle (``oracle/``) and the seeded input generator; no
+value here comes from the CUDA path.  Usage:
+
+    python tests/golden/make_inputs.py cfg1 [cfg2 ...]
+
+Workloads (synthetic stand-ins for the paper's molecules, whose integrals are
+not available; shapes follow the paper's CAS-sized active spaces):
+
+  cfg1: norb 16, 4+4 electrons, Cholesky rank 32, seed 0.  Psi0 = HF + the 49
+        lowest-diagonal single/double substitutions of HF; c and E0 from dense
+        diagonalisation of the 50x50 block.  Expected results with k = 100.
+  cfg2: norb 64, 10+10 electrons, Cholesky rank 96, seed 1.  Psi0 of 10^4
+        determinants grown from a 1250-determinant seed space by three CIPSI
+        doublings (top |e_alpha| selection), coefficients from Davidson to a
+        residual below 1e-10.  Expected results with k = 2 * 10^4.
+
+Files: ``<cfg>_psi0.npz`` (dets, coefs, e0 and metadata) and
+``<cfg>_expected.npz`` (totals, per-generator arrays by rank, selection).
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+from oracle import psi0  # noqa: E402
+from paper_1902_08154_gb300 import synthetic as S  # noqa: E402
+
+CONFIGS = {
+    "cfg1": dict(norb=16, nalpha=4, nbeta=4, rank=32, seed=0, ndet=50, k=100, grow=False),
+    "cfg2": dict(norb=64, nalpha=10, nbeta=10, rank=96, seed=1, ndet=10000, k=20000, grow=True),
+}
+
+
+def log(msg):
+    print(msg, flush=True)
+
+
+def make(name, mem_budget=12 << 30):
+    cfg = CONFIGS[name]
+    t0 = time.time()
+    h, eri = S.hamiltonian(cfg["norb"], cfg["rank"], cfg["seed"])
+    ham = oracle.Hamiltonian(cfg["norb"], cfg["nalpha"], cfg["nbeta"], h, eri)
+    hf = S.hf_det(cfg["norb"], cfg["nalpha"], cfg["nbeta"])
+    if cfg["grow"]:
+        dets, c, e0, info = psi0.cipsi_grow(ham, hf, cfg["ndet"], doublings=3, log=log)
+    else:
+        dets = psi0.seed_space(ham, hf, cfg["ndet"])
+        e0, c, res = psi0.ground_state(ham, dets)
+        info = [{"ndet": len(dets), "e0": e0, "residual": res}]
+    log(f"{name}: psi0 ready ({len(dets)} dets, e0={e0:.12f}) in {time.time() - t0:.1f}s")
+    meta = dict(cfg, digest=S.hamiltonian_digest(h, eri), growth=info)
+    np.savez_compressed(os.path.join(HERE, f"{name}_psi0.npz"), dets=dets, coefs=c, e0=np.float64(e0),
+                        meta=json.dumps(meta))
+    t1 = time.time()
+    out = ham.sweep(dets, c, e0, k=cfg["k"], mem_budget=mem_budget)
+    log(f"{name}: sweep E_PT2={out['e_pt2']:.12f} |A|={out['n_perturbers']} "
+        f"connections={out['n_connections']} in {time.time() - t1:.1f}s")
+    summary = {k: v for k, v in out.items() if not isinstance(v, np.ndarray)}
+    summary["digest"] = [str(x) for x in summary["digest"]]
+    np.savez_compressed(os.path.join(HERE, f"{name}_expected.npz"), sel_dets=out["sel_dets"],
+                        sel_e=out["sel_e"], sel_num=out["sel_num"], eps_by_rank=out["eps_by_rank"],
+                        na_by_rank=out["na_by_rank"], ncon_by_rank=out["ncon_by_rank"],
+                        rank_of=out["rank_of"], summary=json.dumps(summary))
+
+
+if __name__ == "__main__":
+    for name in sys.argv[1:] or ["cfg1"]:
+        make(name)
