@@ -199,6 +199,9 @@ def run_gb300(args):
     device = torch.device("cuda", torch.cuda.current_device())
     qp.load()
     meta, h, eri, dets, coefs, e0 = load_workload()
+    if args.ndet:
+        dets, coefs = dets[: args.ndet].copy(), coefs[: args.ndet].copy()
+        meta = dict(meta, ndet=len(dets), k=min(meta["k"], 2 * len(dets)))
     k = meta["k"]
     stream = torch.cuda.Stream(device=device)
     pt2 = qp.PT2(meta["norb"], meta["nalpha"], meta["nbeta"], h, eri, stream=stream.cuda_stream,
@@ -260,32 +263,36 @@ def run_gb300(args):
     value = units / (ms_step * 1e-3)
     gens_per_s = ndet / (ms_step * 1e-3)
 
-    # end to end through the C ABI with pinned host buffers
-    h_dets = torch.from_numpy(dets.view(np.int64)).pin_memory()
-    h_coefs = torch.from_numpy(coefs).pin_memory()
-    h_sel = torch.zeros((k, 2, nint), dtype=torch.int64).pin_memory()
-    h_sel_e = torch.zeros(k, dtype=torch.float64).pin_memory()
-    e2e_times = []
-    with torch.cuda.stream(stream):
-        for it in range(args.warmup + args.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            res2 = qp.qp_pt2_eval(pt2.ctx, ndet, h_dets, h_coefs, e0, k, h_sel, h_sel_e).as_dict()
-            if dist:
-                distributed_merge(dist, res2, h_sel_e[: res2["n_selected"]].to(device),
-                                  h_sel[: res2["n_selected"]].to(device), k, device)
-            t1 = time.perf_counter()
-            if it >= args.warmup:
-                e2e_times.append(t1 - t0)
-    e2e_T = sum(e2e_times)
-    if dist:
-        tt = torch.tensor([e2e_T], dtype=torch.float64, device=device)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_T = float(tt.item())
-    e2e_val = units / (e2e_T / args.steps)
-    h2d = dets.nbytes + coefs.nbytes
-    d2h = res2["n_selected"] * (2 * nint * 8 + 8) + 88
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the C ABI with pinned host buffers
+        h_dets = torch.from_numpy(dets.view(np.int64)).pin_memory()
+        h_coefs = torch.from_numpy(coefs).pin_memory()
+        h_sel = torch.zeros((k, 2, nint), dtype=torch.int64).pin_memory()
+        h_sel_e = torch.zeros(k, dtype=torch.float64).pin_memory()
+        e2e_times = []
+        with torch.cuda.stream(stream):
+            for it in range(args.warmup + args.steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res2 = qp.qp_pt2_eval(pt2.ctx, ndet, h_dets, h_coefs, e0, k, h_sel, h_sel_e).as_dict()
+                if dist:
+                    distributed_merge(dist, res2, h_sel_e[: res2["n_selected"]].to(device),
+                                      h_sel[: res2["n_selected"]].to(device), k, device)
+                t1 = time.perf_counter()
+                if it >= args.warmup:
+                    e2e_times.append(t1 - t0)
+        e2e_T = sum(e2e_times)
+        if dist:
+            tt = torch.tensor([e2e_T], dtype=torch.float64, device=device)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_T = float(tt.item())
+        e2e_val = units / (e2e_T / args.steps)
+        h2d = dets.nbytes + coefs.nbytes
+        d2h = res2["n_selected"] * (2 * nint * 8 + 8) + 88
+
+        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # roofline of the dominant kernel (the persistent sweep)
     ms_sweep = statistics.mean(sweep_ms)
@@ -302,7 +309,7 @@ def run_gb300(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(meta, world),
             "generators_per_s": gens_per_s, "n_perturbers": units, "e_pt2": res["e_pt2"],
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": e2e,
             "gpu_launches": launches, "roofline": roof, "clocks": ck}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(meta, h, eri, dets, coefs, e0)
@@ -320,6 +327,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--ndet", type=int, default=0,
+                    help="profiling runs only: sweep the first NDET determinants of the stored Psi0")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -7,7 +7,8 @@
 namespace qp {
 
 constexpr int kMaxOrb = 128;
-constexpr int kMaxElec = 64;  // per determinant (both spins); hole masks are uint64
+constexpr int kMaxElec = 64;   // per determinant (both spins); hole masks are uint64
+constexpr int kMaxBatch = kMaxElec + kMaxElec * (kMaxElec - 1) / 2;
 
 // Fold of splitmix64 over the key words: the digest hash of a determinant.
 // splitmix64 is the generator of Steele, Lea & Flood (2014); its finaliser
@@ -48,8 +49,18 @@ __device__ __forceinline__ int count_between(const uint64_t* sw, int lo, int hi)
   return n;
 }
 
+// Per-generator data built by the prep kernel and read by the batch kernel.
+struct GenMeta {
+  uint64_t I[4];            // generator determinant (2*NINT words used)
+  int g;                    // rank of the generator (-1: empty slot)
+  int nrec;                 // coarse-filter records
+  double hii;               // <I|H|I>
+  int occ[kMaxElec];        // spin-orbital codes s*norb+q of I, ordered
+  double F[2][kMaxOrb];     // Fock diagonal of I
+};
+
 struct SweepParams {
-  int norb, nalpha, nbeta, nel;
+  int norb, nalpha, nbeta, nel, nbat;
   int64_t ndet;
   const uint64_t* dets;   // [ndet][2][NINT]
   const double* coefs;    // [ndet]
@@ -60,25 +71,34 @@ struct SweepParams {
   const double* Jm;       // [norb*norb] (pp|qq)
   const double* Km;       // [norb*norb] (pq|qp)
   double e0;
+  int shard_index, shard_count;   // generators of rank shard_index + t*shard_count
+
+  // wave of generator slots
+  int wave_start;                 // first generator position (t) of this wave
+  int wave_slots;                 // slots in this wave
+  int last_wave;                  // 1 on the last wave: final selection compaction
+  int* queue;                     // per-wave item counter
+
+  // per-slot data (capacity ndet records, ent_cap bucket entries)
+  GenMeta* meta;                  // [slots]
+  uint64_t* r_words;              // [slots][ndet][2*NINT]
+  double* r_coef;                 // [slots][ndet]
+  uint64_t* r_hmask;              // [slots][ndet]  holes of I missing from J (occupied index bits)
+  uint64_t* r_part;               // [slots][ndet]  up to 4 particle codes of J outside I, 16 bits each
+  uint32_t* r_flag;               // [slots][ndet]  bit 0: rank(J) < rank(I)
+  int* b_ofs;                     // [slots][nbat + 2]  bucket offsets (bucket nbat: J within degree 2)
+  int32_t* b_ent;                 // [slots][ent_cap]   record indices
+  int64_t ent_cap;
 
   // per-generator outputs, by rank
   double* eps;
   double* s2;
-  long long* na;
-  long long* ncon;
+  unsigned long long* na;
+  unsigned long long* ncon;
   // global accumulators
   unsigned long long* digest;       // [2]
   unsigned long long* min_den_bits; // bits of min |D| (non-negative double)
   unsigned long long* n_tiny;
-  int* queue;                       // next generator rank to take
-  int shard_index, shard_count;     // this call sweeps ranks r = shard_index + t * shard_count
-
-  // per-CTA coarse-filter records (capacity ndet each), structure of arrays
-  uint64_t* f_words;   // [grid][ndet][2*NINT]
-  double* f_coef;      // [grid][ndet]
-  uint64_t* f_hmask;   // [grid][ndet]  holes of I missing from J, by occupied index
-  uint64_t* f_part;    // [grid][ndet]  up to 4 particle spin-orbital codes, 16 bits each (0xFFFF = none)
-  uint32_t* f_flag;    // [grid][ndet]  bit 0: rank(J) < rank(I)
 
   // selection
   int64_t k;
@@ -87,6 +107,7 @@ struct SweepParams {
   double* tk_a;                  // [grid][cap]
   uint64_t* tk_key;              // [grid][cap][2*NINT]
   int* tk_cnt;                   // [grid]
+  unsigned long long* tk_tau;    // [grid] CTA thresholds (bits of |e|)
   unsigned long long* tau_bits;  // global selection threshold (bits of |e|)
 
   int max_cells;

@@ -15,8 +15,9 @@
 #include "common.cuh"
 
 namespace qp {
-cudaError_t launch_sweep(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
-int sweep_blocks_per_sm(int nint, size_t smem);
+cudaError_t launch_prep(int nint, const SweepParams& p, int slots, cudaStream_t st);
+cudaError_t launch_batch(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
+int batch_blocks_per_sm(int nint, size_t smem);
 int sweep_threads();
 }  // namespace qp
 
@@ -38,7 +39,10 @@ static int fail(int code, const std::string& msg) {
   } while (0)
 
 // device error flags
-enum : int { kErrOcc = 1, kErrDup = 2, kErrCoef = 4 };
+enum : int { kErrOcc = 1, kErrDup = 2, kErrCoef = 4, kErrBucket = 8 };
+
+// device memory allowed for the per-generator records and buckets of a wave
+static const size_t kWaveBudget = (size_t)4 << 30;
 
 // ---------------------------------------------------------------------------
 // Small kernels
@@ -230,7 +234,7 @@ struct Buf {
 };
 
 struct qp_pt2_ctx {
-  int norb, nalpha, nbeta, nint, nel;
+  int norb, nalpha, nbeta, nint, nel, nbat;
   int64_t P;
   qp_pt2_config cfg;
   cudaStream_t st;
@@ -241,8 +245,8 @@ struct qp_pt2_ctx {
   // workspace
   Buf in_dets, in_coefs, hkey, hkey2, hidx, hidx2, rkey, rkey2, order, rank_of, cub_tmp;
   Buf eps, s2, na, ncon, acc, res;
-  Buf f_words, f_coef, f_hmask, f_part, f_flag;
-  Buf tk_e, tk_a, tk_key, tk_cnt;
+  Buf meta, r_words, r_coef, r_hmask, r_part, r_flag, b_ofs, b_ent, queues;
+  Buf tk_e, tk_a, tk_key, tk_cnt, tk_tau;
   Buf cand_e, cand_a, cand_key, skey, skey2, perm, perm2, cub_tmp2;
   Buf out_sel, out_e, out_num, out_eps, out_na, out_ncon, out_rank;
   int64_t launches = 0;
@@ -310,6 +314,7 @@ extern "C" int qp_pt2_create(qp_pt2_ctx** out, int norb, int n_alpha, int n_beta
   x->nbeta = n_beta;
   x->nint = (norb - 1) / 64 + 1;
   x->nel = n_alpha + n_beta;
+  x->nbat = x->nel + x->nel * (x->nel - 1) / 2;
   x->P = P;
   x->cfg = c;
   x->st = (cudaStream_t)c.stream;
@@ -343,7 +348,7 @@ extern "C" int qp_pt2_create(qp_pt2_ctx** out, int norb, int n_alpha, int n_beta
   x->max_cells = cells_max(norb, n_alpha, n_beta);
   if (x->max_cells < 1) x->max_cells = 1;
   x->smem = sizeof(double) * x->max_cells + sizeof(uint32_t) * ((x->max_cells + 31) / 32);
-  int bps = sweep_blocks_per_sm(x->nint, x->smem);
+  int bps = batch_blocks_per_sm(x->nint, x->smem);
   if (bps < 1) return bail(QP_ENOTSUP, "the batch accumulator does not fit in shared memory");
   if (c.blocks_per_sm > 0 && c.blocks_per_sm < bps) bps = c.blocks_per_sm;
   x->bps = bps;
@@ -363,8 +368,8 @@ extern "C" void qp_pt2_destroy(qp_pt2_ctx* x) {
   cudaFree(x->d_K);
   Buf* all[] = {&x->in_dets, &x->in_coefs, &x->hkey, &x->hkey2, &x->hidx, &x->hidx2, &x->rkey, &x->rkey2,
                 &x->order, &x->rank_of, &x->cub_tmp, &x->eps, &x->s2, &x->na, &x->ncon, &x->acc,
-                &x->res, &x->f_words, &x->f_coef, &x->f_hmask, &x->f_part, &x->f_flag, &x->tk_e,
-                &x->tk_a, &x->tk_key, &x->tk_cnt, &x->cand_e, &x->cand_a, &x->cand_key, &x->skey,
+                &x->res, &x->meta, &x->r_words, &x->r_coef, &x->r_hmask, &x->r_part, &x->r_flag,
+                &x->b_ofs, &x->b_ent, &x->queues, &x->tk_e, &x->tk_a, &x->tk_key, &x->tk_cnt, &x->tk_tau, &x->cand_e, &x->cand_a, &x->cand_key, &x->skey,
                 &x->skey2, &x->perm, &x->perm2, &x->cub_tmp2, &x->out_sel, &x->out_e, &x->out_num,
                 &x->out_eps, &x->out_na, &x->out_ncon, &x->out_rank};
   for (Buf* b : all) b->release();
@@ -497,22 +502,43 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
   if (herr & kErrCoef) return fail(QP_EINVAL, "a coefficient is not finite");
   if (herr & kErrDup) return fail(QP_EDUP, "duplicate determinant in Psi0");
 
-  // ---- sweep ----
+  // ---- sweep: waves of generator slots, prep + batch kernels ----
   const int grid = x->grid;
   const int64_t cap = k > 0 ? k + x->max_cells : 1;
+  const int shard_count = x->cfg.shard_count, shard_index = x->cfg.shard_index;
+  const int64_t ngen = (ndet > shard_index) ? (ndet - shard_index + shard_count - 1) / shard_count : 0;
+  const int64_t ent_per = x->nel >= 3 ? 3 * x->nel - 3 : 1;
+  const int64_t ent_cap = (int64_t)nd * ent_per;
+  const size_t per_slot = sizeof(GenMeta) + nd * (8 * nw + 8 + 8 + 8 + 4) + 4 * (size_t)(x->nbat + 2) +
+                          4 * (size_t)ent_cap;
+  int64_t W = (int64_t)(kWaveBudget / per_slot);
+  if (W < 1) W = 1;
+  if (W > ngen) W = ngen > 0 ? ngen : 1;
+  const int64_t nwaves = ngen > 0 ? (ngen + W - 1) / W : 0;
+  const size_t ws = (size_t)W;
   if ((rc = x->eps.grow(8 * nd)) || (rc = x->s2.grow(8 * nd)) || (rc = x->na.grow(8 * nd)) ||
-      (rc = x->ncon.grow(8 * nd)) || (rc = x->f_words.grow(8 * nd * nw * grid)) ||
-      (rc = x->f_coef.grow(8 * nd * grid)) || (rc = x->f_hmask.grow(8 * nd * grid)) ||
-      (rc = x->f_part.grow(8 * nd * grid)) || (rc = x->f_flag.grow(4 * nd * grid)) ||
+      (rc = x->ncon.grow(8 * nd)) || (rc = x->meta.grow(sizeof(GenMeta) * ws)) ||
+      (rc = x->r_words.grow(8 * nd * nw * ws)) || (rc = x->r_coef.grow(8 * nd * ws)) ||
+      (rc = x->r_hmask.grow(8 * nd * ws)) || (rc = x->r_part.grow(8 * nd * ws)) ||
+      (rc = x->r_flag.grow(4 * nd * ws)) || (rc = x->b_ofs.grow(4 * (size_t)(x->nbat + 2) * ws)) ||
+      (rc = x->b_ent.grow(4 * (size_t)ent_cap * ws)) || (rc = x->queues.grow(4 * (size_t)(nwaves + 1))) ||
       (rc = x->tk_e.grow(8 * (size_t)cap * grid)) || (rc = x->tk_a.grow(8 * (size_t)cap * grid)) ||
       (rc = x->tk_key.grow(8 * (size_t)cap * grid * nw)) || (rc = x->tk_cnt.grow(4 * (size_t)grid)) ||
-      (rc = x->res.grow(sizeof(DevResult))))
+      (rc = x->tk_tau.grow(8 * (size_t)grid)) || (rc = x->res.grow(sizeof(DevResult))))
     return rc;
+  CUDA_TRY(cudaMemsetAsync(x->eps.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->s2.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->na.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->ncon.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->queues.p, 0, 4 * (size_t)(nwaves + 1), st));
+  CUDA_TRY(cudaMemsetAsync(x->tk_cnt.p, 0, 4 * (size_t)grid, st));
+  CUDA_TRY(cudaMemsetAsync(x->tk_tau.p, 0, 8 * (size_t)grid, st));
   SweepParams p{};
   p.norb = x->norb;
   p.nalpha = x->nalpha;
   p.nbeta = x->nbeta;
   p.nel = x->nel;
+  p.nbat = x->nbat;
   p.ndet = ndet;
   p.dets = d_dets;
   p.coefs = d_coefs;
@@ -523,42 +549,48 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
   p.Jm = x->d_J;
   p.Km = x->d_K;
   p.e0 = e0;
+  p.shard_index = shard_index;
+  p.shard_count = shard_count;
+  p.meta = x->meta.as<GenMeta>();
+  p.r_words = x->r_words.as<uint64_t>();
+  p.r_coef = x->r_coef.as<double>();
+  p.r_hmask = x->r_hmask.as<uint64_t>();
+  p.r_part = x->r_part.as<uint64_t>();
+  p.r_flag = x->r_flag.as<uint32_t>();
+  p.b_ofs = x->b_ofs.as<int>();
+  p.b_ent = x->b_ent.as<int32_t>();
+  p.ent_cap = ent_cap;
   p.eps = x->eps.as<double>();
   p.s2 = x->s2.as<double>();
-  p.na = x->na.as<long long>();
-  p.ncon = x->ncon.as<long long>();
+  p.na = x->na.as<unsigned long long>();
+  p.ncon = x->ncon.as<unsigned long long>();
   p.digest = acc + kAccDigest0;
   p.min_den_bits = acc + kAccMinDen;
   p.n_tiny = acc + kAccTiny;
-  p.queue = reinterpret_cast<int*>(acc + kAccQueue);
-  p.f_words = x->f_words.as<uint64_t>();
-  p.f_coef = x->f_coef.as<double>();
-  p.f_hmask = x->f_hmask.as<uint64_t>();
-  p.f_part = x->f_part.as<uint64_t>();
-  p.f_flag = x->f_flag.as<uint32_t>();
   p.k = k;
   p.cap = cap;
   p.tk_e = x->tk_e.as<double>();
   p.tk_a = x->tk_a.as<double>();
   p.tk_key = x->tk_key.as<uint64_t>();
   p.tk_cnt = x->tk_cnt.as<int>();
+  p.tk_tau = x->tk_tau.as<unsigned long long>();
   p.tau_bits = acc + kAccTau;
   p.max_cells = x->max_cells;
   p.err = d_err;
-  p.shard_index = x->cfg.shard_index;
-  p.shard_count = x->cfg.shard_count;
-  if (x->cfg.shard_count > 1) {
-    CUDA_TRY(cudaMemsetAsync(p.eps, 0, 8 * nd, st));
-    CUDA_TRY(cudaMemsetAsync(p.s2, 0, 8 * nd, st));
-    CUDA_TRY(cudaMemsetAsync(p.na, 0, 8 * nd, st));
-    CUDA_TRY(cudaMemsetAsync(p.ncon, 0, 8 * nd, st));
-  }
   CUDA_TRY(cudaEventRecord(x->ev[1], st));
-  CUDA_TRY(launch_sweep(nint, p, grid, x->smem, st));
+  for (int64_t w = 0; w < nwaves; w++) {
+    p.wave_start = (int)(w * W);
+    p.wave_slots = (int)((ngen - w * W) < W ? (ngen - w * W) : W);
+    p.last_wave = (w == nwaves - 1);
+    p.queue = x->queues.as<int>() + w;
+    CUDA_TRY(launch_prep(nint, p, p.wave_slots, st));
+    CUDA_TRY(launch_batch(nint, p, grid, x->smem, st));
+    x->launches += 2;
+  }
   CUDA_TRY(cudaEventRecord(x->ev[2], st));
-  x->launches++;
   DevResult* dres = x->res.as<DevResult>();
-  finalize_kernel<<<1, 1024, 0, st>>>(ndet, p.eps, p.s2, p.na, p.ncon, dres);
+  finalize_kernel<<<1, 1024, 0, st>>>(ndet, p.eps, p.s2, reinterpret_cast<const long long*>(p.na),
+                                      reinterpret_cast<const long long*>(p.ncon), dres);
   x->launches++;
   CUDA_TRY(cudaGetLastError());
 
@@ -632,9 +664,11 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
   unsigned long long hacc[kAccWords];
   CUDA_TRY(cudaMemcpyAsync(&hres, dres, sizeof(hres), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaEventRecord(x->ev_end, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   x->timed = true;
+  if (herr & kErrBucket) return fail(QP_ECUDA, "internal error: bucket capacity exceeded");
   res->e_pt2 = hres.e_pt2;
   res->sum_e_over_d = hres.s2;
   res->n_perturbers = hres.na;
