@@ -143,6 +143,34 @@ int64_t qp_pt2_last_launches(const qp_pt2_ctx *ctx);
  * Returns QP_EINVAL if no call has completed yet. */
 int qp_pt2_last_timings(const qp_pt2_ctx *ctx, double *ms);
 
+/* The whole sweep without allocating any device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc or cudaFree -- a host program that reserves the GPU's memory up
+ * front and gives its plugins no allocator, or a deployment whose device
+ * footprint must stay fixed.
+ *
+ * No context is used.  h, eri, dets, coefs and (when k > 0) sel_dets and
+ * sel_e must be device memory of the current device (QP_EINVAL otherwise);
+ * layouts are those of qp_pt2_create and qp_pt2_eval; res is host memory.
+ * The work runs on `stream` (a cudaStream_t, NULL = legacy default stream)
+ * and the call returns once it has finished.  Results equal those of
+ * qp_pt2_eval for the same inputs (same rules, same tolerances).
+ *
+ * Scratch: one 64 MiB device array inside the library (static storage),
+ * which every GPU that loads the library holds until the process exits.  The
+ * first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Every call reuses the same array: calls whose GPU work
+ * overlaps (other streams, other threads) race and must not be issued.
+ * Problems whose integral tables, generator order, per-generator records,
+ * selection buffers (one CTA per SM, k + cells entries each) and sort space
+ * do not fit in the array are refused with QP_EINVAL; as a guide, 64
+ * orbitals with 10+10 electrons fit up to roughly 10^3 determinants with
+ * k = 10^3. */
+int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const double *h, const double *eri,
+                        int64_t ndet, const uint64_t *dets, const double *coefs, double e0, int64_t k,
+                        uint64_t *sel_dets, double *sel_e, qp_pt2_result *res, void *stream);
+
 /* Release the context and its device memory.  NULL is accepted. */
 void qp_pt2_destroy(qp_pt2_ctx *ctx);
 

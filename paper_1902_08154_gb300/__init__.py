@@ -28,6 +28,7 @@ EXPORTS = (
     "qp_pt2_destroy",
     "qp_pt2_strerror",
     "qp_pt2_last_error",
+    "qp_pt2_eval_noalloc",
 )
 
 
@@ -95,6 +96,9 @@ def load(path: str = SO):
     L.qp_pt2_strerror.argtypes = [C.c_int]
     L.qp_pt2_last_error.restype = C.c_char_p
     L.qp_pt2_last_error.argtypes = []
+    L.qp_pt2_eval_noalloc.restype = C.c_int
+    L.qp_pt2_eval_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, i64, vp, vp, dbl, i64, vp, vp,
+                                      C.POINTER(Result), vp]
     _lib = L
     return L
 
@@ -145,6 +149,16 @@ def qp_pt2_eval_ex(ctx, ndet, dets, coefs, e0, k, sel_dets=None, sel_e=None, sel
                                _ptr(rank_of), C.byref(res))
     if check:
         _check(rc)
+    return rc, res
+
+
+def qp_pt2_eval_noalloc(norb, n_alpha, n_beta, h, eri, ndet, dets, coefs, e0, k, sel_dets=None, sel_e=None,
+                        stream=None):
+    """The sweep with no device allocation (every array a CUDA tensor); see
+    include/qp_pt2.h.  Returns (return code, Result)."""
+    res = Result()
+    rc = load().qp_pt2_eval_noalloc(norb, n_alpha, n_beta, _ptr(h), _ptr(eri), ndet, _ptr(dets), _ptr(coefs),
+                                    float(e0), k, _ptr(sel_dets), _ptr(sel_e), C.byref(res), stream or None)
     return rc, res
 
 

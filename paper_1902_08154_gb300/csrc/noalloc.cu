@@ -1,0 +1,375 @@
+// noalloc.cu -- qp_pt2_eval_noalloc: the whole EN-PT2 + selection sweep with
+// no device memory allocation at all.
+//
+// Who needs it: a host program that reserves the GPU's memory up front and
+// hands its plugins no allocator, or a deployment whose device-memory
+// footprint is fixed and audited, cannot let a library call cudaMalloc or
+// cudaFree.  Such a caller gives device pointers for every input and output;
+// everything else the sweep needs (integral tables, generator order, per-
+// generator records and buckets, selection buffers, sort space) lives in one
+// file-scope device array of fixed size, loaded with the library on every
+// GPU that loads it and held until the process exits.
+//
+// The array's host-side name is only a stand-in: host code obtains its device
+// address with cudaGetSymbolAddress, once per device, on the first call made
+// on that device (that first call should therefore come before any stream
+// capture).  Every call reuses the same array and leaves its contents behind,
+// so each call clears what must start at zero; two calls whose work overlaps
+// on the GPU (on different streams, or from different threads) race on it.
+#include <cuda_runtime.h>
+
+#include <cub/device/device_radix_sort.cuh>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "../../include/qp_pt2.h"
+#include "common.cuh"
+
+// kernels defined with the main entry points (qp_pt2.cu) and the sweep
+// (sweep.cu); this file launches them unchanged
+struct DevResult {
+  double e_pt2, s2;
+  long long na, ncon;
+};
+__global__ void jk_kernel(int norb, const double* eri, double* Jm, double* Km);
+__global__ void prep_kernel(int64_t ndet, int nint, int norb, int na, int nb, const uint64_t* dets,
+                            const double* coefs, unsigned long long* hkey, int32_t* hidx,
+                            unsigned long long* rkey, int32_t* ridx, int* err);
+__global__ void dup_kernel(int64_t ndet, int nint, const uint64_t* dets, const unsigned long long* hs,
+                           const int32_t* hi, int* err);
+__global__ void rank_kernel(int64_t ndet, const int32_t* order, int32_t* rank_of);
+__global__ void finalize_kernel(int64_t ndet, const double* eps, const double* s2, const long long* na,
+                                const long long* nc, DevResult* out);
+__global__ void gather_kernel(int grid, int nint, int64_t cap, const int* tk_cnt, const double* tk_e,
+                              const double* tk_a, const uint64_t* tk_key, const unsigned long long* tau,
+                              double* ce, double* ca, uint64_t* ck, int* ncand);
+__global__ void sortkey_kernel(int n, int nint, int w, const double* ce, const uint64_t* ck,
+                               const int32_t* perm, unsigned long long* keys);
+__global__ void iota_kernel(int n, int32_t* v);
+__global__ void select_out_kernel(int n, int nint, const int32_t* perm, const double* ce, const double* ca,
+                                  const uint64_t* ck, uint64_t* sel, double* se, double* sn);
+namespace qp {
+cudaError_t launch_prep(int nint, const SweepParams& p, int slots, cudaStream_t st);
+cudaError_t launch_batch(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
+int batch_blocks_per_sm(int nint, size_t smem);
+}  // namespace qp
+
+using namespace qp;
+
+namespace {
+
+constexpr size_t kScratchBytes = (size_t)64 << 20;  // 64 MiB per device
+constexpr int kMaxDevices = 64;
+
+thread_local std::string g_err;  // message of the last failure (for debugging)
+std::mutex g_mu;
+unsigned char* g_base[kMaxDevices] = {nullptr};
+
+int nfail(int code, const std::string& m) {
+  g_err = m;
+  return code;
+}
+
+// Symmetry of h, checked on the device (no host copy of h).
+__global__ void sym_kernel(int norb, const double* h, int* err) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= norb * norb) return;
+  int p = x / norb, q = x % norb;
+  if (q < p && !(fabs(h[p * norb + q] - h[q * norb + p]) <= 1e-12)) atomicOr(err, 16);
+}
+
+// Bump allocation inside the static array.
+struct Carve {
+  unsigned char* base;
+  size_t off = 0;
+  bool ok = true;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    const size_t bytes = sizeof(T) * (count ? count : 1);
+    if (off + bytes > kScratchBytes) {
+      ok = false;
+      return nullptr;
+    }
+    T* p = reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+bool on_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int cells_max(int norb, int na, int nb) {
+  const int va = norb - na, vb = norb - nb;
+  int m = va > vb ? va : vb;
+  int t = va * (va - 1) / 2;
+  m = t > m ? t : m;
+  t = vb * (vb - 1) / 2;
+  m = t > m ? t : m;
+  t = va * vb;
+  m = t > m ? t : m;
+  return m < 1 ? 1 : m;
+}
+
+}  // namespace
+
+// The fixed device array all calls share (see the file header).
+static __device__ __align__(256) unsigned char qp_noalloc_scratch[kScratchBytes];
+
+#define NTRY(expr)                                                                     \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess) return nfail(QP_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const double* h, const double* eri,
+                                   int64_t ndet, const uint64_t* dets, const double* coefs, double e0,
+                                   int64_t k, uint64_t* sel_dets, double* sel_e, qp_pt2_result* res,
+                                   void* stream) {
+  if (!res) return nfail(QP_EINVAL, "res is NULL");
+  memset(res, 0, sizeof(*res));
+  res->min_abs_denominator = INFINITY;
+  if (norb < 1 || norb > kMaxOrb) return nfail(QP_EINVAL, "norb must be in [1, 128]");
+  if (n_alpha < 0 || n_beta < 0 || n_alpha > norb || n_beta > norb || n_alpha + n_beta > kMaxElec)
+    return nfail(QP_EINVAL, "electron counts out of range");
+  if (ndet < 0 || k < 0) return nfail(QP_EINVAL, "ndet and k must be non-negative");
+  if (ndet >= (1ll << 31)) return nfail(QP_EINVAL, "ndet must be below 2^31");
+  if (!std::isfinite(e0)) return nfail(QP_EINVAL, "E0 is not finite");
+  if (ndet == 0) return QP_OK;
+  if (!on_device(h) || !on_device(eri) || !on_device(dets) || !on_device(coefs) ||
+      (k > 0 && (!on_device(sel_dets) || !on_device(sel_e))))
+    return nfail(QP_EINVAL, "every array must be device memory of the current device");
+  cudaStream_t st = (cudaStream_t)stream;
+
+  // ---- the static array of this device ----
+  int dev = 0;
+  NTRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return nfail(QP_ENOTSUP, "device index too large");
+  unsigned char* base;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_base[dev]) {
+      void* ptr = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&ptr, qp_noalloc_scratch);
+      if (e != cudaSuccess || !ptr)
+        return nfail(QP_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_base[dev] = static_cast<unsigned char*>(ptr);
+    }
+    base = g_base[dev];
+  }
+
+  // ---- sizes and layout ----
+  const int nint = (norb - 1) / 64 + 1, nw = 2 * nint, nel = n_alpha + n_beta;
+  const int nbat = nel + nel * (nel - 1) / 2;
+  const int max_cells = cells_max(norb, n_alpha, n_beta);
+  const size_t smem = sizeof(double) * max_cells + sizeof(uint32_t) * ((max_cells + 31) / 32);
+  if (batch_blocks_per_sm(nint, smem) < 1) return nfail(QP_ENOTSUP, "batch accumulator exceeds shared memory");
+  int nsm = 0;
+  NTRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = nsm;  // one CTA per SM keeps the selection buffers small
+  const size_t nd = (size_t)ndet;
+  const int64_t cap = k > 0 ? k + max_cells : 1;
+  const size_t maxc = (size_t)grid * (size_t)(k > 0 ? k : 1);
+  size_t tmp1 = 0, tmp2 = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, tmp1, (unsigned long long*)nullptr, (unsigned long long*)nullptr,
+                                  (int32_t*)nullptr, (int32_t*)nullptr, (int)ndet, 0, 64, st);
+  cub::DeviceRadixSort::SortPairs(nullptr, tmp2, (unsigned long long*)nullptr, (unsigned long long*)nullptr,
+                                  (int32_t*)nullptr, (int32_t*)nullptr, (int)maxc, 0, 64, st);
+  Carve cv{base};
+  double* d_J = cv.take<double>((size_t)norb * norb);
+  double* d_K = cv.take<double>((size_t)norb * norb);
+  unsigned long long* hkey = cv.take<unsigned long long>(nd);
+  unsigned long long* hkey2 = cv.take<unsigned long long>(nd);
+  unsigned long long* rkey = cv.take<unsigned long long>(nd);
+  unsigned long long* rkey2 = cv.take<unsigned long long>(nd);
+  int32_t* hidx = cv.take<int32_t>(nd);
+  int32_t* hidx2 = cv.take<int32_t>(nd);
+  int32_t* order = cv.take<int32_t>(nd);
+  int32_t* rank_of = cv.take<int32_t>(nd);
+  unsigned char* cub_tmp = cv.take<unsigned char>(tmp1 > tmp2 ? tmp1 : tmp2);
+  double* eps = cv.take<double>(nd);
+  double* s2 = cv.take<double>(nd);
+  unsigned long long* na = cv.take<unsigned long long>(nd);
+  unsigned long long* ncon = cv.take<unsigned long long>(nd);
+  unsigned long long* acc = cv.take<unsigned long long>(8);
+  DevResult* dres = cv.take<DevResult>(1);
+  int* queues = cv.take<int>(nd + 1);
+  double* tk_e = cv.take<double>((size_t)cap * grid);
+  double* tk_a = cv.take<double>((size_t)cap * grid);
+  uint64_t* tk_key = cv.take<uint64_t>((size_t)cap * grid * nw);
+  int* tk_cnt = cv.take<int>(grid);
+  unsigned long long* tk_tau = cv.take<unsigned long long>(grid);
+  double* cand_e = cv.take<double>(maxc);
+  double* cand_a = cv.take<double>(maxc);
+  uint64_t* cand_key = cv.take<uint64_t>(maxc * nw);
+  unsigned long long* skey = cv.take<unsigned long long>(maxc);
+  unsigned long long* skey2 = cv.take<unsigned long long>(maxc);
+  int32_t* perm = cv.take<int32_t>(maxc);
+  int32_t* perm2 = cv.take<int32_t>(maxc);
+  if (!cv.ok)
+    return nfail(QP_EINVAL, "ndet or k too large for the 64 MiB static scratch of qp_pt2_eval_noalloc");
+  const int64_t ent_per = nel >= 3 ? 3 * nel - 3 : 1;
+  const int64_t ent_cap = (int64_t)nd * ent_per;
+  const size_t per_slot = sizeof(GenMeta) + nd * (8 * nw + 8 + 8 + 8 + 4) + 4 * (size_t)(nbat + 2) +
+                          4 * (size_t)ent_cap + 6 * 256;
+  const size_t left = kScratchBytes > cv.off ? kScratchBytes - cv.off : 0;
+  int64_t W = (int64_t)(left / per_slot);
+  if (W < 1)
+    return nfail(QP_EINVAL, "ndet too large for the 64 MiB static scratch of qp_pt2_eval_noalloc");
+  const int64_t ngen = ndet;
+  if (W > ngen) W = ngen;
+  const int64_t nwaves = (ngen + W - 1) / W;
+  const size_t wsl = (size_t)W;
+  GenMeta* meta = cv.take<GenMeta>(wsl);
+  uint64_t* r_words = cv.take<uint64_t>(nd * nw * wsl);
+  double* r_coef = cv.take<double>(nd * wsl);
+  uint64_t* r_hmask = cv.take<uint64_t>(nd * wsl);
+  uint64_t* r_part = cv.take<uint64_t>(nd * wsl);
+  uint32_t* r_flag = cv.take<uint32_t>(nd * wsl);
+  int* b_ofs = cv.take<int>((size_t)(nbat + 2) * wsl);
+  int32_t* b_ent = cv.take<int32_t>((size_t)ent_cap * wsl);
+  if (!cv.ok) return nfail(QP_EINVAL, "ndet too large for the 64 MiB static scratch of qp_pt2_eval_noalloc");
+
+  // ---- clear what must start at zero; integral tables; validation ----
+  static const unsigned long long init[8] = {0, 0, 0x7FF0000000000000ull, 0, 0, 0, 0, 0};
+  NTRY(cudaMemcpyAsync(acc, init, sizeof(init), cudaMemcpyHostToDevice, st));
+  int* d_err = reinterpret_cast<int*>(acc + 6);
+  int* d_ncand = reinterpret_cast<int*>(acc + 7);
+  sym_kernel<<<(norb * norb + 255) / 256, 256, 0, st>>>(norb, h, d_err);
+  jk_kernel<<<(norb * norb + 255) / 256, 256, 0, st>>>(norb, eri, d_J, d_K);
+  const int nb = (int)((ndet + 255) / 256);
+  prep_kernel<<<nb, 256, 0, st>>>(ndet, nint, norb, n_alpha, n_beta, dets, coefs, hkey, hidx, rkey, rank_of, d_err);
+  NTRY(cudaGetLastError());
+  NTRY(cub::DeviceRadixSort::SortPairs(cub_tmp, tmp1, hkey, hkey2, hidx, hidx2, (int)ndet, 0, 64, st));
+  dup_kernel<<<nb, 256, 0, st>>>(ndet, nint, dets, hkey2, hidx2, d_err);
+  NTRY(cub::DeviceRadixSort::SortPairs(cub_tmp, tmp1, rkey, rkey2, rank_of, order, (int)ndet, 0, 64, st));
+  rank_kernel<<<nb, 256, 0, st>>>(ndet, order, rank_of);
+  int herr = 0;
+  NTRY(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NTRY(cudaStreamSynchronize(st));
+  if (herr & 16) return nfail(QP_ESYM, "h is not symmetric");
+  if (herr & 1) return nfail(QP_EINVAL, "a determinant has the wrong occupation or bits beyond norb");
+  if (herr & 4) return nfail(QP_EINVAL, "a coefficient is not finite");
+  if (herr & 2) return nfail(QP_EDUP, "duplicate determinant in Psi0");
+
+  // ---- the sweep, in waves ----
+  NTRY(cudaMemsetAsync(eps, 0, 8 * nd, st));
+  NTRY(cudaMemsetAsync(s2, 0, 8 * nd, st));
+  NTRY(cudaMemsetAsync(na, 0, 8 * nd, st));
+  NTRY(cudaMemsetAsync(ncon, 0, 8 * nd, st));
+  NTRY(cudaMemsetAsync(queues, 0, 4 * (nd + 1), st));
+  NTRY(cudaMemsetAsync(tk_cnt, 0, 4 * (size_t)grid, st));
+  NTRY(cudaMemsetAsync(tk_tau, 0, 8 * (size_t)grid, st));
+  SweepParams p{};
+  p.norb = norb;
+  p.nalpha = n_alpha;
+  p.nbeta = n_beta;
+  p.nel = nel;
+  p.nbat = nbat;
+  p.ndet = ndet;
+  p.dets = dets;
+  p.coefs = coefs;
+  p.order = order;
+  p.rank_of = rank_of;
+  p.h = h;
+  p.eri = eri;
+  p.Jm = d_J;
+  p.Km = d_K;
+  p.e0 = e0;
+  p.shard_index = 0;
+  p.shard_count = 1;
+  p.meta = meta;
+  p.r_words = r_words;
+  p.r_coef = r_coef;
+  p.r_hmask = r_hmask;
+  p.r_part = r_part;
+  p.r_flag = r_flag;
+  p.b_ofs = b_ofs;
+  p.b_ent = b_ent;
+  p.ent_cap = ent_cap;
+  p.eps = eps;
+  p.s2 = s2;
+  p.na = na;
+  p.ncon = ncon;
+  p.digest = acc + 0;
+  p.min_den_bits = acc + 2;
+  p.n_tiny = acc + 3;
+  p.k = k;
+  p.cap = cap;
+  p.tk_e = tk_e;
+  p.tk_a = tk_a;
+  p.tk_key = tk_key;
+  p.tk_cnt = tk_cnt;
+  p.tk_tau = tk_tau;
+  p.tau_bits = acc + 4;
+  p.max_cells = max_cells;
+  p.err = d_err;
+  for (int64_t w = 0; w < nwaves; w++) {
+    p.wave_start = (int)(w * W);
+    p.wave_slots = (int)((ngen - w * W) < W ? (ngen - w * W) : W);
+    p.last_wave = (w == nwaves - 1);
+    p.queue = queues + w;
+    NTRY(launch_prep(nint, p, p.wave_slots, st));
+    NTRY(launch_batch(nint, p, grid, smem, st));
+  }
+  finalize_kernel<<<1, 1024, 0, st>>>(ndet, eps, s2, reinterpret_cast<const long long*>(na),
+                                      reinterpret_cast<const long long*>(ncon), dres);
+  NTRY(cudaGetLastError());
+
+  // ---- selection ----
+  int64_t nsel = 0;
+  if (k > 0) {
+    gather_kernel<<<grid, 256, 0, st>>>(grid, nint, cap, tk_cnt, tk_e, tk_a, tk_key, p.tau_bits, cand_e, cand_a,
+                                        cand_key, d_ncand);
+    int ncand = 0;
+    NTRY(cudaMemcpyAsync(&ncand, d_ncand, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NTRY(cudaStreamSynchronize(st));
+    if (ncand > 0) {
+      const int sb = (ncand + 255) / 256;
+      iota_kernel<<<sb, 256, 0, st>>>(ncand, perm);
+      int32_t *pa = perm, *pb = perm2;
+      for (int pass = 0; pass <= nw; pass++) {
+        const int word = (pass < nw) ? (nw - 1 - pass) : nw;
+        sortkey_kernel<<<sb, 256, 0, st>>>(ncand, nint, word, cand_e, cand_key, pa, skey);
+        NTRY(cub::DeviceRadixSort::SortPairs(cub_tmp, tmp2, skey, skey2, pa, pb, ncand, 0, 64, st));
+        int32_t* t = pa;
+        pa = pb;
+        pb = t;
+      }
+      nsel = ncand < k ? ncand : k;
+      select_out_kernel<<<(int)((nsel + 255) / 256), 256, 0, st>>>((int)nsel, nint, pa, cand_e, cand_a, cand_key,
+                                                                 sel_dets, sel_e, nullptr);
+      NTRY(cudaGetLastError());
+    }
+  }
+
+  DevResult hres;
+  unsigned long long hacc[8];
+  NTRY(cudaMemcpyAsync(&hres, dres, sizeof(hres), cudaMemcpyDeviceToHost, st));
+  NTRY(cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st));
+  NTRY(cudaStreamSynchronize(st));
+  if (reinterpret_cast<int*>(hacc + 6)[0] & 8) return nfail(QP_ECUDA, "internal error: bucket capacity exceeded");
+  res->e_pt2 = hres.e_pt2;
+  res->sum_e_over_d = hres.s2;
+  res->n_perturbers = hres.na;
+  res->n_connections = hres.ncon;
+  res->n_selected = nsel;
+  res->n_tiny = (int64_t)hacc[3];
+  res->perturber_digest[0] = hacc[0];
+  res->perturber_digest[1] = hacc[1];
+  double md;
+  memcpy(&md, &hacc[2], sizeof(md));
+  res->min_abs_denominator = md;
+  if (hres.na > 0 && md < 1e-12) return nfail(QP_ESINGULAR, "a denominator E0 - H_aa is below 1e-12");
+  return QP_OK;
+}
