@@ -88,6 +88,7 @@ struct SweepParams {
   uint32_t* r_flag;               // [slots][ndet]  bit 0: rank(J) < rank(I)
   int* b_ofs;                     // [slots][nbat + 2]  bucket offsets (bucket nbat: J within degree 2)
   int32_t* b_ent;                 // [slots][ent_cap]   record indices
+  uint32_t* b_dead;               // [slots][(nbat + 31) / 32]  batches banned as a whole
   int64_t ent_cap;
 
   // per-generator outputs, by rank

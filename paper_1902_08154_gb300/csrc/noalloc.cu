@@ -220,8 +220,9 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
     return nfail(QP_EINVAL, "ndet or k too large for the 64 MiB static scratch of qp_pt2_eval_noalloc");
   const int64_t ent_per = nel >= 3 ? 3 * nel - 3 : 1;
   const int64_t ent_cap = (int64_t)nd * ent_per;
+  const size_t dwords = (size_t)(nbat + 31) / 32;
   const size_t per_slot = sizeof(GenMeta) + nd * (8 * nw + 8 + 8 + 8 + 4) + 4 * (size_t)(nbat + 2) +
-                          4 * (size_t)ent_cap + 6 * 256;
+                          4 * (size_t)ent_cap + 4 * dwords + 7 * 256;
   const size_t left = kScratchBytes > cv.off ? kScratchBytes - cv.off : 0;
   int64_t W = (int64_t)(left / per_slot);
   if (W < 1)
@@ -238,6 +239,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   uint32_t* r_flag = cv.take<uint32_t>(nd * wsl);
   int* b_ofs = cv.take<int>((size_t)(nbat + 2) * wsl);
   int32_t* b_ent = cv.take<int32_t>((size_t)ent_cap * wsl);
+  uint32_t* b_dead = cv.take<uint32_t>(dwords * wsl);
   if (!cv.ok) return nfail(QP_EINVAL, "ndet too large for the 64 MiB static scratch of qp_pt2_eval_noalloc");
 
   // ---- clear what must start at zero; integral tables; validation ----
@@ -296,6 +298,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   p.r_flag = r_flag;
   p.b_ofs = b_ofs;
   p.b_ent = b_ent;
+  p.b_dead = b_dead;
   p.ent_cap = ent_cap;
   p.eps = eps;
   p.s2 = s2;

@@ -245,7 +245,7 @@ struct qp_pt2_ctx {
   // workspace
   Buf in_dets, in_coefs, hkey, hkey2, hidx, hidx2, rkey, rkey2, order, rank_of, cub_tmp;
   Buf eps, s2, na, ncon, acc, res;
-  Buf meta, r_words, r_coef, r_hmask, r_part, r_flag, b_ofs, b_ent, queues;
+  Buf meta, r_words, r_coef, r_hmask, r_part, r_flag, b_ofs, b_ent, b_dead, queues;
   Buf tk_e, tk_a, tk_key, tk_cnt, tk_tau;
   Buf cand_e, cand_a, cand_key, skey, skey2, perm, perm2, cub_tmp2;
   Buf out_sel, out_e, out_num, out_eps, out_na, out_ncon, out_rank;
@@ -369,7 +369,7 @@ extern "C" void qp_pt2_destroy(qp_pt2_ctx* x) {
   Buf* all[] = {&x->in_dets, &x->in_coefs, &x->hkey, &x->hkey2, &x->hidx, &x->hidx2, &x->rkey, &x->rkey2,
                 &x->order, &x->rank_of, &x->cub_tmp, &x->eps, &x->s2, &x->na, &x->ncon, &x->acc,
                 &x->res, &x->meta, &x->r_words, &x->r_coef, &x->r_hmask, &x->r_part, &x->r_flag,
-                &x->b_ofs, &x->b_ent, &x->queues, &x->tk_e, &x->tk_a, &x->tk_key, &x->tk_cnt, &x->tk_tau, &x->cand_e, &x->cand_a, &x->cand_key, &x->skey,
+                &x->b_ofs, &x->b_ent, &x->b_dead, &x->queues, &x->tk_e, &x->tk_a, &x->tk_key, &x->tk_cnt, &x->tk_tau, &x->cand_e, &x->cand_a, &x->cand_key, &x->skey,
                 &x->skey2, &x->perm, &x->perm2, &x->cub_tmp2, &x->out_sel, &x->out_e, &x->out_num,
                 &x->out_eps, &x->out_na, &x->out_ncon, &x->out_rank};
   for (Buf* b : all) b->release();
@@ -509,8 +509,9 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
   const int64_t ngen = (ndet > shard_index) ? (ndet - shard_index + shard_count - 1) / shard_count : 0;
   const int64_t ent_per = x->nel >= 3 ? 3 * x->nel - 3 : 1;
   const int64_t ent_cap = (int64_t)nd * ent_per;
+  const size_t dwords = (size_t)(x->nbat + 31) / 32;
   const size_t per_slot = sizeof(GenMeta) + nd * (8 * nw + 8 + 8 + 8 + 4) + 4 * (size_t)(x->nbat + 2) +
-                          4 * (size_t)ent_cap;
+                          4 * (size_t)ent_cap + 4 * dwords;
   int64_t W = (int64_t)(kWaveBudget / per_slot);
   if (W < 1) W = 1;
   if (W > ngen) W = ngen > 0 ? ngen : 1;
@@ -521,7 +522,7 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
       (rc = x->r_words.grow(8 * nd * nw * ws)) || (rc = x->r_coef.grow(8 * nd * ws)) ||
       (rc = x->r_hmask.grow(8 * nd * ws)) || (rc = x->r_part.grow(8 * nd * ws)) ||
       (rc = x->r_flag.grow(4 * nd * ws)) || (rc = x->b_ofs.grow(4 * (size_t)(x->nbat + 2) * ws)) ||
-      (rc = x->b_ent.grow(4 * (size_t)ent_cap * ws)) || (rc = x->queues.grow(4 * (size_t)(nwaves + 1))) ||
+      (rc = x->b_ent.grow(4 * (size_t)ent_cap * ws)) || (rc = x->b_dead.grow(4 * dwords * ws)) || (rc = x->queues.grow(4 * (size_t)(nwaves + 1))) ||
       (rc = x->tk_e.grow(8 * (size_t)cap * grid)) || (rc = x->tk_a.grow(8 * (size_t)cap * grid)) ||
       (rc = x->tk_key.grow(8 * (size_t)cap * grid * nw)) || (rc = x->tk_cnt.grow(4 * (size_t)grid)) ||
       (rc = x->tk_tau.grow(8 * (size_t)grid)) || (rc = x->res.grow(sizeof(DevResult))))
@@ -559,6 +560,7 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
   p.r_flag = x->r_flag.as<uint32_t>();
   p.b_ofs = x->b_ofs.as<int>();
   p.b_ent = x->b_ent.as<int32_t>();
+  p.b_dead = x->b_dead.as<uint32_t>();
   p.ent_cap = ent_cap;
   p.eps = x->eps.as<double>();
   p.s2 = x->s2.as<double>();

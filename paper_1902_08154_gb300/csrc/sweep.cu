@@ -44,6 +44,7 @@ namespace qp {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kChunk = 1024;  // bucket entries classified per round
+constexpr int kGroup = 8;     // J reaching every cell, handled together
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -131,6 +132,7 @@ template <int NINT>
 __global__ void __launch_bounds__(kThreads) prep_kernel(SweepParams p) {
   constexpr int NW = 2 * NINT;
   __shared__ int s_cnt[kMaxBatch + 2];
+  __shared__ uint32_t s_dead[(kMaxBatch + 31) / 32];
   __shared__ int s_wsum[kWarps];
   __shared__ uint64_t sI[NW];
   __shared__ int s_occ[kMaxElec];
@@ -271,6 +273,35 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(SweepParams p) {
       const int o = atomicAdd(&s_cnt[b], 1);
       if (o < cap) ent[o] = r;
     });
+
+  // ---- batches banned as a whole: a J ranked before I with t <= 1 (one
+  // hole) or t = 0 (two holes) reaches every cell.  Only J with d <= 2 can:
+  // d = 1 (holes {q}) kills every one-hole batch and the pairs holding q;
+  // d = 2 (holes {q1, q2}) kills {q1}, {q2} and {q1, q2}. ----
+  const int dw = (nbat + 31) / 32;
+  for (int w = tid; w < dw; w += kThreads) s_dead[w] = 0u;
+  __syncthreads();
+  auto kill = [&](int b) { atomicOr(&s_dead[b >> 5], 1u << (b & 31)); };
+  for (int r = tid; r < nrec; r += kThreads) {
+    if (!(rf[r] & 1u)) continue;
+    const uint64_t hm = rh[r];
+    const int d = __popcll(hm);
+    if (d == 1) {
+      const int q = __ffsll((long long)hm) - 1;
+      for (int i = 0; i < nel; i++) kill(i);
+      for (int o = 0; o < nel; o++)
+        if (o != q) kill(pair_batch(nel, q < o ? q : o, q < o ? o : q));
+    } else if (d == 2) {
+      const int q1 = __ffsll((long long)hm) - 1;
+      const int q2 = __ffsll((long long)(hm & (hm - 1))) - 1;
+      kill(q1);
+      kill(q2);
+      kill(pair_batch(nel, q1, q2));
+    }
+  }
+  __syncthreads();
+  uint32_t* dead = p.b_dead + (size_t)slot * dw;
+  for (int w = tid; w < dw; w += kThreads) dead[w] = s_dead[w];
 }
 
 // ---------------------------------------------------------------------------
@@ -286,14 +317,20 @@ struct BatchShared {
   double F[2][kMaxOrb];
   double u0[kMaxOrb], u1[kMaxOrb];  // per-batch row sums for H_aa
   double hii, base;
+  float inv_nv1;
+  uint64_t kbase[2 * NINT];  // I with the batch's holes removed
   int g, slot;
   long long item;
   int L0[kChunk], L1[kChunk], L2[kChunk];
   int n0, n1, n2;
-  // one J processed by the whole CTA
-  uint64_t Jw[2 * NINT];
-  double cj;
-  int X[4], T[2], nx, nt;
+  // a group of J reaching every cell, processed by the whole CTA
+  uint64_t gJw[kGroup][2 * NINT];
+  double gcj[kGroup];
+  int gX[kGroup][4], gT[kGroup][2], gnx[kGroup], gnt[kGroup];
+  // two-hole batches: J = K + {x1, x2}; per particle orbital of each slot the
+  // pair index tri(x, r) with the phase parity in bit 31
+  int gRow[kGroup][kMaxOrb], gCol[kGroup][kMaxOrb];
+  int gx1[kGroup], gx2[kGroup], gsr[kGroup], gsc[kGroup];
   int wsum[kWarps];
   // selection
   int tkcnt;
@@ -328,9 +365,12 @@ __device__ __forceinline__ void cell_orbitals(const Batch& B, const BatchShared<
     *s = -1;
   } else if (B.kind == 2) {
     const int nv1 = S.nv[1];
-    *x = c / nv1;
-    *y = c - *x * nv1;
-    *r = S.vir[0][*x];
+    int xx = __float2int_rz((float)c * S.inv_nv1);  // c < 2^14: exact up to one step
+    if (xx * nv1 > c) xx--;
+    if ((xx + 1) * nv1 <= c) xx++;
+    *x = xx;
+    *y = c - xx * nv1;
+    *r = S.vir[0][xx];
     *s = S.vir[1][*y];
   } else {
     int yy = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)c)) * 0.5f);
@@ -522,8 +562,8 @@ __device__ bool prefix_match(const double* te, const uint64_t* tk, int i, const 
 }
 
 template <int NINT>
-__device__ void compact_selection(const SweepParams& p, BatchShared<NINT>& S, double* te, double* ta,
-                                  uint64_t* tk) {
+__device__ __noinline__ void compact_selection(const SweepParams& p, BatchShared<NINT>& S, double* te,
+                                               double* ta, uint64_t* tk) {
   constexpr int NW = 1 + 2 * NINT;
   const int tid = threadIdx.x;
   __syncthreads();
@@ -617,7 +657,7 @@ __device__ void compact_selection(const SweepParams& p, BatchShared<NINT>& S, do
 }
 
 template <int NINT>
-__global__ void __launch_bounds__(kThreads) batch_kernel(SweepParams p) {
+__global__ void __launch_bounds__(kThreads, 4) batch_kernel(SweepParams p) {
   constexpr int NW = 2 * NINT;
   extern __shared__ __align__(16) unsigned char dyn[];
   double* A = reinterpret_cast<double*>(dyn);
@@ -646,6 +686,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(SweepParams p) {
     const int slot = (int)(item / nbat), b = (int)(item - (long long)slot * nbat);
     const GenMeta* M = p.meta + slot;
     if (M->g < 0) continue;
+    if ((p.b_dead[(size_t)slot * ((nbat + 31) / 32) + (b >> 5)] >> (b & 31)) & 1u) continue;
     if (slot != S.slot) {  // load the generator
       __syncthreads();
       if (tid < NW) S.I[tid] = M->I[tid];
@@ -731,6 +772,13 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(SweepParams p) {
     const uint32_t* rf = p.r_flag + rb;
     auto entry = [&](int i) { return i < nb_ ? ent[ob + i] : ent[oa + i - nb_]; };
 
+    if (tid == 0) {
+      S.inv_nv1 = S.nv[1] > 0 ? 1.0f / (float)S.nv[1] : 0.0f;
+#pragma unroll
+      for (int w = 0; w < NW; w++) S.kbase[w] = S.I[w];
+      S.kbase[B.sa * NINT + (B.qa >> 6)] &= ~(1ull << (B.qa & 63));
+      if (B.h == 2) S.kbase[B.sb * NINT + (B.qb >> 6)] &= ~(1ull << (B.qb & 63));
+    }
     // zero the accumulator, the bans; row sums for H_aa
     for (int c = tid; c < B.ncell; c += kThreads) A[c] = 0.0;
     for (int c = tid; c < (B.ncell + 31) / 32; c += kThreads) ban[c] = 0u;
@@ -832,33 +880,93 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(SweepParams p) {
         else S.L2[atomicAdd(&S.n2, 1)] = r;
       }
       __syncthreads();
-      // J reaching every cell: the whole CTA, one J at a time
+      // J reaching every cell: the whole CTA, kGroup of them per pass.
+      // In a two-hole batch such a J is K + {x1, x2}; for a cell R disjoint
+      // from {x1, x2} the element is a double substitution x1 x2 -> R whose
+      // pair indices and phase split into a row part and a column part,
+      // precomputed once per J (cells meeting {x1, x2} take the general path).
       const int n0 = S.n0;
-      for (int j = 0; j < n0; j++) {
-        if (tid == 0) {
-          const int r = S.L0[j];
+      for (int g0 = 0; g0 < n0; g0 += kGroup) {
+        const int m = min(kGroup, n0 - g0);
+        if (tid < m) {
+          const int r = S.L0[g0 + tid];
 #pragma unroll
-          for (int w = 0; w < NW; w++) S.Jw[w] = rw[(size_t)r * NW + w];
-          S.cj = rc[r];
-          excitation_sets<NINT>(B, S, rp[r], rh[r], S.X, &S.nx, S.T, &S.nt);
+          for (int w = 0; w < NW; w++) S.gJw[tid][w] = rw[(size_t)r * NW + w];
+          S.gcj[tid] = rc[r];
+          excitation_sets<NINT>(B, S, rp[r], rh[r], S.gX[tid], &S.gnx[tid], S.gT[tid], &S.gnt[tid]);
+          if (B.h == 2) {
+            const int a = S.gX[tid][0], bb = S.gX[tid][1];
+            const int x1 = a < bb ? a : bb, x2 = a < bb ? bb : a;
+            S.gx1[tid] = x1;
+            S.gx2[tid] = x2;
+            const int s1 = x1 >= norb, s2 = x2 >= norb;
+            S.gsr[tid] = S.vidx[s1][x1 - s1 * norb];
+            S.gsc[tid] = S.vidx[s2][x2 - s2 * norb];
+          }
         }
         __syncthreads();
-        uint64_t Jw[NW];
-#pragma unroll
-        for (int w = 0; w < NW; w++) Jw[w] = S.Jw[w];
-        int X[4], T[2];
-        const int nx = S.nx, nt = S.nt;
-        for (int i = 0; i < 4; i++) X[i] = S.X[i];
-        for (int i = 0; i < 2; i++) T[i] = S.T[i];
-        const double cj = S.cj;
+        const int sl1 = B.sa, sl2 = (B.kind == 2) ? 1 : B.sa;
+        const int nva = S.nv[sl1], nvb = S.nv[sl2];
+        if (B.h == 2) {
+          const int per = nva + nvb;
+          for (int idx = tid; idx < m * per; idx += kThreads) {
+            const int j = idx / per;
+            const int v = idx - j * per;
+            const uint64_t* Jw = S.gJw[j];
+            const int x1 = S.gx1[j] - sl1 * norb, x2 = S.gx2[j] - sl2 * norb;
+            if (v < nva) {
+              const int r = S.vir[sl1][v];
+              int par = 0;
+              if (r != x1) par = count_between<NINT>(Jw + sl1 * NINT, r < x1 ? r : x1, r < x1 ? x1 : r) & 1;
+              S.gRow[j][v] = tri(x1, r) | (par << 31);
+            } else {
+              const int sv = S.vir[sl2][v - nva];
+              int par = 0;
+              if (sv != x2) par = count_between<NINT>(Jw + sl2 * NINT, sv < x2 ? sv : x2, sv < x2 ? x2 : sv) & 1;
+              if (B.kind == 1) {
+                const int lo = sv < x2 ? sv : x2, hi = sv < x2 ? x2 : sv;
+                par ^= (x1 > lo && x1 < hi) ? 1 : 0;
+              }
+              S.gCol[j][v - nva] = tri(x2, sv) | (par << 31);
+            }
+          }
+          __syncthreads();
+        }
         for (int c = tid; c < B.ncell; c += kThreads) {
           if ((ban[c >> 5] >> (c & 31)) & 1u) continue;
           int ro, so, x, y;
           cell_orbitals<NINT>(B, S, c, &ro, &so, &x, &y);
           const int rcode = B.sa * norb + ro;
           const int scode = (B.h == 2) ? B.sb * norb + so : -1;
-          A[c] += cj * element<NINT>(p, Jw, X, nx, T, nt, rcode, scode);
-          con++;
+          double acc = 0.0;
+          for (int j = 0; j < m; j++) {
+            bool general = true;
+            double v = 0.0;
+            if (B.h == 2) {
+              const int sr = S.gsr[j], sc = S.gsc[j];
+              if (B.kind == 2) {
+                if (x != sr && y != sc) {
+                  const int rt = S.gRow[j][x], ct = S.gCol[j][y];
+                  v = p.eri[tri(rt & 0x7fffffff, ct & 0x7fffffff)];
+                  if ((rt ^ ct) < 0) v = -v;
+                  general = false;
+                }
+              } else if (x != sr && x != sc && y != sr && y != sc) {
+                const int a1 = S.gRow[j][x], b2 = S.gCol[j][y];
+                const int a2 = S.gRow[j][y], b1 = S.gCol[j][x];
+                v = p.eri[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - p.eri[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
+                const int x2 = S.gx2[j] - B.sa * norb;
+                const int lo = so < x2 ? so : x2, hi = so < x2 ? x2 : so;
+                const int par = ((a1 ^ b2) < 0 ? 1 : 0) ^ ((ro > lo && ro < hi) ? 1 : 0);
+                if (par) v = -v;
+                general = false;
+              }
+            }
+            if (general) v = element<NINT>(p, S.gJw[j], S.gX[j], S.gnx[j], S.gT[j], S.gnt[j], rcode, scode);
+            acc += S.gcj[j] * v;
+          }
+          A[c] += acc;
+          con += m;
         }
         __syncthreads();
       }
@@ -938,13 +1046,9 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(SweepParams p) {
       acc_min = db < acc_min ? db : acc_min;
       uint64_t key[NW];
 #pragma unroll
-      for (int w = 0; w < NW; w++) key[w] = S.I[w];
-      key[B.sa * NINT + (B.qa >> 6)] &= ~(1ull << (B.qa & 63));
+      for (int w = 0; w < NW; w++) key[w] = S.kbase[w];
       key[B.sa * NINT + (ro >> 6)] |= 1ull << (ro & 63);
-      if (B.h == 2) {
-        key[B.sb * NINT + (B.qb >> 6)] &= ~(1ull << (B.qb & 63));
-        key[B.sb * NINT + (so >> 6)] |= 1ull << (so & 63);
-      }
+      if (B.h == 2) key[B.sb * NINT + (so >> 6)] |= 1ull << (so & 63);
       uint64_t hk = 0;
 #pragma unroll
       for (int w = 0; w < NW; w++) hk = splitmix64(hk ^ key[w]);
