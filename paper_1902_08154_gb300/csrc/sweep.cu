@@ -484,8 +484,10 @@ __device__ __forceinline__ void excitation_sets(const Batch& B, const BatchShare
 
 // <J|H|alpha> with alpha = K + R, K = I - H.
 // holes(J -> alpha) = X - R, particles = T + (R - X).
+// Kept out of line: one copy serves every caller, which keeps the batch
+// kernel's code small enough for the instruction cache.
 template <int NINT>
-__device__ __forceinline__ double element(const SweepParams& p, const uint64_t* Jw, const int* X, int nx,
+__device__ __noinline__ double element(const SweepParams& p, const uint64_t* Jw, const int* X, int nx,
                                           const int* T, int nt, int r, int s) {
   const int norb = p.norb;
   int ho[2], pa[2], nh = 0, npp = 0;
@@ -657,7 +659,7 @@ __device__ __noinline__ void compact_selection(const SweepParams& p, BatchShared
 }
 
 template <int NINT>
-__global__ void __launch_bounds__(kThreads, 4) batch_kernel(SweepParams p) {
+__global__ void __launch_bounds__(kThreads, 3) batch_kernel(SweepParams p) {
   constexpr int NW = 2 * NINT;
   extern __shared__ __align__(16) unsigned char dyn[];
   double* A = reinterpret_cast<double*>(dyn);
