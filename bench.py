@@ -296,6 +296,33 @@ def run_gb300(args):
 
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # mixed precision on the same inputs: FP32 numerator, FP64 accumulation,
+    # denominators and reductions; error stated against the FP64 sweep and
+    # against the oracle's stored value
+    mixed = None
+    if not args.no_mixed:
+        pt2m = qp.PT2(meta["norb"], meta["nalpha"], meta["nbeta"], h, eri, stream=stream.cuda_stream,
+                      shard_index=rank if world > 1 else 0, shard_count=world if world > 1 else 0,
+                      precision=qp.QP_MIXED)
+        mt = []
+        with torch.cuda.stream(stream):
+            for it in range(args.warmup + args.steps):
+                flush.zero_()
+                resm = qp.qp_pt2_eval(pt2m.ctx, ndet, d_dets, d_coefs, e0, k, sel, sel_e).as_dict()
+                if it >= args.warmup:
+                    mt.append(qp.qp_pt2_last_timings(pt2m.ctx)[1])
+        pt2m.close()
+        ms_m = statistics.mean(mt)
+        ref_e = None
+        if not args.ndet:
+            E = np.load(os.path.join(ROOT, "tests", "golden", f"{WORKLOAD}_expected.npz"))
+            ref_e = json.loads(str(E["summary"]))["e_pt2"]
+        mixed = {"value": resm["n_perturbers"] / (ms_m * 1e-3), "unit": UNIT, "ms_per_step": ms_m,
+                 "speedup_vs_fp64": ms_step / ms_m, "e_pt2": resm["e_pt2"],
+                 "abs_err_vs_fp64_gpu": abs(resm["e_pt2"] - res["e_pt2"]),
+                 "abs_err_vs_oracle": None if ref_e is None else abs(resm["e_pt2"] - ref_e),
+                 "stated_tolerance": 1e-6}
+
     # roofline of the dominant kernel (the persistent sweep)
     ms_sweep = statistics.mean(sweep_ms)
     ops = (OPS_PER_CONNECTION * res["n_connections"] + OPS_PER_PERTURBER * res["n_perturbers"]
@@ -312,7 +339,7 @@ def run_gb300(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(meta, world),
             "generators_per_s": gens_per_s, "n_perturbers": units, "e_pt2": res["e_pt2"],
             "e2e": e2e,
-            "gpu_launches": launches, "roofline": roof, "clocks": ck}
+            "gpu_launches": launches, "roofline": roof, "clocks": ck, "mixed_precision": mixed}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(meta, h, eri, dets, coefs, e0)
     print(json.dumps(line), flush=True)
@@ -330,6 +357,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg (profiling runs)")
     ap.add_argument("--ndet", type=int, default=0,
                     help="profiling runs only: sweep the first NDET determinants of the stored Psi0")
     args = ap.parse_args()

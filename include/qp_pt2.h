@@ -75,11 +75,16 @@ extern "C" {
 #define QP_ENOTSUP (-8)    /* configuration not supported by this build */
 
 #define QP_FP64 0          /* every step in FP64 */
+#define QP_MIXED 1         /* numerator <J|H|alpha> gathers and products c_J<J|H|alpha> in
+                              FP32 (FP32 copies of h and eri); each product is added into
+                              an FP64 accumulator A_alpha; denominators E0 - H_aa, e_alpha
+                              and every reduction in FP64.  Error bound per result: about
+                              2^-24 * sum_alpha 2|A_alpha| sum_J |c_J H_Jalpha| / |D_alpha|. */
 
 typedef struct qp_pt2_ctx qp_pt2_ctx; /* opaque, library-owned */
 
 typedef struct {
-    int precision;      /* QP_FP64 */
+    int precision;      /* QP_FP64 or QP_MIXED */
     void *stream;       /* cudaStream_t; NULL = legacy default stream */
     int blocks_per_sm;  /* persistent CTAs per SM; 0 = as many as fit */
     int threads;        /* threads per CTA; 0 = 256 */

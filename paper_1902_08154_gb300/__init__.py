@@ -18,6 +18,7 @@ SO = os.path.join(HERE, "_build", "libqp_pt2.so")
 
 QP_OK, QP_EINVAL, QP_EDUP, QP_ESYM, QP_ESINGULAR, QP_ENOMEM, QP_ECUDA, QP_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -8
 QP_FP64 = 0
+QP_MIXED = 1
 
 EXPORTS = (
     "qp_pt2_create",
@@ -177,10 +178,10 @@ class PT2:
     """Owning wrapper: one context per (Hamiltonian, electron count)."""
 
     def __init__(self, norb, n_alpha, n_beta, h, eri, stream=None, blocks_per_sm=0, shard_index=0,
-                 shard_count=0):
+                 shard_count=0, precision=QP_FP64):
         self.norb, self.n_alpha, self.n_beta = norb, n_alpha, n_beta
         self.nint = (norb - 1) // 64 + 1
-        self.ctx = qp_pt2_create(norb, n_alpha, n_beta, h, eri, stream, blocks_per_sm,
+        self.ctx = qp_pt2_create(norb, n_alpha, n_beta, h, eri, stream, blocks_per_sm, precision=precision,
                                  shard_index=shard_index, shard_count=shard_count)
 
     def close(self):

@@ -68,6 +68,9 @@ struct SweepParams {
   const int32_t* rank_of; // rank by det index
   const double* h;        // [norb*norb]
   const double* eri;      // packed
+  const float* h32;       // FP32 copies for the mixed-precision numerator (NULL in FP64 mode)
+  const float* eri32;
+  int mixed;              // 1: numerator gathers and products in FP32
   const double* Jm;       // [norb*norb] (pp|qq)
   const double* Km;       // [norb*norb] (pq|qp)
   double e0;

@@ -34,7 +34,7 @@ struct DevResult {
   long long na, ncon;
 };
 __global__ void jk_kernel(int norb, const double* eri, double* Jm, double* Km);
-__global__ void prep_kernel(int64_t ndet, int nint, int norb, int na, int nb, const uint64_t* dets,
+__global__ void validate_kernel(int64_t ndet, int nint, int norb, int na, int nb, const uint64_t* dets,
                             const double* coefs, unsigned long long* hkey, int32_t* hidx,
                             unsigned long long* rkey, int32_t* ridx, int* err);
 __global__ void dup_kernel(int64_t ndet, int nint, const uint64_t* dets, const unsigned long long* hs,
@@ -53,7 +53,7 @@ __global__ void select_out_kernel(int n, int nint, const int32_t* perm, const do
 namespace qp {
 cudaError_t launch_prep(int nint, const SweepParams& p, int slots, cudaStream_t st);
 cudaError_t launch_batch(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
-int batch_blocks_per_sm(int nint, size_t smem);
+int batch_blocks_per_sm(int nint, int mixed, size_t smem);
 }  // namespace qp
 
 using namespace qp;
@@ -173,7 +173,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   const int nbat = nel + nel * (nel - 1) / 2;
   const int max_cells = cells_max(norb, n_alpha, n_beta);
   const size_t smem = sizeof(double) * max_cells + sizeof(uint32_t) * ((max_cells + 31) / 32);
-  if (batch_blocks_per_sm(nint, smem) < 1) return nfail(QP_ENOTSUP, "batch accumulator exceeds shared memory");
+  if (batch_blocks_per_sm(nint, 0, smem) < 1) return nfail(QP_ENOTSUP, "batch accumulator exceeds shared memory");
   int nsm = 0;
   NTRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int grid = nsm;  // one CTA per SM keeps the selection buffers small
@@ -250,7 +250,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   sym_kernel<<<(norb * norb + 255) / 256, 256, 0, st>>>(norb, h, d_err);
   jk_kernel<<<(norb * norb + 255) / 256, 256, 0, st>>>(norb, eri, d_J, d_K);
   const int nb = (int)((ndet + 255) / 256);
-  prep_kernel<<<nb, 256, 0, st>>>(ndet, nint, norb, n_alpha, n_beta, dets, coefs, hkey, hidx, rkey, rank_of, d_err);
+  validate_kernel<<<nb, 256, 0, st>>>(ndet, nint, norb, n_alpha, n_beta, dets, coefs, hkey, hidx, rkey, rank_of, d_err);
   NTRY(cudaGetLastError());
   NTRY(cub::DeviceRadixSort::SortPairs(cub_tmp, tmp1, hkey, hkey2, hidx, hidx2, (int)ndet, 0, 64, st));
   dup_kernel<<<nb, 256, 0, st>>>(ndet, nint, dets, hkey2, hidx2, d_err);

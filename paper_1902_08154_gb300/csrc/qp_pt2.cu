@@ -17,7 +17,7 @@
 namespace qp {
 cudaError_t launch_prep(int nint, const SweepParams& p, int slots, cudaStream_t st);
 cudaError_t launch_batch(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
-int batch_blocks_per_sm(int nint, size_t smem);
+int batch_blocks_per_sm(int nint, int mixed, size_t smem);
 int sweep_threads();
 }  // namespace qp
 
@@ -47,6 +47,11 @@ static const size_t kWaveBudget = (size_t)4 << 30;
 // ---------------------------------------------------------------------------
 // Small kernels
 // ---------------------------------------------------------------------------
+__global__ void to_f32_kernel(int64_t n, const double* in, float* out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+
 __global__ void jk_kernel(int norb, const double* eri, double* Jm, double* Km) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= norb * norb) return;
@@ -57,7 +62,7 @@ __global__ void jk_kernel(int norb, const double* eri, double* Jm, double* Km) {
 
 // Occupation counts, bits beyond norb, finite coefficients; key hashes for
 // the duplicate check; generator sort keys.
-__global__ void prep_kernel(int64_t ndet, int nint, int norb, int na, int nb, const uint64_t* dets,
+__global__ void validate_kernel(int64_t ndet, int nint, int norb, int na, int nb, const uint64_t* dets,
                             const double* coefs, unsigned long long* hkey, int32_t* hidx,
                             unsigned long long* rkey, int32_t* ridx, int* err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -242,6 +247,7 @@ struct qp_pt2_ctx {
   int max_cells, bps, grid;
   size_t smem;
   double *d_h = nullptr, *d_eri = nullptr, *d_J = nullptr, *d_K = nullptr;
+  float *d_h32 = nullptr, *d_eri32 = nullptr;  // mixed precision only
   // workspace
   Buf in_dets, in_coefs, hkey, hkey2, hidx, hidx2, rkey, rkey2, order, rank_of, cub_tmp;
   Buf eps, s2, na, ncon, acc, res;
@@ -291,7 +297,7 @@ extern "C" int qp_pt2_create(qp_pt2_ctx** out, int norb, int n_alpha, int n_beta
   if (!h || !eri) return fail(QP_EINVAL, "h or eri is NULL");
   qp_pt2_config c{};
   if (cfg) c = *cfg;
-  if (c.precision != QP_FP64) return fail(QP_ENOTSUP, "only QP_FP64 is implemented");
+  if (c.precision != QP_FP64 && c.precision != QP_MIXED) return fail(QP_EINVAL, "unknown precision");
   if (c.threads != 0 && c.threads != sweep_threads())
     return fail(QP_ENOTSUP, "threads per CTA is fixed at 256 in this build");
   const int64_t M = (int64_t)norb * (norb + 1) / 2, P = M * (M + 1) / 2;
@@ -343,12 +349,19 @@ extern "C" int qp_pt2_create(qp_pt2_ctx** out, int norb, int n_alpha, int n_beta
       cudaMemcpyAsync(x->d_eri, eri, sizeof(double) * P, cudaMemcpyDefault, x->st) != cudaSuccess)
     return bail(QP_ECUDA, "copy of the integrals failed");
   jk_kernel<<<(norb * norb + 255) / 256, 256, 0, x->st>>>(norb, x->d_eri, x->d_J, x->d_K);
+  if (c.precision == QP_MIXED) {
+    if (cudaMalloc(&x->d_h32, sizeof(float) * norb * norb) != cudaSuccess ||
+        cudaMalloc(&x->d_eri32, sizeof(float) * P) != cudaSuccess)
+      return bail(QP_ENOMEM, "device allocation of the FP32 integrals failed");
+    to_f32_kernel<<<(unsigned)((norb * norb + 255) / 256), 256, 0, x->st>>>(norb * norb, x->d_h, x->d_h32);
+    to_f32_kernel<<<(unsigned)((P + 255) / 256), 256, 0, x->st>>>(P, x->d_eri, x->d_eri32);
+  }
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(x->st) != cudaSuccess)
     return bail(QP_ECUDA, "integral tables failed");
   x->max_cells = cells_max(norb, n_alpha, n_beta);
   if (x->max_cells < 1) x->max_cells = 1;
   x->smem = sizeof(double) * x->max_cells + sizeof(uint32_t) * ((x->max_cells + 31) / 32);
-  int bps = batch_blocks_per_sm(x->nint, x->smem);
+  int bps = batch_blocks_per_sm(x->nint, c.precision == QP_MIXED, x->smem);
   if (bps < 1) return bail(QP_ENOTSUP, "the batch accumulator does not fit in shared memory");
   if (c.blocks_per_sm > 0 && c.blocks_per_sm < bps) bps = c.blocks_per_sm;
   x->bps = bps;
@@ -364,6 +377,8 @@ extern "C" void qp_pt2_destroy(qp_pt2_ctx* x) {
   if (x->ev_end) cudaEventDestroy(x->ev_end);
   cudaFree(x->d_h);
   cudaFree(x->d_eri);
+  cudaFree(x->d_h32);
+  cudaFree(x->d_eri32);
   cudaFree(x->d_J);
   cudaFree(x->d_K);
   Buf* all[] = {&x->in_dets, &x->in_coefs, &x->hkey, &x->hkey2, &x->hidx, &x->hidx2, &x->rkey, &x->rkey2,
@@ -474,7 +489,7 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
   int* d_err = reinterpret_cast<int*>(acc + kAccErr);
   const int tb = 256;
   const int nb = (int)((ndet + tb - 1) / tb);
-  prep_kernel<<<nb, tb, 0, st>>>(ndet, nint, x->norb, x->nalpha, x->nbeta, d_dets, d_coefs,
+  validate_kernel<<<nb, tb, 0, st>>>(ndet, nint, x->norb, x->nalpha, x->nbeta, d_dets, d_coefs,
                                  x->hkey.as<unsigned long long>(), x->hidx.as<int32_t>(),
                                  x->rkey.as<unsigned long long>(), x->rank_of.as<int32_t>(), d_err);
   x->launches++;
@@ -547,6 +562,9 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
   p.rank_of = x->rank_of.as<int32_t>();
   p.h = x->d_h;
   p.eri = x->d_eri;
+  p.h32 = x->d_h32;
+  p.eri32 = x->d_eri32;
+  p.mixed = x->cfg.precision == QP_MIXED;
   p.Jm = x->d_J;
   p.Km = x->d_K;
   p.e0 = e0;

@@ -1,1128 +1,18 @@
-// sweep.cu -- sm_103a kernels of the deterministic EN-PT2 + selection sweep
-// (Quantum Package 2.0, arXiv:1902.08154, Appendix "CIPSI selection and PT2
-// energy").
-//
-// Generators are taken in rank order (decreasing c_I^2) in waves of slots.
-// Per wave two kernels run:
-//
-//  prep_kernel (one CTA per generator I of the wave)
-//    - the Fock diagonal of I, so that <alpha|H|alpha> costs a few flops per
-//      alpha (Appendix: "pre-compute the diagonal of the Fock matrix");
-//    - the coarse filter: every internal J within excitation degree 4 of I,
-//      stored as a record (its words, c_J, the holes of I missing from J as a
-//      mask over I's occupied list, the particles of J outside I, and whether
-//      J ranks before I);
-//    - the fine filter, done once per generator by bucketing: a batch is a
-//      hole set H of I (|H| = 1 or 2) holding the alpha = I - H + R for the
-//      particle sets R outside I with the spins of H.  With K = I - H,
-//      t = |K - J| and X = J - K, deg(J, alpha) = t + |H| - |R n X|, so J
-//      reaches batch H only if t <= 2.  With Q the holes of J (d = |Q|),
-//      t = d - |Q n H|: J with d <= 2 reaches every batch, d = 3 the batches
-//      meeting Q, d = 4 the batches inside Q.  Each record is written to the
-//      bucket of every batch it reaches (d <= 2: one shared bucket).
-//
-//  batch_kernel (persistent CTAs, one (generator, batch) item at a time,
-//  items of the heaviest generators first)
-//    loop 1: J ranked before I ban the cells they reach (J that reach every
-//            cell kill the batch); a later J equal to some alpha bans it;
-//    loop 2: J ranked at or after I add c_J <J|H|alpha> into the shared-memory
-//            accumulator A(R) of the cells they reach that are not banned.
-//            J reaching every cell are spread over the whole CTA, J reaching a
-//            row of cells over a warp, J reaching a few cells over a thread;
-//    cells:  every cell left is a perturber of I: e = A^2/(E0 - H_aa) with
-//            H_aa from per-batch row sums of the Fock diagonal, added to eps_I
-//            and offered to the CTA's selection buffer.
-// Matrix elements follow the Slater-Condon rules (Eqs. Hij) with phases from
-// a masked popcount of J's spin string.
-#include <cfloat>
-#include <cstdio>
-
-#include "common.cuh"
+// sweep.cu -- the FP64 sweep kernels (prep, batch) and their launch helpers;
+// the kernels themselves are in sweep_impl.cuh, the mixed-precision batch
+// kernels in sweep_mixed.cu.
+#include "sweep_impl.cuh"
 
 namespace qp {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int kChunk = 1024;  // bucket entries classified per round
-constexpr int kGroup = 8;     // J reaching every cell, handled together
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-__device__ __forceinline__ unsigned long long warp_sum_u(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-__device__ __forceinline__ unsigned long long warp_xor_u(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v ^= __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-__device__ __forceinline__ unsigned long long warp_min_u(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    unsigned long long w = __shfl_xor_sync(kFull, v, o);
-    v = w < v ? w : v;
-  }
-  return v;
-}
-
-// Block-wide exclusive scan of a 0/1 flag; returns this thread's position and
-// the block total.  wsum: kWarps ints of shared memory.
-__device__ __forceinline__ int block_scan_flag(bool f, int* wsum, int* total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned b = __ballot_sync(kFull, f);
-  int before = __popc(b & ((1u << lane) - 1));
-  if (lane == 0) wsum[warp] = __popc(b);
-  __syncthreads();
-  int off = 0, tot = 0;
-#pragma unroll
-  for (int w = 0; w < kWarps; w++) {
-    int c = wsum[w];
-    off += (w < warp) ? c : 0;
-    tot += c;
-  }
-  __syncthreads();
-  *total = tot;
-  return off + before;
-}
-
-__device__ __forceinline__ int pair_batch(int nel, int i, int j) {  // i < j
-  return nel + j * (j - 1) / 2 + i;
-}
-
-// Buckets reached by a record with hole mask hm (see the file header).
-template <typename Fn>
-__device__ __forceinline__ void for_buckets(uint64_t hm, int nel, int nbat, Fn&& fn) {
-  const int d = __popcll(hm);
-  if (d <= 2) {
-    fn(nbat);
-    return;
-  }
-  int Q[4], n = 0;
-  uint64_t m = hm;
-  while (m && n < 4) {
-    Q[n++] = __ffsll((long long)m) - 1;
-    m &= m - 1;
-  }
-  if (d == 3) {
-    for (int i = 0; i < 3; i++) fn(Q[i]);
-    for (int i = 0; i < 3; i++) {
-      const int q = Q[i];
-      for (int o = 0; o < nel; o++) {
-        if (o == q) continue;
-        if (((hm >> o) & 1ull) && o < q) continue;  // pair inside Q: once
-        fn(pair_batch(nel, q < o ? q : o, q < o ? o : q));
-      }
-    }
-  } else {  // d == 4
-    for (int i = 0; i < 4; i++)
-      for (int j = i + 1; j < 4; j++) fn(pair_batch(nel, Q[i], Q[j]));
-  }
-}
-
-// ---------------------------------------------------------------------------
-// prep kernel: one CTA per generator slot of the wave
-// ---------------------------------------------------------------------------
-template <int NINT>
-__global__ void __launch_bounds__(kThreads) prep_kernel(SweepParams p) {
-  constexpr int NW = 2 * NINT;
-  __shared__ int s_cnt[kMaxBatch + 2];
-  __shared__ uint32_t s_dead[(kMaxBatch + 31) / 32];
-  __shared__ int s_wsum[kWarps];
-  __shared__ uint64_t sI[NW];
-  __shared__ int s_occ[kMaxElec];
-  const int slot = blockIdx.x, tid = threadIdx.x;
-  const int norb = p.norb, nel = p.nel, nbat = p.nbat;
-  GenMeta* M = p.meta + slot;
-  const long long t = (long long)p.wave_start + slot;
-  const long long gg = p.shard_index + t * (long long)p.shard_count;
-  if (gg >= p.ndet) {
-    if (tid == 0) {
-      M->g = -1;
-      M->nrec = 0;
-    }
-    return;
-  }
-  const int g = (int)gg, gi = p.order[g];
-  if (tid < NW) sI[tid] = p.dets[(size_t)gi * NW + tid];
-  __syncthreads();
-  if (tid == 0) {
-    int n = 0;
-    for (int s = 0; s < 2; s++)
-      for (int q = 0; q < norb; q++)
-        if ((sI[s * NINT + (q >> 6)] >> (q & 63)) & 1ull) s_occ[n++] = s * norb + q;
-    M->g = g;
-    for (int w = 0; w < 4; w++) M->I[w] = w < NW ? sI[w] : 0ull;
-  }
-  __syncthreads();
-  if (tid < nel) M->occ[tid] = s_occ[tid];
-  // Fock diagonal F_s(q) = h_qq + sum_{j in I} [(qq|jj) - delta_s (qj|jq)]
-  for (int x = tid; x < 2 * norb; x += kThreads) {
-    const int s = x / norb, q = x - s * norb;
-    double f = p.h[q * norb + q];
-    for (int i = 0; i < nel; i++) {
-      const int c = s_occ[i], sj = c >= norb, j = c - sj * norb;
-      f += p.Jm[q * norb + j];
-      if (sj == s) f -= p.Km[q * norb + j];
-    }
-    M->F[s][q] = f;
-  }
-  __syncthreads();
-  if (tid == 0) {  // H_II = 1/2 sum_i (h_ii + F(i))
-    double e = 0.0;
-    for (int i = 0; i < nel; i++) {
-      const int c = s_occ[i], s = c >= norb, q = c - s * norb;
-      e += p.h[q * norb + q] + M->F[s][q];
-    }
-    M->hii = 0.5 * e;
-  }
-
-  // ---- coarse filter: J within degree 4 of I (I itself included) ----
-  const size_t rb = (size_t)slot * (size_t)p.ndet;
-  uint64_t* rw = p.r_words + rb * NW;
-  double* rc = p.r_coef + rb;
-  uint64_t* rh = p.r_hmask + rb;
-  uint64_t* rp = p.r_part + rb;
-  uint32_t* rf = p.r_flag + rb;
-  uint64_t Iw[NW];
-#pragma unroll
-  for (int w = 0; w < NW; w++) Iw[w] = sI[w];
-  int nrec = 0;
-  for (long long base = 0; base < p.ndet; base += kThreads) {
-    const long long j = base + tid;
-    bool keep = false;
-    uint64_t Jw[NW];
-    if (j < p.ndet) {
-      int d = 0;
-#pragma unroll
-      for (int w = 0; w < NW; w++) {
-        Jw[w] = p.dets[(size_t)j * NW + w];
-        d += __popcll(Jw[w] ^ Iw[w]);
-      }
-      keep = d <= 8;
-    }
-    int total;
-    const int pos = block_scan_flag(keep, s_wsum, &total);
-    if (keep) {
-      const int r = nrec + pos;
-      uint64_t hmask = 0, part = ~0ull;
-      int npart = 0;
-#pragma unroll
-      for (int s = 0; s < 2; s++) {
-        int below = (s == 0) ? 0 : p.nalpha;
-#pragma unroll
-        for (int w = 0; w < NINT; w++) {
-          const uint64_t iw = Iw[s * NINT + w], jw = Jw[s * NINT + w];
-          uint64_t miss = iw & ~jw;
-          while (miss) {
-            const int b = __ffsll((long long)miss) - 1;
-            miss &= miss - 1;
-            hmask |= 1ull << (below + __popcll(iw & ((1ull << b) - 1)));
-          }
-          uint64_t extra = jw & ~iw;
-          while (extra) {
-            const int b = __ffsll((long long)extra) - 1;
-            extra &= extra - 1;
-            const uint64_t code = (uint64_t)(s * norb + 64 * w + b);
-            if (npart < 4) part = (part & ~(0xFFFFull << (16 * npart))) | (code << (16 * npart));
-            npart++;
-          }
-          below += __popcll(iw);
-        }
-      }
-#pragma unroll
-      for (int w = 0; w < NW; w++) rw[(size_t)r * NW + w] = Jw[w];
-      rc[r] = p.coefs[j];
-      rh[r] = hmask;
-      rp[r] = part;
-      rf[r] = (p.rank_of[j] < g) ? 1u : 0u;
-    }
-    nrec += total;
-  }
-  if (tid == 0) M->nrec = nrec;
-
-  // ---- buckets: counting sort of the records into the batches they reach ----
-  for (int b = tid; b <= nbat + 1; b += kThreads) s_cnt[b] = 0;
-  __syncthreads();
-  for (int r = tid; r < nrec; r += kThreads)
-    for_buckets(rh[r], nel, nbat, [&](int b) { atomicAdd(&s_cnt[b], 1); });
-  __syncthreads();
-  if (tid == 0) {
-    int run = 0;
-    for (int b = 0; b <= nbat; b++) {
-      const int c = s_cnt[b];
-      s_cnt[b] = run;
-      run += c;
-    }
-    s_cnt[nbat + 1] = run;
-    if (run > p.ent_cap) atomicOr(p.err, 8);
-  }
-  __syncthreads();
-  int* ofs = p.b_ofs + (size_t)slot * (nbat + 2);
-  for (int b = tid; b <= nbat + 1; b += kThreads) ofs[b] = s_cnt[b];
-  __syncthreads();
-  int32_t* ent = p.b_ent + (size_t)slot * (size_t)p.ent_cap;
-  const long long cap = p.ent_cap;
-  for (int r = tid; r < nrec; r += kThreads)
-    for_buckets(rh[r], nel, nbat, [&](int b) {
-      const int o = atomicAdd(&s_cnt[b], 1);
-      if (o < cap) ent[o] = r;
-    });
-
-  // ---- batches banned as a whole: a J ranked before I with t <= 1 (one
-  // hole) or t = 0 (two holes) reaches every cell.  Only J with d <= 2 can:
-  // d = 1 (holes {q}) kills every one-hole batch and the pairs holding q;
-  // d = 2 (holes {q1, q2}) kills {q1}, {q2} and {q1, q2}. ----
-  const int dw = (nbat + 31) / 32;
-  for (int w = tid; w < dw; w += kThreads) s_dead[w] = 0u;
-  __syncthreads();
-  auto kill = [&](int b) { atomicOr(&s_dead[b >> 5], 1u << (b & 31)); };
-  for (int r = tid; r < nrec; r += kThreads) {
-    if (!(rf[r] & 1u)) continue;
-    const uint64_t hm = rh[r];
-    const int d = __popcll(hm);
-    if (d == 1) {
-      const int q = __ffsll((long long)hm) - 1;
-      for (int i = 0; i < nel; i++) kill(i);
-      for (int o = 0; o < nel; o++)
-        if (o != q) kill(pair_batch(nel, q < o ? q : o, q < o ? o : q));
-    } else if (d == 2) {
-      const int q1 = __ffsll((long long)hm) - 1;
-      const int q2 = __ffsll((long long)(hm & (hm - 1))) - 1;
-      kill(q1);
-      kill(q2);
-      kill(pair_batch(nel, q1, q2));
-    }
-  }
-  __syncthreads();
-  uint32_t* dead = p.b_dead + (size_t)slot * dw;
-  for (int w = tid; w < dw; w += kThreads) dead[w] = s_dead[w];
-}
-
-// ---------------------------------------------------------------------------
-// batch kernel
-// ---------------------------------------------------------------------------
-template <int NINT>
-struct BatchShared {
-  uint64_t I[2 * NINT];
-  int occ[kMaxElec];
-  int vir[2][kMaxOrb];
-  int vidx[2][kMaxOrb];
-  int nv[2];
-  double F[2][kMaxOrb];
-  double u0[kMaxOrb], u1[kMaxOrb];  // per-batch row sums for H_aa
-  double hii, base;
-  float inv_nv1;
-  uint64_t kbase[2 * NINT];  // I with the batch's holes removed
-  int g, slot;
-  long long item;
-  int L0[kChunk], L1[kChunk], L2[kChunk];
-  int n0, n1, n2;
-  // a group of J reaching every cell, processed by the whole CTA
-  uint64_t gJw[kGroup][2 * NINT];
-  double gcj[kGroup];
-  int gX[kGroup][4], gT[kGroup][2], gnx[kGroup], gnt[kGroup];
-  // two-hole batches: J = K + {x1, x2}; per particle orbital of each slot the
-  // pair index tri(x, r) with the phase parity in bit 31
-  int gRow[kGroup][kMaxOrb], gCol[kGroup][kMaxOrb];
-  int gx1[kGroup], gx2[kGroup], gsr[kGroup], gsc[kGroup];
-  int wsum[kWarps];
-  // selection
-  int tkcnt;
-  unsigned long long tau;
-  int hist[256];
-  uint64_t pw[1 + 2 * NINT];
-  uint64_t thr[1 + 2 * NINT];
-  int need, group, found_w, found_sh;
-  // reductions
-  double red_d[kWarps][2];
-  unsigned long long red_u[kWarps][6];
-};
-
-struct Batch {
-  int h;            // number of holes (1, 2)
-  int kind;         // 0 single, 1 same-spin double, 2 opposite-spin double
-  int ia, ib;       // occupied indices of the holes in I
-  int ca, cb;       // their spin-orbital codes
-  int sa, sb;       // their spins
-  int qa, qb;       // their orbitals
-  uint64_t hm;      // hole mask over I's occupied list
-  int ncell;
-};
-
-template <int NINT>
-__device__ __forceinline__ void cell_orbitals(const Batch& B, const BatchShared<NINT>& S, int c, int* r,
-                                              int* s, int* x, int* y) {
-  if (B.kind == 0) {
-    *x = c;
-    *y = -1;
-    *r = S.vir[B.sa][c];
-    *s = -1;
-  } else if (B.kind == 2) {
-    const int nv1 = S.nv[1];
-    int xx = __float2int_rz((float)c * S.inv_nv1);  // c < 2^14: exact up to one step
-    if (xx * nv1 > c) xx--;
-    if ((xx + 1) * nv1 <= c) xx++;
-    *x = xx;
-    *y = c - xx * nv1;
-    *r = S.vir[0][xx];
-    *s = S.vir[1][*y];
-  } else {
-    int yy = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)c)) * 0.5f);
-    while (yy * (yy - 1) / 2 > c) yy--;
-    while ((yy + 1) * yy / 2 <= c) yy++;
-    *x = c - yy * (yy - 1) / 2;
-    *y = yy;
-    *r = S.vir[B.sa][*x];
-    *s = S.vir[B.sa][yy];
-  }
-}
-
-__device__ __forceinline__ int pair_cell(int x, int y) {  // x != y virtual indices
-  int lo = x < y ? x : y, hi = x < y ? y : x;
-  return hi * (hi - 1) / 2 + lo;
-}
-
-// Particles of J outside I, filtered to a spin, as orbitals.
-__device__ __forceinline__ int particles_of_spin(uint64_t part, int norb, int spin, int* out) {
-  int n = 0;
-#pragma unroll
-  for (int i = 0; i < 4; i++) {
-    const int c = (int)((part >> (16 * i)) & 0xFFFF);
-    if (c == 0xFFFF) continue;
-    const int s = c >= norb;
-    if (s == spin) out[n++] = c - s * norb;
-  }
-  return n;
-}
-
-// Cells inside the particles of J (t = 2): visited by one thread.
-template <int NINT, typename Fn>
-__device__ __forceinline__ void for_subset_cells(const Batch& B, const BatchShared<NINT>& S, int norb,
-                                                 uint64_t part, Fn&& fn) {
-  if (B.kind == 0) {
-    int P[4];
-    const int np = particles_of_spin(part, norb, B.sa, P);
-    for (int i = 0; i < np; i++) fn(S.vidx[B.sa][P[i]]);
-  } else if (B.kind == 1) {
-    int P[4];
-    const int np = particles_of_spin(part, norb, B.sa, P);
-    for (int i = 0; i < np; i++)
-      for (int j = i + 1; j < np; j++) fn(pair_cell(S.vidx[B.sa][P[i]], S.vidx[B.sa][P[j]]));
-  } else {
-    int Pa[4], Pb[4];
-    const int na = particles_of_spin(part, norb, 0, Pa);
-    const int nb = particles_of_spin(part, norb, 1, Pb);
-    for (int i = 0; i < na; i++)
-      for (int j = 0; j < nb; j++) fn(S.vidx[0][Pa[i]] * S.nv[1] + S.vidx[1][Pb[j]]);
-  }
-}
-
-// Cells touching the particles of J (two-hole batch, t = 1): visited by the
-// 32 lanes of a warp, each cell once.
-template <int NINT, typename Fn>
-__device__ __forceinline__ void for_row_cells(const Batch& B, const BatchShared<NINT>& S, int norb,
-                                              uint64_t part, int lane, Fn&& fn) {
-  if (B.kind == 1) {
-    int P[4];
-    const int np = particles_of_spin(part, norb, B.sa, P);
-    const int nv = S.nv[B.sa];
-    for (int i = 0; i < np; i++) {
-      const int x = S.vidx[B.sa][P[i]];
-      for (int y = lane; y < nv; y += 32) {
-        if (y == x) continue;
-        bool dup = false;  // pair {P[j], P[i]}, j < i, was visited from P[j]
-        for (int j = 0; j < i; j++) dup |= (S.vidx[B.sa][P[j]] == y);
-        if (!dup) fn(pair_cell(x, y));
-      }
-    }
-  } else {  // kind 2
-    int Pa[4], Pb[4];
-    const int na = particles_of_spin(part, norb, 0, Pa);
-    const int nb = particles_of_spin(part, norb, 1, Pb);
-    const int nv0 = S.nv[0], nv1 = S.nv[1];
-    for (int i = 0; i < na; i++) {
-      const int x = S.vidx[0][Pa[i]];
-      for (int y = lane; y < nv1; y += 32) fn(x * nv1 + y);
-    }
-    for (int j = 0; j < nb; j++) {
-      const int y = S.vidx[1][Pb[j]];
-      for (int x = lane; x < nv0; x += 32) {
-        bool dup = false;  // rows of Pa were visited above
-        for (int i = 0; i < na; i++) dup |= (S.vidx[0][Pa[i]] == x);
-        if (!dup) fn(x * nv1 + y);
-      }
-    }
-  }
-}
-
-// X = (particles of J) + (holes of H that J keeps); T = holes of J not in H.
-template <int NINT>
-__device__ __forceinline__ void excitation_sets(const Batch& B, const BatchShared<NINT>& S, uint64_t part,
-                                                uint64_t hm, int* X, int* nx, int* T, int* nt) {
-  int a = 0, b = 0;
-  for (int i = 0; i < 4; i++) {
-    const int c = (int)((part >> (16 * i)) & 0xFFFF);
-    if (c != 0xFFFF && a < 4) X[a++] = c;
-  }
-  if (!((hm >> B.ia) & 1ull) && a < 4) X[a++] = B.ca;
-  if (B.h == 2 && !((hm >> B.ib) & 1ull) && a < 4) X[a++] = B.cb;
-  uint64_t tm = hm & ~B.hm;
-  while (tm && b < 2) {
-    const int i = __ffsll((long long)tm) - 1;
-    tm &= tm - 1;
-    T[b++] = S.occ[i];
-  }
-  *nx = a;
-  *nt = b;
-}
-
-// <J|H|alpha> with alpha = K + R, K = I - H.
-// holes(J -> alpha) = X - R, particles = T + (R - X).
-// Kept out of line: one copy serves every caller, which keeps the batch
-// kernel's code small enough for the instruction cache.
-template <int NINT>
-__device__ __noinline__ double element(const SweepParams& p, const uint64_t* Jw, const int* X, int nx,
-                                          const int* T, int nt, int r, int s) {
-  const int norb = p.norb;
-  int ho[2], pa[2], nh = 0, npp = 0;
-  bool r_in = false, s_in = false;
-  for (int i = 0; i < nx; i++) {
-    const int x = X[i];
-    r_in |= (x == r);
-    s_in |= (x == s);
-    if (x != r && x != s && nh < 2) ho[nh++] = x;
-  }
-  for (int i = 0; i < nt && npp < 2; i++) pa[npp++] = T[i];
-  if (!r_in && npp < 2) pa[npp++] = r;
-  if (s >= 0 && !s_in && npp < 2) pa[npp++] = s;
-  if (nh == 0 || nh != npp) return 0.0;  // not reached: such cells are banned
-  if (nh == 1) {
-    const int sp = ho[0] >= norb, a = ho[0] - sp * norb, b = pa[0] - sp * norb;
-    const uint64_t* sw = Jw + sp * NINT;
-    const int lo = a < b ? a : b, hi = a < b ? b : a;
-    const double sign = (count_between<NINT>(sw, lo, hi) & 1) ? -1.0 : 1.0;
-    double v = p.h[a * norb + b];
-#pragma unroll
-    for (int t = 0; t < 2; t++) {
-#pragma unroll
-      for (int w = 0; w < NINT; w++) {
-        uint64_t bits = Jw[t * NINT + w];
-        while (bits) {
-          const int q = 64 * w + __ffsll((long long)bits) - 1;
-          bits &= bits - 1;
-          v += p.eri[eri_index(a, b, q, q)];
-          if (t == sp) v -= p.eri[eri_index(a, q, q, b)];
-        }
-      }
-    }
-    return sign * v;
-  }
-  // double: order holes and particles by spin-orbital code, pair 1-1, 2-2
-  if (ho[0] > ho[1]) { const int t = ho[0]; ho[0] = ho[1]; ho[1] = t; }
-  if (pa[0] > pa[1]) { const int t = pa[0]; pa[0] = pa[1]; pa[1] = t; }
-  const int s1 = ho[0] >= norb, s2 = ho[1] >= norb;
-  const int h1 = ho[0] - s1 * norb, p1 = pa[0] - s1 * norb;
-  const int h2 = ho[1] - s2 * norb, p2 = pa[1] - s2 * norb;
-  uint64_t w1[NINT];
-#pragma unroll
-  for (int w = 0; w < NINT; w++) w1[w] = Jw[s1 * NINT + w];
-  const int n1 = count_between<NINT>(w1, h1 < p1 ? h1 : p1, h1 < p1 ? p1 : h1);
-  // apply h1 -> p1, then count for h2 -> p2 on the result
-  w1[h1 >> 6] &= ~(1ull << (h1 & 63));
-  w1[p1 >> 6] |= (1ull << (p1 & 63));
-  const int n2 = (s2 == s1) ? count_between<NINT>(w1, h2 < p2 ? h2 : p2, h2 < p2 ? p2 : h2)
-                            : count_between<NINT>(Jw + s2 * NINT, h2 < p2 ? h2 : p2, h2 < p2 ? p2 : h2);
-  double v = p.eri[eri_index(h1, p1, h2, p2)];
-  if (s1 == s2) v -= p.eri[eri_index(h1, p2, h2, p1)];
-  return ((n1 + n2) & 1) ? -v : v;
-}
-
-// ---------------------------------------------------------------------------
-// Selection buffer compaction: keep the k best entries (|e| descending, key
-// ascending) of the CTA's buffer.  MSD radix select over the composite
-// (~bits(|e|), key words), 8-bit digits, then an ordered in-place compaction.
-// ---------------------------------------------------------------------------
-template <int NINT>
-__device__ __forceinline__ uint64_t composite_word(const double* te, const uint64_t* tk, int i, int w) {
-  if (w == 0) return ~(unsigned long long)__double_as_longlong(fabs(te[i]));
-  return tk[(size_t)i * (2 * NINT) + (w - 1)];
-}
-
-template <int NINT>
-__device__ bool prefix_match(const double* te, const uint64_t* tk, int i, const uint64_t* pw, int w,
-                             int keep_sh) {
-  for (int v = 0; v < w; v++)
-    if (composite_word<NINT>(te, tk, i, v) != pw[v]) return false;
-  if (keep_sh >= 64) return true;
-  return (composite_word<NINT>(te, tk, i, w) >> keep_sh) == (pw[w] >> keep_sh);
-}
-
-template <int NINT>
-__device__ __noinline__ void compact_selection(const SweepParams& p, BatchShared<NINT>& S, double* te,
-                                               double* ta, uint64_t* tk) {
-  constexpr int NW = 1 + 2 * NINT;
-  const int tid = threadIdx.x;
-  __syncthreads();
-  const int n = S.tkcnt;
-  const long long k = p.k;
-  if (n <= k) return;
-  if (tid == 0) {
-    S.need = (int)k;
-    for (int w = 0; w < NW; w++) S.pw[w] = 0;
-    S.group = n;
-    S.found_w = NW - 1;
-    S.found_sh = 0;
-  }
-  __syncthreads();
-  bool done = false;
-  for (int w = 0; w < NW && !done; w++) {
-    for (int sh = 56; sh >= 0; sh -= 8) {
-      for (int b = tid; b < 256; b += kThreads) S.hist[b] = 0;
-      __syncthreads();
-      for (int i = tid; i < n; i += kThreads)
-        if (prefix_match<NINT>(te, tk, i, S.pw, w, sh + 8))
-          atomicAdd(&S.hist[(composite_word<NINT>(te, tk, i, w) >> sh) & 255], 1);
-      __syncthreads();
-      if (tid == 0) {
-        int c = 0, d = 255;
-        for (int b = 0; b < 256; b++) {
-          if (c + S.hist[b] >= S.need) {
-            d = b;
-            break;
-          }
-          c += S.hist[b];
-        }
-        S.need -= c;
-        S.group = S.hist[d];
-        S.pw[w] |= (uint64_t)d << sh;
-        S.found_w = w;
-        S.found_sh = sh;
-      }
-      __syncthreads();
-      if (S.group <= 1) {
-        done = true;
-        break;
-      }
-    }
-  }
-  if (S.group == 1) {
-    for (int i = tid; i < n; i += kThreads)
-      if (prefix_match<NINT>(te, tk, i, S.pw, S.found_w, S.found_sh))
-        for (int w = 0; w < NW; w++) S.thr[w] = composite_word<NINT>(te, tk, i, w);
-  } else if (tid == 0) {
-    for (int w = 0; w < NW; w++) S.thr[w] = S.pw[w];
-  }
-  __syncthreads();
-  int out = 0;
-  for (int base = 0; base < n; base += kThreads) {
-    const int i = base + tid;
-    bool keep = false;
-    double e = 0, a = 0;
-    uint64_t key[2 * NINT];
-    if (i < n) {
-      int cmp = 0;
-      for (int w = 0; w < NW && cmp == 0; w++) {
-        const uint64_t x = composite_word<NINT>(te, tk, i, w);
-        cmp = x < S.thr[w] ? -1 : (x > S.thr[w] ? 1 : 0);
-      }
-      keep = cmp <= 0;
-      e = te[i];
-      a = ta[i];
-#pragma unroll
-      for (int w = 0; w < 2 * NINT; w++) key[w] = tk[(size_t)i * (2 * NINT) + w];
-    }
-    int total;
-    const int pos = block_scan_flag(keep, S.wsum, &total);
-    if (keep) {
-      const int o = out + pos;
-      te[o] = e;
-      ta[o] = a;
-#pragma unroll
-      for (int w = 0; w < 2 * NINT; w++) tk[(size_t)o * (2 * NINT) + w] = key[w];
-    }
-    out += total;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    S.tkcnt = out;
-    const unsigned long long t = ~S.thr[0];
-    if (t > S.tau) S.tau = t;
-    atomicMax(p.tau_bits, t);
-  }
-  __syncthreads();
-}
-
-template <int NINT>
-__global__ void __launch_bounds__(kThreads, 3) batch_kernel(SweepParams p) {
-  constexpr int NW = 2 * NINT;
-  extern __shared__ __align__(16) unsigned char dyn[];
-  double* A = reinterpret_cast<double*>(dyn);
-  uint32_t* ban = reinterpret_cast<uint32_t*>(A + p.max_cells);
-  __shared__ BatchShared<NINT> S;
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int norb = p.norb, nel = p.nel, nbat = p.nbat;
-  double* te = p.tk_e + (size_t)blockIdx.x * (size_t)p.cap;
-  double* ta = p.tk_a + (size_t)blockIdx.x * (size_t)p.cap;
-  uint64_t* tk = p.tk_key + (size_t)blockIdx.x * (size_t)p.cap * NW;
-  const long long nitems = (long long)p.wave_slots * nbat;
-
-  if (tid == 0) {
-    S.tkcnt = p.tk_cnt[blockIdx.x];
-    S.tau = p.tk_tau[blockIdx.x];
-    S.slot = -1;
-  }
-
-  for (;;) {
-    __syncthreads();
-    if (tid == 0) S.item = atomicAdd(p.queue, 1);
-    __syncthreads();
-    const long long item = S.item;
-    if (item >= nitems) break;
-    const int slot = (int)(item / nbat), b = (int)(item - (long long)slot * nbat);
-    const GenMeta* M = p.meta + slot;
-    if (M->g < 0) continue;
-    if ((p.b_dead[(size_t)slot * ((nbat + 31) / 32) + (b >> 5)] >> (b & 31)) & 1u) continue;
-    if (slot != S.slot) {  // load the generator
-      __syncthreads();
-      if (tid < NW) S.I[tid] = M->I[tid];
-      if (tid < nel) S.occ[tid] = M->occ[tid];
-      for (int x = tid; x < 2 * norb; x += kThreads) S.F[x / norb][x % norb] = M->F[x / norb][x % norb];
-      __syncthreads();
-      for (int x = tid; x < 2 * norb; x += kThreads) {
-        const int s = x / norb, q = x - s * norb;
-        const uint64_t* sw = S.I + s * NINT;
-        const bool occ = (sw[q >> 6] >> (q & 63)) & 1ull;
-        int below = 0;  // occupied orbitals of spin s below q
-#pragma unroll
-        for (int w = 0; w < NINT; w++) {
-          const int lim = q - 64 * w;
-          if (lim >= 64) below += __popcll(sw[w]);
-          else if (lim > 0) below += __popcll(sw[w] & ((1ull << lim) - 1));
-        }
-        const int v = q - below;
-        S.vidx[s][q] = occ ? -1 : v;
-        if (!occ) S.vir[s][v] = q;
-      }
-      if (tid < 2) {
-        int n = 0;
-#pragma unroll
-        for (int w = 0; w < NINT; w++) n += __popcll(S.I[tid * NINT + w]);
-        S.nv[tid] = norb - n;
-      }
-      if (tid == 0) {
-        S.hii = M->hii;
-        S.g = M->g;
-        S.slot = slot;
-      }
-      __syncthreads();
-    }
-    const int g = S.g;
-
-    // ---- batch geometry ----
-    Batch B;
-    if (b < nel) {
-      B.h = 1;
-      B.ia = b;
-      B.ib = -1;
-    } else {
-      const int t = b - nel;
-      int y = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
-      while (y * (y - 1) / 2 > t) y--;
-      while ((y + 1) * y / 2 <= t) y++;
-      B.h = 2;
-      B.ib = y;
-      B.ia = t - y * (y - 1) / 2;
-    }
-    B.ca = S.occ[B.ia];
-    B.sa = B.ca >= norb;
-    B.qa = B.ca - B.sa * norb;
-    B.hm = 1ull << B.ia;
-    if (B.h == 2) {
-      B.cb = S.occ[B.ib];
-      B.sb = B.cb >= norb;
-      B.qb = B.cb - B.sb * norb;
-      B.hm |= 1ull << B.ib;
-      B.kind = (B.sa == B.sb) ? 1 : 2;
-      const int nv = S.nv[B.sa];
-      B.ncell = (B.kind == 1) ? nv * (nv - 1) / 2 : S.nv[0] * S.nv[1];
-    } else {
-      B.cb = -1;
-      B.sb = -1;
-      B.qb = -1;
-      B.kind = 0;
-      B.ncell = S.nv[B.sa];
-    }
-    if (B.ncell == 0) continue;
-
-    // bucket lists: this batch's bucket, then the shared bucket (degree <= 2)
-    const int* ofs = p.b_ofs + (size_t)slot * (nbat + 2);
-    const int32_t* ent = p.b_ent + (size_t)slot * (size_t)p.ent_cap;
-    const int ob = ofs[b], nb_ = ofs[b + 1] - ob, oa = ofs[nbat], na_ = ofs[nbat + 1] - oa;
-    const int total = nb_ + na_;
-    const size_t rb = (size_t)slot * (size_t)p.ndet;
-    const uint64_t* rw = p.r_words + rb * NW;
-    const double* rc = p.r_coef + rb;
-    const uint64_t* rh = p.r_hmask + rb;
-    const uint64_t* rp = p.r_part + rb;
-    const uint32_t* rf = p.r_flag + rb;
-    auto entry = [&](int i) { return i < nb_ ? ent[ob + i] : ent[oa + i - nb_]; };
-
-    if (tid == 0) {
-      S.inv_nv1 = S.nv[1] > 0 ? 1.0f / (float)S.nv[1] : 0.0f;
-#pragma unroll
-      for (int w = 0; w < NW; w++) S.kbase[w] = S.I[w];
-      S.kbase[B.sa * NINT + (B.qa >> 6)] &= ~(1ull << (B.qa & 63));
-      if (B.h == 2) S.kbase[B.sb * NINT + (B.qb >> 6)] &= ~(1ull << (B.qb & 63));
-    }
-    // zero the accumulator, the bans; row sums for H_aa
-    for (int c = tid; c < B.ncell; c += kThreads) A[c] = 0.0;
-    for (int c = tid; c < (B.ncell + 31) / 32; c += kThreads) ban[c] = 0u;
-    {
-      auto W = [&](int x, int sx, int y, int sy) {
-        double v = p.Jm[x * norb + y];
-        if (sx == sy) v -= p.Km[x * norb + y];
-        return v;
-      };
-      if (B.kind == 0) {
-        const int s = B.sa;
-        for (int x = tid; x < S.nv[s]; x += kThreads) {
-          const int r = S.vir[s][x];
-          S.u0[x] = S.F[s][r] - W(r, s, B.qa, s);
-        }
-        if (tid == 0) S.base = S.hii - S.F[s][B.qa];
-      } else {
-        const int s1 = B.sa, s2 = B.sb;
-        for (int x = tid; x < S.nv[s1]; x += kThreads) {
-          const int r = S.vir[s1][x];
-          S.u0[x] = S.F[s1][r] - W(r, s1, B.qa, s1) - W(r, s1, B.qb, s2);
-        }
-        if (B.kind == 2)
-          for (int y = tid; y < S.nv[s2]; y += kThreads) {
-            const int s = S.vir[s2][y];
-            S.u1[y] = S.F[s2][s] - W(s, s2, B.qa, s1) - W(s, s2, B.qb, s2);
-          }
-        if (tid == 0) S.base = S.hii - S.F[s1][B.qa] - S.F[s2][B.qb] + W(B.qa, s1, B.qb, s2);
-      }
-    }
-    __syncthreads();
-
-    // ---- loop 1: bans ----
-    bool dead = false;
-    for (int c0 = 0; c0 < total; c0 += kChunk) {
-      if (tid == 0) S.n1 = 0;
-      __syncthreads();
-      bool dl = false;
-      const int c1 = min(c0 + kChunk, total);
-      for (int i = c0 + tid; i < c1; i += kThreads) {
-        const int r = entry(i);
-        const uint64_t hm = rh[r];
-        const int t = __popcll(hm & ~B.hm);
-        if (t > 2) continue;
-        if (rf[r] & 1u) {
-          if ((B.h == 1 && t <= 1) || (B.h == 2 && t == 0)) {
-            dl = true;
-          } else if (B.h == 2 && t == 1) {
-            S.L1[atomicAdd(&S.n1, 1)] = r;
-          } else {  // t == 2
-            for_subset_cells<NINT>(B, S, norb, rp[r], [&](int c) { atomicOr(&ban[c >> 5], 1u << (c & 31)); });
-          }
-        } else if (t == 0 && hm == B.hm) {  // J = I - H + X with X a cell: alpha is internal
-          const uint64_t part = rp[r];
-          int P0[4], P1[4], c;
-          if (B.kind == 0) {
-            particles_of_spin(part, norb, B.sa, P0);
-            c = S.vidx[B.sa][P0[0]];
-          } else if (B.kind == 1) {
-            particles_of_spin(part, norb, B.sa, P0);
-            c = pair_cell(S.vidx[B.sa][P0[0]], S.vidx[B.sa][P0[1]]);
-          } else {
-            particles_of_spin(part, norb, 0, P0);
-            particles_of_spin(part, norb, 1, P1);
-            c = S.vidx[0][P0[0]] * S.nv[1] + S.vidx[1][P1[0]];
-          }
-          atomicOr(&ban[c >> 5], 1u << (c & 31));
-        }
-      }
-      if (__syncthreads_or(dl)) {
-        dead = true;
-        break;
-      }
-      for (int j = warp; j < S.n1; j += kWarps)
-        for_row_cells<NINT>(B, S, norb, rp[S.L1[j]], lane,
-                            [&](int c) { atomicOr(&ban[c >> 5], 1u << (c & 31)); });
-      __syncthreads();
-    }
-    if (dead) continue;
-
-    // ---- loop 2: A(R) += c_J <J|H|I - H + R> over J ranked at or after I ----
-    unsigned long long con = 0;
-    for (int c0 = 0; c0 < total; c0 += kChunk) {
-      if (tid == 0) {
-        S.n0 = 0;
-        S.n1 = 0;
-        S.n2 = 0;
-      }
-      __syncthreads();
-      const int c1 = min(c0 + kChunk, total);
-      for (int i = c0 + tid; i < c1; i += kThreads) {
-        const int r = entry(i);
-        if (rf[r] & 1u) continue;
-        const int t = __popcll(rh[r] & ~B.hm);
-        if (t > 2) continue;
-        const bool all = (B.h == 1) ? (t <= 1) : (t == 0);
-        if (all) S.L0[atomicAdd(&S.n0, 1)] = r;
-        else if (t == 1) S.L1[atomicAdd(&S.n1, 1)] = r;
-        else S.L2[atomicAdd(&S.n2, 1)] = r;
-      }
-      __syncthreads();
-      // J reaching every cell: the whole CTA, kGroup of them per pass.
-      // In a two-hole batch such a J is K + {x1, x2}; for a cell R disjoint
-      // from {x1, x2} the element is a double substitution x1 x2 -> R whose
-      // pair indices and phase split into a row part and a column part,
-      // precomputed once per J (cells meeting {x1, x2} take the general path).
-      const int n0 = S.n0;
-      for (int g0 = 0; g0 < n0; g0 += kGroup) {
-        const int m = min(kGroup, n0 - g0);
-        if (tid < m) {
-          const int r = S.L0[g0 + tid];
-#pragma unroll
-          for (int w = 0; w < NW; w++) S.gJw[tid][w] = rw[(size_t)r * NW + w];
-          S.gcj[tid] = rc[r];
-          excitation_sets<NINT>(B, S, rp[r], rh[r], S.gX[tid], &S.gnx[tid], S.gT[tid], &S.gnt[tid]);
-          if (B.h == 2) {
-            const int a = S.gX[tid][0], bb = S.gX[tid][1];
-            const int x1 = a < bb ? a : bb, x2 = a < bb ? bb : a;
-            S.gx1[tid] = x1;
-            S.gx2[tid] = x2;
-            const int s1 = x1 >= norb, s2 = x2 >= norb;
-            S.gsr[tid] = S.vidx[s1][x1 - s1 * norb];
-            S.gsc[tid] = S.vidx[s2][x2 - s2 * norb];
-          }
-        }
-        __syncthreads();
-        const int sl1 = B.sa, sl2 = (B.kind == 2) ? 1 : B.sa;
-        const int nva = S.nv[sl1], nvb = S.nv[sl2];
-        if (B.h == 2) {
-          const int per = nva + nvb;
-          for (int idx = tid; idx < m * per; idx += kThreads) {
-            const int j = idx / per;
-            const int v = idx - j * per;
-            const uint64_t* Jw = S.gJw[j];
-            const int x1 = S.gx1[j] - sl1 * norb, x2 = S.gx2[j] - sl2 * norb;
-            if (v < nva) {
-              const int r = S.vir[sl1][v];
-              int par = 0;
-              if (r != x1) par = count_between<NINT>(Jw + sl1 * NINT, r < x1 ? r : x1, r < x1 ? x1 : r) & 1;
-              S.gRow[j][v] = tri(x1, r) | (par << 31);
-            } else {
-              const int sv = S.vir[sl2][v - nva];
-              int par = 0;
-              if (sv != x2) par = count_between<NINT>(Jw + sl2 * NINT, sv < x2 ? sv : x2, sv < x2 ? x2 : sv) & 1;
-              if (B.kind == 1) {
-                const int lo = sv < x2 ? sv : x2, hi = sv < x2 ? x2 : sv;
-                par ^= (x1 > lo && x1 < hi) ? 1 : 0;
-              }
-              S.gCol[j][v - nva] = tri(x2, sv) | (par << 31);
-            }
-          }
-          __syncthreads();
-        }
-        for (int c = tid; c < B.ncell; c += kThreads) {
-          if ((ban[c >> 5] >> (c & 31)) & 1u) continue;
-          int ro, so, x, y;
-          cell_orbitals<NINT>(B, S, c, &ro, &so, &x, &y);
-          const int rcode = B.sa * norb + ro;
-          const int scode = (B.h == 2) ? B.sb * norb + so : -1;
-          double acc = 0.0;
-          for (int j = 0; j < m; j++) {
-            bool general = true;
-            double v = 0.0;
-            if (B.h == 2) {
-              const int sr = S.gsr[j], sc = S.gsc[j];
-              if (B.kind == 2) {
-                if (x != sr && y != sc) {
-                  const int rt = S.gRow[j][x], ct = S.gCol[j][y];
-                  v = p.eri[tri(rt & 0x7fffffff, ct & 0x7fffffff)];
-                  if ((rt ^ ct) < 0) v = -v;
-                  general = false;
-                }
-              } else if (x != sr && x != sc && y != sr && y != sc) {
-                const int a1 = S.gRow[j][x], b2 = S.gCol[j][y];
-                const int a2 = S.gRow[j][y], b1 = S.gCol[j][x];
-                v = p.eri[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - p.eri[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
-                const int x2 = S.gx2[j] - B.sa * norb;
-                const int lo = so < x2 ? so : x2, hi = so < x2 ? x2 : so;
-                const int par = ((a1 ^ b2) < 0 ? 1 : 0) ^ ((ro > lo && ro < hi) ? 1 : 0);
-                if (par) v = -v;
-                general = false;
-              }
-            }
-            if (general) v = element<NINT>(p, S.gJw[j], S.gX[j], S.gnx[j], S.gT[j], S.gnt[j], rcode, scode);
-            acc += S.gcj[j] * v;
-          }
-          A[c] += acc;
-          con += m;
-        }
-        __syncthreads();
-      }
-      // J reaching a row of cells: one warp each
-      for (int j = warp; j < S.n1; j += kWarps) {
-        const int r = S.L1[j];
-        uint64_t Jw[NW];
-#pragma unroll
-        for (int w = 0; w < NW; w++) Jw[w] = rw[(size_t)r * NW + w];
-        const double cj = rc[r];
-        const uint64_t part = rp[r];
-        int X[4], T[2], nx, nt;
-        excitation_sets<NINT>(B, S, part, rh[r], X, &nx, T, &nt);
-        for_row_cells<NINT>(B, S, norb, part, lane, [&](int c) {
-          if ((ban[c >> 5] >> (c & 31)) & 1u) return;
-          int ro, so, x, y;
-          cell_orbitals<NINT>(B, S, c, &ro, &so, &x, &y);
-          const int rcode = B.sa * norb + ro;
-          const int scode = B.sb * norb + so;
-          atomicAdd(&A[c], cj * element<NINT>(p, Jw, X, nx, T, nt, rcode, scode));
-          con++;
-        });
-      }
-      // J reaching a few cells: one thread each
-      for (int j = tid; j < S.n2; j += kThreads) {
-        const int r = S.L2[j];
-        uint64_t Jw[NW];
-#pragma unroll
-        for (int w = 0; w < NW; w++) Jw[w] = rw[(size_t)r * NW + w];
-        const double cj = rc[r];
-        const uint64_t part = rp[r];
-        int X[4], T[2], nx, nt;
-        excitation_sets<NINT>(B, S, part, rh[r], X, &nx, T, &nt);
-        for_subset_cells<NINT>(B, S, norb, part, [&](int c) {
-          if ((ban[c >> 5] >> (c & 31)) & 1u) return;
-          int ro, so, x, y;
-          cell_orbitals<NINT>(B, S, c, &ro, &so, &x, &y);
-          const int rcode = B.sa * norb + ro;
-          const int scode = (B.h == 2) ? B.sb * norb + so : -1;
-          atomicAdd(&A[c], cj * element<NINT>(p, Jw, X, nx, T, nt, rcode, scode));
-          con++;
-        });
-      }
-      __syncthreads();
-    }
-
-    // ---- cells: the perturbers of I in this batch ----
-    if (p.k > 0) {
-      if (S.tkcnt + B.ncell > p.cap) compact_selection<NINT>(p, S, te, ta, tk);
-      if (tid == 0) {
-        const unsigned long long gt = *((volatile unsigned long long*)p.tau_bits);
-        if (gt > S.tau) S.tau = gt;
-      }
-      __syncthreads();
-    }
-    const unsigned long long tau = S.tau;
-    double acc_e = 0.0, acc_s2 = 0.0;
-    unsigned long long acc_na = 0, acc_d0 = 0, acc_d1 = 0, acc_min = 0x7FF0000000000000ull, acc_tiny = 0;
-    const double base = S.base;
-    for (int c = tid; c < B.ncell; c += kThreads) {
-      if ((ban[c >> 5] >> (c & 31)) & 1u) continue;
-      int ro, so, x, y;
-      cell_orbitals<NINT>(B, S, c, &ro, &so, &x, &y);
-      const double a = A[c];
-      double haa = base + S.u0[x];
-      if (B.kind == 2) haa += S.u1[y] + p.Jm[ro * norb + so];
-      else if (B.kind == 1) haa += S.u0[y] + (p.Jm[ro * norb + so] - p.Km[ro * norb + so]);
-      const double D = p.e0 - haa;
-      const double inv = 1.0 / D;
-      const double q = a * inv;
-      const double e = a * q;
-      acc_e += e;
-      acc_s2 += q * q;
-      acc_na++;
-      if (fabs(a) < 1e-14) acc_tiny++;
-      const unsigned long long db = (unsigned long long)__double_as_longlong(fabs(D));
-      acc_min = db < acc_min ? db : acc_min;
-      uint64_t key[NW];
-#pragma unroll
-      for (int w = 0; w < NW; w++) key[w] = S.kbase[w];
-      key[B.sa * NINT + (ro >> 6)] |= 1ull << (ro & 63);
-      if (B.h == 2) key[B.sb * NINT + (so >> 6)] |= 1ull << (so & 63);
-      uint64_t hk = 0;
-#pragma unroll
-      for (int w = 0; w < NW; w++) hk = splitmix64(hk ^ key[w]);
-      acc_d0 += hk;
-      acc_d1 ^= splitmix64(hk ^ 0x243F6A8885A308D3ull);
-      if (p.k > 0) {
-        const unsigned long long eb = (unsigned long long)__double_as_longlong(fabs(e));
-        if (eb >= tau) {
-          const int pos = atomicAdd(&S.tkcnt, 1);
-          te[pos] = e;
-          ta[pos] = a;
-#pragma unroll
-          for (int w = 0; w < NW; w++) tk[(size_t)pos * NW + w] = key[w];
-        }
-      }
-    }
-    // ---- per-item reduction into the generator's totals ----
-    {
-      const double e = warp_sum(acc_e), s2 = warp_sum(acc_s2);
-      const unsigned long long na = warp_sum_u(acc_na), nc = warp_sum_u(con), d0 = warp_sum_u(acc_d0);
-      const unsigned long long d1 = warp_xor_u(acc_d1), mn = warp_min_u(acc_min), tiny = warp_sum_u(acc_tiny);
-      if (lane == 0) {
-        S.red_d[warp][0] = e;
-        S.red_d[warp][1] = s2;
-        S.red_u[warp][0] = na;
-        S.red_u[warp][1] = nc;
-        S.red_u[warp][2] = d0;
-        S.red_u[warp][3] = d1;
-        S.red_u[warp][4] = mn;
-        S.red_u[warp][5] = tiny;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        double te_ = 0, ts = 0;
-        unsigned long long tn = 0, tc = 0, x0 = 0, x1 = 0, m = 0x7FF0000000000000ull, tt = 0;
-        for (int w = 0; w < kWarps; w++) {
-          te_ += S.red_d[w][0];
-          ts += S.red_d[w][1];
-          tn += S.red_u[w][0];
-          tc += S.red_u[w][1];
-          x0 += S.red_u[w][2];
-          x1 ^= S.red_u[w][3];
-          m = S.red_u[w][4] < m ? S.red_u[w][4] : m;
-          tt += S.red_u[w][5];
-        }
-        if (tn) {
-          atomicAdd(&p.eps[g], te_);
-          atomicAdd(&p.s2[g], ts);
-          atomicAdd(&p.na[g], tn);
-          atomicAdd(&p.ncon[g], tc);
-          atomicAdd(&p.digest[0], x0);
-          atomicXor(&p.digest[1], x1);
-          atomicMin(p.min_den_bits, m);
-          if (tt) atomicAdd(p.n_tiny, tt);
-        }
-      }
-    }
-  }
-  if (p.k > 0 && p.last_wave) compact_selection<NINT>(p, S, te, ta, tk);
-  __syncthreads();
-  if (tid == 0) {
-    p.tk_cnt[blockIdx.x] = S.tkcnt;
-    p.tk_tau[blockIdx.x] = S.tau;
-  }
-}
-
 template __global__ void prep_kernel<1>(SweepParams);
 template __global__ void prep_kernel<2>(SweepParams);
-template __global__ void batch_kernel<1>(SweepParams);
-template __global__ void batch_kernel<2>(SweepParams);
+template __global__ void batch_kernel<1, double>(SweepParams);
+template __global__ void batch_kernel<2, double>(SweepParams);
 
-// host-side launch helpers --------------------------------------------------
+cudaError_t launch_batch_mixed(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
+int batch_blocks_per_sm_mixed(int nint, size_t smem);
+
 cudaError_t launch_prep(int nint, const SweepParams& p, int slots, cudaStream_t st) {
   if (nint == 1) prep_kernel<1><<<slots, kThreads, 0, st>>>(p);
   else prep_kernel<2><<<slots, kThreads, 0, st>>>(p);
@@ -1130,24 +20,26 @@ cudaError_t launch_prep(int nint, const SweepParams& p, int slots, cudaStream_t 
 }
 
 cudaError_t launch_batch(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st) {
+  if (p.mixed) return launch_batch_mixed(nint, p, grid, smem, st);
   if (nint == 1) {
-    cudaFuncSetAttribute(batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    batch_kernel<1><<<grid, kThreads, smem, st>>>(p);
+    cudaFuncSetAttribute(batch_kernel<1, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    batch_kernel<1, double><<<grid, kThreads, smem, st>>>(p);
   } else {
-    cudaFuncSetAttribute(batch_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    batch_kernel<2><<<grid, kThreads, smem, st>>>(p);
+    cudaFuncSetAttribute(batch_kernel<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    batch_kernel<2, double><<<grid, kThreads, smem, st>>>(p);
   }
   return cudaGetLastError();
 }
 
-int batch_blocks_per_sm(int nint, size_t smem) {
+int batch_blocks_per_sm(int nint, int mixed, size_t smem) {
+  if (mixed) return batch_blocks_per_sm_mixed(nint, smem);
   int n = 0;
   if (nint == 1) {
-    cudaFuncSetAttribute(batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<1>, kThreads, smem);
+    cudaFuncSetAttribute(batch_kernel<1, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<1, double>, kThreads, smem);
   } else {
-    cudaFuncSetAttribute(batch_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<2>, kThreads, smem);
+    cudaFuncSetAttribute(batch_kernel<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<2, double>, kThreads, smem);
   }
   return n;
 }

@@ -1,0 +1,33 @@
+// sweep_mixed.cu -- the mixed-precision batch kernels (FP32 integral gathers and
+// products, FP64 accumulation, denominators and reductions); see sweep_impl.cuh.
+#include "sweep_impl.cuh"
+
+namespace qp {
+
+template __global__ void batch_kernel<1, float>(SweepParams);
+template __global__ void batch_kernel<2, float>(SweepParams);
+
+cudaError_t launch_batch_mixed(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st) {
+  if (nint == 1) {
+    cudaFuncSetAttribute(batch_kernel<1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    batch_kernel<1, float><<<grid, kThreads, smem, st>>>(p);
+  } else {
+    cudaFuncSetAttribute(batch_kernel<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    batch_kernel<2, float><<<grid, kThreads, smem, st>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+int batch_blocks_per_sm_mixed(int nint, size_t smem) {
+  int n = 0;
+  if (nint == 1) {
+    cudaFuncSetAttribute(batch_kernel<1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<1, float>, kThreads, smem);
+  } else {
+    cudaFuncSetAttribute(batch_kernel<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<2, float>, kThreads, smem);
+  }
+  return n;
+}
+
+}  // namespace qp

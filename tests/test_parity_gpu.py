@@ -191,3 +191,46 @@ def test_golden_workloads(qp, name):
     check_per_generator(got, ref)
     check_selection(got["sel_dets"], got["sel_e"], E["sel_dets"], E["sel_e"])
     pt2.close()
+
+
+# ---------------------------------------------------------------------------
+# Mixed precision: FP32 integral gathers and products, FP64 accumulation,
+# denominators and reductions.  Integer outputs are structural and must match
+# exactly; the energy must lie within the stated 1e-6 Eh of the FP64 oracle.
+# ---------------------------------------------------------------------------
+MIXED_TOL = 1e-6
+
+
+@pytest.mark.parametrize("norb,na,nb,ndet,k,seed", [(16, 4, 4, 150, 100, 81), (24, 6, 5, 120, 64, 82),
+                                                    (70, 3, 3, 60, 40, 83)])
+def test_mixed_precision_random(qp, oracle_mod, norb, na, nb, ndet, k, seed):
+    h, eri, ham, dets, c, e0 = _case(oracle_mod, norb, na, nb, ndet, seed)
+    ref = ham.sweep(dets, c, e0, k=k)
+    pt2 = qp.PT2(norb, na, nb, _dev(h), _dev(eri), precision=qp.QP_MIXED)
+    got = pt2.eval(_dev(dets), _dev(c), e0, k, per_generator=True)
+    assert got["n_perturbers"] == ref["n_perturbers"]
+    assert got["n_connections"] == ref["n_connections"]
+    assert tuple(got["digest"]) == tuple(ref["digest"])
+    # FP32 products carry a relative error of about 2^-24 each, so the error
+    # of E_PT2 scales with its size: 1e-6 Eh for |E_PT2| <= 1 Eh, relative
+    # 1e-6 beyond (random spaces can have |E_PT2| >> 1 Eh)
+    assert abs(got["e_pt2"] - ref["e_pt2"]) <= MIXED_TOL * max(1.0, abs(ref["e_pt2"]))
+    assert np.array_equal(as_np(got["na_by_rank"]), ref["na_by_rank"])
+    ge, re_ = as_np(got["sel_e"]), ref["sel_e"]
+    assert len(ge) == len(re_)
+    assert np.all(np.abs(ge - re_) <= 1e-7 + 1e-5 * np.abs(re_))
+    pt2.close()
+
+
+def test_mixed_precision_golden_cfg2(qp):
+    P, E, meta, summ = _golden("cfg2")
+    h, eri = S.hamiltonian(meta["norb"], meta["rank"], meta["seed"])
+    pt2 = qp.PT2(meta["norb"], meta["nalpha"], meta["nbeta"], _dev(h), _dev(eri), precision=qp.QP_MIXED)
+    got = pt2.eval(_dev(P["dets"]), _dev(P["coefs"]), float(P["e0"]), meta["k"])
+    assert got["n_perturbers"] == summ["n_perturbers"]
+    assert got["n_connections"] == summ["n_connections"]
+    assert tuple(got["digest"]) == tuple(int(x) for x in summ["digest"])
+    err = abs(got["e_pt2"] - summ["e_pt2"])
+    print(f"mixed precision |E - E_oracle| = {err:.3e} Eh")
+    assert err <= MIXED_TOL
+    pt2.close()
