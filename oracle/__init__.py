@@ -96,6 +96,8 @@ def lib():
         L.or_alpha.argtypes = [P, I64, U64P, DP, U64P, DP, DP, I64P, I64P]
         L.or_hamiltonian.restype = I64
         L.or_hamiltonian.argtypes = [P, I64, U64P, I64, I64P, I64P, DP, I]
+        L.or_gradient.restype = I
+        L.or_gradient.argtypes = [P, I64, U64P, DP, D, DP, DP, DP, DP, I, I64]
         L.or_max_threads.restype = I
         _lib = L
     return _lib
@@ -213,6 +215,21 @@ class Hamiltonian:
                                   _ptr(haa), _ptr(g), _ptr(nc))
         return {"A": float(A[0]), "haa": float(haa[0]), "internal": bool(internal),
                 "gen_rank": int(g[0]), "n_connections": int(nc[0])}
+
+    def gradient(self, dets, coefs, e0, nthreads=0, mem_budget=0):
+        """dE_PT2/dh (symmetric, halves off the diagonal), dE_PT2/d(packed
+        eri), dE_PT2/dE0 and E_PT2, with Psi0 and E0 held fixed."""
+        dets = np.ascontiguousarray(dets, dtype=np.uint64)
+        coefs = np.ascontiguousarray(coefs, dtype=np.float64)
+        dh = np.zeros((self.norb, self.norb))
+        deri = np.zeros(len(self.eri))
+        de0 = np.zeros(1)
+        e = np.zeros(1)
+        rc = lib().or_gradient(self._p, len(dets), _ptr(dets), _ptr(coefs), float(e0), _ptr(dh), _ptr(deri),
+                               _ptr(de0), _ptr(e), int(nthreads), int(mem_budget))
+        if rc != 0:
+            raise ValueError(f"oracle gradient rejected its input (code {rc})")
+        return {"dh": dh, "deri": deri, "de0": float(de0[0]), "e_pt2": float(e[0])}
 
     def hamiltonian_coo(self, dets, nthreads=0):
         """Upper triangle (diagonal included) of H over ``dets``."""

@@ -910,3 +910,185 @@ int or_max_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of E_PT2 with respect to the integrals (Psi0 and E0 fixed).      */
+/*                                                                           */
+/* E_PT2 = sum_alpha A_alpha^2 / D_alpha, A_alpha = sum_J c_J <J|H|alpha>,   */
+/* D_alpha = E0 - <alpha|H|alpha> (Eqs. e2, PT2).  Every matrix element is   */
+/* linear in h and in the integrals (Eqs. Hij), so                           */
+/*   dE/dtheta = sum_alpha [ (2 A/D) sum_J c_J d<J|H|alpha>/dtheta           */
+/*                           + (A/D)^2 d<alpha|H|alpha>/dtheta ],            */
+/*   dE/dE0    = - sum_alpha A^2/D^2.                                        */
+/* Conventions: deri[i] is the derivative with respect to packed entry i;    */
+/* dh is symmetric with dh[p][q] = dh[q][p] = 1/2 dE/du_pq for p != q, where */
+/* u_pq moves h_pq and h_qp together, and dh[p][p] = dE/dh_pp.               */
+/* ------------------------------------------------------------------------ */
+
+/* add w * d<I|H|I>/dtheta */
+static void diag_grad(const or_ham *H, const uint64_t *d, double w, double *dh, double *deri)
+{
+    int norb = H->norb, nint = H->nint;
+    int occ[2 * OR_MAXORB], spin[2 * OR_MAXORB], n = 0;
+    for (int s = 0; s < 2; s++)
+        for (int p = 0; p < norb; p++)
+            if (getbit(d, nint, s, p)) { occ[n] = p; spin[n] = s; n++; }
+    for (int i = 0; i < n; i++) dh[occ[i] * norb + occ[i]] += w;
+    for (int i = 0; i < n; i++)
+        for (int j = i + 1; j < n; j++) {
+            deri[tri(tri(occ[i], occ[i]), tri(occ[j], occ[j]))] += w;
+            if (spin[i] == spin[j]) deri[tri(tri(occ[i], occ[j]), tri(occ[j], occ[i]))] -= w;
+        }
+}
+
+/* add w * d<I|H|J>/dtheta (same case analysis as or_hij) */
+static void hij_grad(const or_ham *H, const uint64_t *I, const uint64_t *Jd, double w, double *dh, double *deri)
+{
+    int norb = H->norb, nint = H->nint;
+    int deg = or_degree(nint, I, Jd);
+    if (deg == 0) { diag_grad(H, I, w, dh, deri); return; }
+    if (deg > 2) return;
+    int hs[2], ho[2], ps[2], po[2], nh = 0, np = 0;
+    for (int s = 0; s < 2; s++)
+        for (int p = 0; p < norb; p++) {
+            int a = getbit(I, nint, s, p), b = getbit(Jd, nint, s, p);
+            if (a && !b) { hs[nh] = s; ho[nh] = p; nh++; }
+            if (!a && b) { ps[np] = s; po[np] = p; np++; }
+        }
+    if (deg == 1) {
+        int s = hs[0], h = ho[0], p = po[0];
+        double ws = w * phase_single(I, nint, s, h, p);
+        dh[h * norb + p] += 0.5 * ws;
+        dh[p * norb + h] += 0.5 * ws;
+        for (int t = 0; t < 2; t++)
+            for (int i = 0; i < norb; i++) {
+                if (!getbit(I, nint, t, i)) continue;
+                deri[tri(tri(h, p), tri(i, i))] += ws;
+                if (t == s) deri[tri(tri(h, i), tri(i, p))] -= ws;
+            }
+        return;
+    }
+    uint64_t I1[2 * OR_MAXNINT];
+    memcpy(I1, I, sizeof(uint64_t) * 2 * nint);
+    double ph = phase_single(I, nint, hs[0], ho[0], po[0]);
+    clrbit(I1, nint, hs[0], ho[0]);
+    setbit(I1, nint, ps[0], po[0]);
+    ph *= phase_single(I1, nint, hs[1], ho[1], po[1]);
+    deri[tri(tri(ho[0], po[0]), tri(ho[1], po[1]))] += w * ph;
+    if (hs[0] == hs[1]) deri[tri(tri(ho[0], po[1]), tri(ho[1], po[0]))] -= w * ph;
+}
+
+/* Plain-definition gradient (pairs grouped by alpha, as in or_sweep).
+ * dh[norb*norb], deri[P], *de0 and *e_pt2 are overwritten. */
+int or_gradient(const or_ham *H, int64_t ndet, const uint64_t *dets, const double *coefs, double e0,
+                double *dh, double *deri, double *de0, double *e_pt2, int nthreads, int64_t mem_budget_bytes)
+{
+    int nint = H->nint, nw = 2 * nint, stride = nw + 1, norb = H->norb;
+    int rc = or_validate(H, ndet, dets);
+    if (rc) return rc;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#else
+    nthreads = 1;
+#endif
+    int64_t m = (int64_t)norb * (norb + 1) / 2, P = m * (m + 1) / 2;
+    uint64_t *srt = (uint64_t *)malloc(sizeof(uint64_t) * nw * (ndet > 0 ? ndet : 1));
+    memcpy(srt, dets, sizeof(uint64_t) * nw * ndet);
+    g_nw_sort = nw;
+    qsort(srt, ndet, sizeof(uint64_t) * nw, key_qcmp);
+    if (mem_budget_bytes <= 0) mem_budget_bytes = (int64_t)4 << 30;
+    double total = (double)ndet * (double)or_n_substitutions(H) * stride * 8.0;
+    int nparts = (int)ceil(total / (double)mem_budget_bytes);
+    if (nparts < 1) nparts = 1;
+    /* per sub-bucket gradient arrays, summed in sub-bucket order at the end */
+    double *gh = (double *)calloc((size_t)OR_NSUB * norb * norb, sizeof(double));
+    double *ge = (double *)calloc((size_t)OR_NSUB * P, sizeof(double));
+    nsum *ee = (nsum *)calloc(OR_NSUB, sizeof(nsum));
+    nsum *e0s = (nsum *)calloc(OR_NSUB, sizeof(nsum));
+    pair_ctx *ctx = (pair_ctx *)calloc(nthreads, sizeof(pair_ctx));
+    for (int t = 0; t < nthreads; t++) {
+        ctx[t].nw = nw; ctx[t].stride = stride; ctx[t].nparts = nparts;
+        ctx[t].cnt = (int64_t *)calloc(OR_NSUB, sizeof(int64_t));
+        ctx[t].cap = (int64_t *)calloc(OR_NSUB, sizeof(int64_t));
+        ctx[t].buf = (uint64_t **)calloc(OR_NSUB, sizeof(uint64_t *));
+    }
+    for (int part = 0; part < nparts; part++) {
+        for (int t = 0; t < nthreads; t++) {
+            ctx[t].part = part;
+            for (int s = 0; s < OR_NSUB; s++) ctx[t].cnt[s] = 0;
+        }
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+        for (int64_t j = 0; j < ndet; j++) {
+            int t = 0;
+#ifdef _OPENMP
+            t = omp_get_thread_num();
+#endif
+            ctx[t].jidx = j;
+            for_each_substitution(H, dets + j * nw, pair_emit, &ctx[t]);
+        }
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+        for (int s = 0; s < OR_NSUB; s++) {
+            int64_t n = 0;
+            for (int t = 0; t < nthreads; t++) n += ctx[t].cnt[s];
+            if (n == 0) continue;
+            uint64_t *rec = (uint64_t *)malloc(sizeof(uint64_t) * stride * n);
+            int64_t off = 0;
+            for (int t = 0; t < nthreads; t++) {
+                memcpy(rec + off * stride, ctx[t].buf[s], sizeof(uint64_t) * stride * ctx[t].cnt[s]);
+                off += ctx[t].cnt[s];
+            }
+            int nwl = nw;
+            qsort_r(rec, n, sizeof(uint64_t) * stride, rec_cmp, &nwl);
+            double *dhs = gh + (size_t)s * norb * norb;
+            double *des = ge + (size_t)s * P;
+            for (int64_t g0 = 0; g0 < n;) {
+                int64_t g1 = g0 + 1;
+                while (g1 < n && keycmp(rec + g1 * stride, rec + g0 * stride, nw) == 0) g1++;
+                const uint64_t *alpha = rec + g0 * stride;
+                if (!is_member(srt, ndet, nw, alpha)) {
+                    nsum A = {0.0, 0.0};
+                    for (int64_t r = g0; r < g1; r++) {
+                        int64_t j = (int64_t)rec[r * stride + nw];
+                        nsum_add(&A, coefs[j] * or_hij(H, dets + j * nw, alpha));
+                    }
+                    double Av = nsum_get(&A);
+                    double D = e0 - or_diag(H, alpha);
+                    double q = Av / D;
+                    nsum_add(&ee[s], Av * Av / D);
+                    nsum_add(&e0s[s], -q * q);
+                    for (int64_t r = g0; r < g1; r++) {
+                        int64_t j = (int64_t)rec[r * stride + nw];
+                        /* d<J|H|alpha> = d<alpha|H|J> for real symmetric integrals */
+                        hij_grad(H, dets + j * nw, alpha, 2.0 * q * coefs[j], dhs, des);
+                    }
+                    diag_grad(H, alpha, q * q, dhs, des);
+                }
+                g0 = g1;
+            }
+            free(rec);
+        }
+    }
+    nsum E = {0, 0}, E0 = {0, 0};
+    for (int s = 0; s < OR_NSUB; s++) {
+        nsum_add(&E, nsum_get(&ee[s]));
+        nsum_add(&E0, nsum_get(&e0s[s]));
+    }
+    *e_pt2 = nsum_get(&E);
+    *de0 = nsum_get(&E0);
+    for (int64_t i = 0; i < (int64_t)norb * norb; i++) {
+        double v = 0.0;
+        for (int s = 0; s < OR_NSUB; s++) v += gh[(size_t)s * norb * norb + i];
+        dh[i] = v;
+    }
+    for (int64_t i = 0; i < P; i++) {
+        double v = 0.0;
+        for (int s = 0; s < OR_NSUB; s++) v += ge[(size_t)s * P + i];
+        deri[i] = v;
+    }
+    for (int t = 0; t < nthreads; t++) {
+        for (int s = 0; s < OR_NSUB; s++) free(ctx[t].buf[s]);
+        free(ctx[t].buf); free(ctx[t].cnt); free(ctx[t].cap);
+    }
+    free(ctx); free(gh); free(ge); free(ee); free(e0s); free(srt);
+    return 0;
+}

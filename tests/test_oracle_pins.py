@@ -364,3 +364,62 @@ def test_packed_integral_symmetry(oracle_mod):
         v = ham.eri_value(p, q, r, s)
         for perm in [(q, p, r, s), (p, q, s, r), (q, p, s, r), (r, s, p, q), (s, r, p, q), (r, s, q, p), (s, r, q, p)]:
             assert ham.eri_value(*perm) == v
+
+
+# ---------------------------------------------------------------------------
+# P8: gradient of E_PT2 with respect to the integrals (Psi0 and E0 fixed)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def grad_case(oracle_mod):
+    norb, na, nb = 9, 3, 3
+    ham, h, eri = _ham(oracle_mod, norb, na, nb, rank=11, seed=91)
+    dets = S.random_excited_dets(norb, na, nb, 40, seed=92)
+    c = S.random_coefs(40, 93, decay=0.05)
+    e0 = min(ham.diag(d) for d in dets) - 1.0
+    g = ham.gradient(dets, c, e0)
+    return oracle_mod, ham, h, eri, dets, c, e0, g
+
+
+def _energy(oracle_mod, norb, na, nb, h, eri, dets, c, e0):
+    return oracle_mod.Hamiltonian(norb, na, nb, h, eri).sweep(dets, c, e0, k=0, per_generator=False)["e_pt2"]
+
+
+def test_gradient_energy_and_de0(grad_case):
+    oracle_mod, ham, h, eri, dets, c, e0, g = grad_case
+    s = ham.sweep(dets, c, e0, k=0)
+    assert g["e_pt2"] == pytest.approx(s["e_pt2"], abs=1e-12)
+    assert g["de0"] == pytest.approx(-s["sum_e_over_d"], rel=1e-12)
+
+
+def test_gradient_euler_identity(grad_case):
+    """E_PT2 is homogeneous of degree 1 in (h, eri, E0): the sum of
+    theta * dE/dtheta over all parameters equals E_PT2."""
+    oracle_mod, ham, h, eri, dets, c, e0, g = grad_case
+    lhs = np.sum(h * g["dh"]) + np.dot(eri, g["deri"]) + e0 * g["de0"]
+    assert lhs == pytest.approx(g["e_pt2"], abs=1e-10)
+
+
+def test_gradient_matches_central_differences(grad_case):
+    oracle_mod, ham, h, eri, dets, c, e0, g = grad_case
+    norb, na, nb = ham.norb, ham.nalpha, ham.nbeta
+    step = 1e-5
+    rng = np.random.default_rng(94)
+    for idx in rng.choice(len(eri), 25, replace=False):
+        ep, em = eri.copy(), eri.copy()
+        ep[idx] += step
+        em[idx] -= step
+        fd = (_energy(oracle_mod, norb, na, nb, h, ep, dets, c, e0) -
+              _energy(oracle_mod, norb, na, nb, h, em, dets, c, e0)) / (2 * step)
+        assert abs(fd - g["deri"][idx]) <= 1e-6 * abs(fd) + 1e-8, (idx, fd, g["deri"][idx])
+    for p, q in [(0, 0), (4, 4), (0, 3), (2, 7), (5, 8)]:
+        hp, hm = h.copy(), h.copy()
+        hp[p, q] += step
+        hm[p, q] -= step
+        if p != q:
+            hp[q, p] += step
+            hm[q, p] -= step
+        fd = (_energy(oracle_mod, norb, na, nb, hp, eri, dets, c, e0) -
+              _energy(oracle_mod, norb, na, nb, hm, eri, dets, c, e0)) / (2 * step)
+        an = g["dh"][p, p] if p == q else g["dh"][p, q] + g["dh"][q, p]
+        assert abs(fd - an) <= 1e-6 * abs(fd) + 1e-8, (p, q, fd, an)
+    assert np.allclose(g["dh"], g["dh"].T, atol=0, rtol=0)
