@@ -138,6 +138,23 @@ int qp_pt2_eval_ex(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, const do
                    double *eps_by_rank, int64_t *na_by_rank, int64_t *ncon_by_rank,
                    int32_t *rank_of, qp_pt2_result *res);
 
+/* Gradient of E_PT2 (adjoint of the sweep), with Psi0's coefficients and E0
+ * held fixed.  Every matrix element is linear in h and the integrals (Eqs.
+ * Hij), so with A_alpha = <Psi0|H|alpha> and D_alpha = E0 - <alpha|H|alpha>
+ * (Eqs. e2, PT2):
+ *   dE/dtheta = sum_alpha [ (2 A/D) sum_J c_J d<J|H|alpha>/dtheta
+ *                           + (A/D)^2 d<alpha|H|alpha>/dtheta ],
+ *   dE/dE0    = - sum_alpha A^2/D^2.
+ * The matrix elements are recomputed (nothing is kept from qp_pt2_eval).
+ * Outputs (host or device memory): dh[norb*norb], symmetric, with
+ * dh[p][q] = dh[q][p] = (1/2) dE/du_pq for p != q where u_pq moves h_pq and
+ * h_qp together, and dh[p][p] = dE/dh_pp; deri[P], the derivative with respect
+ * to each packed entry of eri; *de0.  *res (may be NULL) receives the sweep's
+ * totals (no selection).  FP64 contexts only (QP_ENOTSUP otherwise); with
+ * sharding the gradient is the shard's part and the shards' gradients add. */
+int qp_pt2_grad(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, const double *coefs, double e0,
+                double *dh, double *deri, double *de0, qp_pt2_result *res);
+
 /* Number of device kernel launches made by the last qp_pt2_eval* call of ctx
  * (the library's own kernels; the radix sorts' kernels are not counted). */
 int64_t qp_pt2_last_launches(const qp_pt2_ctx *ctx);

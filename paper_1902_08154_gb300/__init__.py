@@ -30,6 +30,7 @@ EXPORTS = (
     "qp_pt2_strerror",
     "qp_pt2_last_error",
     "qp_pt2_eval_noalloc",
+    "qp_pt2_grad",
 )
 
 
@@ -97,6 +98,8 @@ def load(path: str = SO):
     L.qp_pt2_strerror.argtypes = [C.c_int]
     L.qp_pt2_last_error.restype = C.c_char_p
     L.qp_pt2_last_error.argtypes = []
+    L.qp_pt2_grad.restype = C.c_int
+    L.qp_pt2_grad.argtypes = [vp, i64, vp, vp, dbl, vp, vp, vp, C.POINTER(Result)]
     L.qp_pt2_eval_noalloc.restype = C.c_int
     L.qp_pt2_eval_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, i64, vp, vp, dbl, i64, vp, vp,
                                       C.POINTER(Result), vp]
@@ -161,6 +164,16 @@ def qp_pt2_eval_noalloc(norb, n_alpha, n_beta, h, eri, ndet, dets, coefs, e0, k,
     rc = load().qp_pt2_eval_noalloc(norb, n_alpha, n_beta, _ptr(h), _ptr(eri), ndet, _ptr(dets), _ptr(coefs),
                                     float(e0), k, _ptr(sel_dets), _ptr(sel_e), C.byref(res), stream or None)
     return rc, res
+
+
+def qp_pt2_grad(ctx, ndet, dets, coefs, e0, dh, deri):
+    """Gradient of E_PT2 (see include/qp_pt2.h); fills dh and deri, returns
+    (dE/dE0, Result)."""
+    res = Result()
+    de0 = C.c_double()
+    _check(load().qp_pt2_grad(ctx, ndet, _ptr(dets), _ptr(coefs), float(e0), _ptr(dh), _ptr(deri),
+                              C.byref(de0), C.byref(res)))
+    return de0.value, res
 
 
 def qp_pt2_last_launches(ctx):
@@ -230,3 +243,37 @@ class PT2:
             out.update(eps_by_rank=eps[:ndet], na_by_rank=na[:ndet], ncon_by_rank=nc[:ndet], rank_of=rk[:ndet])
         out["launches"] = qp_pt2_last_launches(self.ctx)
         return out
+
+
+def pt2_energy(h, eri, dets, coefs, e0, n_alpha, n_beta, stream=None):
+    """E_PT2 as a differentiable function of the integrals (and of E0).
+
+    h: CUDA tensor [norb, norb] (symmetric), eri: CUDA tensor of packed
+    integrals, dets / coefs: CUDA tensors, e0: 0-d tensor or float.  The
+    backward pass calls qp_pt2_grad, which recomputes every matrix element
+    (Psi0's coefficients are held fixed).  The gradient returned for h is the
+    symmetric one described in include/qp_pt2.h."""
+    import torch
+
+    class _PT2Energy(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, h_, eri_, e0_):
+            norb = h_.shape[0]
+            pt2 = PT2(norb, n_alpha, n_beta, h_.detach().contiguous(), eri_.detach().contiguous(), stream=stream)
+            ctx.pt2 = pt2
+            ctx.e0 = float(e0_)
+            res = pt2.eval(dets, coefs, ctx.e0, 0)
+            return torch.tensor(res["e_pt2"], dtype=torch.float64, device=h_.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            pt2 = ctx.pt2
+            dh = torch.zeros((pt2.norb, pt2.norb), dtype=torch.float64, device=gout.device)
+            deri = torch.zeros_like(eri)
+            de0, _ = qp_pt2_grad(pt2.ctx, len(dets), dets, coefs, ctx.e0, dh, deri)
+            pt2.close()
+            return gout * dh, gout * deri, gout * de0
+
+    if not torch.is_tensor(e0):
+        e0 = torch.tensor(float(e0), dtype=torch.float64, device=h.device)
+    return _PT2Energy.apply(h, eri, e0)

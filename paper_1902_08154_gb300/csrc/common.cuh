@@ -116,6 +116,12 @@ struct SweepParams {
 
   int max_cells;
   int* err;                      // device error flags (0 = fine)
+
+  // gradient of E_PT2 (Psi0 and E0 fixed); used by the GRAD batch kernel
+  double* g_dh;                  // [norb*norb]  symmetric halves off the diagonal
+  double* g_deri;                // [P]          packed integrals
+  double* g_wF;                  // [ndet][2][norb]  weights of dF^I_s(x) per generator rank
+  double* g_wH;                  // [ndet]           weight of dH_II per generator rank
 };
 
 }  // namespace qp

@@ -19,6 +19,8 @@ cudaError_t launch_prep(int nint, const SweepParams& p, int slots, cudaStream_t 
 cudaError_t launch_batch(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
 int batch_blocks_per_sm(int nint, int mixed, size_t smem);
 int sweep_threads();
+cudaError_t launch_batch_grad(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_grad_gen(int nint, const SweepParams& p, int ngen, cudaStream_t st);
 }  // namespace qp
 
 using namespace qp;
@@ -255,6 +257,8 @@ struct qp_pt2_ctx {
   Buf tk_e, tk_a, tk_key, tk_cnt, tk_tau;
   Buf cand_e, cand_a, cand_key, skey, skey2, perm, perm2, cub_tmp2;
   Buf out_sel, out_e, out_num, out_eps, out_na, out_ncon, out_rank;
+  Buf g_dh, g_deri, g_wF, g_wH;
+  int grad_grid = 0;
   int64_t launches = 0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // call start, sweep start, sweep end
   cudaEvent_t ev_end = nullptr;
@@ -386,7 +390,7 @@ extern "C" void qp_pt2_destroy(qp_pt2_ctx* x) {
                 &x->res, &x->meta, &x->r_words, &x->r_coef, &x->r_hmask, &x->r_part, &x->r_flag,
                 &x->b_ofs, &x->b_ent, &x->b_dead, &x->queues, &x->tk_e, &x->tk_a, &x->tk_key, &x->tk_cnt, &x->tk_tau, &x->cand_e, &x->cand_a, &x->cand_key, &x->skey,
                 &x->skey2, &x->perm, &x->perm2, &x->cub_tmp2, &x->out_sel, &x->out_e, &x->out_num,
-                &x->out_eps, &x->out_na, &x->out_ncon, &x->out_rank};
+                &x->out_eps, &x->out_na, &x->out_ncon, &x->out_rank, &x->g_dh, &x->g_deri, &x->g_wF, &x->g_wH};
   for (Buf* b : all) b->release();
   delete x;
 }
@@ -708,4 +712,212 @@ extern "C" int qp_pt2_eval(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
                            int64_t k, uint64_t* sel_dets, double* sel_e, qp_pt2_result* res) {
   return qp_pt2_eval_ex(x, ndet, dets, coefs, e0, k, sel_dets, sel_e, nullptr, nullptr, nullptr, nullptr,
                         nullptr, res);
+}
+
+// ---------------------------------------------------------------------------
+// Gradient of E_PT2 with respect to h and the packed integrals (Psi0 and E0
+// held fixed): the sweep is repeated in gradient mode, which rebuilds every
+// accumulator A_alpha and scatters (2 A/D) c_J d<J|H|alpha> and
+// (A/D)^2 d<alpha|H|alpha>; dE/dE0 = -sum A^2/D^2.
+// ---------------------------------------------------------------------------
+extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const double* coefs, double e0,
+                           double* dh, double* deri, double* de0, qp_pt2_result* res) {
+  if (!x || !dh || !deri || !de0) return fail(QP_EINVAL, "ctx, dh, deri or de0 is NULL");
+  if (ndet < 0) return fail(QP_EINVAL, "ndet must be non-negative");
+  if (ndet > 0 && (!dets || !coefs)) return fail(QP_EINVAL, "dets or coefs is NULL");
+  if (ndet >= (1ll << 31)) return fail(QP_EINVAL, "ndet must be below 2^31");
+  if (!std::isfinite(e0)) return fail(QP_EINVAL, "E0 is not finite");
+  if (x->cfg.precision != QP_FP64) return fail(QP_ENOTSUP, "the gradient is computed in FP64 contexts only");
+  qp_pt2_result local;
+  if (!res) res = &local;
+  memset(res, 0, sizeof(*res));
+  res->min_abs_denominator = INFINITY;
+  x->launches = 0;
+  x->timed = false;
+  const int norb = x->norb, nint = x->nint, nw = 2 * nint;
+  const size_t nh = (size_t)norb * norb, P = (size_t)x->P;
+  cudaStream_t st = x->st;
+  int rc;
+  double* d_dh;
+  double* d_deri;
+  bool cb_dh, cb_eri;
+  if ((rc = x->g_dh.grow(8 * nh)) || (rc = x->g_deri.grow(8 * P))) return rc;
+  // gradients accumulate in library buffers, then go to the caller's
+  (void)cb_dh;
+  (void)cb_eri;
+  d_dh = x->g_dh.as<double>();
+  d_deri = x->g_deri.as<double>();
+  CUDA_TRY(cudaMemsetAsync(d_dh, 0, 8 * nh, st));
+  CUDA_TRY(cudaMemsetAsync(d_deri, 0, 8 * P, st));
+  if (ndet == 0) {
+    CUDA_TRY(cudaMemcpyAsync(dh, d_dh, 8 * nh, cudaMemcpyDefault, st));
+    CUDA_TRY(cudaMemcpyAsync(deri, d_deri, 8 * P, cudaMemcpyDefault, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    *de0 = 0.0;
+    return QP_OK;
+  }
+  CUDA_TRY(cudaEventRecord(x->ev[0], st));
+  const uint64_t* d_dets;
+  const double* d_coefs;
+  if ((rc = stage_in(x, x->in_dets, dets, (size_t)ndet * nw, &d_dets))) return rc;
+  if ((rc = stage_in(x, x->in_coefs, coefs, (size_t)ndet, &d_coefs))) return rc;
+  const size_t nd = (size_t)ndet;
+  if ((rc = x->hkey.grow(8 * nd)) || (rc = x->hkey2.grow(8 * nd)) || (rc = x->hidx.grow(4 * nd)) ||
+      (rc = x->hidx2.grow(4 * nd)) || (rc = x->rkey.grow(8 * nd)) || (rc = x->rkey2.grow(8 * nd)) ||
+      (rc = x->order.grow(4 * nd)) || (rc = x->rank_of.grow(4 * nd)) || (rc = x->acc.grow(8 * kAccWords)))
+    return rc;
+  unsigned long long* acc = x->acc.as<unsigned long long>();
+  {
+    unsigned long long init[kAccWords] = {0};
+    init[kAccMinDen] = 0x7FF0000000000000ull;
+    CUDA_TRY(cudaMemcpyAsync(acc, init, sizeof(init), cudaMemcpyHostToDevice, st));
+  }
+  int* d_err = reinterpret_cast<int*>(acc + kAccErr);
+  const int nb = (int)((ndet + 255) / 256);
+  validate_kernel<<<nb, 256, 0, st>>>(ndet, nint, norb, x->nalpha, x->nbeta, d_dets, d_coefs,
+                                      x->hkey.as<unsigned long long>(), x->hidx.as<int32_t>(),
+                                      x->rkey.as<unsigned long long>(), x->rank_of.as<int32_t>(), d_err);
+  x->launches++;
+  CUDA_TRY(cudaGetLastError());
+  size_t tmp1 = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, tmp1, x->hkey.as<unsigned long long>(),
+                                  x->hkey2.as<unsigned long long>(), x->hidx.as<int32_t>(),
+                                  x->hidx2.as<int32_t>(), (int)ndet, 0, 64, st);
+  if ((rc = x->cub_tmp.grow(tmp1))) return rc;
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(x->cub_tmp.p, tmp1, x->hkey.as<unsigned long long>(),
+                                           x->hkey2.as<unsigned long long>(), x->hidx.as<int32_t>(),
+                                           x->hidx2.as<int32_t>(), (int)ndet, 0, 64, st));
+  dup_kernel<<<nb, 256, 0, st>>>(ndet, nint, d_dets, x->hkey2.as<unsigned long long>(), x->hidx2.as<int32_t>(), d_err);
+  x->launches++;
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(x->cub_tmp.p, tmp1, x->rkey.as<unsigned long long>(),
+                                           x->rkey2.as<unsigned long long>(), x->rank_of.as<int32_t>(),
+                                           x->order.as<int32_t>(), (int)ndet, 0, 64, st));
+  rank_kernel<<<nb, 256, 0, st>>>(ndet, x->order.as<int32_t>(), x->rank_of.as<int32_t>());
+  x->launches++;
+  int herr = 0;
+  CUDA_TRY(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (herr & kErrOcc) return fail(QP_EINVAL, "a determinant has the wrong occupation or bits beyond norb");
+  if (herr & kErrCoef) return fail(QP_EINVAL, "a coefficient is not finite");
+  if (herr & kErrDup) return fail(QP_EDUP, "duplicate determinant in Psi0");
+
+  // waves (same layout as the sweep, no selection)
+  const int grid = x->grid;
+  const int shard_count = x->cfg.shard_count, shard_index = x->cfg.shard_index;
+  const int64_t ngen = (ndet > shard_index) ? (ndet - shard_index + shard_count - 1) / shard_count : 0;
+  const int64_t ent_per = x->nel >= 3 ? 3 * x->nel - 3 : 1;
+  const int64_t ent_cap = (int64_t)nd * ent_per;
+  const size_t dwords = (size_t)(x->nbat + 31) / 32;
+  const size_t per_slot = sizeof(GenMeta) + nd * (8 * nw + 8 + 8 + 8 + 4) + 4 * (size_t)(x->nbat + 2) +
+                          4 * (size_t)ent_cap + 4 * dwords;
+  int64_t W = (int64_t)(kWaveBudget / per_slot);
+  if (W < 1) W = 1;
+  if (W > ngen) W = ngen > 0 ? ngen : 1;
+  const int64_t nwaves = ngen > 0 ? (ngen + W - 1) / W : 0;
+  const size_t wsl = (size_t)W;
+  if ((rc = x->eps.grow(8 * nd)) || (rc = x->s2.grow(8 * nd)) || (rc = x->na.grow(8 * nd)) ||
+      (rc = x->ncon.grow(8 * nd)) || (rc = x->meta.grow(sizeof(GenMeta) * wsl)) ||
+      (rc = x->r_words.grow(8 * nd * nw * wsl)) || (rc = x->r_coef.grow(8 * nd * wsl)) ||
+      (rc = x->r_hmask.grow(8 * nd * wsl)) || (rc = x->r_part.grow(8 * nd * wsl)) ||
+      (rc = x->r_flag.grow(4 * nd * wsl)) || (rc = x->b_ofs.grow(4 * (size_t)(x->nbat + 2) * wsl)) ||
+      (rc = x->b_ent.grow(4 * (size_t)ent_cap * wsl)) || (rc = x->b_dead.grow(4 * dwords * wsl)) ||
+      (rc = x->queues.grow(4 * (size_t)(nwaves + 1))) || (rc = x->tk_cnt.grow(4 * (size_t)grid)) ||
+      (rc = x->tk_tau.grow(8 * (size_t)grid)) || (rc = x->res.grow(sizeof(DevResult))) ||
+      (rc = x->g_wF.grow(8 * nd * 2 * norb)) || (rc = x->g_wH.grow(8 * nd)))
+    return rc;
+  CUDA_TRY(cudaMemsetAsync(x->eps.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->s2.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->na.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->ncon.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->queues.p, 0, 4 * (size_t)(nwaves + 1), st));
+  CUDA_TRY(cudaMemsetAsync(x->tk_cnt.p, 0, 4 * (size_t)grid, st));
+  CUDA_TRY(cudaMemsetAsync(x->tk_tau.p, 0, 8 * (size_t)grid, st));
+  CUDA_TRY(cudaMemsetAsync(x->g_wF.p, 0, 8 * nd * 2 * norb, st));
+  CUDA_TRY(cudaMemsetAsync(x->g_wH.p, 0, 8 * nd, st));
+  SweepParams p{};
+  p.norb = norb;
+  p.nalpha = x->nalpha;
+  p.nbeta = x->nbeta;
+  p.nel = x->nel;
+  p.nbat = x->nbat;
+  p.ndet = ndet;
+  p.dets = d_dets;
+  p.coefs = d_coefs;
+  p.order = x->order.as<int32_t>();
+  p.rank_of = x->rank_of.as<int32_t>();
+  p.h = x->d_h;
+  p.eri = x->d_eri;
+  p.Jm = x->d_J;
+  p.Km = x->d_K;
+  p.e0 = e0;
+  p.shard_index = shard_index;
+  p.shard_count = shard_count;
+  p.meta = x->meta.as<GenMeta>();
+  p.r_words = x->r_words.as<uint64_t>();
+  p.r_coef = x->r_coef.as<double>();
+  p.r_hmask = x->r_hmask.as<uint64_t>();
+  p.r_part = x->r_part.as<uint64_t>();
+  p.r_flag = x->r_flag.as<uint32_t>();
+  p.b_ofs = x->b_ofs.as<int>();
+  p.b_ent = x->b_ent.as<int32_t>();
+  p.b_dead = x->b_dead.as<uint32_t>();
+  p.ent_cap = ent_cap;
+  p.eps = x->eps.as<double>();
+  p.s2 = x->s2.as<double>();
+  p.na = x->na.as<unsigned long long>();
+  p.ncon = x->ncon.as<unsigned long long>();
+  p.digest = acc + kAccDigest0;
+  p.min_den_bits = acc + kAccMinDen;
+  p.n_tiny = acc + kAccTiny;
+  p.k = 0;
+  p.cap = 1;
+  p.tk_cnt = x->tk_cnt.as<int>();
+  p.tk_tau = x->tk_tau.as<unsigned long long>();
+  p.tau_bits = acc + kAccTau;
+  p.max_cells = x->max_cells;
+  p.err = d_err;
+  p.g_dh = d_dh;
+  p.g_deri = d_deri;
+  p.g_wF = x->g_wF.as<double>();
+  p.g_wH = x->g_wH.as<double>();
+  CUDA_TRY(cudaEventRecord(x->ev[1], st));
+  for (int64_t w = 0; w < nwaves; w++) {
+    p.wave_start = (int)(w * W);
+    p.wave_slots = (int)((ngen - w * W) < W ? (ngen - w * W) : W);
+    p.last_wave = (w == nwaves - 1);
+    p.queue = x->queues.as<int>() + w;
+    CUDA_TRY(launch_prep(nint, p, p.wave_slots, st));
+    CUDA_TRY(launch_batch_grad(nint, p, grid, x->smem, st));
+    x->launches += 2;
+  }
+  CUDA_TRY(launch_grad_gen(nint, p, (int)ndet, st));
+  x->launches++;
+  CUDA_TRY(cudaEventRecord(x->ev[2], st));
+  DevResult* dres = x->res.as<DevResult>();
+  finalize_kernel<<<1, 1024, 0, st>>>(ndet, p.eps, p.s2, reinterpret_cast<const long long*>(p.na),
+                                      reinterpret_cast<const long long*>(p.ncon), dres);
+  x->launches++;
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(dh, d_dh, 8 * nh, cudaMemcpyDefault, st));
+  CUDA_TRY(cudaMemcpyAsync(deri, d_deri, 8 * P, cudaMemcpyDefault, st));
+  DevResult hres;
+  unsigned long long hacc[kAccWords];
+  CUDA_TRY(cudaMemcpyAsync(&hres, dres, sizeof(hres), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaEventRecord(x->ev_end, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  x->timed = true;
+  res->e_pt2 = hres.e_pt2;
+  res->sum_e_over_d = hres.s2;
+  res->n_perturbers = hres.na;
+  res->n_connections = hres.ncon;
+  res->n_tiny = (int64_t)hacc[kAccTiny];
+  res->perturber_digest[0] = hacc[kAccDigest0];
+  res->perturber_digest[1] = hacc[kAccDigest1];
+  double md;
+  memcpy(&md, &hacc[kAccMinDen], sizeof(md));
+  res->min_abs_denominator = md;
+  *de0 = -hres.s2;
+  if (hres.na > 0 && md < 1e-12) return fail(QP_ESINGULAR, "a denominator E0 - H_aa is below 1e-12");
+  return QP_OK;
 }

@@ -9,6 +9,16 @@ template __global__ void prep_kernel<1>(SweepParams);
 template __global__ void prep_kernel<2>(SweepParams);
 template __global__ void batch_kernel<1, double>(SweepParams);
 template __global__ void batch_kernel<2, double>(SweepParams);
+template __global__ void grad_gen_kernel<1>(SweepParams);
+template __global__ void grad_gen_kernel<2>(SweepParams);
+
+cudaError_t launch_batch_grad(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
+
+cudaError_t launch_grad_gen(int nint, const SweepParams& p, int ngen, cudaStream_t st) {
+  if (nint == 1) grad_gen_kernel<1><<<ngen, kThreads, 0, st>>>(p);
+  else grad_gen_kernel<2><<<ngen, kThreads, 0, st>>>(p);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_batch_mixed(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
 int batch_blocks_per_sm_mixed(int nint, size_t smem);

@@ -372,6 +372,9 @@ struct BatchShared {
   // reductions
   double red_d[kWarps][2];
   unsigned long long red_u[kWarps][6];
+  // gradient: sums of (A/D)^2 over the cells of each particle orbital
+  double rowW2[kMaxOrb], colW2[kMaxOrb];
+  double sw2;
 };
 
 struct Batch {
@@ -575,6 +578,71 @@ __device__ __noinline__ NT element(const SweepParams& p, const uint64_t* Jw, con
   return flip_sign(v, (n1 + n2) & 1);
 }
 
+// Gradient of one matrix element: adds w * d<J|H|alpha>/d(theta) into dh
+// (symmetric halves) and the packed integrals, with the same case analysis
+// as element().
+template <int NINT>
+__device__ __noinline__ void element_grad(const SweepParams& p, const uint64_t* Jw, const int* X, int nx,
+                                          const int* T, int nt, int r, int s, double w) {
+  const int norb = p.norb;
+  int ho[2], pa[2], nh = 0, npp = 0;
+  bool r_in = false, s_in = false;
+  for (int i = 0; i < nx; i++) {
+    const int x = X[i];
+    r_in |= (x == r);
+    s_in |= (x == s);
+    if (x != r && x != s && nh < 2) ho[nh++] = x;
+  }
+  for (int i = 0; i < nt && npp < 2; i++) pa[npp++] = T[i];
+  if (!r_in && npp < 2) pa[npp++] = r;
+  if (s >= 0 && !s_in && npp < 2) pa[npp++] = s;
+  if (nh == 0 || nh != npp) return;
+  if (nh == 1) {
+    const int sp = ho[0] >= norb, a = ho[0] - sp * norb, b = pa[0] - sp * norb;
+    const uint64_t* sw = Jw + sp * NINT;
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    const double ws = (count_between<NINT>(sw, lo, hi) & 1) ? -w : w;
+    atomicAdd(&p.g_dh[a * norb + b], 0.5 * ws);
+    atomicAdd(&p.g_dh[b * norb + a], 0.5 * ws);
+#pragma unroll
+    for (int t = 0; t < 2; t++) {
+#pragma unroll
+      for (int wd = 0; wd < NINT; wd++) {
+        uint64_t bits = Jw[t * NINT + wd];
+        while (bits) {
+          const int q = 64 * wd + __ffsll((long long)bits) - 1;
+          bits &= bits - 1;
+          atomicAdd(&p.g_deri[eri_index(a, b, q, q)], ws);
+          if (t == sp) atomicAdd(&p.g_deri[eri_index(a, q, q, b)], -ws);
+        }
+      }
+    }
+    return;
+  }
+  if (ho[0] > ho[1]) { const int t = ho[0]; ho[0] = ho[1]; ho[1] = t; }
+  if (pa[0] > pa[1]) { const int t = pa[0]; pa[0] = pa[1]; pa[1] = t; }
+  const int s1 = ho[0] >= norb, s2 = ho[1] >= norb;
+  const int h1 = ho[0] - s1 * norb, p1 = pa[0] - s1 * norb;
+  const int h2 = ho[1] - s2 * norb, p2 = pa[1] - s2 * norb;
+  uint64_t w1[NINT];
+#pragma unroll
+  for (int wd = 0; wd < NINT; wd++) w1[wd] = Jw[s1 * NINT + wd];
+  const int n1 = count_between<NINT>(w1, h1 < p1 ? h1 : p1, h1 < p1 ? p1 : h1);
+  w1[h1 >> 6] &= ~(1ull << (h1 & 63));
+  w1[p1 >> 6] |= (1ull << (p1 & 63));
+  const int n2 = (s2 == s1) ? count_between<NINT>(w1, h2 < p2 ? h2 : p2, h2 < p2 ? p2 : h2)
+                            : count_between<NINT>(Jw + s2 * NINT, h2 < p2 ? h2 : p2, h2 < p2 ? p2 : h2);
+  const double ws = ((n1 + n2) & 1) ? -w : w;
+  atomicAdd(&p.g_deri[eri_index(h1, p1, h2, p2)], ws);
+  if (s1 == s2) atomicAdd(&p.g_deri[eri_index(h1, p2, h2, p1)], -ws);
+}
+
+// w * dW(x, y)/d(theta), W(x, y) = (xx|yy) - delta_spin (xy|yx)
+__device__ __forceinline__ void w_grad(const SweepParams& p, int x, int sx, int y, int sy, double w) {
+  atomicAdd(&p.g_deri[eri_index(x, x, y, y)], w);
+  if (sx == sy) atomicAdd(&p.g_deri[eri_index(x, y, y, x)], -w);
+}
+
 // ---------------------------------------------------------------------------
 // Selection buffer compaction: keep the k best entries (|e| descending, key
 // ascending) of the CTA's buffer.  MSD radix select over the composite
@@ -690,7 +758,7 @@ __device__ __noinline__ void compact_selection(const SweepParams& p, BatchShared
   __syncthreads();
 }
 
-template <int NINT, typename NT>
+template <int NINT, typename NT, bool GRAD = false>
 __global__ void __launch_bounds__(kThreads, 3) batch_kernel(SweepParams p) {
   constexpr int NW = 2 * NINT;
   extern __shared__ __align__(16) unsigned char dyn[];
@@ -816,6 +884,11 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(SweepParams p) {
     }
     // zero the accumulator, the bans; row sums for H_aa
     for (int c = tid; c < B.ncell; c += kThreads) A[c] = 0.0;
+    if (GRAD)
+      for (int x = tid; x < kMaxOrb; x += kThreads) {
+        S.rowW2[x] = 0.0;
+        S.colW2[x] = 0.0;
+      }
     for (int c = tid; c < (B.ncell + 31) / 32; c += kThreads) ban[c] = 0u;
     {
       auto W = [&](int x, int sx, int y, int sy) {
@@ -1075,6 +1148,15 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(SweepParams p) {
       acc_e += e;
       acc_s2 += q * q;
       acc_na++;
+      if (GRAD) {
+        // numerator weight 2A/D for loop 3; (A/D)^2 weights the diagonal
+        A[c] = 2.0 * q;
+        const double w2 = q * q;
+        atomicAdd(&S.rowW2[x], w2);
+        if (B.kind == 2) atomicAdd(&S.colW2[y], w2);
+        if (B.kind == 1) atomicAdd(&S.rowW2[y], w2);
+        if (B.h == 2) w_grad(p, ro, B.sa, so, B.sb, w2);
+      }
       // |a| < 1e-14, compared on the bit pattern (no FP64 compare)
       if (((unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull) < 0x3D06849B86A12B9Bull) acc_tiny++;
       const unsigned long long db = (unsigned long long)__double_as_longlong(fabs(D));
@@ -1129,6 +1211,7 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(SweepParams p) {
           m = S.red_u[w][4] < m ? S.red_u[w][4] : m;
           tt += S.red_u[w][5];
         }
+        S.sw2 = ts;
         if (tn) {
           atomicAdd(&p.eps[g], te_);
           atomicAdd(&p.s2[g], ts);
@@ -1141,12 +1224,156 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(SweepParams p) {
         }
       }
     }
+    if (GRAD) {
+      __syncthreads();
+      // ---- loop 3: c_J (2A/D) d<J|H|alpha> over the same (J, cell) pairs ----
+      for (int c0 = 0; c0 < total; c0 += kChunk) {
+        if (tid == 0) {
+          S.n0 = 0;
+          S.n1 = 0;
+          S.n2 = 0;
+        }
+        __syncthreads();
+        const int c1 = min(c0 + kChunk, total);
+        for (int i = c0 + tid; i < c1; i += kThreads) {
+          const int r = entry(i);
+          if (rf[r] & 1u) continue;
+          const int t = __popcll(rh[r] & ~B.hm);
+          if (t > 2) continue;
+          const bool all = (B.h == 1) ? (t <= 1) : (t == 0);
+          if (all) S.L0[atomicAdd(&S.n0, 1)] = r;
+          else if (t == 1) S.L1[atomicAdd(&S.n1, 1)] = r;
+          else S.L2[atomicAdd(&S.n2, 1)] = r;
+        }
+        __syncthreads();
+        for (int j = 0; j < S.n0; j++) {
+          const int r = S.L0[j];
+          uint64_t Jw[NW];
+#pragma unroll
+          for (int w = 0; w < NW; w++) Jw[w] = rw[(size_t)r * NW + w];
+          const double cj = rc[r];
+          int X[4], T[2], nx, nt;
+          excitation_sets<NINT, NT>(B, S, rp[r], rh[r], X, &nx, T, &nt);
+          for (int c = tid; c < B.ncell; c += kThreads) {
+            if ((ban[c >> 5] >> (c & 31)) & 1u) continue;
+            int ro, so, x, y;
+            cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
+            element_grad<NINT>(p, Jw, X, nx, T, nt, B.sa * norb + ro, (B.h == 2) ? B.sb * norb + so : -1, cj * A[c]);
+          }
+        }
+        for (int j = warp; j < S.n1; j += kWarps) {
+          const int r = S.L1[j];
+          uint64_t Jw[NW];
+#pragma unroll
+          for (int w = 0; w < NW; w++) Jw[w] = rw[(size_t)r * NW + w];
+          const double cj = rc[r];
+          const uint64_t part = rp[r];
+          int X[4], T[2], nx, nt;
+          excitation_sets<NINT, NT>(B, S, part, rh[r], X, &nx, T, &nt);
+          for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
+            if ((ban[c >> 5] >> (c & 31)) & 1u) return;
+            int ro, so, x, y;
+            cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
+            element_grad<NINT>(p, Jw, X, nx, T, nt, B.sa * norb + ro, B.sb * norb + so, cj * A[c]);
+          });
+        }
+        for (int j = tid; j < S.n2; j += kThreads) {
+          const int r = S.L2[j];
+          uint64_t Jw[NW];
+#pragma unroll
+          for (int w = 0; w < NW; w++) Jw[w] = rw[(size_t)r * NW + w];
+          const double cj = rc[r];
+          const uint64_t part = rp[r];
+          int X[4], T[2], nx, nt;
+          excitation_sets<NINT, NT>(B, S, part, rh[r], X, &nx, T, &nt);
+          for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
+            if ((ban[c >> 5] >> (c & 31)) & 1u) return;
+            int ro, so, x, y;
+            cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
+            element_grad<NINT>(p, Jw, X, nx, T, nt, B.sa * norb + ro, (B.h == 2) ? B.sb * norb + so : -1,
+                               cj * A[c]);
+          });
+        }
+        __syncthreads();
+      }
+      // ---- diagonal: H_aa = H_II - F(a) [- F(b) + W(a,b)] + F(r) [+ F(s)]
+      //      - W(r,a) [- W(r,b) - W(s,a) - W(s,b) + W(r,s)]; the W(r,s) terms
+      //      were scattered per cell, the rest goes by row sums ----
+      double* wF = p.g_wF + (size_t)g * 2 * norb;
+      const int s1 = B.sa, s2 = (B.h == 2) ? B.sb : B.sa;
+      for (int x = tid; x < S.nv[s1]; x += kThreads) {
+        const double wr = S.rowW2[x];
+        if (wr == 0.0) continue;
+        const int r = S.vir[s1][x];
+        atomicAdd(&wF[s1 * norb + r], wr);
+        w_grad(p, r, s1, B.qa, B.sa, -wr);
+        if (B.h == 2) w_grad(p, r, s1, B.qb, B.sb, -wr);
+      }
+      if (B.kind == 2)
+        for (int y = tid; y < S.nv[s2]; y += kThreads) {
+          const double wc = S.colW2[y];
+          if (wc == 0.0) continue;
+          const int sv = S.vir[s2][y];
+          atomicAdd(&wF[s2 * norb + sv], wc);
+          w_grad(p, sv, s2, B.qa, B.sa, -wc);
+          w_grad(p, sv, s2, B.qb, B.sb, -wc);
+        }
+      if (tid == 0 && S.sw2 != 0.0) {
+        const double sw = S.sw2;
+        atomicAdd(&p.g_wH[g], sw);
+        atomicAdd(&wF[B.sa * norb + B.qa], -sw);
+        if (B.h == 2) {
+          atomicAdd(&wF[B.sb * norb + B.qb], -sw);
+          w_grad(p, B.qa, B.sa, B.qb, B.sb, sw);
+        }
+      }
+    }
   }
   if (p.k > 0 && p.last_wave) compact_selection<NINT, NT>(p, S, te, ta, tk);
   __syncthreads();
   if (tid == 0) {
     p.tk_cnt[blockIdx.x] = S.tkcnt;
     p.tk_tau[blockIdx.x] = S.tau;
+  }
+}
+
+// Per generator: wH * dH_II + sum_{s,x} wF[s][x] * dF^I_s(x), with
+// F^I_s(x) = h_xx + sum_{j in I} W(x, j) and H_II = sum_i h_ii + sum_{i<j} W(i, j).
+template <int NINT>
+__global__ void __launch_bounds__(kThreads) grad_gen_kernel(SweepParams p) {
+  constexpr int NW = 2 * NINT;
+  __shared__ int s_occ[kMaxElec];
+  const int g = blockIdx.x, tid = threadIdx.x, norb = p.norb, nel = p.nel;
+  const double wH = p.g_wH[g];
+  const double* wF = p.g_wF + (size_t)g * 2 * norb;
+  const uint64_t* I = p.dets + (size_t)p.order[g] * NW;
+  if (tid == 0) {
+    int n = 0;
+    for (int s = 0; s < 2; s++)
+      for (int q = 0; q < norb; q++)
+        if ((I[s * NINT + (q >> 6)] >> (q & 63)) & 1ull) s_occ[n++] = s * norb + q;
+  }
+  __syncthreads();
+  if (wH != 0.0)
+    for (int ij = tid; ij < nel * nel; ij += kThreads) {
+      const int i = ij / nel, j = ij - i * nel;
+      const int ci = s_occ[i], si = ci >= norb, qi = ci - si * norb;
+      if (i == j) atomicAdd(&p.g_dh[qi * norb + qi], wH);
+      else if (i < j) {
+        const int cj = s_occ[j], sj = cj >= norb, qj = cj - sj * norb;
+        w_grad(p, qi, si, qj, sj, wH);
+      }
+    }
+  for (int x = tid; x < 2 * norb; x += kThreads) {
+    const double w = wF[x];
+    if (w == 0.0) continue;
+    const int s = x / norb, q = x - s * norb;
+    atomicAdd(&p.g_dh[q * norb + q], w);
+    for (int i = 0; i < nel; i++) {
+      const int c = s_occ[i], sj = c >= norb, j = c - sj * norb;
+      atomicAdd(&p.g_deri[eri_index(q, q, j, j)], w);
+      if (sj == s) atomicAdd(&p.g_deri[eri_index(q, j, j, q)], -w);
+    }
   }
 }
 

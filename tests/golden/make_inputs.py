@@ -11,6 +11,10 @@ not available; shapes follow the paper's CAS-sized active spaces):
   cfg1: norb 16, 4+4 electrons, Cholesky rank 32, seed 0.  Psi0 = HF + the 49
         lowest-diagonal single/double substitutions of HF; c and E0 from dense
         diagonalisation of the 50x50 block.  Expected results with k = 100.
+  cfg4: norb 48, 8+8 electrons, Cholesky rank 72, seed 3.  Psi0 of 2*10^4
+        determinants grown from 2500 by three CIPSI doublings; expected sweep
+        results with k = 2*10^4 and the oracle's full gradient
+        (dE/dh, dE/d(packed eri), dE/dE0) in ``cfg4_gradient.npz``.
   cfg2: norb 64, 10+10 electrons, Cholesky rank 96, seed 1.  Psi0 of 10^4
         determinants grown from a 1250-determinant seed space by three CIPSI
         doublings (top |e_alpha| selection), coefficients from Davidson to a
@@ -39,6 +43,7 @@ from paper_1902_08154_gb300 import synthetic as S  # noqa: E402
 CONFIGS = {
     "cfg1": dict(norb=16, nalpha=4, nbeta=4, rank=32, seed=0, ndet=50, k=100, grow=False),
     "cfg2": dict(norb=64, nalpha=10, nbeta=10, rank=96, seed=1, ndet=10000, k=20000, grow=True),
+    "cfg4": dict(norb=48, nalpha=8, nbeta=8, rank=72, seed=3, ndet=20000, k=40000, grow=True, gradient=True),
 }
 
 
@@ -72,6 +77,12 @@ def make(name, mem_budget=12 << 30):
                         sel_e=out["sel_e"], sel_num=out["sel_num"], eps_by_rank=out["eps_by_rank"],
                         na_by_rank=out["na_by_rank"], ncon_by_rank=out["ncon_by_rank"],
                         rank_of=out["rank_of"], summary=json.dumps(summary))
+    if cfg.get("gradient"):
+        t2 = time.time()
+        g = ham.gradient(dets, c, e0, mem_budget=mem_budget)
+        log(f"{name}: gradient in {time.time() - t2:.1f}s (E_PT2 {g['e_pt2']:.12f})")
+        np.savez_compressed(os.path.join(HERE, f"{name}_gradient.npz"), dh=g["dh"], deri=g["deri"],
+                            de0=np.float64(g["de0"]), e_pt2=np.float64(g["e_pt2"]))
 
 
 if __name__ == "__main__":
