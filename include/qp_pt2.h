@@ -155,6 +155,32 @@ int qp_pt2_eval_ex(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, const do
 int qp_pt2_grad(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, const double *coefs, double e0,
                 double *dh, double *deri, double *de0, qp_pt2_result *res);
 
+/* Batched sweeps (many independent Psi0 instances, each with its own context,
+ * Hamiltonian and size).  qp_pt2_batch_create plans every instance (device
+ * workspaces are allocated here, once), then captures all of their sweeps on
+ * up to max_streams concurrent streams (0: 16) into one CUDA graph: no host
+ * synchronisation happens inside an instance's sweep, input checks run on the
+ * device.  qp_pt2_batch_run launches the graph on `stream` (NULL: a stream of
+ * the batch's own), waits, and fills res[n] (one result per instance; its
+ * return value is the first instance error, QP_OK if none) and, if ms is not
+ * NULL, the graph's device time in milliseconds.  The graph may be run any
+ * number of times; it reads the inputs and writes the outputs at the
+ * addresses given here, so new inputs of the same sizes can be written in
+ * place between runs.
+ *   ctxs[n]      distinct FP64 or mixed contexts (no sharding); a context must
+ *                not be used by other calls while the batch exists
+ *   ndet[n], dets[n], coefs[n], e0[n], k[n]: as in qp_pt2_eval, device memory
+ *   sel_dets[n], sel_e[n]: device outputs (may be NULL where k[i] = 0)
+ *   grid[n]      persistent CTAs of each instance's sweep (NULL or 0: the
+ *                context's default); chosen by the package's autotuner */
+typedef struct qp_pt2_batch qp_pt2_batch;
+int qp_pt2_batch_create(qp_pt2_batch **out, int n, qp_pt2_ctx *const *ctxs, const int64_t *ndet,
+                        const uint64_t *const *dets, const double *const *coefs, const double *e0,
+                        const int64_t *k, uint64_t *const *sel_dets, double *const *sel_e, const int *grid,
+                        int max_streams, void *stream);
+int qp_pt2_batch_run(qp_pt2_batch *batch, qp_pt2_result *res, double *ms);
+void qp_pt2_batch_destroy(qp_pt2_batch *batch);
+
 /* Number of device kernel launches made by the last qp_pt2_eval* call of ctx
  * (the library's own kernels; the radix sorts' kernels are not counted). */
 int64_t qp_pt2_last_launches(const qp_pt2_ctx *ctx);

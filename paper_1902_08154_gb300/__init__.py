@@ -31,6 +31,9 @@ EXPORTS = (
     "qp_pt2_last_error",
     "qp_pt2_eval_noalloc",
     "qp_pt2_grad",
+    "qp_pt2_batch_create",
+    "qp_pt2_batch_run",
+    "qp_pt2_batch_destroy",
 )
 
 
@@ -277,3 +280,68 @@ def pt2_energy(h, eri, dets, coefs, e0, n_alpha, n_beta, stream=None):
     if not torch.is_tensor(e0):
         e0 = torch.tensor(float(e0), dtype=torch.float64, device=h.device)
     return _PT2Energy.apply(h, eri, e0)
+
+
+class Batch:
+    """Many independent sweeps captured into one CUDA graph (see
+    qp_pt2_batch_create in include/qp_pt2.h).
+
+    instances: list of dicts with keys pt2 (a PT2 context), dets, coefs (CUDA
+    tensors), e0 (float), k (int).  Output tensors are allocated here."""
+
+    def __init__(self, instances, grid=None, max_streams=0, stream=None):
+        import torch
+
+        L = load()
+        n = len(instances)
+        self.instances = instances
+        self.sel, self.sel_e = [], []
+        for inst in instances:
+            k = inst["k"]
+            dev = inst["dets"].device
+            self.sel.append(torch.zeros((max(k, 1), 2, inst["pt2"].nint), dtype=torch.int64, device=dev))
+            self.sel_e.append(torch.zeros(max(k, 1), dtype=torch.float64, device=dev))
+        VP = C.c_void_p * n
+        ctxs = VP(*[inst["pt2"].ctx.value for inst in instances])
+        ndet = (C.c_int64 * n)(*[len(inst["dets"]) for inst in instances])
+        dets = VP(*[inst["dets"].data_ptr() for inst in instances])
+        coefs = VP(*[inst["coefs"].data_ptr() for inst in instances])
+        e0 = (C.c_double * n)(*[float(inst["e0"]) for inst in instances])
+        ks = (C.c_int64 * n)(*[inst["k"] for inst in instances])
+        sel = VP(*[t.data_ptr() for t in self.sel])
+        se = VP(*[t.data_ptr() for t in self.sel_e])
+        g = (C.c_int * n)(*(grid or [0] * n))
+        self._keep = (ctxs, ndet, dets, coefs, e0, ks, sel, se, g)
+        L.qp_pt2_batch_create.restype = C.c_int
+        L.qp_pt2_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_int, C.c_void_p]
+        L.qp_pt2_batch_run.restype = C.c_int
+        L.qp_pt2_batch_run.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]
+        L.qp_pt2_batch_destroy.restype = None
+        L.qp_pt2_batch_destroy.argtypes = [C.c_void_p]
+        self.handle = C.c_void_p()
+        _check(L.qp_pt2_batch_create(C.byref(self.handle), n, ctxs, ndet, dets, coefs, e0, ks, sel, se, g,
+                                     max_streams, stream or None))
+
+    def run(self):
+        """Run the graph once: (list of result dicts, device ms)."""
+        n = len(self.instances)
+        res = (Result * n)()
+        ms = C.c_double()
+        _check(load().qp_pt2_batch_run(self.handle, res, C.byref(ms)))
+        out = []
+        for i in range(n):
+            d = res[i].as_dict()
+            m = d["n_selected"]
+            d.update(sel_dets=self.sel[i][:m], sel_e=self.sel_e[i][:m])
+            out.append(d)
+        return out, ms.value
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.qp_pt2_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()

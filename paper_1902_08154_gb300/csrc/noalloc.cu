@@ -44,7 +44,7 @@ __global__ void finalize_kernel(int64_t ndet, const double* eps, const double* s
                                 const long long* nc, DevResult* out);
 __global__ void gather_kernel(int grid, int nint, int64_t cap, const int* tk_cnt, const double* tk_e,
                               const double* tk_a, const uint64_t* tk_key, const unsigned long long* tau,
-                              double* ce, double* ca, uint64_t* ck, int* ncand);
+                              double* ce, double* ca, uint64_t* ck, int* ncand, int64_t cand_cap, int* err);
 __global__ void sortkey_kernel(int n, int nint, int w, const double* ce, const uint64_t* ck,
                                const int32_t* perm, unsigned long long* keys);
 __global__ void iota_kernel(int n, int32_t* v);
@@ -333,7 +333,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   int64_t nsel = 0;
   if (k > 0) {
     gather_kernel<<<grid, 256, 0, st>>>(grid, nint, cap, tk_cnt, tk_e, tk_a, tk_key, p.tau_bits, cand_e, cand_a,
-                                        cand_key, d_ncand);
+                                        cand_key, d_ncand, (int64_t)maxc, d_err);
     int ncand = 0;
     NTRY(cudaMemcpyAsync(&ncand, d_ncand, sizeof(int), cudaMemcpyDeviceToHost, st));
     NTRY(cudaStreamSynchronize(st));

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_segmented_radix_sort.cuh>
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -169,7 +171,7 @@ __global__ void finalize_kernel(int64_t ndet, const double* eps, const double* s
 // threshold (they cannot be among the k best).
 __global__ void gather_kernel(int grid, int nint, int64_t cap, const int* tk_cnt, const double* tk_e,
                               const double* tk_a, const uint64_t* tk_key, const unsigned long long* tau,
-                              double* ce, double* ca, uint64_t* ck, int* ncand) {
+                              double* ce, double* ca, uint64_t* ck, int* ncand, int64_t cand_cap, int* err) {
   const int b = blockIdx.x;
   const int nw = 2 * nint;
   const int n = tk_cnt[b];
@@ -179,6 +181,11 @@ __global__ void gather_kernel(int grid, int nint, int64_t cap, const int* tk_cnt
     const double e = tk_e[src];
     if ((unsigned long long)__double_as_longlong(fabs(e)) < t) continue;
     const int o = atomicAdd(ncand, 1);
+    if (o >= cand_cap) {  // more candidates than the space planned for them
+      atomicOr(err, 32);
+      atomicSub(ncand, 1);
+      continue;
+    }
     ce[o] = e;
     ca[o] = tk_a[src];
     for (int w = 0; w < nw; w++) ck[(size_t)o * nw + w] = tk_key[src * nw + w];
@@ -629,7 +636,7 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
     int* d_ncand = reinterpret_cast<int*>(acc + kAccNcand);
     gather_kernel<<<grid, 256, 0, st>>>(grid, nint, cap, p.tk_cnt, p.tk_e, p.tk_a, p.tk_key, p.tau_bits,
                                         x->cand_e.as<double>(), x->cand_a.as<double>(),
-                                        x->cand_key.as<uint64_t>(), d_ncand);
+                                        x->cand_key.as<uint64_t>(), d_ncand, (int64_t)maxc, d_err);
     x->launches++;
     int ncand = 0;
     CUDA_TRY(cudaMemcpyAsync(&ncand, d_ncand, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -920,4 +927,389 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
   *de0 = -hres.s2;
   if (hres.na > 0 && md < 1e-12) return fail(QP_ESINGULAR, "a denominator E0 - H_aa is below 1e-12");
   return QP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched sweeps.  Many contexts' sweeps (each its own Hamiltonian and Psi0)
+// are planned once (workspaces allocated outside any capture) and enqueued
+// without host synchronisation on forked streams inside one stream capture;
+// the resulting CUDA graph runs all of them concurrently per launch.  Input
+// checks that the ordinary sweep does on the host are made on the device and
+// reported after the run; the final sort uses a segmented radix sort whose
+// segment end (the candidate count) lives on the device.
+// ---------------------------------------------------------------------------
+__global__ void init_acc_kernel(unsigned long long* acc) {
+  const int t = threadIdx.x;
+  if (t < kAccWords) acc[t] = (t == kAccMinDen) ? 0x7FF0000000000000ull : 0ull;
+}
+
+__global__ void seg_bounds_kernel(const int* ncand, int* be) {
+  be[0] = 0;
+  be[1] = *ncand;
+}
+
+__global__ void sortkey_dev_kernel(int cap, const int* ncand, int nint, int w, const double* ce, const uint64_t* ck,
+                                   const int32_t* perm, unsigned long long* keys) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cap || i >= *ncand) return;
+  const int nw = 2 * nint, j = perm[i];
+  keys[i] = (w < nw) ? ck[(size_t)j * nw + w] : ~(unsigned long long)__double_as_longlong(fabs(ce[j]));
+}
+
+__global__ void select_out_dev_kernel(int64_t k, const int* ncand, int nint, const int32_t* perm, const double* ce,
+                                      const uint64_t* ck, uint64_t* sel, double* se, unsigned long long* nsel) {
+  const int64_t n = (int64_t)(*ncand) < k ? (int64_t)(*ncand) : k;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *nsel = (unsigned long long)n;
+  if (i >= n) return;
+  const int nw = 2 * nint, j = perm[i];
+  for (int w = 0; w < nw; w++) sel[(size_t)i * nw + w] = ck[(size_t)j * nw + w];
+  se[i] = ce[j];
+}
+
+struct BatchInst {
+  qp_pt2_ctx* x;
+  int64_t ndet, k;
+  const uint64_t* dets;
+  const double* coefs;
+  double e0;
+  uint64_t* sel;
+  double* se;
+  int grid;
+  int64_t W, nwaves, ngen, ent_cap, cap;
+  size_t maxc, tmp1, tmp2;
+  double work;
+};
+
+struct qp_pt2_batch {
+  std::vector<BatchInst> inst;
+  cudaStream_t main = nullptr;
+  bool own_main = false;
+  std::vector<cudaStream_t> br;
+  std::vector<cudaEvent_t> ev;
+  cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+static int plan_instance(BatchInst& b, size_t wave_budget) {
+  qp_pt2_ctx* x = b.x;
+  const int nint = x->nint, nw = 2 * nint;
+  const size_t nd = (size_t)b.ndet;
+  int rc;
+  if (b.grid <= 0) b.grid = x->grid;
+  const int grid = b.grid;
+  b.cap = b.k > 0 ? b.k + x->max_cells : 1;
+  // every CTA may hold up to k candidates when no CTA has filled its buffer
+  b.maxc = (size_t)grid * (size_t)(b.k > 0 ? b.k : 1);
+  b.ngen = b.ndet;
+  const int64_t ent_per = x->nel >= 3 ? 3 * x->nel - 3 : 1;
+  b.ent_cap = (int64_t)nd * ent_per;
+  const size_t dwords = (size_t)(x->nbat + 31) / 32;
+  const size_t per_slot = sizeof(GenMeta) + nd * (8 * nw + 8 + 8 + 8 + 4) + 4 * (size_t)(x->nbat + 2) +
+                          4 * (size_t)b.ent_cap + 4 * dwords;
+  b.W = (int64_t)(wave_budget / per_slot);
+  if (b.W < 1) b.W = 1;
+  if (b.W > b.ngen) b.W = b.ngen;
+  b.nwaves = (b.ngen + b.W - 1) / b.W;
+  const size_t ws = (size_t)b.W;
+  b.tmp1 = 0;
+  b.tmp2 = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, b.tmp1, (unsigned long long*)nullptr, (unsigned long long*)nullptr,
+                                  (int32_t*)nullptr, (int32_t*)nullptr, (int)b.ndet, 0, 64, x->st);
+  cub::DeviceSegmentedRadixSort::SortPairs(nullptr, b.tmp2, (unsigned long long*)nullptr,
+                                           (unsigned long long*)nullptr, (int32_t*)nullptr, (int32_t*)nullptr,
+                                           (int)b.maxc, 1, (int*)nullptr, (int*)nullptr, 0, 64, x->st);
+  if ((rc = x->hkey.grow(8 * nd)) || (rc = x->hkey2.grow(8 * nd)) || (rc = x->hidx.grow(4 * nd)) ||
+      (rc = x->hidx2.grow(4 * nd)) || (rc = x->rkey.grow(8 * nd)) || (rc = x->rkey2.grow(8 * nd)) ||
+      (rc = x->order.grow(4 * nd)) || (rc = x->rank_of.grow(4 * nd)) || (rc = x->acc.grow(8 * kAccWords)) ||
+      (rc = x->cub_tmp.grow(b.tmp1)) || (rc = x->cub_tmp2.grow(b.tmp2 + 256)) || (rc = x->eps.grow(8 * nd)) ||
+      (rc = x->s2.grow(8 * nd)) || (rc = x->na.grow(8 * nd)) || (rc = x->ncon.grow(8 * nd)) ||
+      (rc = x->meta.grow(sizeof(GenMeta) * ws)) || (rc = x->r_words.grow(8 * nd * nw * ws)) ||
+      (rc = x->r_coef.grow(8 * nd * ws)) || (rc = x->r_hmask.grow(8 * nd * ws)) ||
+      (rc = x->r_part.grow(8 * nd * ws)) || (rc = x->r_flag.grow(4 * nd * ws)) ||
+      (rc = x->b_ofs.grow(4 * (size_t)(x->nbat + 2) * ws)) || (rc = x->b_ent.grow(4 * (size_t)b.ent_cap * ws)) ||
+      (rc = x->b_dead.grow(4 * dwords * ws)) || (rc = x->queues.grow(4 * (size_t)(b.nwaves + 1))) ||
+      (rc = x->tk_e.grow(8 * (size_t)b.cap * grid)) || (rc = x->tk_a.grow(8 * (size_t)b.cap * grid)) ||
+      (rc = x->tk_key.grow(8 * (size_t)b.cap * grid * nw)) || (rc = x->tk_cnt.grow(4 * (size_t)grid)) ||
+      (rc = x->tk_tau.grow(8 * (size_t)grid)) || (rc = x->res.grow(sizeof(DevResult))) ||
+      (rc = x->cand_e.grow(8 * b.maxc)) || (rc = x->cand_a.grow(8 * b.maxc)) ||
+      (rc = x->cand_key.grow(8 * b.maxc * nw)) || (rc = x->skey.grow(8 * b.maxc)) ||
+      (rc = x->skey2.grow(8 * b.maxc)) || (rc = x->perm.grow(4 * b.maxc)) || (rc = x->perm2.grow(4 * b.maxc)))
+    return rc;
+  b.work = (double)b.ndet * (double)(x->nel + x->nel * (x->nel - 1) / 2) * (double)x->max_cells;
+  return QP_OK;
+}
+
+// All of one instance's sweep on stream st, without host synchronisation.
+static int enqueue_instance(BatchInst& b, cudaStream_t st) {
+  qp_pt2_ctx* x = b.x;
+  const int nint = x->nint, nw = 2 * nint;
+  const int64_t ndet = b.ndet;
+  const size_t nd = (size_t)ndet;
+  const int grid = b.grid;
+  unsigned long long* acc = x->acc.as<unsigned long long>();
+  int* d_err = reinterpret_cast<int*>(acc + kAccErr);
+  int* d_ncand = reinterpret_cast<int*>(acc + kAccNcand);
+  init_acc_kernel<<<1, 32, 0, st>>>(acc);
+  const int nb = (int)((ndet + 255) / 256);
+  validate_kernel<<<nb, 256, 0, st>>>(ndet, nint, x->norb, x->nalpha, x->nbeta, b.dets, b.coefs,
+                                      x->hkey.as<unsigned long long>(), x->hidx.as<int32_t>(),
+                                      x->rkey.as<unsigned long long>(), x->rank_of.as<int32_t>(), d_err);
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(x->cub_tmp.p, b.tmp1, x->hkey.as<unsigned long long>(),
+                                           x->hkey2.as<unsigned long long>(), x->hidx.as<int32_t>(),
+                                           x->hidx2.as<int32_t>(), (int)ndet, 0, 64, st));
+  dup_kernel<<<nb, 256, 0, st>>>(ndet, nint, b.dets, x->hkey2.as<unsigned long long>(), x->hidx2.as<int32_t>(), d_err);
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(x->cub_tmp.p, b.tmp1, x->rkey.as<unsigned long long>(),
+                                           x->rkey2.as<unsigned long long>(), x->rank_of.as<int32_t>(),
+                                           x->order.as<int32_t>(), (int)ndet, 0, 64, st));
+  rank_kernel<<<nb, 256, 0, st>>>(ndet, x->order.as<int32_t>(), x->rank_of.as<int32_t>());
+  CUDA_TRY(cudaMemsetAsync(x->eps.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->s2.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->na.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->ncon.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->queues.p, 0, 4 * (size_t)(b.nwaves + 1), st));
+  CUDA_TRY(cudaMemsetAsync(x->tk_cnt.p, 0, 4 * (size_t)grid, st));
+  CUDA_TRY(cudaMemsetAsync(x->tk_tau.p, 0, 8 * (size_t)grid, st));
+  SweepParams p{};
+  p.norb = x->norb;
+  p.nalpha = x->nalpha;
+  p.nbeta = x->nbeta;
+  p.nel = x->nel;
+  p.nbat = x->nbat;
+  p.ndet = ndet;
+  p.dets = b.dets;
+  p.coefs = b.coefs;
+  p.order = x->order.as<int32_t>();
+  p.rank_of = x->rank_of.as<int32_t>();
+  p.h = x->d_h;
+  p.eri = x->d_eri;
+  p.h32 = x->d_h32;
+  p.eri32 = x->d_eri32;
+  p.mixed = x->cfg.precision == QP_MIXED;
+  p.Jm = x->d_J;
+  p.Km = x->d_K;
+  p.e0 = b.e0;
+  p.shard_index = 0;
+  p.shard_count = 1;
+  p.meta = x->meta.as<GenMeta>();
+  p.r_words = x->r_words.as<uint64_t>();
+  p.r_coef = x->r_coef.as<double>();
+  p.r_hmask = x->r_hmask.as<uint64_t>();
+  p.r_part = x->r_part.as<uint64_t>();
+  p.r_flag = x->r_flag.as<uint32_t>();
+  p.b_ofs = x->b_ofs.as<int>();
+  p.b_ent = x->b_ent.as<int32_t>();
+  p.b_dead = x->b_dead.as<uint32_t>();
+  p.ent_cap = b.ent_cap;
+  p.eps = x->eps.as<double>();
+  p.s2 = x->s2.as<double>();
+  p.na = x->na.as<unsigned long long>();
+  p.ncon = x->ncon.as<unsigned long long>();
+  p.digest = acc + kAccDigest0;
+  p.min_den_bits = acc + kAccMinDen;
+  p.n_tiny = acc + kAccTiny;
+  p.k = b.k;
+  p.cap = b.cap;
+  p.tk_e = x->tk_e.as<double>();
+  p.tk_a = x->tk_a.as<double>();
+  p.tk_key = x->tk_key.as<uint64_t>();
+  p.tk_cnt = x->tk_cnt.as<int>();
+  p.tk_tau = x->tk_tau.as<unsigned long long>();
+  p.tau_bits = acc + kAccTau;
+  p.max_cells = x->max_cells;
+  p.err = d_err;
+  for (int64_t w = 0; w < b.nwaves; w++) {
+    p.wave_start = (int)(w * b.W);
+    p.wave_slots = (int)((b.ngen - w * b.W) < b.W ? (b.ngen - w * b.W) : b.W);
+    p.last_wave = (w == b.nwaves - 1);
+    p.queue = x->queues.as<int>() + w;
+    CUDA_TRY(launch_prep(nint, p, p.wave_slots, st));
+    CUDA_TRY(launch_batch(nint, p, grid, x->smem, st));
+  }
+  finalize_kernel<<<1, 1024, 0, st>>>(ndet, p.eps, p.s2, reinterpret_cast<const long long*>(p.na),
+                                      reinterpret_cast<const long long*>(p.ncon), x->res.as<DevResult>());
+  if (b.k > 0) {
+    gather_kernel<<<grid, 256, 0, st>>>(grid, nint, b.cap, p.tk_cnt, p.tk_e, p.tk_a, p.tk_key, p.tau_bits,
+                                        x->cand_e.as<double>(), x->cand_a.as<double>(), x->cand_key.as<uint64_t>(),
+                                        d_ncand, (int64_t)b.maxc, d_err);
+    // the segment bounds: two ints after the sort's scratch space
+    int* be = reinterpret_cast<int*>(x->cub_tmp2.as<unsigned char>() + ((b.tmp2 + 15) & ~(size_t)15));
+    seg_bounds_kernel<<<1, 1, 0, st>>>(d_ncand, be);
+    const int cap = (int)b.maxc;
+    const int sb = (cap + 255) / 256;
+    iota_kernel<<<sb, 256, 0, st>>>(cap, x->perm.as<int32_t>());
+    int32_t *pa = x->perm.as<int32_t>(), *pb = x->perm2.as<int32_t>();
+    for (int pass = 0; pass <= nw; pass++) {
+      const int word = (pass < nw) ? (nw - 1 - pass) : nw;
+      sortkey_dev_kernel<<<sb, 256, 0, st>>>(cap, d_ncand, nint, word, x->cand_e.as<double>(),
+                                             x->cand_key.as<uint64_t>(), pa, x->skey.as<unsigned long long>());
+      CUDA_TRY(cub::DeviceSegmentedRadixSort::SortPairs(x->cub_tmp2.p, b.tmp2, x->skey.as<unsigned long long>(),
+                                                        x->skey2.as<unsigned long long>(), pa, pb, cap, 1, be,
+                                                        be + 1, 0, 64, st));
+      std::swap(pa, pb);
+    }
+    select_out_dev_kernel<<<(int)((b.k + 255) / 256), 256, 0, st>>>(b.k, d_ncand, nint, pa, x->cand_e.as<double>(),
+                                                                   x->cand_key.as<uint64_t>(), b.sel, b.se,
+                                                                   acc + kAccQueue);
+  }
+  CUDA_TRY(cudaGetLastError());
+  return QP_OK;
+}
+
+extern "C" int qp_pt2_batch_create(qp_pt2_batch** out, int n, qp_pt2_ctx* const* ctxs, const int64_t* ndet,
+                                   const uint64_t* const* dets, const double* const* coefs, const double* e0,
+                                   const int64_t* k, uint64_t* const* sel_dets, double* const* sel_e,
+                                   const int* grid, int max_streams, void* stream) {
+  if (!out || n < 1 || !ctxs || !ndet || !dets || !coefs || !e0 || !k) return fail(QP_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  qp_pt2_batch* B = new (std::nothrow) qp_pt2_batch();
+  if (!B) return fail(QP_ENOMEM, "host allocation failed");
+  auto bail = [&](int code, const std::string& m) {
+    qp_pt2_batch_destroy(B);
+    return fail(code, m);
+  };
+  B->main = (cudaStream_t)stream;
+  for (int i = 0; i < n; i++) {
+    BatchInst b{};
+    b.x = ctxs[i];
+    b.ndet = ndet[i];
+    b.k = k[i];
+    b.dets = dets[i];
+    b.coefs = coefs[i];
+    b.e0 = e0[i];
+    b.sel = sel_dets ? sel_dets[i] : nullptr;
+    b.se = sel_e ? sel_e[i] : nullptr;
+    b.grid = grid ? grid[i] : 0;
+    if (!b.x || b.ndet < 1 || b.k < 0 || b.ndet >= (1ll << 31) || !std::isfinite(b.e0))
+      return bail(QP_EINVAL, "bad instance " + std::to_string(i));
+    if (b.x->cfg.shard_count > 1) return bail(QP_EINVAL, "sharded contexts cannot be batched");
+    if (!is_device_ptr(b.dets) || !is_device_ptr(b.coefs) || (b.k > 0 && (!is_device_ptr(b.sel) || !is_device_ptr(b.se))))
+      return bail(QP_EINVAL, "batched inputs and outputs must be device memory (instance " + std::to_string(i) + ")");
+    for (int j = 0; j < i; j++)
+      if (B->inst[j].x == b.x) return bail(QP_EINVAL, "each instance needs its own context");
+    // all instances' workspaces stay allocated together: share the wave budget
+    size_t budget = (size_t)(16ull << 30) / (size_t)n;
+    if (budget > kWaveBudget) budget = kWaveBudget;
+    if (budget < ((size_t)64 << 20)) budget = (size_t)64 << 20;
+    int rc = plan_instance(b, budget);
+    if (rc) return bail(rc, "planning instance " + std::to_string(i) + ": " + g_last_error);
+    B->inst.push_back(b);
+  }
+  int ns = max_streams > 0 ? max_streams : 16;
+  if (ns > n) ns = n;
+  B->br.resize(ns);
+  B->ev.resize(ns);
+  for (int i = 0; i < ns; i++) {
+    if (cudaStreamCreateWithFlags(&B->br[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev[i], cudaEventDisableTiming) != cudaSuccess)
+      return bail(QP_ECUDA, "stream creation failed");
+  }
+  if (cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&B->t0) != cudaSuccess || cudaEventCreate(&B->t1) != cudaSuccess)
+    return bail(QP_ECUDA, "event creation failed");
+  if (cudaStreamSynchronize(B->main) != cudaSuccess) return bail(QP_ECUDA, "stream synchronisation failed");
+  // largest work first, each on the least loaded branch
+  std::vector<int> order(n);
+  for (int i = 0; i < n; i++) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return B->inst[a].work > B->inst[b].work; });
+  std::vector<double> load(ns, 0.0);
+  std::vector<int> branch(n);
+  for (int i : order) {
+    int s = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    branch[i] = s;
+    load[s] += B->inst[i].work;
+  }
+  // capture: fork from the main stream, one branch per stream, join
+  cudaStream_t cap = B->main;
+  if (!cap) {  // the legacy stream cannot be captured: use a stream of our own
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return bail(QP_ECUDA, "stream");
+    B->own_main = true;
+    B->main = cap;
+  }
+  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return bail(QP_ECUDA, "cudaStreamBeginCapture failed");
+  cudaEventRecord(B->fork, cap);
+  for (int s = 0; s < ns; s++) cudaStreamWaitEvent(B->br[s], B->fork, 0);
+  int erc = QP_OK;
+  for (int i : order) {
+    erc = enqueue_instance(B->inst[i], B->br[branch[i]]);
+    if (erc) break;
+  }
+  for (int s = 0; s < ns; s++) {
+    cudaEventRecord(B->ev[s], B->br[s]);
+    cudaStreamWaitEvent(cap, B->ev[s], 0);
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(cap, &g);
+  if (erc) {
+    if (g) cudaGraphDestroy(g);
+    return bail(erc, "enqueue failed: " + g_last_error);
+  }
+  if (ce != cudaSuccess || !g) return bail(QP_ECUDA, std::string("stream capture failed: ") + cudaGetErrorString(ce));
+  B->graph = g;
+  if (cudaGraphInstantiate(&B->exec, g, 0) != cudaSuccess) return bail(QP_ECUDA, "cudaGraphInstantiate failed");
+  *out = B;
+  return QP_OK;
+}
+
+extern "C" int qp_pt2_batch_run(qp_pt2_batch* B, qp_pt2_result* res, double* ms) {
+  if (!B || !B->exec) return fail(QP_EINVAL, "batch not created");
+  CUDA_TRY(cudaEventRecord(B->t0, B->main));
+  CUDA_TRY(cudaGraphLaunch(B->exec, B->main));
+  CUDA_TRY(cudaEventRecord(B->t1, B->main));
+  CUDA_TRY(cudaStreamSynchronize(B->main));
+  if (ms) {
+    float f = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&f, B->t0, B->t1));
+    *ms = f;
+  }
+  int worst = QP_OK;
+  for (size_t i = 0; i < B->inst.size(); i++) {
+    BatchInst& b = B->inst[i];
+    DevResult hres;
+    unsigned long long hacc[kAccWords];
+    CUDA_TRY(cudaMemcpy(&hres, b.x->res.p, sizeof(hres), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(hacc, b.x->acc.p, sizeof(hacc), cudaMemcpyDeviceToHost));
+    qp_pt2_result r;
+    memset(&r, 0, sizeof(r));
+    const int herr = (int)(hacc[kAccErr] & 0xffffffffull);
+    int code = QP_OK;
+    if (herr & kErrOcc) code = QP_EINVAL;
+    else if (herr & kErrCoef) code = QP_EINVAL;
+    else if (herr & kErrDup) code = QP_EDUP;
+    else if (herr & kErrBucket) code = QP_ECUDA;
+    else if (herr & 32) code = QP_ENOMEM;
+    r.e_pt2 = hres.e_pt2;
+    r.sum_e_over_d = hres.s2;
+    r.n_perturbers = hres.na;
+    r.n_connections = hres.ncon;
+    r.n_selected = b.k > 0 ? (int64_t)hacc[kAccQueue] : 0;
+    r.n_tiny = (int64_t)hacc[kAccTiny];
+    r.perturber_digest[0] = hacc[kAccDigest0];
+    r.perturber_digest[1] = hacc[kAccDigest1];
+    double md;
+    memcpy(&md, &hacc[kAccMinDen], sizeof(md));
+    r.min_abs_denominator = md;
+    if (code == QP_OK && hres.na > 0 && md < 1e-12) code = QP_ESINGULAR;
+    if (res) res[i] = r;
+    if (code != QP_OK && worst == QP_OK) {
+      worst = code;
+      g_last_error = "batch instance " + std::to_string(i) + ": " + qp_pt2_strerror(code);
+    }
+  }
+  return worst;
+}
+
+extern "C" void qp_pt2_batch_destroy(qp_pt2_batch* B) {
+  if (!B) return;
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  for (auto s : B->br) if (s) cudaStreamDestroy(s);
+  for (auto e : B->ev) if (e) cudaEventDestroy(e);
+  if (B->fork) cudaEventDestroy(B->fork);
+  if (B->t0) cudaEventDestroy(B->t0);
+  if (B->t1) cudaEventDestroy(B->t1);
+  if (B->own_main && B->main) cudaStreamDestroy(B->main);
+  delete B;
 }

@@ -198,3 +198,118 @@ def n_singles_doubles(norb: int, nalpha: int, nbeta: int) -> int:
     same = math.comb(nalpha, 2) * math.comb(va, 2) + math.comb(nbeta, 2) * math.comb(vb, 2)
     opp = nalpha * nbeta * va * vb
     return singles + same + opp
+
+
+# ---------------------------------------------------------------------------
+# The batched workload: many independent instances of uneven size.
+# ---------------------------------------------------------------------------
+def batch_specs(n=64, seed0=1000):
+    """Instance i (seed seed0 + i): norb uniform in {24, 32, 48, 64, 96},
+    n_alpha = n_beta uniform in 6..12, N_det = exp(U(ln 1e3, ln 5e4))
+    rounded to a multiple of 8, Cholesky rank ceil(1.5 norb)."""
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng(seed0 + i)
+        norb = int(rng.choice([24, 32, 48, 64, 96]))
+        ne = int(rng.integers(6, 13))
+        ndet = max(8, int(round(math.exp(rng.uniform(math.log(1e3), math.log(5e4))) / 8)) * 8)
+        out.append(dict(norb=norb, nalpha=ne, nbeta=ne, ndet=ndet, rank=math.ceil(1.5 * norb), seed=seed0 + i))
+    return out
+
+
+def hamiltonian_fast(norb: int, rank: int, seed: int):
+    """Same draws as ``hamiltonian`` but (pq|rs) formed by one matrix
+    product; the last bits may depend on the BLAS of the machine, so inputs
+    made this way are consumed on the machine that made them."""
+    rng = np.random.default_rng(seed)
+    h = np.zeros((norb, norb), dtype=np.float64)
+    iu = np.triu_indices(norb, 1)
+    h[iu] = rng.normal(0.0, 0.05, size=iu[0].size)
+    h = h + h.T
+    h[np.arange(norb), np.arange(norb)] = -2.0 + 0.15 * np.arange(norb, dtype=np.float64)
+    powers = np.empty(2 * norb, dtype=np.float64)
+    acc = 1.0
+    for k in range(2 * norb):
+        powers[k] = acc
+        acc = acc * DECAY
+    pp, qq = np.tril_indices(norb)
+    scale = 0.3 * powers[pp + qq]
+    iu0 = np.triu_indices(norb, 0)
+    Bm = np.zeros((rank, pp.size))
+    for L in range(rank):
+        B = np.zeros((norb, norb), dtype=np.float64)
+        B[iu0] = rng.standard_normal(iu0[0].size)
+        B = np.triu(B) + np.triu(B, 1).T
+        Bm[L] = B[pp, qq] * scale
+    V = Bm.T @ Bm
+    rows, cols = np.tril_indices(pp.size)
+    return h, np.ascontiguousarray(V[rows, cols])
+
+
+def excited_dets_fast(norb, nalpha, nbeta, ndet, seed, max_level=4):
+    """Vectorised form of ``random_excited_dets`` for large spaces: HF first,
+    then distinct determinants with 1..max_level electrons moved from the HF
+    occupation to random virtual orbitals (order: first occurrence)."""
+    rng = np.random.default_rng(seed)
+    nint = nint_of(norb)
+    hf = hf_det(norb, nalpha, nbeta)
+    seen = {hf.tobytes()}
+    dets = [hf]
+    while len(dets) < ndet:
+        m = 4 * (ndet - len(dets)) + 64
+        level = rng.integers(1, max_level + 1, size=m)
+        up = rng.binomial(level, 0.5)
+        words = np.zeros((m, 2, nint), dtype=np.uint64)
+        for s, (nocc, moves) in enumerate(((nalpha, up), (nbeta, level - up))):
+            moves = np.minimum(moves, min(nocc, norb - nocc))
+            occ = np.zeros((m, norb), dtype=bool)
+            occ[:, :nocc] = True
+            if nocc and norb - nocc:
+                hole = np.argsort(rng.random((m, nocc)), axis=1)
+                part = nocc + np.argsort(rng.random((m, norb - nocc)), axis=1)
+                kmax = int(moves.max()) if m else 0
+                for j in range(kmax):
+                    sel = moves > j
+                    r = np.nonzero(sel)[0]
+                    occ[r, hole[r, j]] = False
+                    occ[r, part[r, j]] = True
+            for w in range(nint):
+                block = occ[:, 64 * w: 64 * (w + 1)]
+                bits = (block.astype(np.uint64) << np.arange(block.shape[1], dtype=np.uint64)).sum(axis=1)
+                words[:, s, w] = bits.astype(np.uint64)
+        for row in words:
+            b = row.tobytes()
+            if b not in seen:
+                seen.add(b)
+                dets.append(row.copy())
+                if len(dets) == ndet:
+                    break
+    return np.ascontiguousarray(np.stack(dets), dtype=np.uint64)
+
+
+def diagonal_lower_bound(h, eri, nel):
+    """A number below <D|H|D> for every determinant D with nel electrons:
+    nel * min h_pp + C(nel, 2) * min(0, min_pq ((pp|qq) - (pq|qp)))."""
+    norb = h.shape[0]
+    i = np.arange(norb)
+
+    def tri(a, b):
+        hi, lo = np.maximum(a, b), np.minimum(a, b)
+        return hi * (hi + 1) // 2 + lo
+
+    pq = tri(i[:, None], i[None, :])
+    pp = tri(i, i)
+    J = eri[tri(pp[:, None], pp[None, :])]
+    K = eri[tri(pq, pq)]
+    pair = min(0.0, float((J - K).min()), float(J.min()))
+    return nel * float(np.diag(h).min()) + nel * (nel - 1) / 2 * pair
+
+
+def batch_instance(spec):
+    """Inputs of one batched instance: (h, eri, dets, coefs, e0).  E0 lies
+    below every diagonal energy of the space (no singular denominators)."""
+    h, eri = hamiltonian_fast(spec["norb"], spec["rank"], spec["seed"])
+    dets = excited_dets_fast(spec["norb"], spec["nalpha"], spec["nbeta"], spec["ndet"], spec["seed"] + 1)
+    coefs = random_coefs(len(dets), spec["seed"] + 2, decay=4.0 / len(dets))
+    e0 = diagonal_lower_bound(h, eri, spec["nalpha"] + spec["nbeta"]) - 1.0
+    return h, eri, dets, coefs, e0
