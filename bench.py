@@ -398,6 +398,7 @@ def run_gb300(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(meta, world),
             "generators_per_s": gens_per_s, "n_perturbers": units, "e_pt2": res["e_pt2"],
+            "rpt2": qp.rpt2(res, e0),
             "e2e": e2e,
             "gpu_launches": launches, "roofline": roof, "clocks": ck, "mixed_precision": mixed,
             "batched": batched}

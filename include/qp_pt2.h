@@ -95,7 +95,8 @@ typedef struct {
 
 typedef struct {
     double e_pt2;               /* E_PT2 (Eq. PT2) */
-    double sum_e_over_d;        /* sum_alpha A^2/D^2 = -dSigma/dE at E0 (Sec. rPT2) */
+    double sum_e_over_d;        /* sum_alpha A^2/D^2 = -dSigma/dE at E0 (Sec. "Renormalized
+                                   PT2"): Z = 1/(1 + sum_e_over_d), E_rPT2 = E0 + Z E_PT2 */
     double min_abs_denominator; /* min |E0 - H_aa| over perturbers (inf if none) */
     int64_t n_perturbers;       /* |A|: external determinants connected to Psi0 */
     int64_t n_connections;      /* pairs (J, alpha), alpha in A, deg(J,alpha) <= 2 */

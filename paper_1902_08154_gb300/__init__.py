@@ -67,6 +67,14 @@ class Result(C.Structure):
         }
 
 
+def rpt2(res, e0):
+    """Renormalised PT2 (Sec. "Renormalized PT2"): with
+    dSigma/dE at E0 = -sum_alpha A^2/D^2 (returned by every sweep),
+    Z = 1 / (1 + sum A^2/D^2) lies in (0, 1] and E = E0 + Z E_PT2."""
+    z = 1.0 / (1.0 + res["sum_e_over_d"])
+    return {"z": z, "e_rpt2": float(e0) + z * res["e_pt2"]}
+
+
 class QPError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{msg} (code {code})")
@@ -240,6 +248,7 @@ class PT2:
                                  sn if k else None, eps, na, nc, rk, check=check)
         out = res.as_dict()
         out["rc"] = rc
+        out.update(rpt2(out, e0))
         m = res.n_selected
         out.update(sel_dets=sel[:m], sel_e=se[:m], sel_num=sn[:m])
         if per_generator:

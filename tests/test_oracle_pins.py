@@ -423,3 +423,23 @@ def test_gradient_matches_central_differences(grad_case):
         an = g["dh"][p, p] if p == q else g["dh"][p, q] + g["dh"][q, p]
         assert abs(fd - an) <= 1e-6 * abs(fd) + 1e-8, (p, q, fd, an)
     assert np.allclose(g["dh"], g["dh"].T, atol=0, rtol=0)
+
+
+# ---------------------------------------------------------------------------
+# Renormalised PT2 (Sec. "Renormalized PT2", Eqs. E2-w, Z)
+# ---------------------------------------------------------------------------
+def test_rpt2_self_energy_derivative_and_z(small_case):
+    """Sigma(E) = sum A^2/(E - H_aa): Sigma(E0) = E_PT2, dSigma/dE at E0 =
+    -sum A^2/D^2 (central difference), and Z = 1/(1 + sum A^2/D^2) in (0, 1]."""
+    import paper_1902_08154_gb300 as qp
+
+    ham, h, eri, dets, c, e0 = small_case
+    base = ham.sweep(dets, c, e0, k=0)
+    d = 1e-5
+    sp = ham.sweep(dets, c, e0 + d, k=0)["e_pt2"]
+    sm = ham.sweep(dets, c, e0 - d, k=0)["e_pt2"]
+    assert (sp - sm) / (2 * d) == pytest.approx(-base["sum_e_over_d"], rel=1e-7)
+    r = qp.rpt2(base, e0)
+    assert 0.0 < r["z"] <= 1.0
+    assert r["e_rpt2"] == pytest.approx(e0 + r["z"] * base["e_pt2"], abs=1e-14)
+    assert abs(r["e_rpt2"] - e0) <= abs(base["e_pt2"])  # rPT2 damps the correction
