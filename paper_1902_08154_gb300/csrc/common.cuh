@@ -9,6 +9,7 @@ namespace qp {
 constexpr int kMaxOrb = 128;
 constexpr int kMaxElec = 64;   // per determinant (both spins); hole masks are uint64
 constexpr int kMaxBatch = kMaxElec + kMaxElec * (kMaxElec - 1) / 2;
+constexpr int kSelBins = 1024;  // |e| histogram: 128 binary exponents (2^-100 .. 2^27) x 8 sub-bins
 
 // Fold of splitmix64 over the key words: the digest hash of a determinant.
 // splitmix64 is the generator of Steele, Lea & Flood (2014); its finaliser
@@ -113,6 +114,7 @@ struct SweepParams {
   int* tk_cnt;                   // [grid]
   unsigned long long* tk_tau;    // [grid] CTA thresholds (bits of |e|)
   unsigned long long* tau_bits;  // global selection threshold (bits of |e|)
+  unsigned int* sel_hist;        // [kSelBins] counts of candidates offered to the buffers, by |e| bin
 
   int max_cells;
   int* err;                      // device error flags (0 = fine)

@@ -209,6 +209,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   uint64_t* tk_key = cv.take<uint64_t>((size_t)cap * grid * nw);
   int* tk_cnt = cv.take<int>(grid);
   unsigned long long* tk_tau = cv.take<unsigned long long>(grid);
+  unsigned int* sel_hist = cv.take<unsigned int>(kSelBins);
   double* cand_e = cv.take<double>(maxc);
   double* cand_a = cv.take<double>(maxc);
   uint64_t* cand_key = cv.take<uint64_t>(maxc * nw);
@@ -272,6 +273,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   NTRY(cudaMemsetAsync(queues, 0, 4 * (nd + 1), st));
   NTRY(cudaMemsetAsync(tk_cnt, 0, 4 * (size_t)grid, st));
   NTRY(cudaMemsetAsync(tk_tau, 0, 8 * (size_t)grid, st));
+  NTRY(cudaMemsetAsync(sel_hist, 0, 4 * (size_t)kSelBins, st));
   SweepParams p{};
   p.norb = norb;
   p.nalpha = n_alpha;
@@ -315,6 +317,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   p.tk_cnt = tk_cnt;
   p.tk_tau = tk_tau;
   p.tau_bits = acc + 4;
+  p.sel_hist = sel_hist;
   p.max_cells = max_cells;
   p.err = d_err;
   for (int64_t w = 0; w < nwaves; w++) {

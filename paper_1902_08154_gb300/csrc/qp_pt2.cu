@@ -261,7 +261,7 @@ struct qp_pt2_ctx {
   Buf in_dets, in_coefs, hkey, hkey2, hidx, hidx2, rkey, rkey2, order, rank_of, cub_tmp;
   Buf eps, s2, na, ncon, acc, res;
   Buf meta, r_words, r_coef, r_hmask, r_part, r_flag, b_ofs, b_ent, b_dead, queues;
-  Buf tk_e, tk_a, tk_key, tk_cnt, tk_tau;
+  Buf tk_e, tk_a, tk_key, tk_cnt, tk_tau, sel_hist;
   Buf cand_e, cand_a, cand_key, skey, skey2, perm, perm2, cub_tmp2;
   Buf out_sel, out_e, out_num, out_eps, out_na, out_ncon, out_rank;
   Buf g_dh, g_deri, g_wF, g_wH;
@@ -395,7 +395,7 @@ extern "C" void qp_pt2_destroy(qp_pt2_ctx* x) {
   Buf* all[] = {&x->in_dets, &x->in_coefs, &x->hkey, &x->hkey2, &x->hidx, &x->hidx2, &x->rkey, &x->rkey2,
                 &x->order, &x->rank_of, &x->cub_tmp, &x->eps, &x->s2, &x->na, &x->ncon, &x->acc,
                 &x->res, &x->meta, &x->r_words, &x->r_coef, &x->r_hmask, &x->r_part, &x->r_flag,
-                &x->b_ofs, &x->b_ent, &x->b_dead, &x->queues, &x->tk_e, &x->tk_a, &x->tk_key, &x->tk_cnt, &x->tk_tau, &x->cand_e, &x->cand_a, &x->cand_key, &x->skey,
+                &x->b_ofs, &x->b_ent, &x->b_dead, &x->queues, &x->tk_e, &x->tk_a, &x->tk_key, &x->tk_cnt, &x->tk_tau, &x->sel_hist, &x->cand_e, &x->cand_a, &x->cand_key, &x->skey,
                 &x->skey2, &x->perm, &x->perm2, &x->cub_tmp2, &x->out_sel, &x->out_e, &x->out_num,
                 &x->out_eps, &x->out_na, &x->out_ncon, &x->out_rank, &x->g_dh, &x->g_deri, &x->g_wF, &x->g_wH};
   for (Buf* b : all) b->release();
@@ -551,8 +551,10 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
       (rc = x->b_ent.grow(4 * (size_t)ent_cap * ws)) || (rc = x->b_dead.grow(4 * dwords * ws)) || (rc = x->queues.grow(4 * (size_t)(nwaves + 1))) ||
       (rc = x->tk_e.grow(8 * (size_t)cap * grid)) || (rc = x->tk_a.grow(8 * (size_t)cap * grid)) ||
       (rc = x->tk_key.grow(8 * (size_t)cap * grid * nw)) || (rc = x->tk_cnt.grow(4 * (size_t)grid)) ||
-      (rc = x->tk_tau.grow(8 * (size_t)grid)) || (rc = x->res.grow(sizeof(DevResult))))
+      (rc = x->tk_tau.grow(8 * (size_t)grid)) || (rc = x->res.grow(sizeof(DevResult))) ||
+      (rc = x->sel_hist.grow(4 * (size_t)kSelBins)))
     return rc;
+  CUDA_TRY(cudaMemsetAsync(x->sel_hist.p, 0, 4 * (size_t)kSelBins, st));
   CUDA_TRY(cudaMemsetAsync(x->eps.p, 0, 8 * nd, st));
   CUDA_TRY(cudaMemsetAsync(x->s2.p, 0, 8 * nd, st));
   CUDA_TRY(cudaMemsetAsync(x->na.p, 0, 8 * nd, st));
@@ -606,6 +608,7 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
   p.tk_cnt = x->tk_cnt.as<int>();
   p.tk_tau = x->tk_tau.as<unsigned long long>();
   p.tau_bits = acc + kAccTau;
+  p.sel_hist = x->sel_hist.as<unsigned int>();
   p.max_cells = x->max_cells;
   p.err = d_err;
   CUDA_TRY(cudaEventRecord(x->ev[1], st));
@@ -881,6 +884,7 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
   p.tk_cnt = x->tk_cnt.as<int>();
   p.tk_tau = x->tk_tau.as<unsigned long long>();
   p.tau_bits = acc + kAccTau;
+  p.sel_hist = x->sel_hist.as<unsigned int>();
   p.max_cells = x->max_cells;
   p.err = d_err;
   p.g_dh = d_dh;
@@ -1033,7 +1037,7 @@ static int plan_instance(BatchInst& b, size_t wave_budget) {
       (rc = x->tk_e.grow(8 * (size_t)b.cap * grid)) || (rc = x->tk_a.grow(8 * (size_t)b.cap * grid)) ||
       (rc = x->tk_key.grow(8 * (size_t)b.cap * grid * nw)) || (rc = x->tk_cnt.grow(4 * (size_t)grid)) ||
       (rc = x->tk_tau.grow(8 * (size_t)grid)) || (rc = x->res.grow(sizeof(DevResult))) ||
-      (rc = x->cand_e.grow(8 * b.maxc)) || (rc = x->cand_a.grow(8 * b.maxc)) ||
+      (rc = x->sel_hist.grow(4 * (size_t)kSelBins)) || (rc = x->cand_e.grow(8 * b.maxc)) || (rc = x->cand_a.grow(8 * b.maxc)) ||
       (rc = x->cand_key.grow(8 * b.maxc * nw)) || (rc = x->skey.grow(8 * b.maxc)) ||
       (rc = x->skey2.grow(8 * b.maxc)) || (rc = x->perm.grow(4 * b.maxc)) || (rc = x->perm2.grow(4 * b.maxc)))
     return rc;
@@ -1052,6 +1056,7 @@ static int enqueue_instance(BatchInst& b, cudaStream_t st) {
   int* d_err = reinterpret_cast<int*>(acc + kAccErr);
   int* d_ncand = reinterpret_cast<int*>(acc + kAccNcand);
   init_acc_kernel<<<1, 32, 0, st>>>(acc);
+  CUDA_TRY(cudaMemsetAsync(x->sel_hist.p, 0, 4 * (size_t)kSelBins, st));
   const int nb = (int)((ndet + 255) / 256);
   validate_kernel<<<nb, 256, 0, st>>>(ndet, nint, x->norb, x->nalpha, x->nbeta, b.dets, b.coefs,
                                       x->hkey.as<unsigned long long>(), x->hidx.as<int32_t>(),
@@ -1117,6 +1122,7 @@ static int enqueue_instance(BatchInst& b, cudaStream_t st) {
   p.tk_cnt = x->tk_cnt.as<int>();
   p.tk_tau = x->tk_tau.as<unsigned long long>();
   p.tau_bits = acc + kAccTau;
+  p.sel_hist = x->sel_hist.as<unsigned int>();
   p.max_cells = x->max_cells;
   p.err = d_err;
   for (int64_t w = 0; w < b.nwaves; w++) {

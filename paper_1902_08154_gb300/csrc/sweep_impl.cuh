@@ -648,6 +648,56 @@ __device__ __forceinline__ void w_grad(const SweepParams& p, int x, int sx, int 
 // ascending) of the CTA's buffer.  MSD radix select over the composite
 // (~bits(|e|), key words), 8-bit digits, then an ordered in-place compaction.
 // ---------------------------------------------------------------------------
+// Selection histogram bins: the binary exponent of |e| (2^-100 .. 2^27) and
+// the top 3 mantissa bits, so that a bin's lower edge is a double whose bits
+// are easy to form.  Values below 2^-100 fall in bin 0, whose edge is taken as
+// 0; values of 2^28 and above fall in the last bin, whose edge is below them.
+__device__ __forceinline__ int sel_bin(unsigned long long ebits) {
+  const int ex = (int)(ebits >> 52) - 923;
+  if (ex < 0) return 0;
+  if (ex > 127) return kSelBins - 1;
+  return ex * 8 + (int)((ebits >> 49) & 7ull);
+}
+__device__ __forceinline__ unsigned long long sel_bin_edge(int b) {
+  return ((unsigned long long)(b / 8 + 923) << 52) | ((unsigned long long)(b % 8) << 49);
+}
+
+// A lower bound of the k-th largest |e| of the whole sweep: the lower edge of
+// the highest bin at which at least k distinct perturbers (each counted once,
+// when offered to a selection buffer) have |e| at or above the edge.
+static __device__ unsigned long long hist_threshold(const unsigned int* hist, long long k) {
+  const int lane = threadIdx.x & 31;
+  constexpr int per = kSelBins / 32;
+  // lane l owns bins [l*per, (l+1)*per); sums from the top
+  unsigned long long mine = 0;
+  for (int b = 0; b < per; b++) mine += hist[lane * per + b];
+  unsigned long long suffix = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long v = __shfl_down_sync(0xffffffffu, suffix, o);
+    if (lane + o < 32) suffix += v;
+  }
+  // suffix = counts in bins of lanes >= lane; the lane whose block holds the
+  // k-th count from the top walks its bins
+  const unsigned long long above_me = suffix - mine;
+  unsigned long long res = 0;
+  const bool holder = (above_me < (unsigned long long)k) && (suffix >= (unsigned long long)k);
+  if (holder) {
+    unsigned long long cum = above_me;
+    for (int b = per - 1; b >= 0; b--) {
+      cum += hist[lane * per + b];
+      if (cum >= (unsigned long long)k) {
+        const int bin = lane * per + b;
+        res = bin > 0 ? sel_bin_edge(bin) : 0ull;
+        break;
+      }
+    }
+  }
+  // broadcast from the holder lane (at most one)
+  const unsigned m = __ballot_sync(0xffffffffu, holder);
+  if (m == 0) return 0ull;
+  return __shfl_sync(0xffffffffu, res, __ffs(m) - 1);
+}
+
 template <int NINT>
 __device__ __forceinline__ uint64_t composite_word(const double* te, const uint64_t* tk, int i, int w) {
   if (w == 0) return ~(unsigned long long)__double_as_longlong(fabs(te[i]));
@@ -749,11 +799,15 @@ __device__ __noinline__ void compact_selection(const SweepParams& p, BatchShared
     out += total;
   }
   __syncthreads();
-  if (tid == 0) {
-    S.tkcnt = out;
-    const unsigned long long t = ~S.thr[0];
-    if (t > S.tau) S.tau = t;
-    atomicMax(p.tau_bits, t);
+  if (tid < 32) {
+    const unsigned long long th = hist_threshold(p.sel_hist, k);
+    if (tid == 0) {
+      S.tkcnt = out;
+      unsigned long long t = ~S.thr[0];
+      t = th > t ? th : t;
+      if (t > S.tau) S.tau = t;
+      atomicMax(p.tau_bits, t);
+    }
   }
   __syncthreads();
 }
@@ -1174,6 +1228,7 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(SweepParams p) {
       if (p.k > 0) {
         const unsigned long long eb = (unsigned long long)__double_as_longlong(fabs(e));
         if (eb >= tau) {
+          atomicAdd(&p.sel_hist[sel_bin(eb)], 1u);
           const int pos = atomicAdd(&S.tkcnt, 1);
           te[pos] = e;
           ta[pos] = a;

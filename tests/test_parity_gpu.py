@@ -174,7 +174,7 @@ def _golden(name):
     return P, E, meta, summ
 
 
-@pytest.mark.parametrize("name", ["cfg1", "cfg2"])
+@pytest.mark.parametrize("name", ["cfg1", "cfg2", "cfg4"])
 def test_golden_workloads(qp, name):
     P, E, meta, summ = _golden(name)
     h, eri = S.hamiltonian(meta["norb"], meta["rank"], meta["seed"])
