@@ -5,12 +5,12 @@
 
 namespace qp {
 
-template __global__ void prep_kernel<1>(SweepParams);
-template __global__ void prep_kernel<2>(SweepParams);
-template __global__ void batch_kernel<1, double>(SweepParams);
-template __global__ void batch_kernel<2, double>(SweepParams);
-template __global__ void grad_gen_kernel<1>(SweepParams);
-template __global__ void grad_gen_kernel<2>(SweepParams);
+template __global__ void prep_kernel<1>(const __grid_constant__ SweepParams);
+template __global__ void prep_kernel<2>(const __grid_constant__ SweepParams);
+template __global__ void batch_kernel<1, double>(const __grid_constant__ SweepParams);
+template __global__ void batch_kernel<2, double>(const __grid_constant__ SweepParams);
+template __global__ void grad_gen_kernel<1>(const __grid_constant__ SweepParams);
+template __global__ void grad_gen_kernel<2>(const __grid_constant__ SweepParams);
 
 cudaError_t launch_batch_grad(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
 

@@ -6,8 +6,8 @@
 
 namespace qp {
 
-template __global__ void batch_kernel<1, double, true>(SweepParams);
-template __global__ void batch_kernel<2, double, true>(SweepParams);
+template __global__ void batch_kernel<1, double, true>(const __grid_constant__ SweepParams);
+template __global__ void batch_kernel<2, double, true>(const __grid_constant__ SweepParams);
 
 cudaError_t launch_batch_grad(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st) {
   if (nint == 1) {

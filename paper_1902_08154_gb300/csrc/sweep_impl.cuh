@@ -159,7 +159,7 @@ __device__ __forceinline__ void for_buckets(uint64_t hm, int nel, int nbat, Fn&&
 // prep kernel: one CTA per generator slot of the wave
 // ---------------------------------------------------------------------------
 template <int NINT>
-__global__ void __launch_bounds__(kThreads) prep_kernel(SweepParams p) {
+__global__ void __launch_bounds__(kThreads) prep_kernel(const __grid_constant__ SweepParams p) {
   constexpr int NW = 2 * NINT;
   __shared__ int s_cnt[kMaxBatch + 2];
   __shared__ uint32_t s_dead[(kMaxBatch + 31) / 32];
@@ -356,7 +356,8 @@ struct BatchShared {
   // a group of J reaching every cell, processed by the whole CTA
   uint64_t gJw[kGroup][2 * NINT];
   NT gcj[kGroup];
-  int gX[kGroup][4], gT[kGroup][2], gnx[kGroup], gnt[kGroup];
+  uint32_t gX[kGroup], gT[kGroup];
+  int gnx[kGroup], gnt[kGroup];
   // two-hole batches: J = K + {x1, x2}; per particle orbital of each slot the
   // pair index tri(x, r) with the phase parity in bit 31
   int gRow[kGroup][kMaxOrb], gCol[kGroup][kMaxOrb];
@@ -421,17 +422,27 @@ __device__ __forceinline__ int pair_cell(int x, int y) {  // x != y virtual indi
   return hi * (hi - 1) / 2 + lo;
 }
 
-// Particles of J outside I, filtered to a spin, as orbitals.
-__device__ __forceinline__ int particles_of_spin(uint64_t part, int norb, int spin, int* out) {
-  int n = 0;
+// Small sets are packed 8 bits per entry into a 32-bit register (orbitals
+// < 128, spin-orbital codes < 256) with the count kept beside them: arrays
+// indexed at run time would live in local memory.
+__device__ __forceinline__ int pk(uint32_t v, int i) { return (int)((v >> (8 * i)) & 0xFFu); }
+
+// Particles of J outside I, filtered to a spin, as orbitals (packed).
+__device__ __forceinline__ uint32_t particles_of_spin(uint64_t part, int norb, int spin, int* n) {
+  uint32_t out = 0;
+  int k = 0;
 #pragma unroll
   for (int i = 0; i < 4; i++) {
     const int c = (int)((part >> (16 * i)) & 0xFFFF);
     if (c == 0xFFFF) continue;
     const int s = c >= norb;
-    if (s == spin) out[n++] = c - s * norb;
+    if (s == spin) {
+      out |= (uint32_t)(c - s * norb) << (8 * k);
+      k++;
+    }
   }
-  return n;
+  *n = k;
+  return out;
 }
 
 // Cells inside the particles of J (t = 2): visited by one thread.
@@ -439,20 +450,20 @@ template <int NINT, typename NT, typename Fn>
 __device__ __forceinline__ void for_subset_cells(const Batch& B, const BatchShared<NINT, NT>& S, int norb,
                                                  uint64_t part, Fn&& fn) {
   if (B.kind == 0) {
-    int P[4];
-    const int np = particles_of_spin(part, norb, B.sa, P);
-    for (int i = 0; i < np; i++) fn(S.vidx[B.sa][P[i]]);
+    int np;
+    const uint32_t P = particles_of_spin(part, norb, B.sa, &np);
+    for (int i = 0; i < np; i++) fn(S.vidx[B.sa][pk(P, i)]);
   } else if (B.kind == 1) {
-    int P[4];
-    const int np = particles_of_spin(part, norb, B.sa, P);
+    int np;
+    const uint32_t P = particles_of_spin(part, norb, B.sa, &np);
     for (int i = 0; i < np; i++)
-      for (int j = i + 1; j < np; j++) fn(pair_cell(S.vidx[B.sa][P[i]], S.vidx[B.sa][P[j]]));
+      for (int j = i + 1; j < np; j++) fn(pair_cell(S.vidx[B.sa][pk(P, i)], S.vidx[B.sa][pk(P, j)]));
   } else {
-    int Pa[4], Pb[4];
-    const int na = particles_of_spin(part, norb, 0, Pa);
-    const int nb = particles_of_spin(part, norb, 1, Pb);
+    int na, nb;
+    const uint32_t Pa = particles_of_spin(part, norb, 0, &na);
+    const uint32_t Pb = particles_of_spin(part, norb, 1, &nb);
     for (int i = 0; i < na; i++)
-      for (int j = 0; j < nb; j++) fn(S.vidx[0][Pa[i]] * S.nv[1] + S.vidx[1][Pb[j]]);
+      for (int j = 0; j < nb; j++) fn(S.vidx[0][pk(Pa, i)] * S.nv[1] + S.vidx[1][pk(Pb, j)]);
   }
 }
 
@@ -462,32 +473,32 @@ template <int NINT, typename NT, typename Fn>
 __device__ __forceinline__ void for_row_cells(const Batch& B, const BatchShared<NINT, NT>& S, int norb,
                                               uint64_t part, int lane, Fn&& fn) {
   if (B.kind == 1) {
-    int P[4];
-    const int np = particles_of_spin(part, norb, B.sa, P);
+    int np;
+    const uint32_t P = particles_of_spin(part, norb, B.sa, &np);
     const int nv = S.nv[B.sa];
     for (int i = 0; i < np; i++) {
-      const int x = S.vidx[B.sa][P[i]];
+      const int x = S.vidx[B.sa][pk(P, i)];
       for (int y = lane; y < nv; y += 32) {
         if (y == x) continue;
         bool dup = false;  // pair {P[j], P[i]}, j < i, was visited from P[j]
-        for (int j = 0; j < i; j++) dup |= (S.vidx[B.sa][P[j]] == y);
+        for (int j = 0; j < i; j++) dup |= (S.vidx[B.sa][pk(P, j)] == y);
         if (!dup) fn(pair_cell(x, y));
       }
     }
   } else {  // kind 2
-    int Pa[4], Pb[4];
-    const int na = particles_of_spin(part, norb, 0, Pa);
-    const int nb = particles_of_spin(part, norb, 1, Pb);
+    int na, nb;
+    const uint32_t Pa = particles_of_spin(part, norb, 0, &na);
+    const uint32_t Pb = particles_of_spin(part, norb, 1, &nb);
     const int nv0 = S.nv[0], nv1 = S.nv[1];
     for (int i = 0; i < na; i++) {
-      const int x = S.vidx[0][Pa[i]];
+      const int x = S.vidx[0][pk(Pa, i)];
       for (int y = lane; y < nv1; y += 32) fn(x * nv1 + y);
     }
     for (int j = 0; j < nb; j++) {
-      const int y = S.vidx[1][Pb[j]];
+      const int y = S.vidx[1][pk(Pb, j)];
       for (int x = lane; x < nv0; x += 32) {
         bool dup = false;  // rows of Pa were visited above
-        for (int i = 0; i < na; i++) dup |= (S.vidx[0][Pa[i]] == x);
+        for (int i = 0; i < na; i++) dup |= (S.vidx[0][pk(Pa, i)] == x);
         if (!dup) fn(x * nv1 + y);
       }
     }
@@ -495,23 +506,28 @@ __device__ __forceinline__ void for_row_cells(const Batch& B, const BatchShared<
 }
 
 // X = (particles of J) + (holes of H that J keeps); T = holes of J not in H.
+// Both sets are spin-orbital codes, packed (see pk).
 template <int NINT, typename NT>
 __device__ __forceinline__ void excitation_sets(const Batch& B, const BatchShared<NINT, NT>& S, uint64_t part,
-                                                uint64_t hm, int* X, int* nx, int* T, int* nt) {
+                                                uint64_t hm, uint32_t* X, int* nx, uint32_t* T, int* nt) {
   int a = 0, b = 0;
+  uint32_t xs = 0, ts = 0;
+#pragma unroll
   for (int i = 0; i < 4; i++) {
-    const int c = (int)((part >> (16 * i)) & 0xFFFF);
-    if (c != 0xFFFF && a < 4) X[a++] = c;
+    const uint32_t c = (uint32_t)((part >> (16 * i)) & 0xFFFF);
+    if (c != 0xFFFFu && a < 4) xs |= c << (8 * a++);
   }
-  if (!((hm >> B.ia) & 1ull) && a < 4) X[a++] = B.ca;
-  if (B.h == 2 && !((hm >> B.ib) & 1ull) && a < 4) X[a++] = B.cb;
+  if (!((hm >> B.ia) & 1ull) && a < 4) xs |= (uint32_t)B.ca << (8 * a++);
+  if (B.h == 2 && !((hm >> B.ib) & 1ull) && a < 4) xs |= (uint32_t)B.cb << (8 * a++);
   uint64_t tm = hm & ~B.hm;
   while (tm && b < 2) {
     const int i = __ffsll((long long)tm) - 1;
     tm &= tm - 1;
-    T[b++] = S.occ[i];
+    ts |= (uint32_t)S.occ[i] << (8 * b++);
   }
+  *X = xs;
   *nx = a;
+  *T = ts;
   *nt = b;
 }
 
@@ -519,21 +535,20 @@ __device__ __forceinline__ void excitation_sets(const Batch& B, const BatchShare
 // holes(J -> alpha) = X - R, particles = T + (R - X).
 // Kept out of line: one copy serves every caller, which keeps the batch
 // kernel's code small enough for the instruction cache.
+// Jw points to the record's words in global or shared memory; the sets are
+// packed codes; nothing is passed through local memory.
 template <int NINT, typename NT>
-__device__ __noinline__ NT element(const SweepParams& p, const uint64_t* Jw, const int* X, int nx, const int* T,
-                                   int nt, int r, int s) {
-  const int norb = p.norb;
-  const NT* eri = numer_eri<NT>(p);
-  const NT* hh = numer_h<NT>(p);
+__device__ __noinline__ NT element(const NT* eri, const NT* hh, int norb, const uint64_t* Jw, uint32_t X, int nx,
+                                   uint32_t T, int nt, int r, int s) {
   int ho[2], pa[2], nh = 0, npp = 0;
   bool r_in = false, s_in = false;
   for (int i = 0; i < nx; i++) {
-    const int x = X[i];
+    const int x = pk(X, i);
     r_in |= (x == r);
     s_in |= (x == s);
     if (x != r && x != s && nh < 2) ho[nh++] = x;
   }
-  for (int i = 0; i < nt && npp < 2; i++) pa[npp++] = T[i];
+  for (int i = 0; i < nt && npp < 2; i++) pa[npp++] = pk(T, i);
   if (!r_in && npp < 2) pa[npp++] = r;
   if (s >= 0 && !s_in && npp < 2) pa[npp++] = s;
   if (nh == 0 || nh != npp) return NT(0);  // not reached: such cells are banned
@@ -582,18 +597,17 @@ __device__ __noinline__ NT element(const SweepParams& p, const uint64_t* Jw, con
 // (symmetric halves) and the packed integrals, with the same case analysis
 // as element().
 template <int NINT>
-__device__ __noinline__ void element_grad(const SweepParams& p, const uint64_t* Jw, const int* X, int nx,
-                                          const int* T, int nt, int r, int s, double w) {
-  const int norb = p.norb;
+__device__ __noinline__ void element_grad(double* g_dh, double* g_deri, int norb, const uint64_t* Jw, uint32_t X,
+                                          int nx, uint32_t T, int nt, int r, int s, double w) {
   int ho[2], pa[2], nh = 0, npp = 0;
   bool r_in = false, s_in = false;
   for (int i = 0; i < nx; i++) {
-    const int x = X[i];
+    const int x = pk(X, i);
     r_in |= (x == r);
     s_in |= (x == s);
     if (x != r && x != s && nh < 2) ho[nh++] = x;
   }
-  for (int i = 0; i < nt && npp < 2; i++) pa[npp++] = T[i];
+  for (int i = 0; i < nt && npp < 2; i++) pa[npp++] = pk(T, i);
   if (!r_in && npp < 2) pa[npp++] = r;
   if (s >= 0 && !s_in && npp < 2) pa[npp++] = s;
   if (nh == 0 || nh != npp) return;
@@ -602,8 +616,8 @@ __device__ __noinline__ void element_grad(const SweepParams& p, const uint64_t* 
     const uint64_t* sw = Jw + sp * NINT;
     const int lo = a < b ? a : b, hi = a < b ? b : a;
     const double ws = (count_between<NINT>(sw, lo, hi) & 1) ? -w : w;
-    atomicAdd(&p.g_dh[a * norb + b], 0.5 * ws);
-    atomicAdd(&p.g_dh[b * norb + a], 0.5 * ws);
+    atomicAdd(&g_dh[a * norb + b], 0.5 * ws);
+    atomicAdd(&g_dh[b * norb + a], 0.5 * ws);
 #pragma unroll
     for (int t = 0; t < 2; t++) {
 #pragma unroll
@@ -612,8 +626,8 @@ __device__ __noinline__ void element_grad(const SweepParams& p, const uint64_t* 
         while (bits) {
           const int q = 64 * wd + __ffsll((long long)bits) - 1;
           bits &= bits - 1;
-          atomicAdd(&p.g_deri[eri_index(a, b, q, q)], ws);
-          if (t == sp) atomicAdd(&p.g_deri[eri_index(a, q, q, b)], -ws);
+          atomicAdd(&g_deri[eri_index(a, b, q, q)], ws);
+          if (t == sp) atomicAdd(&g_deri[eri_index(a, q, q, b)], -ws);
         }
       }
     }
@@ -633,8 +647,8 @@ __device__ __noinline__ void element_grad(const SweepParams& p, const uint64_t* 
   const int n2 = (s2 == s1) ? count_between<NINT>(w1, h2 < p2 ? h2 : p2, h2 < p2 ? p2 : h2)
                             : count_between<NINT>(Jw + s2 * NINT, h2 < p2 ? h2 : p2, h2 < p2 ? p2 : h2);
   const double ws = ((n1 + n2) & 1) ? -w : w;
-  atomicAdd(&p.g_deri[eri_index(h1, p1, h2, p2)], ws);
-  if (s1 == s2) atomicAdd(&p.g_deri[eri_index(h1, p2, h2, p1)], -ws);
+  atomicAdd(&g_deri[eri_index(h1, p1, h2, p2)], ws);
+  if (s1 == s2) atomicAdd(&g_deri[eri_index(h1, p2, h2, p1)], -ws);
 }
 
 // w * dW(x, y)/d(theta), W(x, y) = (xx|yy) - delta_spin (xy|yx)
@@ -813,13 +827,14 @@ __device__ __noinline__ void compact_selection(const SweepParams& p, BatchShared
 }
 
 template <int NINT, typename NT, bool GRAD = false>
-__global__ void __launch_bounds__(kThreads, 3) batch_kernel(SweepParams p) {
+__global__ void __launch_bounds__(kThreads, 3) batch_kernel(const __grid_constant__ SweepParams p) {
   constexpr int NW = 2 * NINT;
   extern __shared__ __align__(16) unsigned char dyn[];
   double* A = reinterpret_cast<double*>(dyn);
   uint32_t* ban = reinterpret_cast<uint32_t*>(A + p.max_cells);
   __shared__ BatchShared<NINT, NT> S;
   const NT* eri_n = numer_eri<NT>(p);
+  const NT* h_n = numer_h<NT>(p);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int norb = p.norb, nel = p.nel, nbat = p.nbat;
@@ -995,17 +1010,17 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(SweepParams p) {
           }
         } else if (t == 0 && hm == B.hm) {  // J = I - H + X with X a cell: alpha is internal
           const uint64_t part = rp[r];
-          int P0[4], P1[4], c;
+          int n0, n1, c;
           if (B.kind == 0) {
-            particles_of_spin(part, norb, B.sa, P0);
-            c = S.vidx[B.sa][P0[0]];
+            const uint32_t P0 = particles_of_spin(part, norb, B.sa, &n0);
+            c = S.vidx[B.sa][pk(P0, 0)];
           } else if (B.kind == 1) {
-            particles_of_spin(part, norb, B.sa, P0);
-            c = pair_cell(S.vidx[B.sa][P0[0]], S.vidx[B.sa][P0[1]]);
+            const uint32_t P0 = particles_of_spin(part, norb, B.sa, &n0);
+            c = pair_cell(S.vidx[B.sa][pk(P0, 0)], S.vidx[B.sa][pk(P0, 1)]);
           } else {
-            particles_of_spin(part, norb, 0, P0);
-            particles_of_spin(part, norb, 1, P1);
-            c = S.vidx[0][P0[0]] * S.nv[1] + S.vidx[1][P1[0]];
+            const uint32_t P0 = particles_of_spin(part, norb, 0, &n0);
+            const uint32_t P1 = particles_of_spin(part, norb, 1, &n1);
+            c = S.vidx[0][pk(P0, 0)] * S.nv[1] + S.vidx[1][pk(P1, 0)];
           }
           atomicOr(&ban[c >> 5], 1u << (c & 31));
         }
@@ -1055,9 +1070,15 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(SweepParams p) {
 #pragma unroll
           for (int w = 0; w < NW; w++) S.gJw[tid][w] = rw[(size_t)r * NW + w];
           S.gcj[tid] = (NT)rc[r];
-          excitation_sets<NINT, NT>(B, S, rp[r], rh[r], S.gX[tid], &S.gnx[tid], S.gT[tid], &S.gnt[tid]);
+          uint32_t xs, ts;
+          int nxs, nts;
+          excitation_sets<NINT, NT>(B, S, rp[r], rh[r], &xs, &nxs, &ts, &nts);
+          S.gX[tid] = xs;
+          S.gT[tid] = ts;
+          S.gnx[tid] = nxs;
+          S.gnt[tid] = nts;
           if (B.h == 2) {
-            const int a = S.gX[tid][0], bb = S.gX[tid][1];
+            const int a = pk(xs, 0), bb = pk(xs, 1);
             const int x1 = a < bb ? a : bb, x2 = a < bb ? bb : a;
             S.gx1[tid] = x1;
             S.gx2[tid] = x2;
@@ -1123,7 +1144,7 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(SweepParams p) {
                 general = false;
               }
             }
-            if (general) v = element<NINT, NT>(p, S.gJw[j], S.gX[j], S.gnx[j], S.gT[j], S.gnt[j], rcode, scode);
+            if (general) v = element<NINT, NT>(eri_n, h_n, norb, S.gJw[j], S.gX[j], S.gnx[j], S.gT[j], S.gnt[j], rcode, scode);
             acc += (double)(S.gcj[j] * v);
           }
           A[c] += acc;
@@ -1134,40 +1155,38 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(SweepParams p) {
       // J reaching a row of cells: one warp each
       for (int j = warp; j < S.n1; j += kWarps) {
         const int r = S.L1[j];
-        uint64_t Jw[NW];
-#pragma unroll
-        for (int w = 0; w < NW; w++) Jw[w] = rw[(size_t)r * NW + w];
+        const uint64_t* Jw = rw + (size_t)r * NW;
         const NT cj = (NT)rc[r];
         const uint64_t part = rp[r];
-        int X[4], T[2], nx, nt;
-        excitation_sets<NINT, NT>(B, S, part, rh[r], X, &nx, T, &nt);
+        uint32_t X, T;
+        int nx, nt;
+        excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
         for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
           if ((ban[c >> 5] >> (c & 31)) & 1u) return;
           int ro, so, x, y;
           cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
           const int rcode = B.sa * norb + ro;
           const int scode = B.sb * norb + so;
-          atomicAdd(&A[c], (double)(cj * element<NINT, NT>(p, Jw, X, nx, T, nt, rcode, scode)));
+          atomicAdd(&A[c], (double)(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode)));
           con++;
         });
       }
       // J reaching a few cells: one thread each
       for (int j = tid; j < S.n2; j += kThreads) {
         const int r = S.L2[j];
-        uint64_t Jw[NW];
-#pragma unroll
-        for (int w = 0; w < NW; w++) Jw[w] = rw[(size_t)r * NW + w];
+        const uint64_t* Jw = rw + (size_t)r * NW;
         const NT cj = (NT)rc[r];
         const uint64_t part = rp[r];
-        int X[4], T[2], nx, nt;
-        excitation_sets<NINT, NT>(B, S, part, rh[r], X, &nx, T, &nt);
+        uint32_t X, T;
+        int nx, nt;
+        excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
         for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
           if ((ban[c >> 5] >> (c & 31)) & 1u) return;
           int ro, so, x, y;
           cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
           const int rcode = B.sa * norb + ro;
           const int scode = (B.h == 2) ? B.sb * norb + so : -1;
-          atomicAdd(&A[c], (double)(cj * element<NINT, NT>(p, Jw, X, nx, T, nt, rcode, scode)));
+          atomicAdd(&A[c], (double)(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode)));
           con++;
         });
       }
@@ -1215,11 +1234,11 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(SweepParams p) {
       if (((unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull) < 0x3D06849B86A12B9Bull) acc_tiny++;
       const unsigned long long db = (unsigned long long)__double_as_longlong(fabs(D));
       acc_min = db < acc_min ? db : acc_min;
-      uint64_t key[NW];
+      uint64_t key[NW];  // alpha's words; selects keep them in registers
+      const int kwr = B.sa * NINT + (ro >> 6), kws = (B.h == 2) ? B.sb * NINT + (so >> 6) : -1;
 #pragma unroll
-      for (int w = 0; w < NW; w++) key[w] = S.kbase[w];
-      key[B.sa * NINT + (ro >> 6)] |= 1ull << (ro & 63);
-      if (B.h == 2) key[B.sb * NINT + (so >> 6)] |= 1ull << (so & 63);
+      for (int w = 0; w < NW; w++)
+        key[w] = S.kbase[w] | (w == kwr ? 1ull << (ro & 63) : 0ull) | (w == kws ? 1ull << (so & 63) : 0ull);
       uint64_t hk = 0;
 #pragma unroll
       for (int w = 0; w < NW; w++) hk = splitmix64(hk ^ key[w]);
@@ -1303,49 +1322,46 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(SweepParams p) {
         __syncthreads();
         for (int j = 0; j < S.n0; j++) {
           const int r = S.L0[j];
-          uint64_t Jw[NW];
-#pragma unroll
-          for (int w = 0; w < NW; w++) Jw[w] = rw[(size_t)r * NW + w];
+          const uint64_t* Jw = rw + (size_t)r * NW;
           const double cj = rc[r];
-          int X[4], T[2], nx, nt;
-          excitation_sets<NINT, NT>(B, S, rp[r], rh[r], X, &nx, T, &nt);
+          uint32_t X, T;
+          int nx, nt;
+          excitation_sets<NINT, NT>(B, S, rp[r], rh[r], &X, &nx, &T, &nt);
           for (int c = tid; c < B.ncell; c += kThreads) {
             if ((ban[c >> 5] >> (c & 31)) & 1u) continue;
             int ro, so, x, y;
             cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-            element_grad<NINT>(p, Jw, X, nx, T, nt, B.sa * norb + ro, (B.h == 2) ? B.sb * norb + so : -1, cj * A[c]);
+            element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, (B.h == 2) ? B.sb * norb + so : -1, cj * A[c]);
           }
         }
         for (int j = warp; j < S.n1; j += kWarps) {
           const int r = S.L1[j];
-          uint64_t Jw[NW];
-#pragma unroll
-          for (int w = 0; w < NW; w++) Jw[w] = rw[(size_t)r * NW + w];
+          const uint64_t* Jw = rw + (size_t)r * NW;
           const double cj = rc[r];
           const uint64_t part = rp[r];
-          int X[4], T[2], nx, nt;
-          excitation_sets<NINT, NT>(B, S, part, rh[r], X, &nx, T, &nt);
+          uint32_t X, T;
+          int nx, nt;
+          excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
           for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
             if ((ban[c >> 5] >> (c & 31)) & 1u) return;
             int ro, so, x, y;
             cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-            element_grad<NINT>(p, Jw, X, nx, T, nt, B.sa * norb + ro, B.sb * norb + so, cj * A[c]);
+            element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, B.sb * norb + so, cj * A[c]);
           });
         }
         for (int j = tid; j < S.n2; j += kThreads) {
           const int r = S.L2[j];
-          uint64_t Jw[NW];
-#pragma unroll
-          for (int w = 0; w < NW; w++) Jw[w] = rw[(size_t)r * NW + w];
+          const uint64_t* Jw = rw + (size_t)r * NW;
           const double cj = rc[r];
           const uint64_t part = rp[r];
-          int X[4], T[2], nx, nt;
-          excitation_sets<NINT, NT>(B, S, part, rh[r], X, &nx, T, &nt);
+          uint32_t X, T;
+          int nx, nt;
+          excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
           for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
             if ((ban[c >> 5] >> (c & 31)) & 1u) return;
             int ro, so, x, y;
             cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-            element_grad<NINT>(p, Jw, X, nx, T, nt, B.sa * norb + ro, (B.h == 2) ? B.sb * norb + so : -1,
+            element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, (B.h == 2) ? B.sb * norb + so : -1,
                                cj * A[c]);
           });
         }
@@ -1395,7 +1411,7 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(SweepParams p) {
 // Per generator: wH * dH_II + sum_{s,x} wF[s][x] * dF^I_s(x), with
 // F^I_s(x) = h_xx + sum_{j in I} W(x, j) and H_II = sum_i h_ii + sum_{i<j} W(i, j).
 template <int NINT>
-__global__ void __launch_bounds__(kThreads) grad_gen_kernel(SweepParams p) {
+__global__ void __launch_bounds__(kThreads) grad_gen_kernel(const __grid_constant__ SweepParams p) {
   constexpr int NW = 2 * NINT;
   __shared__ int s_occ[kMaxElec];
   const int g = blockIdx.x, tid = threadIdx.x, norb = p.norb, nel = p.nel;

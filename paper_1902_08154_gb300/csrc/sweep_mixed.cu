@@ -4,8 +4,8 @@
 
 namespace qp {
 
-template __global__ void batch_kernel<1, float>(SweepParams);
-template __global__ void batch_kernel<2, float>(SweepParams);
+template __global__ void batch_kernel<1, float>(const __grid_constant__ SweepParams);
+template __global__ void batch_kernel<2, float>(const __grid_constant__ SweepParams);
 
 cudaError_t launch_batch_mixed(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st) {
   if (nint == 1) {
