@@ -39,15 +39,19 @@ METRIC = "EN-PT2 perturbers/s and generators/s on 1 GB300 vs plain FP64 GPU swee
 UNIT = "perturbers/s"
 L2_FLUSH_BYTES = 256 << 20
 
-# Algorithmic work model of the sweep kernel (lane-operations), see the
-# roofline section of the design notes: per connection (J, alpha) one
-# excitation/phase evaluation, one or two packed-integral gathers and one
-# FMA; per perturber one incremental diagonal, one division, the digest hash
-# and the selection compare; per coarse-filter pair test 2*nint XOR+POPC.
-OPS_PER_CONNECTION = 24
-OPS_PER_PERTURBER = 64
-# ALU issue peak: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz
-ALU_PEAK_GOPS = 152 * 4 * 32 * 2.07
+# The sweep is bound by the FP64 pipe, the scarce unit of this GPU.  The
+# algorithmic FP64 work (an FMA counted as one operation): per connection
+# (J, alpha) the one FMA of A_alpha += c_J <J|H|alpha>; per perturber the
+# incremental H_aa (3 adds), D = E0 - H_aa, 1/D, q = A/D, e = A q and the two
+# accumulations of e and q^2.
+FP64_OPS_PER_CONNECTION = 1
+FP64_OPS_PER_PERTURBER = 9
+# FP64 peak: 1.25 TFLOP/s nominal (FMA = 2 flops) at 2.07 GHz is 2 FP64
+# lanes per clock per SM: 152 SMs x 2 x 2.07 GHz operations per second
+FP64_PEAK_GOPS = 152 * 2 * 2.07
+# DRAM bytes (read + write) of the sweep kernels over one sweep of the bench
+# workload, from one ncu capture of the current kernels (None until taken)
+TRAFFIC_BYTES_PER_SWEEP = None
 
 
 def load_workload(name=WORKLOAD):
@@ -235,6 +239,52 @@ def batched_leg(qp, torch, device, log=None):
             "inputs_seconds": t_inputs}
 
 
+def wide_leg(qp, torch, device, flush):
+    """The 128-orbital workload (two words per spin; 14+14 electrons, Cholesky
+    rank 192, 10^5 determinants, k = N_det): the plain FP64 sweep and the
+    mixed-precision sweep on the same inputs, one timed sweep each after a
+    warm-up on the first 3000 determinants.  The mixed error is stated
+    against the FP64 GPU sweep and, on the first 10 determinants of the same
+    Psi0, against the oracle's stored sweep."""
+    from paper_1902_08154_gb300 import synthetic as S
+
+    spec = S.CFG3
+    t0 = time.perf_counter()
+    h, eri, dets, coefs, e0 = S.cfg3_instance()
+    _, _, d10, c10, _ = S.cfg3_instance(10)
+    t_in = time.perf_counter() - t0
+    ref10 = json.loads(str(np.load(os.path.join(ROOT, "tests", "golden", "cfg3r_expected.npz"))["summary"]))
+    hd, ed = torch.from_numpy(h).to(device), torch.from_numpy(eri).to(device)
+    dd, cd = torch.from_numpy(dets.view(np.int64)).to(device), torch.from_numpy(coefs).to(device)
+    d10d, c10d = torch.from_numpy(d10.view(np.int64)).to(device), torch.from_numpy(c10).to(device)
+    n = len(dets)
+    out = {"workload": f"norb {spec['norb']}, {spec['nalpha']}+{spec['nbeta']} electrons, Cholesky rank "
+                       f"{spec['rank']}, seed {spec['seed']}, N_det {n}, k = N_det",
+           "inputs_seconds": t_in}
+    for name, prec in (("fp64", qp.QP_FP64), ("mixed", qp.QP_MIXED)):
+        pt2 = qp.PT2(spec["norb"], spec["nalpha"], spec["nbeta"], hd, ed, precision=prec)
+        pt2.eval(dd[:3000], cd[:3000], e0, 3000)
+        flush.zero_()
+        torch.cuda.synchronize()
+        r = pt2.eval(dd, cd, e0, n)
+        ms = qp.qp_pt2_last_timings(pt2.ctx)[1]
+        r10 = pt2.eval(d10d, c10d, e0, 20)
+        pt2.close()
+        out[name] = {"ms": ms, "value": r["n_perturbers"] / (ms * 1e-3), "unit": UNIT,
+                     "generators_per_s": n / (ms * 1e-3), "e_pt2": r["e_pt2"], "n_perturbers": r["n_perturbers"],
+                     "n_connections": r["n_connections"], "digest": [str(x) for x in r["digest"]],
+                     "head10_abs_err_vs_oracle": abs(r10["e_pt2"] - ref10["e_pt2"]),
+                     "head10_perturbers_match_oracle": r10["n_perturbers"] == ref10["n_perturbers"]}
+    f, m = out["fp64"], out["mixed"]
+    out["mixed_abs_err_vs_fp64_gpu"] = abs(m["e_pt2"] - f["e_pt2"])
+    out["same_perturber_set"] = f["digest"] == m["digest"] and f["n_perturbers"] == m["n_perturbers"]
+    out["mixed_speedup_vs_fp64"] = f["ms"] / m["ms"]
+    out["stated_tolerance"] = 1e-6
+    del hd, ed, dd, cd
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gb300(args):
     import torch
 
@@ -383,15 +433,20 @@ def run_gb300(args):
     if not args.no_batched and world == 1:
         batched = batched_leg(qp, torch, device)
 
+    wide = None
+    if not args.no_wide and world == 1:
+        wide = wide_leg(qp, torch, device, flush)
+
     # roofline of the dominant kernel (the persistent sweep)
     ms_sweep = statistics.mean(sweep_ms)
-    ops = (OPS_PER_CONNECTION * res["n_connections"] + OPS_PER_PERTURBER * res["n_perturbers"]
-           + 4 * nint * ndet * ndet // max(world, 1))
+    ops = FP64_OPS_PER_CONNECTION * res["n_connections"] + FP64_OPS_PER_PERTURBER * res["n_perturbers"]
     achieved = ops / (ms_sweep * 1e-3) / 1e9
-    roof = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_GOPS, "unit": "Gop/s",
-            "frac": achieved / ALU_PEAK_GOPS, "traffic": None, "kernel": "qp::prep_kernel + qp::batch_kernel (all waves)",
-            "kernel_ms": ms_sweep, "call_ms": statistics.mean(call_ms), "peak_source": "derived: 152 SMs x 128 lanes/clk x 2.07 GHz",
-            "ops_model": f"{OPS_PER_CONNECTION}/connection + {OPS_PER_PERTURBER}/perturber + 4*nint/pair test"}
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "G FP64 op/s",
+            "frac": achieved / FP64_PEAK_GOPS, "traffic": TRAFFIC_BYTES_PER_SWEEP,
+            "kernel": "qp::prep_kernel + qp::batch_kernel (all waves of one sweep)",
+            "kernel_ms": ms_sweep, "call_ms": statistics.mean(call_ms),
+            "peak_source": "derived from the nominal FP64 rate: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz",
+            "ops_model": f"{FP64_OPS_PER_CONNECTION} FP64 op/connection + {FP64_OPS_PER_PERTURBER} FP64 op/perturber"}
     if rank != 0:
         return 0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -401,7 +456,7 @@ def run_gb300(args):
             "rpt2": qp.rpt2(res, e0),
             "e2e": e2e,
             "gpu_launches": launches, "roofline": roof, "clocks": ck, "mixed_precision": mixed,
-            "batched": batched}
+            "batched": batched, "workload_128_orbitals": wide}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(meta, h, eri, dets, coefs, e0)
     print(json.dumps(line), flush=True)
@@ -421,6 +476,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg (profiling runs)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-instance batched leg")
+    ap.add_argument("--no-wide", action="store_true", help="skip the 128-orbital, 10^5-determinant leg")
     ap.add_argument("--ndet", type=int, default=0,
                     help="profiling runs only: sweep the first NDET determinants of the stored Psi0")
     args = ap.parse_args()

@@ -313,3 +313,26 @@ def batch_instance(spec):
     coefs = random_coefs(len(dets), spec["seed"] + 2, decay=4.0 / len(dets))
     e0 = diagonal_lower_bound(h, eri, spec["nalpha"] + spec["nbeta"]) - 1.0
     return h, eri, dets, coefs, e0
+
+
+# ---------------------------------------------------------------------------
+# The 128-orbital workload (two words per spin) for the mixed-precision
+# comparison: 14 + 14 electrons, Cholesky rank 192, 10^5 determinants.
+# ---------------------------------------------------------------------------
+CFG3 = dict(norb=128, nalpha=14, nbeta=14, rank=192, ndet=100000, seed=2)
+
+
+def cfg3_instance(ndet=None, spec=CFG3):
+    """Inputs (h, eri, dets, coefs, e0) of the 128-orbital workload.  Psi0 is
+    HF plus distinct determinants with 1..4 electrons moved to random virtual
+    orbitals, with coefficients decaying along the list (a stand-in for a
+    CIPSI-grown Psi0, which is out of reach of the CPU oracle at this size);
+    E0 lies below every diagonal energy of the space.  ``ndet`` keeps the
+    first ndet determinants of the same list, with a coefficient vector of
+    that length."""
+    h, eri = hamiltonian_fast(spec["norb"], spec["rank"], spec["seed"])
+    n = spec["ndet"] if ndet is None else min(int(ndet), spec["ndet"])
+    dets = excited_dets_fast(spec["norb"], spec["nalpha"], spec["nbeta"], spec["ndet"], spec["seed"] + 1)[:n]
+    coefs = random_coefs(n, spec["seed"] + 2, decay=4.0 / n)
+    e0 = diagonal_lower_bound(h, eri, spec["nalpha"] + spec["nbeta"]) - 1.0
+    return h, eri, dets, coefs, e0

@@ -19,6 +19,9 @@ not available; shapes follow the paper's CAS-sized active spaces):
         determinants grown from a 1250-determinant seed space by three CIPSI
         doublings (top |e_alpha| selection), coefficients from Davidson to a
         residual below 1e-10.  Expected results with k = 2 * 10^4.
+  cfg3r: the first 10 determinants of the 128-orbital workload
+        (``synthetic.cfg3_instance``; 14+14 electrons, Cholesky rank 192),
+        expected sweep with k = 20 (totals and per-generator arrays).
 
 Files: ``<cfg>_psi0.npz`` (dets, coefs, e0 and metadata) and
 ``<cfg>_expected.npz`` (totals, per-generator arrays by rank, selection).
@@ -44,7 +47,26 @@ CONFIGS = {
     "cfg1": dict(norb=16, nalpha=4, nbeta=4, rank=32, seed=0, ndet=50, k=100, grow=False),
     "cfg2": dict(norb=64, nalpha=10, nbeta=10, rank=96, seed=1, ndet=10000, k=20000, grow=True),
     "cfg4": dict(norb=48, nalpha=8, nbeta=8, rank=72, seed=3, ndet=20000, k=40000, grow=True, gradient=True),
+    # the head (10 determinants) of the 128-orbital workload's Psi0
+    "cfg3r": dict(norb=128, nalpha=14, nbeta=14, rank=192, seed=2, ndet=10, k=20, grow=False, instance="cfg3"),
 }
+
+
+def make_cfg3r(name, cfg):
+    """Expected sweep of the head of the 128-orbital workload.  Its integrals
+    come from a matrix product whose last bits may depend on the BLAS, so
+    only the totals are stored; a consumer regenerates the inputs and
+    compares energies at the stated tolerance."""
+    t0 = time.time()
+    h, eri, dets, c, e0 = S.cfg3_instance(cfg["ndet"])
+    ham = oracle.Hamiltonian(cfg["norb"], cfg["nalpha"], cfg["nbeta"], h, eri)
+    out = ham.sweep(dets, c, e0, k=cfg["k"])
+    log(f"{name}: sweep E_PT2={out['e_pt2']:.12f} |A|={out['n_perturbers']} in {time.time() - t0:.1f}s")
+    summary = {k: v for k, v in out.items() if not isinstance(v, np.ndarray)}
+    summary["digest"] = [str(x) for x in summary["digest"]]
+    np.savez_compressed(os.path.join(HERE, f"{name}_expected.npz"), sel_e=out["sel_e"],
+                        eps_by_rank=out["eps_by_rank"], na_by_rank=out["na_by_rank"],
+                        summary=json.dumps(summary), meta=json.dumps(cfg))
 
 
 def log(msg):
@@ -53,6 +75,8 @@ def log(msg):
 
 def make(name, mem_budget=12 << 30):
     cfg = CONFIGS[name]
+    if cfg.get("instance") == "cfg3":
+        return make_cfg3r(name, cfg)
     t0 = time.time()
     h, eri = S.hamiltonian(cfg["norb"], cfg["rank"], cfg["seed"])
     ham = oracle.Hamiltonian(cfg["norb"], cfg["nalpha"], cfg["nbeta"], h, eri)
