@@ -50,8 +50,8 @@ FP64_OPS_PER_PERTURBER = 9
 # lanes per clock per SM: 152 SMs x 2 x 2.07 GHz operations per second
 FP64_PEAK_GOPS = 152 * 2 * 2.07
 # DRAM bytes (read + write) of the sweep kernels over one sweep of the bench
-# workload, from one ncu capture of the current kernels (None until taken)
-TRAFFIC_BYTES_PER_SWEEP = None
+# workload (prep 3.09 + 12.19 GB, batch 4.55 + 0.25 GB), from one ncu capture
+TRAFFIC_BYTES_PER_SWEEP = 20.1e9
 
 
 def load_workload(name=WORKLOAD):
@@ -442,7 +442,7 @@ def run_gb300(args):
     ops = FP64_OPS_PER_CONNECTION * res["n_connections"] + FP64_OPS_PER_PERTURBER * res["n_perturbers"]
     achieved = ops / (ms_sweep * 1e-3) / 1e9
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "G FP64 op/s",
-            "frac": achieved / FP64_PEAK_GOPS, "traffic": TRAFFIC_BYTES_PER_SWEEP,
+            "frac": achieved / FP64_PEAK_GOPS, "traffic": None if args.ndet else TRAFFIC_BYTES_PER_SWEEP,
             "kernel": "qp::prep_kernel + qp::batch_kernel (all waves of one sweep)",
             "kernel_ms": ms_sweep, "call_ms": statistics.mean(call_ms),
             "peak_source": "derived from the nominal FP64 rate: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz",
