@@ -56,6 +56,7 @@ struct GenMeta {
   int g;                    // rank of the generator (-1: empty slot)
   int nrec;                 // coarse-filter records
   double hii;               // <I|H|I>
+  double cI;                // c_I
   int occ[kMaxElec];        // spin-orbital codes s*norb+q of I, ordered
   double F[2][kMaxOrb];     // Fock diagonal of I
 };

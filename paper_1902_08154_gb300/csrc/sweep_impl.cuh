@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(const __grid_constant__ 
       for (int q = 0; q < norb; q++)
         if ((sI[s * NINT + (q >> 6)] >> (q & 63)) & 1ull) s_occ[n++] = s * norb + q;
     M->g = g;
+    M->cI = p.coefs[gi];
     for (int w = 0; w < 4; w++) M->I[w] = w < NW ? sI[w] : 0ull;
   }
   __syncthreads();
@@ -346,6 +347,11 @@ struct BatchShared {
   int nv[2];
   double F[2][kMaxOrb];
   double u0[kMaxOrb], u1[kMaxOrb];  // per-batch row sums for H_aa
+  double dx[kMaxOrb];               // E0 - base - u0[x]
+  // two-hole batches: <I|H|I - H + R> by the pair tables of the all-cell
+  // fast path, built for J = I (its X is the hole pair H itself)
+  int iRow[kMaxOrb], iCol[kMaxOrb];
+  NT cI;
   double hii, base;
   float inv_nv1;
   uint64_t kbase[2 * NINT];  // I with the batch's holes removed
@@ -888,6 +894,7 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(const __grid_constan
       }
       if (tid == 0) {
         S.hii = M->hii;
+        S.cI = (NT)M->cI;
         S.g = M->g;
         S.slot = slot;
       }
@@ -984,9 +991,29 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(const __grid_constan
             S.u1[y] = S.F[s2][s] - W(s, s2, B.qa, s1) - W(s, s2, B.qb, s2);
           }
         if (tid == 0) S.base = S.hii - S.F[s1][B.qa] - S.F[s2][B.qb] + W(B.qa, s1, B.qb, s2);
+        // pair tables of J = I: rows tri(qa, r) and columns tri(qb, s) with
+        // the phases of qa -> r and qb -> s on I's strings
+        const int sl2 = (B.kind == 2) ? 1 : s1;
+        const int nva = S.nv[s1];
+        for (int v = tid; v < nva + S.nv[sl2]; v += kThreads) {
+          if (v < nva) {
+            const int r = S.vir[s1][v];
+            const int par = count_between<NINT>(S.I + s1 * NINT, r < B.qa ? r : B.qa, r < B.qa ? B.qa : r) & 1;
+            S.iRow[v] = tri(B.qa, r) | (par << 31);
+          } else {
+            const int sv = S.vir[sl2][v - nva];
+            int par = count_between<NINT>(S.I + sl2 * NINT, sv < B.qb ? sv : B.qb, sv < B.qb ? B.qb : sv) & 1;
+            if (B.kind == 1) {
+              const int lo = sv < B.qb ? sv : B.qb, hi = sv < B.qb ? B.qb : sv;
+              par ^= (B.qa > lo && B.qa < hi) ? 1 : 0;
+            }
+            S.iCol[v - nva] = tri(B.qb, sv) | (par << 31);
+          }
+        }
       }
     }
     __syncthreads();
+    for (int x = tid; x < S.nv[B.sa]; x += kThreads) S.dx[x] = (p.e0 - S.base) - S.u0[x];
 
     // ---- loop 1: bans ----
     bool dead = false;
@@ -1049,7 +1076,9 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(const __grid_constan
       for (int i = c0 + tid; i < c1; i += kThreads) {
         const int r = entry(i);
         if (rf[r] & 1u) continue;
-        const int t = __popcll(rh[r] & ~B.hm);
+        const uint64_t hmr = rh[r];
+        if (B.h == 2 && hmr == 0ull) continue;  // J = I: added in the cells pass
+        const int t = __popcll(hmr & ~B.hm);
         if (t > 2) continue;
         const bool all = (B.h == 1) ? (t <= 1) : (t == 0);
         if (all) S.L0[atomicAdd(&S.n0, 1)] = r;
@@ -1205,16 +1234,29 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(const __grid_constan
     const unsigned long long tau = S.tau;
     double acc_e = 0.0, acc_s2 = 0.0;
     unsigned long long acc_na = 0, acc_d0 = 0, acc_d1 = 0, acc_min = 0x7FF0000000000000ull, acc_tiny = 0;
-    const double base = S.base;
     for (int c = tid; c < B.ncell; c += kThreads) {
       if ((ban[c >> 5] >> (c & 31)) & 1u) continue;
       int ro, so, x, y;
       cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-      const double a = A[c];
-      double haa = base + S.u0[x];
-      if (B.kind == 2) haa += S.u1[y] + p.Jm[ro * norb + so];
-      else if (B.kind == 1) haa += S.u0[y] + (p.Jm[ro * norb + so] - p.Km[ro * norb + so]);
-      const double D = p.e0 - haa;
+      double a = A[c];
+      if (B.h == 2) {  // the generator's own term c_I <I|H|alpha>
+        NT v;
+        const int a1 = S.iRow[x], b2 = S.iCol[y];
+        if (B.kind == 2) {
+          v = flip_sign(eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)], (a1 ^ b2) < 0);
+        } else {
+          const int a2 = S.iRow[y], b1 = S.iCol[x];
+          v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
+          const int lo = so < B.qb ? so : B.qb, hi = so < B.qb ? B.qb : so;
+          v = flip_sign(v, ((a1 ^ b2) < 0 ? 1 : 0) ^ ((ro > lo && ro < hi) ? 1 : 0));
+        }
+        a += (double)(S.cI * v);
+        con++;
+      }
+      // D = E0 - H_aa from the per-batch row sums
+      double D = S.dx[x];
+      if (B.kind == 2) D -= S.u1[y] + p.Jm[ro * norb + so];
+      else if (B.kind == 1) D -= S.u0[y] + (p.Jm[ro * norb + so] - p.Km[ro * norb + so]);
       const double inv = 1.0 / D;
       const double q = a * inv;
       const double e = a * q;
