@@ -113,6 +113,22 @@ __device__ __forceinline__ const double* numer_h<double>(const SweepParams& p) {
 template <>
 __device__ __forceinline__ const float* numer_h<float>(const SweepParams& p) { return p.h32; }
 
+// 1/d by Newton-Raphson iteration for the reciprocal, r <- r + r (1 - d r),
+// from the hardware's approximate FP64 reciprocal (PTX rcp.approx.ftz.f64,
+// relative error below 2^-22).  Each step squares the relative error, so two
+// steps reach the rounding level of FP64 (a few ulp), with four FMAs on the
+// FP64 pipe instead of a correctly rounded division.  |d| must be a normal
+// number (the sweep's denominators are bounded away from 0 and infinity;
+// tiny ones take the plain division).
+__device__ __forceinline__ double recip_nr(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
 // v with its sign flipped when neg: a bit operation, no floating-point pipe.
 __device__ __forceinline__ double flip_sign(double v, bool neg) {
   return __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
@@ -720,7 +736,7 @@ static __device__ unsigned long long hist_threshold(const unsigned int* hist, lo
 
 template <int NINT>
 __device__ __forceinline__ uint64_t composite_word(const double* te, const uint64_t* tk, int i, int w) {
-  if (w == 0) return ~(unsigned long long)__double_as_longlong(fabs(te[i]));
+  if (w == 0) return ~((unsigned long long)__double_as_longlong(te[i]) & 0x7FFFFFFFFFFFFFFFull);
   return tk[(size_t)i * (2 * NINT) + (w - 1)];
 }
 
@@ -832,8 +848,11 @@ __device__ __noinline__ void compact_selection(const SweepParams& p, BatchShared
   __syncthreads();
 }
 
+// Three CTAs per SM for one word per spin; two words per spin come with
+// larger accumulators (at most two CTAs fit in shared memory), so those
+// kernels take the registers of two CTAs and do not spill.
 template <int NINT, typename NT, bool GRAD = false>
-__global__ void __launch_bounds__(kThreads, 3) batch_kernel(const __grid_constant__ SweepParams p) {
+__global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(const __grid_constant__ SweepParams p) {
   constexpr int NW = 2 * NINT;
   extern __shared__ __align__(16) unsigned char dyn[];
   double* A = reinterpret_cast<double*>(dyn);
@@ -1257,7 +1276,9 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(const __grid_constan
       double D = S.dx[x];
       if (B.kind == 2) D -= S.u1[y] + p.Jm[ro * norb + so];
       else if (B.kind == 1) D -= S.u0[y] + (p.Jm[ro * norb + so] - p.Km[ro * norb + so]);
-      const double inv = 1.0 / D;
+      // |D| in [2^-500, 2^500]: Newton reciprocal; otherwise the division
+      const unsigned long long dex = ((unsigned long long)__double_as_longlong(D) >> 52) & 0x7FFull;
+      const double inv = (dex > 523ull && dex < 1523ull) ? recip_nr(D) : 1.0 / D;
       const double q = a * inv;
       const double e = a * q;
       acc_e += e;
@@ -1274,7 +1295,8 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(const __grid_constan
       }
       // |a| < 1e-14, compared on the bit pattern (no FP64 compare)
       if (((unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull) < 0x3D06849B86A12B9Bull) acc_tiny++;
-      const unsigned long long db = (unsigned long long)__double_as_longlong(fabs(D));
+      // |D| and |e| as bit patterns: masking the sign keeps them off the FP64 pipe
+      const unsigned long long db = (unsigned long long)__double_as_longlong(D) & 0x7FFFFFFFFFFFFFFFull;
       acc_min = db < acc_min ? db : acc_min;
       uint64_t key[NW];  // alpha's words; selects keep them in registers
       const int kwr = B.sa * NINT + (ro >> 6), kws = (B.h == 2) ? B.sb * NINT + (so >> 6) : -1;
@@ -1287,7 +1309,7 @@ __global__ void __launch_bounds__(kThreads, 3) batch_kernel(const __grid_constan
       acc_d0 += hk;
       acc_d1 ^= splitmix64(hk ^ 0x243F6A8885A308D3ull);
       if (p.k > 0) {
-        const unsigned long long eb = (unsigned long long)__double_as_longlong(fabs(e));
+        const unsigned long long eb = (unsigned long long)__double_as_longlong(e) & 0x7FFFFFFFFFFFFFFFull;
         if (eb >= tau) {
           atomicAdd(&p.sel_hist[sel_bin(eb)], 1u);
           const int pos = atomicAdd(&S.tkcnt, 1);
