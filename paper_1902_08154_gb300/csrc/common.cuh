@@ -63,6 +63,10 @@ struct GenMeta {
 
 struct SweepParams {
   int norb, nalpha, nbeta, nel, nbat;
+  // tile2 = 1: every opposite-spin two-hole batch is split into two work
+  // items over halves of its rows (its accumulator would not fit twice in an
+  // SM's shared memory); nper = work items per generator
+  int tile2, nper;
   int64_t ndet;
   const uint64_t* dets;   // [ndet][2][NINT]
   const double* coefs;    // [ndet]

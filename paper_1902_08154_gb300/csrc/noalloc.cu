@@ -280,6 +280,8 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   p.nbeta = n_beta;
   p.nel = nel;
   p.nbat = nbat;
+  p.tile2 = 0;
+  p.nper = nbat;
   p.ndet = ndet;
   p.dets = dets;
   p.coefs = coefs;

@@ -254,6 +254,7 @@ struct qp_pt2_ctx {
   cudaStream_t st;
   int device, nsm;
   int max_cells, bps, grid;
+  int tile2;  // opposite-spin batches split in two row tiles
   size_t smem;
   double *d_h = nullptr, *d_eri = nullptr, *d_J = nullptr, *d_K = nullptr;
   float *d_h32 = nullptr, *d_eri32 = nullptr;  // mixed precision only
@@ -371,8 +372,26 @@ extern "C" int qp_pt2_create(qp_pt2_ctx** out, int norb, int n_alpha, int n_beta
     return bail(QP_ECUDA, "integral tables failed");
   x->max_cells = cells_max(norb, n_alpha, n_beta);
   if (x->max_cells < 1) x->max_cells = 1;
+  x->tile2 = 0;
   x->smem = sizeof(double) * x->max_cells + sizeof(uint32_t) * ((x->max_cells + 31) / 32);
   int bps = batch_blocks_per_sm(x->nint, c.precision == QP_MIXED, x->smem);
+  if (x->nint == 2 && bps < 2 && n_alpha > 0 && n_beta > 0) {
+    // the opposite-spin accumulator fits only once per SM: split those
+    // batches in two tiles of rows, so that two CTAs share the SM
+    const int va = norb - n_alpha, vb = norb - n_beta;
+    int m = cells_max(norb, n_alpha, n_beta);
+    if (m == va * vb) {
+      m = ((va + 1) / 2) * vb;
+      const int others[4] = {va, vb, va * (va - 1) / 2, vb * (vb - 1) / 2};
+      for (int o : others) m = o > m ? o : m;
+    }
+    if (m < x->max_cells) {
+      x->tile2 = 1;
+      x->max_cells = m;
+      x->smem = sizeof(double) * x->max_cells + sizeof(uint32_t) * ((x->max_cells + 31) / 32);
+      bps = batch_blocks_per_sm(x->nint, c.precision == QP_MIXED, x->smem);
+    }
+  }
   if (bps < 1) return bail(QP_ENOTSUP, "the batch accumulator does not fit in shared memory");
   if (c.blocks_per_sm > 0 && c.blocks_per_sm < bps) bps = c.blocks_per_sm;
   x->bps = bps;
@@ -568,6 +587,8 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
   p.nbeta = x->nbeta;
   p.nel = x->nel;
   p.nbat = x->nbat;
+  p.tile2 = x->tile2;
+  p.nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
   p.ndet = ndet;
   p.dets = d_dets;
   p.coefs = d_coefs;
@@ -850,6 +871,8 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
   p.nbeta = x->nbeta;
   p.nel = x->nel;
   p.nbat = x->nbat;
+  p.tile2 = x->tile2;
+  p.nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
   p.ndet = ndet;
   p.dets = d_dets;
   p.coefs = d_coefs;
@@ -1082,6 +1105,8 @@ static int enqueue_instance(BatchInst& b, cudaStream_t st) {
   p.nbeta = x->nbeta;
   p.nel = x->nel;
   p.nbat = x->nbat;
+  p.tile2 = x->tile2;
+  p.nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
   p.ndet = ndet;
   p.dets = b.dets;
   p.coefs = b.coefs;

@@ -409,6 +409,7 @@ struct Batch {
   int qa, qb;       // their orbitals
   uint64_t hm;      // hole mask over I's occupied list
   int ncell;
+  int clo, nct;     // this work item's cells: [clo, clo + nct) (a tile of the batch)
 };
 
 template <int NINT, typename NT>
@@ -437,6 +438,12 @@ __device__ __forceinline__ void cell_orbitals(const Batch& B, const BatchShared<
     *r = S.vir[B.sa][*x];
     *s = S.vir[B.sa][yy];
   }
+}
+
+// Bans cell c (an index over the whole batch) when it lies in this item's tile.
+__device__ __forceinline__ void ban_cell(uint32_t* ban, const Batch& B, int c) {
+  const int cc = c - B.clo;
+  if ((unsigned)cc < (unsigned)B.nct) atomicOr(&ban[cc >> 5], 1u << (cc & 31));
 }
 
 __device__ __forceinline__ int pair_cell(int x, int y) {  // x != y virtual indices
@@ -866,7 +873,8 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
   double* te = p.tk_e + (size_t)blockIdx.x * (size_t)p.cap;
   double* ta = p.tk_a + (size_t)blockIdx.x * (size_t)p.cap;
   uint64_t* tk = p.tk_key + (size_t)blockIdx.x * (size_t)p.cap * NW;
-  const long long nitems = (long long)p.wave_slots * nbat;
+  const int nper = p.nper;
+  const long long nitems = (long long)p.wave_slots * nper;
 
   if (tid == 0) {
     S.tkcnt = p.tk_cnt[blockIdx.x];
@@ -880,7 +888,16 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
     __syncthreads();
     const long long item = S.item;
     if (item >= nitems) break;
-    const int slot = (int)(item / nbat), b = (int)(item - (long long)slot * nbat);
+    const int slot = (int)(item / nper), j = (int)(item - (long long)slot * nper);
+    // item j < nbat: batch j (the first tile of a split batch); j >= nbat:
+    // the second tile of the (j - nbat)-th opposite-spin batch
+    int b = j, tile = 0;
+    if (j >= nbat) {
+      const int k = j - nbat, na = p.nalpha;
+      const int ia = k % na, ib = na + k / na;
+      b = nel + ib * (ib - 1) / 2 + ia;
+      tile = 1;
+    }
     const GenMeta* M = p.meta + slot;
     if (M->g < 0) continue;
     if ((p.b_dead[(size_t)slot * ((nbat + 31) / 32) + (b >> 5)] >> (b & 31)) & 1u) continue;
@@ -955,7 +972,14 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
       B.kind = 0;
       B.ncell = S.nv[B.sa];
     }
-    if (B.ncell == 0) continue;
+    B.clo = 0;
+    B.nct = B.ncell;
+    if (p.tile2 && B.kind == 2) {  // rows [0, h) or [h, nv0)
+      const int h = (S.nv[0] + 1) / 2;
+      B.clo = tile ? h * S.nv[1] : 0;
+      B.nct = (tile ? S.nv[0] - h : h) * S.nv[1];
+    }
+    if (B.nct <= 0) continue;
 
     // bucket lists: this batch's bucket, then the shared bucket (degree <= 2)
     const int* ofs = p.b_ofs + (size_t)slot * (nbat + 2);
@@ -978,13 +1002,13 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
       if (B.h == 2) S.kbase[B.sb * NINT + (B.qb >> 6)] &= ~(1ull << (B.qb & 63));
     }
     // zero the accumulator, the bans; row sums for H_aa
-    for (int c = tid; c < B.ncell; c += kThreads) A[c] = 0.0;
+    for (int c = tid; c < B.nct; c += kThreads) A[c] = 0.0;
     if (GRAD)
       for (int x = tid; x < kMaxOrb; x += kThreads) {
         S.rowW2[x] = 0.0;
         S.colW2[x] = 0.0;
       }
-    for (int c = tid; c < (B.ncell + 31) / 32; c += kThreads) ban[c] = 0u;
+    for (int c = tid; c < (B.nct + 31) / 32; c += kThreads) ban[c] = 0u;
     {
       auto W = [&](int x, int sx, int y, int sy) {
         double v = p.Jm[x * norb + y];
@@ -1052,7 +1076,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
           } else if (B.h == 2 && t == 1) {
             S.L1[atomicAdd(&S.n1, 1)] = r;
           } else {  // t == 2
-            for_subset_cells<NINT, NT>(B, S, norb, rp[r], [&](int c) { atomicOr(&ban[c >> 5], 1u << (c & 31)); });
+            for_subset_cells<NINT, NT>(B, S, norb, rp[r], [&](int c) { ban_cell(ban, B, c); });
           }
         } else if (t == 0 && hm == B.hm) {  // J = I - H + X with X a cell: alpha is internal
           const uint64_t part = rp[r];
@@ -1068,7 +1092,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
             const uint32_t P1 = particles_of_spin(part, norb, 1, &n1);
             c = S.vidx[0][pk(P0, 0)] * S.nv[1] + S.vidx[1][pk(P1, 0)];
           }
-          atomicOr(&ban[c >> 5], 1u << (c & 31));
+          ban_cell(ban, B, c);
         }
       }
       if (__syncthreads_or(dl)) {
@@ -1077,7 +1101,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
       }
       for (int j = warp; j < S.n1; j += kWarps)
         for_row_cells<NINT, NT>(B, S, norb, rp[S.L1[j]], lane,
-                            [&](int c) { atomicOr(&ban[c >> 5], 1u << (c & 31)); });
+                            [&](int c) { ban_cell(ban, B, c); });
       __syncthreads();
     }
     if (dead) continue;
@@ -1163,10 +1187,10 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
           }
           __syncthreads();
         }
-        for (int c = tid; c < B.ncell; c += kThreads) {
-          if ((ban[c >> 5] >> (c & 31)) & 1u) continue;
+        for (int cc = tid; cc < B.nct; cc += kThreads) {
+          if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
           int ro, so, x, y;
-          cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
+          cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
           const int rcode = B.sa * norb + ro;
           const int scode = (B.h == 2) ? B.sb * norb + so : -1;
           double acc = 0.0;
@@ -1195,7 +1219,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
             if (general) v = element<NINT, NT>(eri_n, h_n, norb, S.gJw[j], S.gX[j], S.gnx[j], S.gT[j], S.gnt[j], rcode, scode);
             acc += (double)(S.gcj[j] * v);
           }
-          A[c] += acc;
+          A[cc] += acc;
           con += m;
         }
         __syncthreads();
@@ -1210,12 +1234,13 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
         int nx, nt;
         excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
         for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
-          if ((ban[c >> 5] >> (c & 31)) & 1u) return;
+          const int cc = c - B.clo;
+          if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
           int ro, so, x, y;
           cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
           const int rcode = B.sa * norb + ro;
           const int scode = B.sb * norb + so;
-          atomicAdd(&A[c], (double)(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode)));
+          atomicAdd(&A[cc], (double)(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode)));
           con++;
         });
       }
@@ -1229,12 +1254,13 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
         int nx, nt;
         excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
         for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
-          if ((ban[c >> 5] >> (c & 31)) & 1u) return;
+          const int cc = c - B.clo;
+          if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
           int ro, so, x, y;
           cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
           const int rcode = B.sa * norb + ro;
           const int scode = (B.h == 2) ? B.sb * norb + so : -1;
-          atomicAdd(&A[c], (double)(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode)));
+          atomicAdd(&A[cc], (double)(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode)));
           con++;
         });
       }
@@ -1243,7 +1269,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
 
     // ---- cells: the perturbers of I in this batch ----
     if (p.k > 0) {
-      if (S.tkcnt + B.ncell > p.cap) compact_selection<NINT, NT>(p, S, te, ta, tk);
+      if (S.tkcnt + B.nct > p.cap) compact_selection<NINT, NT>(p, S, te, ta, tk);
       if (tid == 0) {
         const unsigned long long gt = *((volatile unsigned long long*)p.tau_bits);
         if (gt > S.tau) S.tau = gt;
@@ -1253,11 +1279,11 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
     const unsigned long long tau = S.tau;
     double acc_e = 0.0, acc_s2 = 0.0;
     unsigned long long acc_na = 0, acc_d0 = 0, acc_d1 = 0, acc_min = 0x7FF0000000000000ull, acc_tiny = 0;
-    for (int c = tid; c < B.ncell; c += kThreads) {
-      if ((ban[c >> 5] >> (c & 31)) & 1u) continue;
+    for (int cc = tid; cc < B.nct; cc += kThreads) {
+      if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
       int ro, so, x, y;
-      cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-      double a = A[c];
+      cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
+      double a = A[cc];
       if (B.h == 2) {  // the generator's own term c_I <I|H|alpha>
         NT v;
         const int a1 = S.iRow[x], b2 = S.iCol[y];
@@ -1286,7 +1312,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
       acc_na++;
       if (GRAD) {
         // numerator weight 2A/D for loop 3; (A/D)^2 weights the diagonal
-        A[c] = 2.0 * q;
+        A[cc] = 2.0 * q;
         const double w2 = q * q;
         atomicAdd(&S.rowW2[x], w2);
         if (B.kind == 2) atomicAdd(&S.colW2[y], w2);
@@ -1391,11 +1417,11 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
           uint32_t X, T;
           int nx, nt;
           excitation_sets<NINT, NT>(B, S, rp[r], rh[r], &X, &nx, &T, &nt);
-          for (int c = tid; c < B.ncell; c += kThreads) {
-            if ((ban[c >> 5] >> (c & 31)) & 1u) continue;
+          for (int cc = tid; cc < B.nct; cc += kThreads) {
+            if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
             int ro, so, x, y;
-            cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-            element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, (B.h == 2) ? B.sb * norb + so : -1, cj * A[c]);
+            cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
+            element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, (B.h == 2) ? B.sb * norb + so : -1, cj * A[cc]);
           }
         }
         for (int j = warp; j < S.n1; j += kWarps) {
@@ -1407,10 +1433,11 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
           int nx, nt;
           excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
           for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
-            if ((ban[c >> 5] >> (c & 31)) & 1u) return;
+            const int cc = c - B.clo;
+            if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
             int ro, so, x, y;
             cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-            element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, B.sb * norb + so, cj * A[c]);
+            element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, B.sb * norb + so, cj * A[cc]);
           });
         }
         for (int j = tid; j < S.n2; j += kThreads) {
@@ -1422,11 +1449,12 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
           int nx, nt;
           excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
           for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
-            if ((ban[c >> 5] >> (c & 31)) & 1u) return;
+            const int cc = c - B.clo;
+            if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
             int ro, so, x, y;
             cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
             element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, (B.h == 2) ? B.sb * norb + so : -1,
-                               cj * A[c]);
+                               cj * A[cc]);
           });
         }
         __syncthreads();

@@ -52,7 +52,8 @@ def _gpu_energy(qp, pt2, dd, cd, e0):
 
 
 @pytest.mark.parametrize("norb,na,nb,ndet,seed", [(10, 3, 3, 40, 101), (16, 4, 4, 120, 102), (24, 5, 4, 80, 103),
-                                                  (68, 2, 2, 30, 104)])
+                                                  (68, 2, 2, 30, 104),
+                                                  (112, 3, 3, 16, 105)])  # tiled opposite-spin batches
 def test_gradient_matches_oracle(qp, oracle_mod, norb, na, nb, ndet, seed):
     h, eri = S.hamiltonian(norb, min(norb + 2, 12), seed)
     ham = oracle_mod.Hamiltonian(norb, na, nb, h, eri)

@@ -86,6 +86,7 @@ def test_random_spaces_one_word(qp, oracle_mod, norb, na, nb, ndet, k, seed):
     (70, 3, 3, 60, 50, 12, 6),
     (80, 4, 3, 50, 40, 13, 5),
     (128, 2, 2, 30, 20, 14, 3),
+    (112, 3, 3, 40, 30, 15, 4),  # opposite-spin batches split in two row tiles
 ])
 def test_random_spaces_two_words(qp, oracle_mod, norb, na, nb, ndet, k, seed, rank):
     h, eri, ham, dets, c, e0 = _case(oracle_mod, norb, na, nb, ndet, seed, rank=rank)
