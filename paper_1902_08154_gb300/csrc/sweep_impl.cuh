@@ -115,18 +115,30 @@ __device__ __forceinline__ const float* numer_h<float>(const SweepParams& p) { r
 
 // 1/d by Newton-Raphson iteration for the reciprocal, r <- r + r (1 - d r),
 // from the hardware's approximate FP64 reciprocal (PTX rcp.approx.ftz.f64,
-// relative error below 2^-22).  Each step squares the relative error, so two
-// steps reach the rounding level of FP64 (a few ulp), with four FMAs on the
-// FP64 pipe instead of a correctly rounded division.  |d| must be a normal
-// number (the sweep's denominators are bounded away from 0 and infinity;
-// tiny ones take the plain division).
+// relative error below 2^-22).  Each step squares the relative error: two
+// steps reach the rounding level of FP64 (a few ulp) with four FMAs on the
+// FP64 pipe instead of a correctly rounded division; one step leaves a
+// relative error near 2^-44, used by the mixed-precision sweep, whose
+// budget is 1e-6 Eh.  |d| must be a normal number (the sweep's denominators
+// are bounded away from 0 and infinity; others take the plain division).
+template <int STEPS>
 __device__ __forceinline__ double recip_nr(double d) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
+#pragma unroll
+  for (int i = 0; i < STEPS; i++) {
+    const double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+  }
+  return r;
+}
+
+// Bit pattern of |x|.  The mask is applied in inline PTX: written in C++ the
+// compiler recognises it as fabs and issues it on the FP64 pipe.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  unsigned long long b;
+  asm("and.b64 %0, %1, 0x7FFFFFFFFFFFFFFF;" : "=l"(b) : "l"((unsigned long long)__double_as_longlong(x)));
+  return b;
 }
 
 // v with its sign flipped when neg: a bit operation, no floating-point pipe.
@@ -1304,7 +1316,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
       else if (B.kind == 1) D -= S.u0[y] + (p.Jm[ro * norb + so] - p.Km[ro * norb + so]);
       // |D| in [2^-500, 2^500]: Newton reciprocal; otherwise the division
       const unsigned long long dex = ((unsigned long long)__double_as_longlong(D) >> 52) & 0x7FFull;
-      const double inv = (dex > 523ull && dex < 1523ull) ? recip_nr(D) : 1.0 / D;
+      const double inv = (dex > 523ull && dex < 1523ull) ? recip_nr<sizeof(NT) == 8 ? 2 : 1>(D) : 1.0 / D;
       const double q = a * inv;
       const double e = a * q;
       acc_e += e;
@@ -1320,9 +1332,9 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
         if (B.h == 2) w_grad(p, ro, B.sa, so, B.sb, w2);
       }
       // |a| < 1e-14, compared on the bit pattern (no FP64 compare)
-      if (((unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull) < 0x3D06849B86A12B9Bull) acc_tiny++;
-      // |D| and |e| as bit patterns: masking the sign keeps them off the FP64 pipe
-      const unsigned long long db = (unsigned long long)__double_as_longlong(D) & 0x7FFFFFFFFFFFFFFFull;
+      if (abs_bits(a) < 0x3D06849B86A12B9Bull) acc_tiny++;
+      // |D| and |e| as bit patterns, off the FP64 pipe
+      const unsigned long long db = abs_bits(D);
       acc_min = db < acc_min ? db : acc_min;
       uint64_t key[NW];  // alpha's words; selects keep them in registers
       const int kwr = B.sa * NINT + (ro >> 6), kws = (B.h == 2) ? B.sb * NINT + (so >> 6) : -1;
@@ -1335,7 +1347,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
       acc_d0 += hk;
       acc_d1 ^= splitmix64(hk ^ 0x243F6A8885A308D3ull);
       if (p.k > 0) {
-        const unsigned long long eb = (unsigned long long)__double_as_longlong(e) & 0x7FFFFFFFFFFFFFFFull;
+        const unsigned long long eb = abs_bits(e);
         if (eb >= tau) {
           atomicAdd(&p.sel_hist[sel_bin(eb)], 1u);
           const int pos = atomicAdd(&S.tkcnt, 1);
