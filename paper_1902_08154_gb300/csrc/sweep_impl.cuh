@@ -405,7 +405,7 @@ struct BatchShared {
   uint64_t thr[1 + 2 * NINT];
   int need, group, found_w, found_sh;
   // reductions
-  double red_d[kWarps][2];
+  double red_t[2][kThreads];  // per-thread e and (A/D)^2 sums of the item
   unsigned long long red_u[kWarps][6];
   // gradient: sums of (A/D)^2 over the cells of each particle orbital
   double rowW2[kMaxOrb], colW2[kMaxOrb];
@@ -1318,8 +1318,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
       const unsigned long long dex = ((unsigned long long)__double_as_longlong(D) >> 52) & 0x7FFull;
       const double inv = (dex > 523ull && dex < 1523ull) ? recip_nr<sizeof(NT) == 8 ? 2 : 1>(D) : 1.0 / D;
       const double q = a * inv;
-      const double e = a * q;
-      acc_e += e;
+      acc_e = fma(a, q, acc_e);  // e = A q
       acc_s2 += q * q;
       acc_na++;
       if (GRAD) {
@@ -1346,7 +1345,12 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
       for (int w = 0; w < NW; w++) hk = splitmix64(hk ^ key[w]);
       acc_d0 += hk;
       acc_d1 ^= splitmix64(hk ^ 0x243F6A8885A308D3ull);
-      if (p.k > 0) {
+      // e = A q is formed only when it can reach the threshold: with biased
+      // exponents ea, eq of A and q, |A q| < 2^(ea + eq - 2044), so
+      // ea + eq <= et + 1021 (et: the exponent of tau) puts it below tau
+      const int ea = (int)(abs_bits(a) >> 52), eqx = (int)(abs_bits(q) >> 52);
+      if (p.k > 0 && (tau == 0ull || ea + eqx > (int)(tau >> 52) + 1021)) {
+        const double e = a * q;
         const unsigned long long eb = abs_bits(e);
         if (eb >= tau) {
           atomicAdd(&p.sel_hist[sel_bin(eb)], 1u);
@@ -1360,12 +1364,13 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
     }
     // ---- per-item reduction into the generator's totals ----
     {
-      const double e = warp_sum(acc_e), s2 = warp_sum(acc_s2);
+      // FP64 sums through shared memory and one warp: a shuffle tree in every
+      // warp would spend five FP64 adds per lane per quantity
+      S.red_t[0][tid] = acc_e;
+      S.red_t[1][tid] = acc_s2;
       const unsigned long long na = warp_sum_u(acc_na), nc = warp_sum_u(con), d0 = warp_sum_u(acc_d0);
       const unsigned long long d1 = warp_xor_u(acc_d1), mn = warp_min_u(acc_min), tiny = warp_sum_u(acc_tiny);
       if (lane == 0) {
-        S.red_d[warp][0] = e;
-        S.red_d[warp][1] = s2;
         S.red_u[warp][0] = na;
         S.red_u[warp][1] = nc;
         S.red_u[warp][2] = d0;
@@ -1374,12 +1379,19 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
         S.red_u[warp][5] = tiny;
       }
       __syncthreads();
+      double se = 0.0, ss = 0.0;
+      if (warp == 0) {
+        for (int i = lane; i < kThreads; i += 32) {
+          se += S.red_t[0][i];
+          ss += S.red_t[1][i];
+        }
+        se = warp_sum(se);
+        ss = warp_sum(ss);
+      }
       if (tid == 0) {
-        double te_ = 0, ts = 0;
+        const double te_ = se, ts = ss;
         unsigned long long tn = 0, tc = 0, x0 = 0, x1 = 0, m = 0x7FF0000000000000ull, tt = 0;
         for (int w = 0; w < kWarps; w++) {
-          te_ += S.red_d[w][0];
-          ts += S.red_d[w][1];
           tn += S.red_u[w][0];
           tc += S.red_u[w][1];
           x0 += S.red_u[w][2];
