@@ -269,6 +269,19 @@ def wide_leg(qp, torch, device, flush):
         r = pt2.eval(dd, cd, e0, n)
         ms = qp.qp_pt2_last_timings(pt2.ctx)[1]
         r10 = pt2.eval(d10d, c10d, e0, 20)
+        if prec == qp.QP_FP64:
+            # hybrid deterministic/stochastic E_PT2 to a 0.2 % statistical error
+            from paper_1902_08154_gb300 import stochastic as ST
+
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = ST.stochastic_pt2(pt2, dd, cd, e0, rel_err=0.002, seed=11)
+            t_st = time.perf_counter() - t0
+            out["hybrid_stochastic"] = {
+                "seconds": t_st, "e_pt2": st["e_pt2"], "error": st["error"], "prefix": st["prefix"],
+                "generators_computed": st["computed"], "draws": st["draws"], "iterations": st["iterations"],
+                "deviation_from_deterministic": st["e_pt2"] - r["e_pt2"],
+                "speedup_vs_deterministic": (ms * 1e-3) / t_st, "rel_err_target": 0.002}
         pt2.close()
         out[name] = {"ms": ms, "value": r["n_perturbers"] / (ms * 1e-3), "unit": UNIT,
                      "generators_per_s": n / (ms * 1e-3), "e_pt2": r["e_pt2"], "n_perturbers": r["n_perturbers"],

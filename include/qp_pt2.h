@@ -139,6 +139,24 @@ int qp_pt2_eval_ex(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, const do
                    double *eps_by_rank, int64_t *na_by_rank, int64_t *ncon_by_rank,
                    int32_t *rank_of, qp_pt2_result *res);
 
+/* The sweep of a subset of the generators (the building block of the
+ * hybrid deterministic/stochastic E_PT2, Sec. "Stochastic selection",
+ * Eqs. calpha and edetstoch): E_PT2 = sum_I eps_I over the generators sorted
+ * by decreasing c_I^2, and each eps_I (its set A_I by the canonical rule)
+ * depends on the whole Psi0 but not on which other eps are computed.
+ * ranks[ngen] is a HOST array of distinct generator ranks in [0, ndet)
+ * (rank 0 = largest c_I^2, ties by input index); only those generators are
+ * swept.  gen_eps / gen_na / gen_ncon (each may be NULL; host or device)
+ * receive eps_I, |A_I| and the connection count of each listed generator, in
+ * list order.  *res holds the totals over the listed generators and the
+ * selection is the best min(k, ...) of their perturbers.  The list overrides
+ * sharding.  QP_EINVAL for a rank out of range, a repeated rank or a device
+ * pointer for ranks. */
+int qp_pt2_eval_gens(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, const double *coefs,
+                     double e0, int64_t ngen, const int32_t *ranks, int64_t k, uint64_t *sel_dets,
+                     double *sel_e, double *gen_eps, int64_t *gen_na, int64_t *gen_ncon,
+                     qp_pt2_result *res);
+
 /* Gradient of E_PT2 (adjoint of the sweep), with Psi0's coefficients and E0
  * held fixed.  Every matrix element is linear in h and the integrals (Eqs.
  * Hij), so with A_alpha = <Psi0|H|alpha> and D_alpha = E0 - <alpha|H|alpha>

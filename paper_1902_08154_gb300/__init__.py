@@ -24,6 +24,7 @@ EXPORTS = (
     "qp_pt2_create",
     "qp_pt2_eval",
     "qp_pt2_eval_ex",
+    "qp_pt2_eval_gens",
     "qp_pt2_last_launches",
     "qp_pt2_last_timings",
     "qp_pt2_destroy",
@@ -99,6 +100,8 @@ def load(path: str = SO):
     L.qp_pt2_eval.argtypes = [vp, i64, vp, vp, dbl, i64, vp, vp, C.POINTER(Result)]
     L.qp_pt2_eval_ex.restype = C.c_int
     L.qp_pt2_eval_ex.argtypes = [vp, i64, vp, vp, dbl, i64, vp, vp, vp, vp, vp, vp, vp, C.POINTER(Result)]
+    L.qp_pt2_eval_gens.restype = C.c_int
+    L.qp_pt2_eval_gens.argtypes = [vp, i64, vp, vp, dbl, i64, vp, i64, vp, vp, vp, vp, vp, C.POINTER(Result)]
     L.qp_pt2_last_launches.restype = i64
     L.qp_pt2_last_launches.argtypes = [vp]
     L.qp_pt2_last_timings.restype = C.c_int
@@ -162,6 +165,19 @@ def qp_pt2_eval_ex(ctx, ndet, dets, coefs, e0, k, sel_dets=None, sel_e=None, sel
     rc = load().qp_pt2_eval_ex(ctx, ndet, _ptr(dets), _ptr(coefs), float(e0), k, _ptr(sel_dets), _ptr(sel_e),
                                _ptr(sel_num), _ptr(eps_by_rank), _ptr(na_by_rank), _ptr(ncon_by_rank),
                                _ptr(rank_of), C.byref(res))
+    if check:
+        _check(rc)
+    return rc, res
+
+
+def qp_pt2_eval_gens(ctx, ndet, dets, coefs, e0, ranks, k=0, sel_dets=None, sel_e=None, gen_eps=None, gen_na=None,
+                     gen_ncon=None, check=True):
+    """Sweep of the listed generator ranks only (``ranks``: host int32 array)."""
+    ranks = np.ascontiguousarray(ranks, dtype=np.int32)
+    res = Result()
+    rc = load().qp_pt2_eval_gens(ctx, ndet, _ptr(dets), _ptr(coefs), float(e0), len(ranks), _ptr(ranks), k,
+                                 _ptr(sel_dets), _ptr(sel_e), _ptr(gen_eps), _ptr(gen_na), _ptr(gen_ncon),
+                                 C.byref(res))
     if check:
         _check(rc)
     return rc, res
@@ -254,6 +270,31 @@ class PT2:
         if per_generator:
             out.update(eps_by_rank=eps[:ndet], na_by_rank=na[:ndet], ncon_by_rank=nc[:ndet], rank_of=rk[:ndet])
         out["launches"] = qp_pt2_last_launches(self.ctx)
+        return out
+
+    def eval_generators(self, dets, coefs, e0, ranks, k=0):
+        """Sweep of the generators of the listed ranks (0 = largest c_I^2):
+        their eps_I, |A_I| and connections (host arrays, list order), the
+        totals over them and, with k > 0, the best k of their perturbers
+        (in the memory kind of ``dets``)."""
+        ranks = np.ascontiguousarray(ranks, dtype=np.int32)
+        n = len(ranks)
+        eps = np.zeros(max(n, 1))
+        na = np.zeros(max(n, 1), dtype=np.int64)
+        nc = np.zeros(max(n, 1), dtype=np.int64)
+        if isinstance(dets, np.ndarray):
+            sel = np.zeros((max(k, 1), 2, self.nint), dtype=np.uint64)
+            se = np.zeros(max(k, 1))
+        else:
+            import torch
+
+            sel = torch.zeros((max(k, 1), 2, self.nint), dtype=torch.int64, device=dets.device)
+            se = torch.zeros(max(k, 1), dtype=torch.float64, device=dets.device)
+        _, res = qp_pt2_eval_gens(self.ctx, len(dets), dets, coefs, e0, ranks, k, sel if k else None,
+                                  se if k else None, eps, na, nc)
+        out = res.as_dict()
+        m = res.n_selected
+        out.update(eps=eps[:n], na=na[:n], ncon=nc[:n], sel_dets=sel[:m], sel_e=se[:m])
         return out
 
 

@@ -81,6 +81,7 @@ struct SweepParams {
   const double* Km;       // [norb*norb] (pq|qp)
   double e0;
   int shard_index, shard_count;   // generators of rank shard_index + t*shard_count
+  const int32_t* gen_list;        // if set: the generator of slot t has rank gen_list[t]
 
   // wave of generator slots
   int wave_start;                 // first generator position (t) of this wave

@@ -262,7 +262,7 @@ struct qp_pt2_ctx {
   Buf in_dets, in_coefs, hkey, hkey2, hidx, hidx2, rkey, rkey2, order, rank_of, cub_tmp;
   Buf eps, s2, na, ncon, acc, res;
   Buf meta, r_words, r_coef, r_hmask, r_part, r_flag, b_ofs, b_ent, b_dead, queues;
-  Buf tk_e, tk_a, tk_key, tk_cnt, tk_tau, sel_hist;
+  Buf tk_e, tk_a, tk_key, tk_cnt, tk_tau, sel_hist, gen_list, gen_out;
   Buf cand_e, cand_a, cand_key, skey, skey2, perm, perm2, cub_tmp2;
   Buf out_sel, out_e, out_num, out_eps, out_na, out_ncon, out_rank;
   Buf g_dh, g_deri, g_wF, g_wH;
@@ -414,7 +414,7 @@ extern "C" void qp_pt2_destroy(qp_pt2_ctx* x) {
   Buf* all[] = {&x->in_dets, &x->in_coefs, &x->hkey, &x->hkey2, &x->hidx, &x->hidx2, &x->rkey, &x->rkey2,
                 &x->order, &x->rank_of, &x->cub_tmp, &x->eps, &x->s2, &x->na, &x->ncon, &x->acc,
                 &x->res, &x->meta, &x->r_words, &x->r_coef, &x->r_hmask, &x->r_part, &x->r_flag,
-                &x->b_ofs, &x->b_ent, &x->b_dead, &x->queues, &x->tk_e, &x->tk_a, &x->tk_key, &x->tk_cnt, &x->tk_tau, &x->sel_hist, &x->cand_e, &x->cand_a, &x->cand_key, &x->skey,
+                &x->b_ofs, &x->b_ent, &x->b_dead, &x->queues, &x->tk_e, &x->tk_a, &x->tk_key, &x->tk_cnt, &x->tk_tau, &x->sel_hist, &x->gen_list, &x->gen_out, &x->cand_e, &x->cand_a, &x->cand_key, &x->skey,
                 &x->skey2, &x->perm, &x->perm2, &x->cub_tmp2, &x->out_sel, &x->out_e, &x->out_num,
                 &x->out_eps, &x->out_na, &x->out_ncon, &x->out_rank, &x->g_dh, &x->g_deri, &x->g_wF, &x->g_wH};
   for (Buf* b : all) b->release();
@@ -481,10 +481,26 @@ static int out_target(Buf& b, T* user, size_t count, T** dst, bool* copy_back) {
   return QP_OK;
 }
 
-extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const double* coefs,
-                              double e0, int64_t k, uint64_t* sel_dets, double* sel_e, double* sel_num,
-                              double* eps_by_rank, int64_t* na_by_rank, int64_t* ncon_by_rank,
-                              int32_t* rank_of_out, qp_pt2_result* res) {
+// eps, |A_I| and connections of the listed generators (by rank).
+__global__ void gather_gen_kernel(int64_t n, const int32_t* ranks, const double* eps, const unsigned long long* na,
+                                  const unsigned long long* ncon, double* out_eps, int64_t* out_na,
+                                  int64_t* out_ncon) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int r = ranks[i];
+  out_eps[i] = eps[r];
+  out_na[i] = (int64_t)na[r];
+  out_ncon[i] = (int64_t)ncon[r];
+}
+
+// The sweep; with gen_ranks (host array of ngen_list distinct ranks) only
+// those generators are swept and their eps, |A_I| and connections are
+// written to gen_eps / gen_na / gen_ncon in list order.
+static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const double* coefs, double e0,
+                     int64_t k, uint64_t* sel_dets, double* sel_e, double* sel_num, double* eps_by_rank,
+                     int64_t* na_by_rank, int64_t* ncon_by_rank, int32_t* rank_of_out, qp_pt2_result* res,
+                     const int32_t* gen_ranks, int64_t ngen_list, double* gen_eps, int64_t* gen_na,
+                     int64_t* gen_ncon) {
   if (!x || !res) return fail(QP_EINVAL, "ctx or res is NULL");
   if (ndet < 0 || k < 0) return fail(QP_EINVAL, "ndet and k must be non-negative");
   if (ndet > 0 && (!dets || !coefs)) return fail(QP_EINVAL, "dets or coefs is NULL");
@@ -551,7 +567,15 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
   const int grid = x->grid;
   const int64_t cap = k > 0 ? k + x->max_cells : 1;
   const int shard_count = x->cfg.shard_count, shard_index = x->cfg.shard_index;
-  const int64_t ngen = (ndet > shard_index) ? (ndet - shard_index + shard_count - 1) / shard_count : 0;
+  const int64_t ngen = gen_ranks ? ngen_list
+                                 : (ndet > shard_index) ? (ndet - shard_index + shard_count - 1) / shard_count : 0;
+  if (gen_ranks) {
+    if ((rc = x->gen_list.grow(4 * (size_t)(ngen > 0 ? ngen : 1))) ||
+        (rc = x->gen_out.grow(24 * (size_t)(ngen > 0 ? ngen : 1))))
+      return rc;
+    if (ngen > 0)
+      CUDA_TRY(cudaMemcpyAsync(x->gen_list.p, gen_ranks, 4 * (size_t)ngen, cudaMemcpyHostToDevice, st));
+  }
   const int64_t ent_per = x->nel >= 3 ? 3 * x->nel - 3 : 1;
   const int64_t ent_cap = (int64_t)nd * ent_per;
   const size_t dwords = (size_t)(x->nbat + 31) / 32;
@@ -604,6 +628,7 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
   p.e0 = e0;
   p.shard_index = shard_index;
   p.shard_count = shard_count;
+  p.gen_list = gen_ranks ? x->gen_list.as<int32_t>() : nullptr;
   p.meta = x->meta.as<GenMeta>();
   p.r_words = x->r_words.as<uint64_t>();
   p.r_coef = x->r_coef.as<double>();
@@ -714,6 +739,18 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
   if ((rc = copy_out(eps_by_rank, p.eps, 8 * nd)) || (rc = copy_out(na_by_rank, p.na, 8 * nd)) ||
       (rc = copy_out(ncon_by_rank, p.ncon, 8 * nd)) || (rc = copy_out(rank_of_out, p.rank_of, 4 * nd)))
     return rc;
+  if (gen_ranks && ngen > 0) {
+    double* ge = x->gen_out.as<double>();
+    int64_t* gn = reinterpret_cast<int64_t*>(ge + ngen);
+    int64_t* gc = gn + ngen;
+    gather_gen_kernel<<<(unsigned)((ngen + 255) / 256), 256, 0, st>>>(ngen, x->gen_list.as<int32_t>(), p.eps, p.na,
+                                                                       p.ncon, ge, gn, gc);
+    x->launches++;
+    CUDA_TRY(cudaGetLastError());
+    if ((rc = copy_out(gen_eps, ge, 8 * (size_t)ngen)) || (rc = copy_out(gen_na, gn, 8 * (size_t)ngen)) ||
+        (rc = copy_out(gen_ncon, gc, 8 * (size_t)ngen)))
+      return rc;
+  }
 
   DevResult hres;
   unsigned long long hacc[kAccWords];
@@ -737,6 +774,34 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
   res->min_abs_denominator = md;
   if (hres.na > 0 && md < 1e-12) return fail(QP_ESINGULAR, "a denominator E0 - H_aa is below 1e-12");
   return QP_OK;
+}
+
+extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const double* coefs,
+                              double e0, int64_t k, uint64_t* sel_dets, double* sel_e, double* sel_num,
+                              double* eps_by_rank, int64_t* na_by_rank, int64_t* ncon_by_rank,
+                              int32_t* rank_of_out, qp_pt2_result* res) {
+  return eval_core(x, ndet, dets, coefs, e0, k, sel_dets, sel_e, sel_num, eps_by_rank, na_by_rank, ncon_by_rank,
+                   rank_of_out, res, nullptr, 0, nullptr, nullptr, nullptr);
+}
+
+extern "C" int qp_pt2_eval_gens(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const double* coefs,
+                                double e0, int64_t ngen, const int32_t* ranks, int64_t k, uint64_t* sel_dets,
+                                double* sel_e, double* gen_eps, int64_t* gen_na, int64_t* gen_ncon,
+                                qp_pt2_result* res) {
+  if (!x || !res) return fail(QP_EINVAL, "ctx or res is NULL");
+  if (ngen < 0 || (ngen > 0 && !ranks)) return fail(QP_EINVAL, "ngen is negative or ranks is NULL");
+  if (ngen > ndet) return fail(QP_EINVAL, "more generators than determinants");
+  if (ngen > 0 && is_device_ptr(ranks)) return fail(QP_EINVAL, "ranks must be a host array");
+  {
+    std::vector<int32_t> srt(ranks, ranks + ngen);
+    std::sort(srt.begin(), srt.end());
+    for (int64_t i = 0; i < ngen; i++) {
+      if (srt[i] < 0 || srt[i] >= ndet) return fail(QP_EINVAL, "a generator rank is outside [0, ndet)");
+      if (i > 0 && srt[i] == srt[i - 1]) return fail(QP_EINVAL, "a generator rank is listed twice");
+    }
+  }
+  return eval_core(x, ndet, dets, coefs, e0, k, sel_dets, sel_e, nullptr, nullptr, nullptr, nullptr, nullptr, res,
+                   ranks, ngen, gen_eps, gen_na, gen_ncon);
 }
 
 extern "C" int qp_pt2_eval(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const double* coefs, double e0,

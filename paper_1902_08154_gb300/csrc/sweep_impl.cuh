@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(const __grid_constant__ 
   const int norb = p.norb, nel = p.nel, nbat = p.nbat;
   GenMeta* M = p.meta + slot;
   const long long t = (long long)p.wave_start + slot;
-  const long long gg = p.shard_index + t * (long long)p.shard_count;
+  const long long gg = p.gen_list ? (long long)p.gen_list[t] : p.shard_index + t * (long long)p.shard_count;
   if (gg >= p.ndet) {
     if (tid == 0) {
       M->g = -1;
