@@ -73,6 +73,7 @@ extern "C" {
 #define QP_ENOMEM (-5)     /* device allocation failed */
 #define QP_ECUDA (-6)      /* CUDA runtime error */
 #define QP_ENOTSUP (-8)    /* configuration not supported by this build */
+#define QP_ENOTCONV (-9)  /* Davidson stopped above its residual tolerance */
 
 #define QP_FP64 0          /* every step in FP64 */
 #define QP_MIXED 1         /* numerator <J|H|alpha> gathers and products c_J<J|H|alpha> in
@@ -156,6 +157,34 @@ int qp_pt2_eval_gens(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, const 
                      double e0, int64_t ngen, const int32_t *ranks, int64_t k, uint64_t *sel_dets,
                      double *sel_e, double *gen_eps, int64_t *gen_na, int64_t *gen_ncon,
                      qp_pt2_result *res);
+
+/* The variational step of CIPSI (Sec. "Davidson diagonalization"): the
+ * Hamiltonian over Psi0 and its lowest eigenpair.
+ *
+ * qp_pt2_sigma: S[k] = H U[k] for nvec vectors (U, S: [nvec][ndet], host or
+ * device), H the matrix of Psi0's determinants (Slater-Condon rules,
+ * Eqs. Hij).  H is rebuilt on every call (device memory freed on return).
+ *
+ * qp_pt2_davidson: the lowest eigenvalue *e0 and its normalised eigenvector
+ * coefs[ndet] (host or device; coefs[0] >= 0), by Davidson's method with the
+ * diagonal preconditioner, starting from guess (NULL: the determinant of
+ * lowest H_II), until the residual norm |H c - e0 c| <= tol or max_iter
+ * basis extensions (QP_ENOTCONV, outputs still written).  *e0 is the
+ * Rayleigh quotient of the returned vector.  info (may be NULL) receives the
+ * iteration count, the final residual, the number of stored off-diagonal
+ * elements and the build and solve times.  Psi0 is validated as for
+ * qp_pt2_eval (QP_EINVAL, QP_EDUP).  Allocates device memory for H and the
+ * basis (32 vectors). */
+typedef struct {
+  int iterations, converged;
+  double residual;
+  int64_t nnz;
+  double build_ms, solve_ms;
+} qp_pt2_davidson_info;
+
+int qp_pt2_sigma(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, int nvec, const double *U, double *S);
+int qp_pt2_davidson(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, const double *guess, double tol,
+                    int max_iter, double *coefs, double *e0, qp_pt2_davidson_info *info);
 
 /* Gradient of E_PT2 (adjoint of the sweep), with Psi0's coefficients and E0
  * held fixed.  Every matrix element is linear in h and the integrals (Eqs.

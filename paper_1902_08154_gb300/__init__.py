@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SO = os.path.join(HERE, "_build", "libqp_pt2.so")
 
 QP_OK, QP_EINVAL, QP_EDUP, QP_ESYM, QP_ESINGULAR, QP_ENOMEM, QP_ECUDA, QP_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -8
+QP_ENOTCONV = -9
 QP_FP64 = 0
 QP_MIXED = 1
 
@@ -25,6 +26,8 @@ EXPORTS = (
     "qp_pt2_eval",
     "qp_pt2_eval_ex",
     "qp_pt2_eval_gens",
+    "qp_pt2_sigma",
+    "qp_pt2_davidson",
     "qp_pt2_last_launches",
     "qp_pt2_last_timings",
     "qp_pt2_destroy",
@@ -76,6 +79,14 @@ def rpt2(res, e0):
     return {"z": z, "e_rpt2": float(e0) + z * res["e_pt2"]}
 
 
+class DavidsonInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("residual", C.c_double), ("nnz", C.c_int64),
+                ("build_ms", C.c_double), ("solve_ms", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class QPError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{msg} (code {code})")
@@ -100,6 +111,10 @@ def load(path: str = SO):
     L.qp_pt2_eval.argtypes = [vp, i64, vp, vp, dbl, i64, vp, vp, C.POINTER(Result)]
     L.qp_pt2_eval_ex.restype = C.c_int
     L.qp_pt2_eval_ex.argtypes = [vp, i64, vp, vp, dbl, i64, vp, vp, vp, vp, vp, vp, vp, C.POINTER(Result)]
+    L.qp_pt2_sigma.restype = C.c_int
+    L.qp_pt2_sigma.argtypes = [vp, i64, vp, C.c_int, vp, vp]
+    L.qp_pt2_davidson.restype = C.c_int
+    L.qp_pt2_davidson.argtypes = [vp, i64, vp, vp, dbl, C.c_int, vp, vp, C.POINTER(DavidsonInfo)]
     L.qp_pt2_eval_gens.restype = C.c_int
     L.qp_pt2_eval_gens.argtypes = [vp, i64, vp, vp, dbl, i64, vp, i64, vp, vp, vp, vp, vp, C.POINTER(Result)]
     L.qp_pt2_last_launches.restype = i64
@@ -181,6 +196,23 @@ def qp_pt2_eval_gens(ctx, ndet, dets, coefs, e0, ranks, k=0, sel_dets=None, sel_
     if check:
         _check(rc)
     return rc, res
+
+
+def qp_pt2_sigma(ctx, ndet, dets, U, S):
+    """S[k] = H U[k] over Psi0 (U, S: [nvec, ndet], host or device)."""
+    _check(load().qp_pt2_sigma(ctx, ndet, _ptr(dets), int(U.shape[0]), _ptr(U), _ptr(S)))
+    return S
+
+
+def qp_pt2_davidson(ctx, ndet, dets, coefs_out, guess=None, tol=1e-10, max_iter=1000, check=True):
+    """Lowest eigenpair of H over Psi0; returns (rc, e0, info dict)."""
+    e0 = C.c_double(0.0)
+    info = DavidsonInfo()
+    rc = load().qp_pt2_davidson(ctx, ndet, _ptr(dets), _ptr(guess), float(tol), int(max_iter), _ptr(coefs_out),
+                                C.byref(e0), C.byref(info))
+    if check:
+        _check(rc)
+    return rc, e0.value, info.as_dict()
 
 
 def qp_pt2_eval_noalloc(norb, n_alpha, n_beta, h, eri, ndet, dets, coefs, e0, k, sel_dets=None, sel_e=None,
@@ -271,6 +303,27 @@ class PT2:
             out.update(eps_by_rank=eps[:ndet], na_by_rank=na[:ndet], ncon_by_rank=nc[:ndet], rank_of=rk[:ndet])
         out["launches"] = qp_pt2_last_launches(self.ctx)
         return out
+
+    def sigma(self, dets, U):
+        """H U over Psi0 for the rows of U ([nvec, ndet]), in U's memory kind."""
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.float64)
+            S = np.zeros_like(U)
+        else:
+            U = U.contiguous()
+            S = U.new_zeros(U.shape)
+        return qp_pt2_sigma(self.ctx, len(dets), dets, U, S)
+
+    def davidson(self, dets, guess=None, tol=1e-10, max_iter=1000):
+        """(E0, coefficients, info) of the lowest eigenpair of H over Psi0."""
+        if isinstance(dets, np.ndarray):
+            c = np.zeros(len(dets))
+        else:
+            import torch
+
+            c = torch.zeros(len(dets), dtype=torch.float64, device=dets.device)
+        _, e0, info = qp_pt2_davidson(self.ctx, len(dets), dets, c, guess, tol, max_iter)
+        return e0, c, info
 
     def eval_generators(self, dets, coefs, e0, ranks, k=0):
         """Sweep of the generators of the listed ranks (0 = largest c_I^2):

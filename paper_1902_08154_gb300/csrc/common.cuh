@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+struct qp_pt2_ctx;
+
 namespace qp {
 
 constexpr int kMaxOrb = 128;
@@ -49,6 +51,16 @@ __device__ __forceinline__ int count_between(const uint64_t* sw, int lo, int hi)
   }
   return n;
 }
+
+// What the Hamiltonian/Davidson unit needs of a context (filled by
+// qp_pt2.cu, which owns the context), and the library's error reporter.
+struct CtxView {
+  int norb, nalpha, nbeta, nint, nel, device;
+  const double *h, *eri, *Jm, *Km;  // device copies, [norb*norb] and packed
+  cudaStream_t st;
+};
+int ctx_view(const struct ::qp_pt2_ctx* x, CtxView* v);
+int report(int code, const char* msg);
 
 // Per-generator data built by the prep kernel and read by the batch kernel.
 struct GenMeta {

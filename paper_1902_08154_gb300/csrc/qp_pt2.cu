@@ -273,6 +273,25 @@ struct qp_pt2_ctx {
   bool timed = false;
 };
 
+namespace qp {
+int ctx_view(const qp_pt2_ctx* x, CtxView* v) {
+  if (!x || !v) return fail(QP_EINVAL, "ctx is NULL");
+  v->norb = x->norb;
+  v->nalpha = x->nalpha;
+  v->nbeta = x->nbeta;
+  v->nint = x->nint;
+  v->nel = x->nel;
+  v->device = x->device;
+  v->h = x->d_h;
+  v->eri = x->d_eri;
+  v->Jm = x->d_J;
+  v->Km = x->d_K;
+  v->st = x->st;
+  return QP_OK;
+}
+int report(int code, const char* msg) { return fail(code, msg); }
+}  // namespace qp
+
 // accumulator block layout (unsigned long long words)
 enum { kAccDigest0 = 0, kAccDigest1, kAccMinDen, kAccTiny, kAccTau, kAccQueue, kAccErr, kAccNcand, kAccWords };
 
@@ -445,6 +464,7 @@ extern "C" const char* qp_pt2_strerror(int code) {
     case QP_ENOMEM: return "device memory allocation failed";
     case QP_ECUDA: return "CUDA runtime error";
     case QP_ENOTSUP: return "not supported by this build";
+    case QP_ENOTCONV: return "Davidson did not reach the residual tolerance";
     default: return "unknown error";
   }
 }
