@@ -99,6 +99,8 @@ def lib():
         L.or_gradient.restype = I
         L.or_gradient.argtypes = [P, I64, U64P, DP, D, DP, DP, DP, DP, I, I64]
         L.or_max_threads.restype = I
+        L.or_set_target.restype = None
+        L.or_set_target.argtypes = [P, I, U64P, I, U64P, U64P]
         _lib = L
     return _lib
 
@@ -128,6 +130,15 @@ class Hamiltonian:
         d = np.ascontiguousarray(d, dtype=np.uint64)
         assert d.shape == (2, self.nint), d.shape
         return d
+
+    def set_target(self, ref=None, max_exc=-1, core=None, deleted=None):
+        """Restrict the external space to a target space (CISD-like with ref
+        and max_exc, CAS-like with core/deleted masks in determinant
+        layout); all None clears it."""
+        on = int(ref is not None or core is not None or deleted is not None)
+        arrs = [None if a is None else self._det(a) for a in (ref, core, deleted)]
+        self._tgt = arrs  # keep alive
+        lib().or_set_target(self._p, on, _ptr(arrs[0]), int(max_exc), _ptr(arrs[1]), _ptr(arrs[2]))
 
     def eri_value(self, p, q, r, s):
         return lib().or_eri(self._p, p, q, r, s)

@@ -8,6 +8,9 @@
  * no code, header, table or constant with it.
  *
  * What is computed, and where the paper defines it:
+ *   - Target spaces (Sec. "Selected CI", the remark that the method applies
+ *     to CAS, CIS, CISD, ... spaces): external determinants outside the
+ *     target space contribute nothing (or_set_target; a filter on alpha).
  *   - Slater-Condon rules for <I|H|I>, <I|H|I_p^r>, <I|H|I_pq^rs>
  *     (Sec. "Matrix elements of the Hamiltonian", Eqs. Hij).  Phases are
  *     obtained by COUNTING the occupied spin orbitals between hole and particle
@@ -65,7 +68,38 @@ typedef struct or_ham {
     double *eri; /* packed, 8-fold */
     double *J;   /* J[p*norb+q] = (pp|qq) */
     double *K;   /* K[p*norb+q] = (pq|qp) */
+    /* target space (Sec. "Selected CI" remark on CAS/CISD spaces): external
+     * determinants outside it contribute nothing */
+    int tgt_on, tgt_max_exc;
+    uint64_t tgt_ref[4], tgt_core[4], tgt_del[4];
 } or_ham;
+
+/* alpha belongs to the target space: every core spin orbital occupied, no
+ * deleted one occupied, and (when max_exc >= 0) at most max_exc electrons
+ * moved from the reference determinant. */
+static int in_target(const or_ham *H, const uint64_t *a)
+{
+    if (!H->tgt_on) return 1;
+    int moved = 0;
+    for (int w = 0; w < 2 * H->nint; w++) {
+        if ((a[w] & H->tgt_core[w]) != H->tgt_core[w]) return 0;
+        if (a[w] & H->tgt_del[w]) return 0;
+        moved += __builtin_popcountll(a[w] ^ H->tgt_ref[w]);
+    }
+    return H->tgt_max_exc < 0 || moved / 2 <= H->tgt_max_exc;
+}
+
+/* Sets the target space; ref/core/deleted may be NULL (no constraint). */
+void or_set_target(or_ham *H, int on, const uint64_t *ref, int max_exc, const uint64_t *core, const uint64_t *deleted)
+{
+    H->tgt_on = on;
+    H->tgt_max_exc = ref ? max_exc : -1;
+    for (int w = 0; w < 4; w++) {
+        H->tgt_ref[w] = (ref && w < 2 * H->nint) ? ref[w] : 0;
+        H->tgt_core[w] = (core && w < 2 * H->nint) ? core[w] : 0;
+        H->tgt_del[w] = (deleted && w < 2 * H->nint) ? deleted[w] : 0;
+    }
+}
 
 static int64_t tri(int64_t a, int64_t b)
 {
@@ -498,6 +532,7 @@ typedef struct {
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
+    const or_ham *H;
     int nw, stride;      /* stride = nw + 1 words: key then J index */
     int nparts, part;
     int64_t *cnt, *cap;  /* per sub-bucket */
@@ -508,6 +543,7 @@ typedef struct {
 static void pair_emit(void *vctx, const uint64_t *alpha)
 {
     pair_ctx *c = (pair_ctx *)vctx;
+    if (!in_target(c->H, alpha)) return;  /* outside the target space: no contribution */
     uint64_t hk = or_key_hash(c->nw, alpha);
     if ((int)((hk >> 32) % (uint64_t)c->nparts) != c->part) return;
     int sub = (int)((hk & 0xffffffffull) % OR_NSUB);
@@ -601,7 +637,7 @@ int or_sweep(const or_ham *H, int64_t ndet, const uint64_t *dets, const double *
     /* per-thread, per-sub-bucket record buffers */
     pair_ctx *ctx = (pair_ctx *)calloc(nthreads, sizeof(pair_ctx));
     for (int t = 0; t < nthreads; t++) {
-        ctx[t].nw = nw; ctx[t].stride = stride; ctx[t].nparts = nparts;
+        ctx[t].H = H; ctx[t].nw = nw; ctx[t].stride = stride; ctx[t].nparts = nparts;
         ctx[t].cnt = (int64_t *)calloc(OR_NSUB, sizeof(int64_t));
         ctx[t].cap = (int64_t *)calloc(OR_NSUB, sizeof(int64_t));
         ctx[t].buf = (uint64_t **)calloc(OR_NSUB, sizeof(uint64_t *));
@@ -779,7 +815,7 @@ int or_generator(const or_ham *H, int64_t ndet, const uint64_t *dets, const doub
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
     for (int64_t c = 0; c < nc; c++) {
         const uint64_t *alpha = cand + c * nw;
-        int skip = 0;
+        int skip = !in_target(H, alpha);
         int64_t con = 0;
         nsum A = {0.0, 0.0};
         for (int64_t f = 0; f < nf && !skip; f++) {
@@ -1007,7 +1043,7 @@ int or_gradient(const or_ham *H, int64_t ndet, const uint64_t *dets, const doubl
     nsum *e0s = (nsum *)calloc(OR_NSUB, sizeof(nsum));
     pair_ctx *ctx = (pair_ctx *)calloc(nthreads, sizeof(pair_ctx));
     for (int t = 0; t < nthreads; t++) {
-        ctx[t].nw = nw; ctx[t].stride = stride; ctx[t].nparts = nparts;
+        ctx[t].H = H; ctx[t].nw = nw; ctx[t].stride = stride; ctx[t].nparts = nparts;
         ctx[t].cnt = (int64_t *)calloc(OR_NSUB, sizeof(int64_t));
         ctx[t].cap = (int64_t *)calloc(OR_NSUB, sizeof(int64_t));
         ctx[t].buf = (uint64_t **)calloc(OR_NSUB, sizeof(uint64_t *));
