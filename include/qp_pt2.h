@@ -140,6 +140,19 @@ int qp_pt2_eval_ex(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, const do
                    double *eps_by_rank, int64_t *na_by_rank, int64_t *ncon_by_rank,
                    int32_t *rank_of, qp_pt2_result *res);
 
+/* Target space (Sec. "Selected CI": the sweep applies to CAS, CIS, CISD ...
+ * spaces, with the contributions of external determinants outside the
+ * target space set to zero).  Later sweeps, subset sweeps and gradients of
+ * ctx count an external determinant alpha only if every spin orbital set
+ * in core is occupied in alpha, none set in deleted is, and, when ref is
+ * given and max_exc >= 0, alpha differs from ref by at most max_exc
+ * electrons.  ref, core, deleted: HOST arrays in determinant layout
+ * ([2][nint] words), each may be NULL; all NULL clears the target space.
+ * QP_EINVAL if a spin orbital is both core and deleted.  Psi0 itself is not
+ * restricted. */
+int qp_pt2_set_target(qp_pt2_ctx *ctx, const uint64_t *ref, int max_exc, const uint64_t *core,
+                      const uint64_t *deleted);
+
 /* The sweep of a subset of the generators (the building block of the
  * hybrid deterministic/stochastic E_PT2, Sec. "Stochastic selection",
  * Eqs. calpha and edetstoch): E_PT2 = sum_I eps_I over the generators sorted

@@ -27,6 +27,7 @@ EXPORTS = (
     "qp_pt2_eval_ex",
     "qp_pt2_eval_gens",
     "qp_pt2_sigma",
+    "qp_pt2_set_target",
     "qp_pt2_davidson",
     "qp_pt2_last_launches",
     "qp_pt2_last_timings",
@@ -111,6 +112,8 @@ def load(path: str = SO):
     L.qp_pt2_eval.argtypes = [vp, i64, vp, vp, dbl, i64, vp, vp, C.POINTER(Result)]
     L.qp_pt2_eval_ex.restype = C.c_int
     L.qp_pt2_eval_ex.argtypes = [vp, i64, vp, vp, dbl, i64, vp, vp, vp, vp, vp, vp, vp, C.POINTER(Result)]
+    L.qp_pt2_set_target.restype = C.c_int
+    L.qp_pt2_set_target.argtypes = [vp, vp, C.c_int, vp, vp]
     L.qp_pt2_sigma.restype = C.c_int
     L.qp_pt2_sigma.argtypes = [vp, i64, vp, C.c_int, vp, vp]
     L.qp_pt2_davidson.restype = C.c_int
@@ -303,6 +306,13 @@ class PT2:
             out.update(eps_by_rank=eps[:ndet], na_by_rank=na[:ndet], ncon_by_rank=nc[:ndet], rank_of=rk[:ndet])
         out["launches"] = qp_pt2_last_launches(self.ctx)
         return out
+
+    def set_target(self, ref=None, max_exc=-1, core=None, deleted=None):
+        """Restrict the external space (see qp_pt2_set_target); host arrays
+        in determinant layout, all None clears it."""
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.uint64) for a in (ref, core, deleted)]
+        self._tgt = arrs
+        _check(load().qp_pt2_set_target(self.ctx, _ptr(arrs[0]), int(max_exc), _ptr(arrs[1]), _ptr(arrs[2])))
 
     def sigma(self, dets, U):
         """H U over Psi0 for the rows of U ([nvec, ndet]), in U's memory kind."""

@@ -94,6 +94,10 @@ struct SweepParams {
   double e0;
   int shard_index, shard_count;   // generators of rank shard_index + t*shard_count
   const int32_t* gen_list;        // if set: the generator of slot t has rank gen_list[t]
+  // target space: alpha must hold every core spin orbital, no deleted one,
+  // and (tgt_max_exc >= 0) at most tgt_max_exc electrons moved from tgt_ref
+  int tgt_on, tgt_max_exc;
+  uint64_t tgt_ref[4], tgt_core[4], tgt_del[4];
 
   // wave of generator slots
   int wave_start;                 // first generator position (t) of this wave

@@ -255,6 +255,8 @@ struct qp_pt2_ctx {
   int device, nsm;
   int max_cells, bps, grid;
   int tile2;  // opposite-spin batches split in two row tiles
+  int tgt_on = 0, tgt_max_exc = -1;  // target space (qp_pt2_set_target)
+  uint64_t tgt_ref[4] = {0, 0, 0, 0}, tgt_core[4] = {0, 0, 0, 0}, tgt_del[4] = {0, 0, 0, 0};
   size_t smem;
   double *d_h = nullptr, *d_eri = nullptr, *d_J = nullptr, *d_K = nullptr;
   float *d_h32 = nullptr, *d_eri32 = nullptr;  // mixed precision only
@@ -438,6 +440,25 @@ extern "C" void qp_pt2_destroy(qp_pt2_ctx* x) {
                 &x->out_eps, &x->out_na, &x->out_ncon, &x->out_rank, &x->g_dh, &x->g_deri, &x->g_wF, &x->g_wH};
   for (Buf* b : all) b->release();
   delete x;
+}
+
+extern "C" int qp_pt2_set_target(qp_pt2_ctx* x, const uint64_t* ref, int max_exc, const uint64_t* core,
+                                 const uint64_t* deleted) {
+  if (!x) return fail(QP_EINVAL, "ctx is NULL");
+  const int nw = 2 * x->nint;
+  for (const uint64_t* a : {ref, core, deleted})
+    if (a && is_device_ptr(a)) return fail(QP_EINVAL, "target-space masks must be host arrays");
+  if (core && deleted)
+    for (int w = 0; w < nw; w++)
+      if (core[w] & deleted[w]) return fail(QP_EINVAL, "a spin orbital is both core and deleted");
+  x->tgt_on = (ref || core || deleted) ? 1 : 0;
+  x->tgt_max_exc = ref ? max_exc : -1;
+  for (int w = 0; w < 4; w++) {
+    x->tgt_ref[w] = (ref && w < nw) ? ref[w] : 0;
+    x->tgt_core[w] = (core && w < nw) ? core[w] : 0;
+    x->tgt_del[w] = (deleted && w < nw) ? deleted[w] : 0;
+  }
+  return QP_OK;
 }
 
 extern "C" int64_t qp_pt2_last_launches(const qp_pt2_ctx* x) { return x ? x->launches : 0; }
@@ -633,6 +654,13 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   p.nbat = x->nbat;
   p.tile2 = x->tile2;
   p.nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
+  p.tgt_on = x->tgt_on;
+  p.tgt_max_exc = x->tgt_max_exc;
+  for (int w = 0; w < 4; w++) {
+    p.tgt_ref[w] = x->tgt_ref[w];
+    p.tgt_core[w] = x->tgt_core[w];
+    p.tgt_del[w] = x->tgt_del[w];
+  }
   p.ndet = ndet;
   p.dets = d_dets;
   p.coefs = d_coefs;
@@ -958,6 +986,13 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
   p.nbat = x->nbat;
   p.tile2 = x->tile2;
   p.nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
+  p.tgt_on = x->tgt_on;
+  p.tgt_max_exc = x->tgt_max_exc;
+  for (int w = 0; w < 4; w++) {
+    p.tgt_ref[w] = x->tgt_ref[w];
+    p.tgt_core[w] = x->tgt_core[w];
+    p.tgt_del[w] = x->tgt_del[w];
+  }
   p.ndet = ndet;
   p.dets = d_dets;
   p.coefs = d_coefs;
@@ -1192,6 +1227,13 @@ static int enqueue_instance(BatchInst& b, cudaStream_t st) {
   p.nbat = x->nbat;
   p.tile2 = x->tile2;
   p.nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
+  p.tgt_on = x->tgt_on;
+  p.tgt_max_exc = x->tgt_max_exc;
+  for (int w = 0; w < 4; w++) {
+    p.tgt_ref[w] = x->tgt_ref[w];
+    p.tgt_core[w] = x->tgt_core[w];
+    p.tgt_del[w] = x->tgt_del[w];
+  }
   p.ndet = ndet;
   p.dets = b.dets;
   p.coefs = b.coefs;

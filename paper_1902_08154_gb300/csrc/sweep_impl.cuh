@@ -1069,6 +1069,24 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
     }
     __syncthreads();
     for (int x = tid; x < S.nv[B.sa]; x += kThreads) S.dx[x] = (p.e0 - S.base) - S.u0[x];
+    if (p.tgt_on) {  // cells outside the target space contribute nothing: ban them
+      for (int cc = tid; cc < B.nct; cc += kThreads) {
+        int ro, so, x, y;
+        cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
+        const int kwr = B.sa * NINT + (ro >> 6), kws = (B.h == 2) ? B.sb * NINT + (so >> 6) : -1;
+        bool ok = true;
+        int moved = 0;
+#pragma unroll
+        for (int w = 0; w < NW; w++) {
+          const uint64_t k = S.kbase[w] | (w == kwr ? 1ull << (ro & 63) : 0ull) | (w == kws ? 1ull << (so & 63) : 0ull);
+          ok &= (k & p.tgt_core[w]) == p.tgt_core[w];
+          ok &= (k & p.tgt_del[w]) == 0ull;
+          moved += __popcll(k ^ p.tgt_ref[w]);
+        }
+        if (p.tgt_max_exc >= 0) ok &= (moved >> 1) <= p.tgt_max_exc;
+        if (!ok) atomicOr(&ban[cc >> 5], 1u << (cc & 31));
+      }
+    }
 
     // ---- loop 1: bans ----
     bool dead = false;
