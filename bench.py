@@ -50,8 +50,8 @@ FP64_OPS_PER_PERTURBER = 9
 # lanes per clock per SM: 152 SMs x 2 x 2.07 GHz operations per second
 FP64_PEAK_GOPS = 152 * 2 * 2.07
 # DRAM bytes (read + write) of the sweep kernels over one sweep of the bench
-# workload (prep 3.09 + 12.19 GB, batch 4.55 + 0.25 GB), from one ncu capture
-TRAFFIC_BYTES_PER_SWEEP = None
+# workload (prep 3.09 + 12.19 GB, batch 4.54 + 0.23 GB), from one ncu capture
+TRAFFIC_BYTES_PER_SWEEP = 20.04e9
 
 
 def load_workload(name=WORKLOAD):
@@ -457,7 +457,7 @@ def run_gb300(args):
     # eigenpair by Davidson (residual 1e-10), against the stored E0 of the
     # oracle's Davidson
     dav = None
-    if world == 1 and not args.ndet:
+    if world == 1 and not args.ndet and not args.no_davidson:
         e0d, _, di = pt2.davidson(d_dets, tol=1e-10)
         dav = {"ms": di["build_ms"] + di["solve_ms"], "build_ms": di["build_ms"], "solve_ms": di["solve_ms"],
                "iterations": di["iterations"], "nnz": di["nnz"], "e0": e0d,
@@ -503,6 +503,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg (profiling runs)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-instance batched leg")
     ap.add_argument("--no-wide", action="store_true", help="skip the 128-orbital, 10^5-determinant leg")
+    ap.add_argument("--no-davidson", action="store_true", help="skip the Davidson leg")
     ap.add_argument("--ndet", type=int, default=0,
                     help="profiling runs only: sweep the first NDET determinants of the stored Psi0")
     args = ap.parse_args()
