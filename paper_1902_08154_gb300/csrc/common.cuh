@@ -62,6 +62,13 @@ struct CtxView {
 int ctx_view(const struct ::qp_pt2_ctx* x, CtxView* v);
 int report(int code, const char* msg);
 
+// Bucket entries per coarse-filter record: a record with holes Q of I
+// (d = |Q|) is listed once in the shared bucket (d <= 2), once per hole
+// (d = 3) or once per pair of holes (d = 4).
+__host__ __device__ inline long long bucket_entries_per_record(int nel) {
+  return nel >= 4 ? 6 : (nel == 3 ? 3 : 1);
+}
+
 // Per-generator data built by the prep kernel and read by the batch kernel.
 struct GenMeta {
   uint64_t I[4];            // generator determinant (2*NINT words used)

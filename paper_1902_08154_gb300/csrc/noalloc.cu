@@ -219,7 +219,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   int32_t* perm2 = cv.take<int32_t>(maxc);
   if (!cv.ok)
     return nfail(QP_EINVAL, "ndet or k too large for the 64 MiB static scratch of qp_pt2_eval_noalloc");
-  const int64_t ent_per = nel >= 3 ? 3 * nel - 3 : 1;
+  const int64_t ent_per = bucket_entries_per_record(nel);
   const int64_t ent_cap = (int64_t)nd * ent_per;
   const size_t dwords = (size_t)(nbat + 31) / 32;
   const size_t per_slot = sizeof(GenMeta) + nd * (8 * nw + 8 + 8 + 8 + 4) + 4 * (size_t)(nbat + 2) +

@@ -617,7 +617,7 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
     if (ngen > 0)
       CUDA_TRY(cudaMemcpyAsync(x->gen_list.p, gen_ranks, 4 * (size_t)ngen, cudaMemcpyHostToDevice, st));
   }
-  const int64_t ent_per = x->nel >= 3 ? 3 * x->nel - 3 : 1;
+  const int64_t ent_per = bucket_entries_per_record(x->nel);
   const int64_t ent_cap = (int64_t)nd * ent_per;
   const size_t dwords = (size_t)(x->nbat + 31) / 32;
   const size_t per_slot = sizeof(GenMeta) + nd * (8 * nw + 8 + 8 + 8 + 4) + 4 * (size_t)(x->nbat + 2) +
@@ -949,7 +949,7 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
   const int grid = x->grid;
   const int shard_count = x->cfg.shard_count, shard_index = x->cfg.shard_index;
   const int64_t ngen = (ndet > shard_index) ? (ndet - shard_index + shard_count - 1) / shard_count : 0;
-  const int64_t ent_per = x->nel >= 3 ? 3 * x->nel - 3 : 1;
+  const int64_t ent_per = bucket_entries_per_record(x->nel);
   const int64_t ent_cap = (int64_t)nd * ent_per;
   const size_t dwords = (size_t)(x->nbat + 31) / 32;
   const size_t per_slot = sizeof(GenMeta) + nd * (8 * nw + 8 + 8 + 8 + 4) + 4 * (size_t)(x->nbat + 2) +
@@ -1150,7 +1150,7 @@ static int plan_instance(BatchInst& b, size_t wave_budget) {
   // every CTA may hold up to k candidates when no CTA has filled its buffer
   b.maxc = (size_t)grid * (size_t)(b.k > 0 ? b.k : 1);
   b.ngen = b.ndet;
-  const int64_t ent_per = x->nel >= 3 ? 3 * x->nel - 3 : 1;
+  const int64_t ent_per = bucket_entries_per_record(x->nel);
   b.ent_cap = (int64_t)nd * ent_per;
   const size_t dwords = (size_t)(x->nbat + 31) / 32;
   const size_t per_slot = sizeof(GenMeta) + nd * (8 * nw + 8 + 8 + 8 + 4) + 4 * (size_t)(x->nbat + 2) +

@@ -18,8 +18,10 @@
 //      t = |K - J| and X = J - K, deg(J, alpha) = t + |H| - |R n X|, so J
 //      reaches batch H only if t <= 2.  With Q the holes of J (d = |Q|),
 //      t = d - |Q n H|: J with d <= 2 reaches every batch, d = 3 the batches
-//      meeting Q, d = 4 the batches inside Q.  Each record is written to the
-//      bucket of every batch it reaches (d <= 2: one shared bucket).
+//      meeting Q, d = 4 the batches inside Q.  Records with d <= 2 go to one
+//      shared bucket, those with d = 3 to the list of each of their holes
+//      (a batch reads the lists of its holes), those with d = 4 to the
+//      bucket of each pair of their holes.
 //
 //  batch_kernel (persistent CTAs, one (generator, batch) item at a time,
 //  items of the heaviest generators first)
@@ -167,16 +169,8 @@ __device__ __forceinline__ void for_buckets(uint64_t hm, int nel, int nbat, Fn&&
     Q[n++] = __ffsll((long long)m) - 1;
     m &= m - 1;
   }
-  if (d == 3) {
+  if (d == 3) {  // the list of each hole q: read by the batches holding q
     for (int i = 0; i < 3; i++) fn(Q[i]);
-    for (int i = 0; i < 3; i++) {
-      const int q = Q[i];
-      for (int o = 0; o < nel; o++) {
-        if (o == q) continue;
-        if (((hm >> o) & 1ull) && o < q) continue;  // pair inside Q: once
-        fn(pair_batch(nel, q < o ? q : o, q < o ? o : q));
-      }
-    }
   } else {  // d == 4
     for (int i = 0; i < 4; i++)
       for (int j = i + 1; j < 4; j++) fn(pair_batch(nel, Q[i], Q[j]));
@@ -996,15 +990,26 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
     // bucket lists: this batch's bucket, then the shared bucket (degree <= 2)
     const int* ofs = p.b_ofs + (size_t)slot * (nbat + 2);
     const int32_t* ent = p.b_ent + (size_t)slot * (size_t)p.ent_cap;
+    // entries: the batch's own bucket (one-hole batch {a}: the d = 3 records
+    // holding a; two-hole batch: the d = 4 records holding both holes), then
+    // for a two-hole batch {a, b} the d = 3 lists of a and of b (a record
+    // holding both is taken from a's list only), then the shared bucket
     const int ob = ofs[b], nb_ = ofs[b + 1] - ob, oa = ofs[nbat], na_ = ofs[nbat + 1] - oa;
-    const int total = nb_ + na_;
+    const int o1 = (B.h == 2) ? ofs[B.ia] : 0, n1_ = (B.h == 2) ? ofs[B.ia + 1] - o1 : 0;
+    const int o2 = (B.h == 2) ? ofs[B.ib] : 0, n2_ = (B.h == 2) ? ofs[B.ib + 1] - o2 : 0;
+    const int s1 = nb_, s2 = s1 + n1_, s3 = s2 + n2_;
+    const int total = s3 + na_;
     const size_t rb = (size_t)slot * (size_t)p.ndet;
     const uint64_t* rw = p.r_words + rb * NW;
     const double* rc = p.r_coef + rb;
     const uint64_t* rh = p.r_hmask + rb;
     const uint64_t* rp = p.r_part + rb;
     const uint32_t* rf = p.r_flag + rb;
-    auto entry = [&](int i) { return i < nb_ ? ent[ob + i] : ent[oa + i - nb_]; };
+    auto entry = [&](int i) {
+      return i < s1 ? ent[ob + i] : (i < s2 ? ent[o1 + i - s1] : (i < s3 ? ent[o2 + i - s2] : ent[oa + i - s3]));
+    };
+    // a d = 3 record of b's list that also holds a was taken from a's list
+    auto dup = [&](int i, uint64_t hm) { return i >= s2 && i < s3 && ((hm >> B.ia) & 1ull); };
 
     if (tid == 0) {
       S.inv_nv1 = S.nv[1] > 0 ? 1.0f / (float)S.nv[1] : 0.0f;
@@ -1098,6 +1103,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
       for (int i = c0 + tid; i < c1; i += kThreads) {
         const int r = entry(i);
         const uint64_t hm = rh[r];
+        if (dup(i, hm)) continue;
         const int t = __popcll(hm & ~B.hm);
         if (t > 2) continue;
         if (rf[r] & 1u) {
@@ -1150,6 +1156,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
         const int r = entry(i);
         if (rf[r] & 1u) continue;
         const uint64_t hmr = rh[r];
+        if (dup(i, hmr)) continue;
         if (B.h == 2 && hmr == 0ull) continue;  // J = I: added in the cells pass
         const int t = __popcll(hmr & ~B.hm);
         if (t > 2) continue;
@@ -1444,6 +1451,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
         for (int i = c0 + tid; i < c1; i += kThreads) {
           const int r = entry(i);
           if (rf[r] & 1u) continue;
+          if (dup(i, rh[r])) continue;
           const int t = __popcll(rh[r] & ~B.hm);
           if (t > 2) continue;
           const bool all = (B.h == 1) ? (t <= 1) : (t == 0);
