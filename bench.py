@@ -50,8 +50,8 @@ FP64_OPS_PER_PERTURBER = 9
 # lanes per clock per SM: 152 SMs x 2 x 2.07 GHz operations per second
 FP64_PEAK_GOPS = 152 * 2 * 2.07
 # DRAM bytes (read + write) of the sweep kernels over one sweep of the bench
-# workload (prep 3.09 + 12.19 GB, batch 4.54 + 0.23 GB), from one ncu capture
-TRAFFIC_BYTES_PER_SWEEP = None
+# workload (prep 1.11 + 5.15 GB, batch 2.86 + 0.25 GB), from one ncu capture
+TRAFFIC_BYTES_PER_SWEEP = 9.38e9
 
 
 def load_workload(name=WORKLOAD):
