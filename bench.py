@@ -124,25 +124,40 @@ class Clocks:
 
 def cpu_baseline(meta, h, eri, dets, coefs, e0, budget_s=15.0, stride=97):
     """The oracle's per-generator definition on a bounded sample of
-    generators (ranks 0, stride, 2*stride, ...), all host cores."""
+    generators (ranks 0, stride, 2*stride, ...), all host cores; then on one
+    core over the same generators from rank `stride` on (rank 0, the
+    HF-like generator, is far heavier than the rest)."""
     import oracle
 
     ham = oracle.Hamiltonian(meta["norb"], meta["nalpha"], meta["nbeta"], h, eri)
     threads = oracle.max_threads()
     t0 = time.perf_counter()
-    ranks, npert, ncon = [], 0, 0
+    ranks, per, npert, ncon = [], [], 0, 0
     g = 0
     while g < len(dets) and (time.perf_counter() - t0) < budget_s:
+        tg = time.perf_counter()
         r = ham.generator(dets, coefs, e0, g, nthreads=threads)
+        per.append((g, r["n_perturbers"], time.perf_counter() - tg))
         npert += r["n_perturbers"]
         ncon += r["n_connections"]
         ranks.append(g)
         g += stride
     dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    n1, tall, g1 = 0, 0.0, 0
+    for g, n, t in per[1:]:
+        if time.perf_counter() - t1 > budget_s / 3:
+            break
+        n1 += ham.generator(dets, coefs, e0, g, nthreads=1)["n_perturbers"]
+        tall += t
+        g1 += 1
+    dt1 = time.perf_counter() - t1
     return {"value": npert / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"per-generator oracle on {len(ranks)} of {len(dets)} generators (ranks 0, {stride}, "
                       f"{2 * stride}, ...): {npert} perturbers in {dt:.2f} s",
-            "generators_per_s": len(ranks) / dt, "seconds": dt}
+            "generators_per_s": len(ranks) / dt, "seconds": dt,
+            "single_core": {"value": n1 / dt1 if g1 > 0 else None, "unit": UNIT, "cores": 1, "generators": g1,
+                            "seconds": dt1, "all_cores_on_same_generators": n1 / tall if tall > 0 else None}}
 
 
 def run_reference(args):

@@ -125,3 +125,19 @@ def test_cipsi_growth_matches_oracle(qp, oracle_mod):
             assert a["e_pt2"] == pytest.approx(b["e_pt2"], abs=1e-10)
     assert {d.tobytes() for d in dets} == {d.tobytes() for d in ref_dets}
     assert e_fin == pytest.approx(ref_e0, abs=1e-9)
+
+
+def test_davidson_two_words_per_spin(qp, oracle_mod):
+    """Determinants across the 64-bit word boundary (70 orbitals)."""
+    from oracle import psi0
+
+    norb, na, nb = 70, 3, 3
+    h, eri = S.hamiltonian(norb, 6, 68)
+    ham = oracle_mod.Hamiltonian(norb, na, nb, h, eri)
+    dets = S.random_excited_dets(norb, na, nb, 250, 69)
+    w, v = np.linalg.eigh(psi0.hamiltonian_matrix(ham, dets).toarray())
+    pt2 = qp.PT2(norb, na, nb, _dev(h), _dev(eri))
+    e0, c, info = pt2.davidson(_dev(dets), tol=1e-10)
+    pt2.close()
+    assert e0 == pytest.approx(w[0], abs=1e-10)
+    assert abs(abs(np.dot(c.cpu().numpy(), v[:, 0])) - 1.0) <= 1e-12
