@@ -381,6 +381,7 @@ struct BatchShared {
   long long item;
   int L0[kChunk], L1[kChunk], L2[kChunk];
   int n0, n1, n2;
+  int cnext;  // next row-reaching J (then subset block) to draw
   // a group of J reaching every cell, processed by the whole CTA
   uint64_t gJw[kGroup][2 * NINT];
   NT gcj[kGroup];
@@ -1149,6 +1150,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
         S.n0 = 0;
         S.n1 = 0;
         S.n2 = 0;
+        S.cnext = 0;
       }
       __syncthreads();
       const int c1 = min(c0 + kChunk, total);
@@ -1261,45 +1263,58 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
         }
         __syncthreads();
       }
-      // J reaching a row of cells: one warp each
-      for (int j = warp; j < S.n1; j += kWarps) {
-        const int r = S.L1[j];
-        const uint64_t* Jw = rw + (size_t)r * NW;
-        const NT cj = (NT)rc[r];
-        const uint64_t part = rp[r];
-        uint32_t X, T;
-        int nx, nt;
-        excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
-        for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
-          const int cc = c - B.clo;
-          if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
-          int ro, so, x, y;
-          cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-          const int rcode = B.sa * norb + ro;
-          const int scode = B.sb * norb + so;
-          atomicAdd(&A[cc], (double)(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode)));
-          con++;
-        });
-      }
-      // J reaching a few cells: one thread each
-      for (int j = tid; j < S.n2; j += kThreads) {
-        const int r = S.L2[j];
-        const uint64_t* Jw = rw + (size_t)r * NW;
-        const NT cj = (NT)rc[r];
-        const uint64_t part = rp[r];
-        uint32_t X, T;
-        int nx, nt;
-        excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
-        for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
-          const int cc = c - B.clo;
-          if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
-          int ro, so, x, y;
-          cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-          const int rcode = B.sa * norb + ro;
-          const int scode = (B.h == 2) ? B.sb * norb + so : -1;
-          atomicAdd(&A[cc], (double)(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode)));
-          con++;
-        });
+      // J reaching a row of cells (one warp each), then J reaching a few
+      // cells (one lane each, 32 per draw), drawn by the warps as they free up
+      {
+        const int n1 = S.n1, n2 = S.n2;
+        for (;;) {
+          int jd = 0;
+          if (lane == 0) jd = atomicAdd(&S.cnext, 1);
+          jd = __shfl_sync(kFull, jd, 0);
+          if (jd < n1) {
+            const int j = jd;
+            const int r = S.L1[j];
+            const uint64_t* Jw = rw + (size_t)r * NW;
+            const NT cj = (NT)rc[r];
+            const uint64_t part = rp[r];
+            uint32_t X, T;
+            int nx, nt;
+            excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
+            for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
+              const int cc = c - B.clo;
+              if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
+              int ro, so, x, y;
+              cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
+              const int rcode = B.sa * norb + ro;
+              const int scode = B.sb * norb + so;
+              atomicAdd(&A[cc], (double)(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode)));
+              con++;
+            });
+          } else {
+            const int j0 = (jd - n1) * 32;
+            if (j0 >= n2) break;
+            const int j = j0 + lane;
+            if (j < n2) {
+              const int r = S.L2[j];
+              const uint64_t* Jw = rw + (size_t)r * NW;
+              const NT cj = (NT)rc[r];
+              const uint64_t part = rp[r];
+              uint32_t X, T;
+              int nx, nt;
+              excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
+              for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
+                const int cc = c - B.clo;
+                if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
+                int ro, so, x, y;
+                cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
+                const int rcode = B.sa * norb + ro;
+                const int scode = (B.h == 2) ? B.sb * norb + so : -1;
+                atomicAdd(&A[cc], (double)(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode)));
+                con++;
+              });
+            }
+          }
+        }
       }
       __syncthreads();
     }
