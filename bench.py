@@ -468,6 +468,37 @@ def run_gb300(args):
     if not args.no_wide and world == 1:
         wide = wide_leg(qp, torch, device, flush)
 
+    # the adjoint (pattern 3) on the stored 48-orbital workload: dE_PT2/dh,
+    # dE_PT2/d(packed eri) and dE/dE0, against the oracle's stored gradient
+    adj = None
+    if world == 1 and not args.ndet and not args.no_davidson:
+        G = np.load(os.path.join(ROOT, "tests", "golden", "cfg4_gradient.npz"))
+        P4 = np.load(os.path.join(ROOT, "tests", "golden", "cfg4_psi0.npz"))
+        m4 = json.loads(str(P4["meta"]))
+        from paper_1902_08154_gb300 import synthetic as S4
+
+        h4, eri4 = S4.hamiltonian(m4["norb"], m4["rank"], m4["seed"])
+        ctx4 = qp.PT2(m4["norb"], m4["nalpha"], m4["nbeta"], torch.from_numpy(h4).to(device),
+                      torch.from_numpy(eri4).to(device))
+        d4 = torch.from_numpy(P4["dets"].view(np.int64)).to(device)
+        c4 = torch.from_numpy(P4["coefs"]).to(device)
+        dh4 = torch.zeros((m4["norb"], m4["norb"]), dtype=torch.float64, device=device)
+        de4 = torch.zeros(len(eri4), dtype=torch.float64, device=device)
+        qp.qp_pt2_grad(ctx4.ctx, len(d4), d4, c4, float(P4["e0"]), dh4, de4)
+        ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ta.record()
+        g0, r4 = qp.qp_pt2_grad(ctx4.ctx, len(d4), d4, c4, float(P4["e0"]), dh4, de4)
+        tb.record()
+        torch.cuda.synchronize()
+        ctx4.close()
+        scale = max(1.0, float(np.abs(G["deri"]).max()))
+        adj = {"workload": f"norb {m4['norb']}, {m4['nalpha']}+{m4['nbeta']} electrons, N_det {len(d4)}",
+               "ms": ta.elapsed_time(tb), "e_pt2": r4.e_pt2,
+               "max_rel_err_vs_oracle": max(float(np.abs(de4.cpu().numpy() - G["deri"]).max()),
+                                            float(np.abs(dh4.cpu().numpy() - G["dh"]).max())) / scale,
+               "de0_abs_err_vs_oracle": abs(g0 - float(G["de0"]))}
+
     # the variational step on the same Psi0: H over Psi0 and its lowest
     # eigenpair by Davidson (residual 1e-10), against the stored E0 of the
     # oracle's Davidson
@@ -497,7 +528,7 @@ def run_gb300(args):
             "rpt2": qp.rpt2(res, e0),
             "e2e": e2e,
             "gpu_launches": launches, "roofline": roof, "clocks": ck, "mixed_precision": mixed,
-            "batched": batched, "workload_128_orbitals": wide, "davidson": dav}
+            "batched": batched, "workload_128_orbitals": wide, "davidson": dav, "adjoint": adj}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(meta, h, eri, dets, coefs, e0)
     print(json.dumps(line), flush=True)

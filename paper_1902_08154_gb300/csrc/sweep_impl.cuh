@@ -1460,6 +1460,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
           S.n0 = 0;
           S.n1 = 0;
           S.n2 = 0;
+          S.cnext = 0;
         }
         __syncthreads();
         const int c1 = min(c0 + kChunk, total);
@@ -1489,38 +1490,51 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
             element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, (B.h == 2) ? B.sb * norb + so : -1, cj * A[cc]);
           }
         }
-        for (int j = warp; j < S.n1; j += kWarps) {
-          const int r = S.L1[j];
-          const uint64_t* Jw = rw + (size_t)r * NW;
-          const double cj = rc[r];
-          const uint64_t part = rp[r];
-          uint32_t X, T;
-          int nx, nt;
-          excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
-          for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
-            const int cc = c - B.clo;
-            if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
-            int ro, so, x, y;
-            cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-            element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, B.sb * norb + so, cj * A[cc]);
-          });
-        }
-        for (int j = tid; j < S.n2; j += kThreads) {
-          const int r = S.L2[j];
-          const uint64_t* Jw = rw + (size_t)r * NW;
-          const double cj = rc[r];
-          const uint64_t part = rp[r];
-          uint32_t X, T;
-          int nx, nt;
-          excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
-          for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
-            const int cc = c - B.clo;
-            if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
-            int ro, so, x, y;
-            cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-            element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, (B.h == 2) ? B.sb * norb + so : -1,
-                               cj * A[cc]);
-          });
+        {  // row-reaching J (a warp each), then subset-reaching J (32 per draw), drawn dynamically
+          const int n1 = S.n1, n2 = S.n2;
+          for (;;) {
+            int jd = 0;
+            if (lane == 0) jd = atomicAdd(&S.cnext, 1);
+            jd = __shfl_sync(kFull, jd, 0);
+            if (jd < n1) {
+              const int j = jd;
+              const int r = S.L1[j];
+              const uint64_t* Jw = rw + (size_t)r * NW;
+              const double cj = rc[r];
+              const uint64_t part = rp[r];
+              uint32_t X, T;
+              int nx, nt;
+              excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
+              for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
+                const int cc = c - B.clo;
+                if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
+                int ro, so, x, y;
+                cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
+                element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, B.sb * norb + so, cj * A[cc]);
+              });
+            } else {
+              const int j0 = (jd - n1) * 32;
+              if (j0 >= n2) break;
+              const int j = j0 + lane;
+              if (j < n2) {
+                const int r = S.L2[j];
+                const uint64_t* Jw = rw + (size_t)r * NW;
+                const double cj = rc[r];
+                const uint64_t part = rp[r];
+                uint32_t X, T;
+                int nx, nt;
+                excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
+                for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
+                  const int cc = c - B.clo;
+                  if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
+                  int ro, so, x, y;
+                  cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
+                  element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, (B.h == 2) ? B.sb * norb + so : -1,
+                                     cj * A[cc]);
+                });
+              }
+            }
+          }
         }
         __syncthreads();
       }
