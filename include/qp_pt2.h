@@ -18,6 +18,12 @@
  * generator and batches of alpha sharing the holes of the generator, with
  * matrix elements from the Slater-Condon rules (Eqs. Hij).
  *
+ * Around the sweep: its adjoint (qp_pt2_grad), batches of independent sweeps
+ * in one CUDA graph (qp_pt2_batch_*), sweeps of a subset of the generators
+ * for the hybrid deterministic/stochastic E_PT2 (qp_pt2_eval_gens), target
+ * spaces (qp_pt2_set_target), and the variational step: H over Psi0 and its
+ * lowest eigenpair (qp_pt2_sigma, qp_pt2_davidson).
+ *
  * Conventions shared by every entry point
  * ----------------------------------------
  * Orbitals are 0-based, 1 <= norb <= 128; nint = (norb-1)/64 + 1.
@@ -48,8 +54,11 @@
  * Pointers: every array argument may be host memory or device memory of the
  * current device; the library detects which (cudaPointerGetAttributes) and
  * copies host arrays through its own device workspace.  The library never
- * frees or retains caller memory.  Calls run on the stream of the context's
- * configuration and return after the stream has finished the call's work.
+ * frees or retains caller memory.  Exceptions are stated at the entry
+ * point: the rank list of qp_pt2_eval_gens and the masks of
+ * qp_pt2_set_target are host arrays, and qp_pt2_eval_noalloc takes device
+ * arrays only.  Calls run on the stream of the context's configuration and
+ * return after the stream has finished the call's work.
  *
  * Errors: every entry point returns QP_OK (0) or a negative code; no call
  * aborts, traps or throws.  qp_pt2_strerror() names a code;
