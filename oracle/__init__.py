@@ -98,6 +98,8 @@ def lib():
         L.or_hamiltonian.argtypes = [P, I64, U64P, I64, I64P, I64P, DP, I]
         L.or_gradient.restype = I
         L.or_gradient.argtypes = [P, I64, U64P, DP, D, DP, DP, DP, DP, I, I64]
+        L.or_states.restype = I
+        L.or_states.argtypes = [P, I64, U64P, I, DP, DP, I64, U64P, DP, DP, DP, DP, C.c_void_p, I]
         L.or_max_threads.restype = I
         L.or_set_target.restype = None
         L.or_set_target.argtypes = [P, I, U64P, I, U64P, U64P]
@@ -226,6 +228,33 @@ class Hamiltonian:
                                   _ptr(haa), _ptr(g), _ptr(nc))
         return {"A": float(A[0]), "haa": float(haa[0]), "internal": bool(internal),
                 "gen_rank": int(g[0]), "n_connections": int(nc[0])}
+
+    def states(self, dets, coefs, e0, k, nthreads=0):
+        """Several states: ``coefs`` [nst][ndet], ``e0`` [nst].  Per-state
+        E_PT2 and sum A^2/D^2, the shared counts and digest, and the k best
+        determinants by the multi-state criterion (``sel_crit``) with A of
+        state 0 (``sel_num``)."""
+        dets = np.ascontiguousarray(dets, dtype=np.uint64)
+        coefs = np.ascontiguousarray(np.atleast_2d(coefs), dtype=np.float64)
+        e0 = np.ascontiguousarray(np.atleast_1d(e0), dtype=np.float64)
+        nst = coefs.shape[0]
+        if coefs.shape[1] != len(dets) or len(e0) != nst:
+            raise ValueError("coefs must be [nst][ndet] and e0 [nst]")
+        sel = np.zeros((max(k, 1), 2, self.nint), dtype=np.uint64)
+        crit = np.zeros(max(k, 1))
+        num = np.zeros(max(k, 1))
+        ept2 = np.zeros(nst)
+        s2 = np.zeros(nst)
+        res = Result()
+        rc = lib().or_states(self._p, len(dets), _ptr(dets), nst, _ptr(coefs), _ptr(e0), int(k), _ptr(sel),
+                             _ptr(crit), _ptr(num), _ptr(ept2), _ptr(s2), C.byref(res), int(nthreads))
+        if rc != 0:
+            raise ValueError(f"oracle states rejected its input (code {rc})")
+        out = res.as_dict()
+        m = res.n_selected
+        out.update(e_pt2_states=ept2, sum_e_over_d_states=s2, sel_dets=sel[:m], sel_crit=crit[:m],
+                   sel_num=num[:m])
+        return out
 
     def gradient(self, dets, coefs, e0, nthreads=0, mem_budget=0):
         """dE_PT2/dh (symmetric, halves off the diagonal), dE_PT2/d(packed

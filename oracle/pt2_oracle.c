@@ -24,7 +24,9 @@
  *     decreasing c_I^2 (Eqs. calpha, edetstoch; Appendix "CIPSI selection and
  *     PT2 energy")
  *   - selection of the k external determinants of largest |e_alpha|
- *     (Sec. "The basic algorithm", step 4).
+ *     (Sec. "The basic algorithm", step 4);
+ *   - several states: one PT2 per state and the selection criterion of
+ *     Angeli et al. quoted in Sec. "Selected CI" (or_states).
  *
  * Readings taken where the paper is silent (each is listed in the design
  * notes): "connected" means structurally connected (excitation degree 1 or 2);
@@ -44,6 +46,8 @@
  *                    g: every substitution alpha of I is tested against every
  *                    internal J within excitation degree 4 of I (the only J
  *                    that can be within degree 2 of alpha).
+ *   or_states     -- several states: the plain definition with every alpha
+ *                    formed once and A_k taken over all internal J.
  */
 #define _GNU_SOURCE
 #include <math.h>
@@ -894,6 +898,143 @@ int or_alpha(const or_ham *H, int64_t ndet, const uint64_t *dets, const double *
     *ncon = con;
     free(rank_of);
     return internal;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Several states at once (Sec. "Selected CI", the multi-state criterion of  */
+/* Angeli et al.).  One PT2 per state k,                                     */
+/*   E_PT2,k = sum_alpha A_k^2 / (E0_k - H_aa),  A_k = <Psi0_k|H|alpha>,     */
+/* and the selection criterion                                               */
+/*   e~_alpha = sum_k c_alpha,k A_k / max_I c_Ik^2,                          */
+/*   c_alpha,k = A_k / (E0_k - H_aa).                                        */
+/* Plain definition: the external space is the sorted, de-duplicated set of  */
+/* the single and double substitutions of every internal determinant, less   */
+/* the internal ones (and those outside the target space); for each alpha    */
+/* every internal J is tested and A_k = sum_J c_Jk <J|H|alpha> is formed     */
+/* directly.  No generator order enters.                                     */
+/* ------------------------------------------------------------------------ */
+
+#define OR_MAXST 8
+
+/*
+ * coefs: [nst][ndet] (state k's coefficients at coefs + k*ndet); e0: [nst].
+ * Outputs: e_pt2[nst], sum_e_over_d[nst]; res holds the counts, the digest,
+ * min |E0_k - H_aa| over alpha and k, n_tiny (|A_0| < 1e-14), and e_pt2 /
+ * sum_e_over_d of state 0.  The selection (k entries, best first by |e~|,
+ * ties by key) goes to sel_dets, sel_crit (e~) and sel_num (A_0).
+ * Returns 0, -1 (bad sizes, a state with no nonzero coefficient) or a
+ * validation code of or_validate.
+ */
+int or_states(const or_ham *H, int64_t ndet, const uint64_t *dets, int nst, const double *coefs,
+              const double *e0, int64_t k, uint64_t *sel_dets, double *sel_crit, double *sel_num,
+              double *e_pt2, double *sum_e_over_d, or_result *res, int nthreads)
+{
+    int nint = H->nint, nw = 2 * nint;
+    memset(res, 0, sizeof(*res));
+    res->min_abs_den = INFINITY;
+    if (nst < 1 || nst > OR_MAXST || k < 0) return -1;
+    int rc = or_validate(H, ndet, dets);
+    if (rc) return rc;
+    for (int s = 0; s < nst; s++) { e_pt2[s] = 0.0; sum_e_over_d[s] = 0.0; }
+    if (ndet == 0) return 0;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#else
+    nthreads = 1;
+#endif
+    /* weights 1 / max_I c_Ik^2 */
+    double w[OR_MAXST];
+    for (int s = 0; s < nst; s++) {
+        double m = 0.0;
+        for (int64_t i = 0; i < ndet; i++) {
+            double c = coefs[(size_t)s * ndet + i];
+            if (c * c > m) m = c * c;
+        }
+        if (!(m > 0.0)) return -1;
+        w[s] = 1.0 / m;
+    }
+    /* every substitution of every internal determinant, sorted */
+    int64_t nsub = or_n_substitutions(H), ncand = ndet * nsub;
+    uint64_t *cand = (uint64_t *)malloc(sizeof(uint64_t) * nw * (ncand > 0 ? ncand : 1));
+    for (int64_t i = 0; i < ndet; i++) or_substitutions(H, dets + i * nw, nsub, cand + i * nsub * nw);
+    uint64_t *srt = (uint64_t *)malloc(sizeof(uint64_t) * nw * ndet);
+    memcpy(srt, dets, sizeof(uint64_t) * nw * ndet);
+    g_nw_sort = nw;
+    qsort(cand, ncand, sizeof(uint64_t) * nw, key_qcmp);
+    qsort(srt, ndet, sizeof(uint64_t) * nw, key_qcmp);
+    /* distinct, external, inside the target space */
+    int64_t m = 0;
+    for (int64_t i = 0; i < ncand; i++) {
+        const uint64_t *a = cand + i * nw;
+        if (i > 0 && keycmp(a, cand + (i - 1) * nw, nw) == 0) continue;
+        if (is_member(srt, ndet, nw, a) || !in_target(H, a)) continue;
+        if (m != i) memcpy(cand + m * nw, a, sizeof(uint64_t) * nw);
+        m++;
+    }
+    /* A_k and H_aa per alpha */
+    double *A = (double *)calloc((size_t)(m > 0 ? m : 1) * nst, sizeof(double));
+    double *haa = (double *)malloc(sizeof(double) * (m > 0 ? m : 1));
+    int64_t *nc = (int64_t *)calloc((size_t)(m > 0 ? m : 1), sizeof(int64_t));
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
+#endif
+    for (int64_t a = 0; a < m; a++) {
+        const uint64_t *al = cand + a * nw;
+        nsum acc[OR_MAXST];
+        for (int s = 0; s < nst; s++) { acc[s].s = 0.0; acc[s].c = 0.0; }
+        int64_t n = 0;
+        for (int64_t j = 0; j < ndet; j++) {
+            const uint64_t *J = dets + j * nw;
+            if (or_degree(nint, J, al) > 2) continue;
+            double v = or_hij(H, J, al);
+            for (int s = 0; s < nst; s++) nsum_add(&acc[s], coefs[(size_t)s * ndet + j] * v);
+            n++;
+        }
+        for (int s = 0; s < nst; s++) A[(size_t)a * nst + s] = nsum_get(&acc[s]);
+        haa[a] = or_diag(H, al);
+        nc[a] = n;
+    }
+    /* totals and the selection, in alpha order */
+    nsum E[OR_MAXST], S2[OR_MAXST];
+    for (int s = 0; s < nst; s++) { E[s].s = E[s].c = 0.0; S2[s].s = S2[s].c = 0.0; }
+    topk tk;
+    topk_init(&tk, nw, k > 0 ? k : 1);
+    tk.k = k;
+    for (int64_t a = 0; a < m; a++) {
+        const uint64_t *al = cand + a * nw;
+        double crit = 0.0;
+        for (int s = 0; s < nst; s++) {
+            double Av = A[(size_t)a * nst + s], D = e0[s] - haa[a];
+            double e = Av * Av / D, q = Av / D;
+            nsum_add(&E[s], e);
+            nsum_add(&S2[s], q * q);
+            crit += w[s] * e;   /* c_alpha,k A_k / max_I c_Ik^2 */
+            if (fabs(D) < res->min_abs_den) res->min_abs_den = fabs(D);
+        }
+        res->n_perturbers++;
+        res->n_connections += nc[a];
+        if (fabs(A[(size_t)a * nst]) < 1e-14) res->n_tiny++;
+        uint64_t hk = or_key_hash(nw, al);
+        res->digest[0] += hk;
+        res->digest[1] ^= splitmix64(hk ^ 0x243F6A8885A308D3ull);
+        topk_push(&tk, crit, A[(size_t)a * nst], al);
+    }
+    for (int s = 0; s < nst; s++) { e_pt2[s] = nsum_get(&E[s]); sum_e_over_d[s] = nsum_get(&S2[s]); }
+    res->e_pt2 = e_pt2[0];
+    res->sum_e_over_d = sum_e_over_d[0];
+    int64_t *ord = (int64_t *)malloc(sizeof(int64_t) * (tk.n > 0 ? tk.n : 1));
+    for (int64_t i = 0; i < tk.n; i++) ord[i] = i;
+    qsort_r(ord, tk.n, sizeof(int64_t), topk_entry_cmp, &tk);
+    for (int64_t i = 0; i < tk.n; i++) {
+        if (sel_dets) memcpy(sel_dets + i * nw, tk.key + ord[i] * nw, 8 * nw);
+        if (sel_crit) sel_crit[i] = tk.e[ord[i]];
+        if (sel_num) sel_num[i] = tk.num[ord[i]];
+    }
+    res->n_selected = tk.n;
+    free(ord);
+    topk_free(&tk);
+    free(A); free(haa); free(nc); free(cand); free(srt);
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */
