@@ -21,8 +21,9 @@
  * Around the sweep: its adjoint (qp_pt2_grad), batches of independent sweeps
  * in one CUDA graph (qp_pt2_batch_*), sweeps of a subset of the generators
  * for the hybrid deterministic/stochastic E_PT2 (qp_pt2_eval_gens), target
- * spaces (qp_pt2_set_target), and the variational step: H over Psi0 and its
- * lowest eigenpair (qp_pt2_sigma, qp_pt2_davidson).
+ * spaces (qp_pt2_set_target), several states with the multi-state selection
+ * criterion (qp_pt2_eval_states), and the variational step: H over Psi0 and
+ * its lowest eigenpair (qp_pt2_sigma, qp_pt2_davidson).
  *
  * Conventions shared by every entry point
  * ----------------------------------------
@@ -55,9 +56,9 @@
  * current device; the library detects which (cudaPointerGetAttributes) and
  * copies host arrays through its own device workspace.  The library never
  * frees or retains caller memory.  Exceptions are stated at the entry
- * point: the rank list of qp_pt2_eval_gens and the masks of
- * qp_pt2_set_target are host arrays, and qp_pt2_eval_noalloc takes device
- * arrays only.  Calls run on the stream of the context's configuration and
+ * point: the rank list of qp_pt2_eval_gens, the energies of
+ * qp_pt2_eval_states and the masks of qp_pt2_set_target are host arrays,
+ * and qp_pt2_eval_noalloc takes device arrays only.  Calls run on the stream of the context's configuration and
  * return after the stream has finished the call's work.
  *
  * Errors: every entry point returns QP_OK (0) or a negative code; no call
@@ -179,6 +180,30 @@ int qp_pt2_eval_gens(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, const 
                      double e0, int64_t ngen, const int32_t *ranks, int64_t k, uint64_t *sel_dets,
                      double *sel_e, double *gen_eps, int64_t *gen_na, int64_t *gen_ncon,
                      qp_pt2_result *res);
+
+/* Several states at once (Sec. "Selected CI": one PT2 calculation per
+ * state, and the selection criterion of Angeli et al.):
+ *
+ *   A_s(alpha)     = <Psi0_s|H|alpha>,   c_alpha,s = A_s / (E0_s - H_aa)
+ *   E_PT2,s        = sum over external alpha of A_s^2 / (E0_s - H_aa)
+ *   e~(alpha)      = sum_s c_alpha,s A_s / max_I c_Is^2
+ *
+ * over the external determinants of the common internal space (dets).
+ * nstates in [1, 4]; coefs is double[nstates][ndet] (state s at
+ * coefs + s*ndet, host or device); e0 is a HOST array of nstates energies.
+ * res is an array of nstates results: res[s].e_pt2 and sum_e_over_d are
+ * state s's; the counts, digest, n_selected and n_tiny (of state 0's A) are
+ * shared; min_abs_denominator is the minimum over alpha and states.  The
+ * selection keeps the k determinants of largest |e~| (ties by key):
+ * sel_dets [k][2][nint], sel_crit [k] (e~), sel_num [k] (state 0's A); each
+ * may be NULL when k = 0.  FP64 contexts only (QP_ENOTSUP for mixed
+ * precision, or when nstates accumulators of the largest batch do not fit
+ * in one CTA's shared memory); QP_EINVAL for nstates out of range or a
+ * state whose coefficients are all zero.  Target spaces and sharding apply
+ * as in qp_pt2_eval. */
+int qp_pt2_eval_states(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, int nstates,
+                       const double *coefs, const double *e0, int64_t k, uint64_t *sel_dets,
+                       double *sel_crit, double *sel_num, qp_pt2_result *res);
 
 /* The variational step of CIPSI (Sec. "Davidson diagonalization"): the
  * Hamiltonian over Psi0 and its lowest eigenpair.

@@ -26,6 +26,7 @@ EXPORTS = (
     "qp_pt2_eval",
     "qp_pt2_eval_ex",
     "qp_pt2_eval_gens",
+    "qp_pt2_eval_states",
     "qp_pt2_sigma",
     "qp_pt2_set_target",
     "qp_pt2_davidson",
@@ -120,6 +121,8 @@ def load(path: str = SO):
     L.qp_pt2_davidson.argtypes = [vp, i64, vp, vp, dbl, C.c_int, vp, vp, C.POINTER(DavidsonInfo)]
     L.qp_pt2_eval_gens.restype = C.c_int
     L.qp_pt2_eval_gens.argtypes = [vp, i64, vp, vp, dbl, i64, vp, i64, vp, vp, vp, vp, vp, C.POINTER(Result)]
+    L.qp_pt2_eval_states.restype = C.c_int
+    L.qp_pt2_eval_states.argtypes = [vp, i64, vp, C.c_int, vp, vp, i64, vp, vp, vp, C.POINTER(Result)]
     L.qp_pt2_last_launches.restype = i64
     L.qp_pt2_last_launches.argtypes = [vp]
     L.qp_pt2_last_timings.restype = C.c_int
@@ -199,6 +202,19 @@ def qp_pt2_eval_gens(ctx, ndet, dets, coefs, e0, ranks, k=0, sel_dets=None, sel_
     if check:
         _check(rc)
     return rc, res
+
+
+def qp_pt2_eval_states(ctx, ndet, dets, coefs, e0, k=0, sel_dets=None, sel_crit=None, sel_num=None, check=True):
+    """Several states at once (``coefs``: [nstates, ndet]; ``e0``: host
+    energies); returns (return code, list of per-state Results)."""
+    e0 = np.ascontiguousarray(np.atleast_1d(e0), dtype=np.float64)
+    nst = len(e0)
+    res = (Result * max(nst, 1))()
+    rc = load().qp_pt2_eval_states(ctx, ndet, _ptr(dets), nst, _ptr(coefs), _ptr(e0), k, _ptr(sel_dets),
+                                   _ptr(sel_crit), _ptr(sel_num), res)
+    if check:
+        _check(rc)
+    return rc, [res[i] for i in range(nst)]
 
 
 def qp_pt2_sigma(ctx, ndet, dets, U, S):
@@ -334,6 +350,35 @@ class PT2:
             c = torch.zeros(len(dets), dtype=torch.float64, device=dets.device)
         _, e0, info = qp_pt2_davidson(self.ctx, len(dets), dets, c, guess, tol, max_iter)
         return e0, c, info
+
+    def eval_states(self, dets, coefs, e0, k, check=True):
+        """Several states of one internal space (``coefs`` [nstates, ndet],
+        ``e0`` [nstates]): per-state E_PT2 and sum A^2/D^2, the shared
+        counts, and the k determinants of largest multi-state criterion
+        (``sel_crit``) with state 0's numerator (``sel_num``), in the memory
+        kind of ``dets``."""
+        if isinstance(dets, np.ndarray):
+            coefs = np.ascontiguousarray(np.atleast_2d(coefs), dtype=np.float64)
+            sel = np.zeros((max(k, 1), 2, self.nint), dtype=np.uint64)
+            sc = np.zeros(max(k, 1))
+            sn = np.zeros(max(k, 1))
+        else:
+            import torch
+
+            coefs = coefs.reshape(-1, len(dets)).contiguous()
+            sel = torch.zeros((max(k, 1), 2, self.nint), dtype=torch.int64, device=dets.device)
+            sc = torch.zeros(max(k, 1), dtype=torch.float64, device=dets.device)
+            sn = torch.zeros(max(k, 1), dtype=torch.float64, device=dets.device)
+        rc, res = qp_pt2_eval_states(self.ctx, len(dets), dets, coefs, e0, k, sel if k else None,
+                                     sc if k else None, sn if k else None, check=check)
+        out = res[0].as_dict()
+        out["rc"] = rc
+        out["e_pt2_states"] = np.array([r.e_pt2 for r in res])
+        out["sum_e_over_d_states"] = np.array([r.sum_e_over_d for r in res])
+        m = res[0].n_selected
+        out.update(sel_dets=sel[:m], sel_crit=sc[:m], sel_num=sn[:m])
+        out["launches"] = qp_pt2_last_launches(self.ctx)
+        return out
 
     def eval_generators(self, dets, coefs, e0, ranks, k=0):
         """Sweep of the generators of the listed ranks (0 = largest c_I^2):

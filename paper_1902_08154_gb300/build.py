@@ -13,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 SO = os.path.join(OUT, "libqp_pt2.so")
-UNITS = ["qp_pt2.cu", "sweep.cu", "sweep_mixed.cu", "sweep_grad.cu", "noalloc.cu", "davidson.cu"]
+UNITS = ["qp_pt2.cu", "sweep.cu", "sweep_mixed.cu", "sweep_grad.cu", "sweep_states.cu", "noalloc.cu",
+         "davidson.cu"]
 HEADERS = ["common.cuh", "sweep_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -12,6 +12,7 @@ constexpr int kMaxOrb = 128;
 constexpr int kMaxElec = 64;   // per determinant (both spins); hole masks are uint64
 constexpr int kMaxBatch = kMaxElec + kMaxElec * (kMaxElec - 1) / 2;
 constexpr int kSelBins = 1024;  // |e| histogram: 128 binary exponents (2^-100 .. 2^27) x 8 sub-bins
+constexpr int kMaxStates = 4;   // states of one multi-state sweep
 
 // Fold of splitmix64 over the key words: the digest hash of a determinant.
 // splitmix64 is the generator of Steele, Lea & Flood (2014); its finaliser
@@ -105,6 +106,14 @@ struct SweepParams {
   // and (tgt_max_exc >= 0) at most tgt_max_exc electrons moved from tgt_ref
   int tgt_on, tgt_max_exc;
   uint64_t tgt_ref[4], tgt_core[4], tgt_del[4];
+  // several states (nst > 1, multi-state batch kernel only): state s has its
+  // coefficients at coefs + s*ndet, its records' coefficients at
+  // r_coef + s*rc_stride, its E0 in st_e0[s], its per-generator sums at
+  // eps + s*ndet and s2 + s*ndet; st_cmax[s] holds the bits of max_I |c_Is|
+  int nst;
+  int64_t rc_stride;
+  double st_e0[kMaxStates];
+  const unsigned long long* st_cmax;
 
   // wave of generator slots
   int wave_start;                 // first generator position (t) of this wave

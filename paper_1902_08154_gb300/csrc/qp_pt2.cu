@@ -23,6 +23,9 @@ int batch_blocks_per_sm(int nint, int mixed, size_t smem);
 int sweep_threads();
 cudaError_t launch_batch_grad(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_grad_gen(int nint, const SweepParams& p, int ngen, cudaStream_t st);
+size_t states_smem(int max_cells, int nst);
+int batch_blocks_per_sm_states(int nint, size_t smem);
+cudaError_t launch_batch_states(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
 }  // namespace qp
 
 using namespace qp;
@@ -122,6 +125,26 @@ struct DevResult {
   double e_pt2, s2;
   long long na, ncon;
 };
+
+// Several states: every coefficient finite, and per state (blockIdx.y) the
+// bits of max_I |c_Is| (non-negative doubles order as their bit patterns).
+__global__ void state_scan_kernel(int64_t ndet, const double* coefs, unsigned long long* cmax, int* err) {
+  const int s = blockIdx.y;
+  unsigned long long m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndet; i += (int64_t)gridDim.x * blockDim.x) {
+    const double c = coefs[(size_t)s * ndet + i];
+    if (!isfinite(c)) atomicOr(err, kErrCoef);
+    else {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(c));
+      m = b > m ? b : m;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(&cmax[s], m);
+}
 
 // One block: fixed-order sums over generators (rank order), each thread a
 // contiguous slice with Neumaier compensation, then a fixed tree.
@@ -264,7 +287,7 @@ struct qp_pt2_ctx {
   Buf in_dets, in_coefs, hkey, hkey2, hidx, hidx2, rkey, rkey2, order, rank_of, cub_tmp;
   Buf eps, s2, na, ncon, acc, res;
   Buf meta, r_words, r_coef, r_hmask, r_part, r_flag, b_ofs, b_ent, b_dead, queues;
-  Buf tk_e, tk_a, tk_key, tk_cnt, tk_tau, sel_hist, gen_list, gen_out;
+  Buf tk_e, tk_a, tk_key, tk_cnt, tk_tau, sel_hist, gen_list, gen_out, st_cmax;
   Buf cand_e, cand_a, cand_key, skey, skey2, perm, perm2, cub_tmp2;
   Buf out_sel, out_e, out_num, out_eps, out_na, out_ncon, out_rank;
   Buf g_dh, g_deri, g_wF, g_wH;
@@ -536,19 +559,35 @@ __global__ void gather_gen_kernel(int64_t n, const int32_t* ranks, const double*
 
 // The sweep; with gen_ranks (host array of ngen_list distinct ranks) only
 // those generators are swept and their eps, |A_I| and connections are
-// written to gen_eps / gen_na / gen_ncon in list order.
+// written to gen_eps / gen_na / gen_ncon in list order.  nst > 0 selects
+// the multi-state form: coefs holds nst states ([nst][ndet]), e0s (host)
+// their energies, res nst results, and sel_e receives the multi-state
+// criterion; e0 is then ignored.  The generator order is that of state 0
+// (no output depends on the order).
 static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const double* coefs, double e0,
                      int64_t k, uint64_t* sel_dets, double* sel_e, double* sel_num, double* eps_by_rank,
                      int64_t* na_by_rank, int64_t* ncon_by_rank, int32_t* rank_of_out, qp_pt2_result* res,
                      const int32_t* gen_ranks, int64_t ngen_list, double* gen_eps, int64_t* gen_na,
-                     int64_t* gen_ncon) {
+                     int64_t* gen_ncon, int nst = 0, const double* e0s = nullptr) {
+  const bool ms = nst > 0;
+  const int nsts = ms ? nst : 1;
   if (!x || !res) return fail(QP_EINVAL, "ctx or res is NULL");
   if (ndet < 0 || k < 0) return fail(QP_EINVAL, "ndet and k must be non-negative");
   if (ndet > 0 && (!dets || !coefs)) return fail(QP_EINVAL, "dets or coefs is NULL");
   if (ndet >= (1ll << 31)) return fail(QP_EINVAL, "ndet must be below 2^31");
+  if (ms) {
+    if (nst > kMaxStates) return fail(QP_EINVAL, "nstates must be in [1, 4]");
+    if (!e0s) return fail(QP_EINVAL, "e0 is NULL");
+    for (int s = 0; s < nst; s++)
+      if (!std::isfinite(e0s[s])) return fail(QP_EINVAL, "E0 is not finite");
+    if (x->cfg.precision != QP_FP64) return fail(QP_ENOTSUP, "the multi-state sweep is FP64 only");
+    e0 = e0s[0];
+  }
   if (!std::isfinite(e0)) return fail(QP_EINVAL, "E0 is not finite");
-  memset(res, 0, sizeof(*res));
-  res->min_abs_denominator = INFINITY;
+  for (int s = 0; s < nsts; s++) {
+    memset(res + s, 0, sizeof(*res));
+    res[s].min_abs_denominator = INFINITY;
+  }
   x->launches = 0;
   x->timed = false;
   if (ndet == 0) return QP_OK;
@@ -559,7 +598,7 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   const double* d_coefs;
   CUDA_TRY(cudaEventRecord(x->ev[0], st));
   if ((rc = stage_in(x, x->in_dets, dets, (size_t)ndet * nw, &d_dets))) return rc;
-  if ((rc = stage_in(x, x->in_coefs, coefs, (size_t)ndet, &d_coefs))) return rc;
+  if ((rc = stage_in(x, x->in_coefs, coefs, (size_t)ndet * nsts, &d_coefs))) return rc;
 
   // ---- validation and generator order ----
   const size_t nd = (size_t)ndet;
@@ -597,15 +636,35 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
                                            x->order.as<int32_t>(), (int)ndet, 0, 64, st));
   rank_kernel<<<nb, tb, 0, st>>>(ndet, x->order.as<int32_t>(), x->rank_of.as<int32_t>());
   x->launches++;
+  unsigned long long hcmax[kMaxStates] = {0};
+  if (ms) {  // every state's coefficients: finite, and max_I |c_Is|
+    if ((rc = x->st_cmax.grow(8 * (size_t)kMaxStates))) return rc;
+    CUDA_TRY(cudaMemsetAsync(x->st_cmax.p, 0, 8 * (size_t)kMaxStates, st));
+    const int sb = (int)std::min<int64_t>((ndet + tb - 1) / tb, 1024);
+    state_scan_kernel<<<dim3(sb, nst), tb, 0, st>>>(ndet, d_coefs, x->st_cmax.as<unsigned long long>(), d_err);
+    x->launches++;
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(hcmax, x->st_cmax.p, 8 * (size_t)nst, cudaMemcpyDeviceToHost, st));
+  }
   int herr = 0;
   CUDA_TRY(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   if (herr & kErrOcc) return fail(QP_EINVAL, "a determinant has the wrong occupation or bits beyond norb");
   if (herr & kErrCoef) return fail(QP_EINVAL, "a coefficient is not finite");
   if (herr & kErrDup) return fail(QP_EDUP, "duplicate determinant in Psi0");
+  for (int s = 0; s < (ms ? nst : 0); s++)
+    if (hcmax[s] == 0ull) return fail(QP_EINVAL, "a state has no nonzero coefficient");
 
   // ---- sweep: waves of generator slots, prep + batch kernels ----
-  const int grid = x->grid;
+  size_t smem = x->smem;
+  int grid = x->grid;
+  if (ms) {  // nst accumulators per CTA: fewer CTAs per SM may fit
+    smem = states_smem(x->max_cells, nst);
+    int bps = batch_blocks_per_sm_states(nint, smem);
+    if (bps < 1) return fail(QP_ENOTSUP, "the accumulators of this many states do not fit in shared memory");
+    if (bps > x->bps) bps = x->bps;
+    grid = bps * x->nsm;
+  }
   const int64_t cap = k > 0 ? k + x->max_cells : 1;
   const int shard_count = x->cfg.shard_count, shard_index = x->cfg.shard_index;
   const int64_t ngen = gen_ranks ? ngen_list
@@ -620,27 +679,27 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   const int64_t ent_per = bucket_entries_per_record(x->nel);
   const int64_t ent_cap = (int64_t)nd * ent_per;
   const size_t dwords = (size_t)(x->nbat + 31) / 32;
-  const size_t per_slot = sizeof(GenMeta) + nd * (8 * nw + 8 + 8 + 8 + 4) + 4 * (size_t)(x->nbat + 2) +
-                          4 * (size_t)ent_cap + 4 * dwords;
+  const size_t per_slot = sizeof(GenMeta) + nd * (8 * nw + 8 * (size_t)nsts + 8 + 8 + 4) +
+                          4 * (size_t)(x->nbat + 2) + 4 * (size_t)ent_cap + 4 * dwords;
   int64_t W = (int64_t)(kWaveBudget / per_slot);
   if (W < 1) W = 1;
   if (W > ngen) W = ngen > 0 ? ngen : 1;
   const int64_t nwaves = ngen > 0 ? (ngen + W - 1) / W : 0;
   const size_t ws = (size_t)W;
-  if ((rc = x->eps.grow(8 * nd)) || (rc = x->s2.grow(8 * nd)) || (rc = x->na.grow(8 * nd)) ||
+  if ((rc = x->eps.grow(8 * nd * nsts)) || (rc = x->s2.grow(8 * nd * nsts)) || (rc = x->na.grow(8 * nd)) ||
       (rc = x->ncon.grow(8 * nd)) || (rc = x->meta.grow(sizeof(GenMeta) * ws)) ||
-      (rc = x->r_words.grow(8 * nd * nw * ws)) || (rc = x->r_coef.grow(8 * nd * ws)) ||
+      (rc = x->r_words.grow(8 * nd * nw * ws)) || (rc = x->r_coef.grow(8 * nd * ws * nsts)) ||
       (rc = x->r_hmask.grow(8 * nd * ws)) || (rc = x->r_part.grow(8 * nd * ws)) ||
       (rc = x->r_flag.grow(4 * nd * ws)) || (rc = x->b_ofs.grow(4 * (size_t)(x->nbat + 2) * ws)) ||
       (rc = x->b_ent.grow(4 * (size_t)ent_cap * ws)) || (rc = x->b_dead.grow(4 * dwords * ws)) || (rc = x->queues.grow(4 * (size_t)(nwaves + 1))) ||
       (rc = x->tk_e.grow(8 * (size_t)cap * grid)) || (rc = x->tk_a.grow(8 * (size_t)cap * grid)) ||
       (rc = x->tk_key.grow(8 * (size_t)cap * grid * nw)) || (rc = x->tk_cnt.grow(4 * (size_t)grid)) ||
-      (rc = x->tk_tau.grow(8 * (size_t)grid)) || (rc = x->res.grow(sizeof(DevResult))) ||
+      (rc = x->tk_tau.grow(8 * (size_t)grid)) || (rc = x->res.grow(sizeof(DevResult) * nsts)) ||
       (rc = x->sel_hist.grow(4 * (size_t)kSelBins)))
     return rc;
   CUDA_TRY(cudaMemsetAsync(x->sel_hist.p, 0, 4 * (size_t)kSelBins, st));
-  CUDA_TRY(cudaMemsetAsync(x->eps.p, 0, 8 * nd, st));
-  CUDA_TRY(cudaMemsetAsync(x->s2.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->eps.p, 0, 8 * nd * nsts, st));
+  CUDA_TRY(cudaMemsetAsync(x->s2.p, 0, 8 * nd * nsts, st));
   CUDA_TRY(cudaMemsetAsync(x->na.p, 0, 8 * nd, st));
   CUDA_TRY(cudaMemsetAsync(x->ncon.p, 0, 8 * nd, st));
   CUDA_TRY(cudaMemsetAsync(x->queues.p, 0, 4 * (size_t)(nwaves + 1), st));
@@ -705,6 +764,12 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   p.sel_hist = x->sel_hist.as<unsigned int>();
   p.max_cells = x->max_cells;
   p.err = d_err;
+  if (ms) {
+    p.nst = nst;
+    p.rc_stride = (int64_t)(nd * ws);
+    for (int s = 0; s < nst; s++) p.st_e0[s] = e0s[s];
+    p.st_cmax = x->st_cmax.as<unsigned long long>();
+  }
   CUDA_TRY(cudaEventRecord(x->ev[1], st));
   for (int64_t w = 0; w < nwaves; w++) {
     p.wave_start = (int)(w * W);
@@ -712,14 +777,18 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
     p.last_wave = (w == nwaves - 1);
     p.queue = x->queues.as<int>() + w;
     CUDA_TRY(launch_prep(nint, p, p.wave_slots, st));
-    CUDA_TRY(launch_batch(nint, p, grid, x->smem, st));
+    if (ms) CUDA_TRY(launch_batch_states(nint, p, grid, smem, st));
+    else CUDA_TRY(launch_batch(nint, p, grid, smem, st));
     x->launches += 2;
   }
   CUDA_TRY(cudaEventRecord(x->ev[2], st));
   DevResult* dres = x->res.as<DevResult>();
-  finalize_kernel<<<1, 1024, 0, st>>>(ndet, p.eps, p.s2, reinterpret_cast<const long long*>(p.na),
-                                      reinterpret_cast<const long long*>(p.ncon), dres);
-  x->launches++;
+  for (int s = 0; s < nsts; s++) {
+    finalize_kernel<<<1, 1024, 0, st>>>(ndet, p.eps + (size_t)s * nd, p.s2 + (size_t)s * nd,
+                                        reinterpret_cast<const long long*>(p.na),
+                                        reinterpret_cast<const long long*>(p.ncon), dres + s);
+    x->launches++;
+  }
   CUDA_TRY(cudaGetLastError());
 
   // ---- selection merge ----
@@ -800,27 +869,29 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
       return rc;
   }
 
-  DevResult hres;
+  DevResult hres[kMaxStates];
   unsigned long long hacc[kAccWords];
-  CUDA_TRY(cudaMemcpyAsync(&hres, dres, sizeof(hres), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(hres, dres, sizeof(DevResult) * nsts, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaEventRecord(x->ev_end, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   x->timed = true;
   if (herr & kErrBucket) return fail(QP_ECUDA, "internal error: bucket capacity exceeded");
-  res->e_pt2 = hres.e_pt2;
-  res->sum_e_over_d = hres.s2;
-  res->n_perturbers = hres.na;
-  res->n_connections = hres.ncon;
-  res->n_selected = nsel;
-  res->n_tiny = (int64_t)hacc[kAccTiny];
-  res->perturber_digest[0] = hacc[kAccDigest0];
-  res->perturber_digest[1] = hacc[kAccDigest1];
   double md;
   memcpy(&md, &hacc[kAccMinDen], sizeof(md));
-  res->min_abs_denominator = md;
-  if (hres.na > 0 && md < 1e-12) return fail(QP_ESINGULAR, "a denominator E0 - H_aa is below 1e-12");
+  for (int s = 0; s < nsts; s++) {
+    res[s].e_pt2 = hres[s].e_pt2;
+    res[s].sum_e_over_d = hres[s].s2;
+    res[s].n_perturbers = hres[s].na;
+    res[s].n_connections = hres[s].ncon;
+    res[s].n_selected = nsel;
+    res[s].n_tiny = (int64_t)hacc[kAccTiny];
+    res[s].perturber_digest[0] = hacc[kAccDigest0];
+    res[s].perturber_digest[1] = hacc[kAccDigest1];
+    res[s].min_abs_denominator = md;
+  }
+  if (hres[0].na > 0 && md < 1e-12) return fail(QP_ESINGULAR, "a denominator E0 - H_aa is below 1e-12");
   return QP_OK;
 }
 
@@ -850,6 +921,14 @@ extern "C" int qp_pt2_eval_gens(qp_pt2_ctx* x, int64_t ndet, const uint64_t* det
   }
   return eval_core(x, ndet, dets, coefs, e0, k, sel_dets, sel_e, nullptr, nullptr, nullptr, nullptr, nullptr, res,
                    ranks, ngen, gen_eps, gen_na, gen_ncon);
+}
+
+extern "C" int qp_pt2_eval_states(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, int nstates,
+                                  const double* coefs, const double* e0, int64_t k, uint64_t* sel_dets,
+                                  double* sel_crit, double* sel_num, qp_pt2_result* res) {
+  if (nstates < 1) return fail(QP_EINVAL, "nstates must be in [1, 4]");
+  return eval_core(x, ndet, dets, coefs, 0.0, k, sel_dets, sel_crit, sel_num, nullptr, nullptr, nullptr, nullptr,
+                   res, nullptr, 0, nullptr, nullptr, nullptr, nstates, e0);
 }
 
 extern "C" int qp_pt2_eval(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const double* coefs, double e0,

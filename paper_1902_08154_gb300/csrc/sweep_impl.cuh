@@ -291,6 +291,7 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(const __grid_constant__ 
 #pragma unroll
       for (int w = 0; w < NW; w++) rw[(size_t)r * NW + w] = Jw[w];
       rc[r] = p.coefs[j];
+      for (int st = 1; st < p.nst; st++) rc[st * p.rc_stride + r] = p.coefs[(size_t)st * p.ndet + j];
       rh[r] = hmask;
       rp[r] = part;
       rf[r] = (p.rank_of[j] < g) ? 1u : 0u;
@@ -865,12 +866,29 @@ __device__ __noinline__ void compact_selection(const SweepParams& p, BatchShared
 // Three CTAs per SM for one word per spin; two words per spin come with
 // larger accumulators (at most two CTAs fit in shared memory), so those
 // kernels take the registers of two CTAs and do not spill.
-template <int NINT, typename NT, bool GRAD = false>
+//
+// MS = true: the multi-state form (several states at once, FP64 only).
+// Each state s has its own accumulator A_s (dynamic shared memory, one
+// stride of max_cells each); a (J, cell) element is formed once and added
+// with c_Js to every A_s.  The cells pass forms e_s = A_s^2/(E0_s - H_aa)
+// for every state, sums each into its own eps and s2, and offers the
+// determinant to the selection with the criterion sum_s w_s e_s,
+// w_s = 1/max_I c_Is^2 (Sec. "Selected CI", the criterion of Angeli et al.).
+template <int NINT, typename NT, bool GRAD = false, bool MS = false>
 __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(const __grid_constant__ SweepParams p) {
+  static_assert(!(MS && GRAD), "the gradient is a one-state form");
+  static_assert(!MS || sizeof(NT) == 8, "the multi-state form is FP64");
   constexpr int NW = 2 * NINT;
   extern __shared__ __align__(16) unsigned char dyn[];
   double* A = reinterpret_cast<double*>(dyn);
-  uint32_t* ban = reinterpret_cast<uint32_t*>(A + p.max_cells);
+  const int mc = p.max_cells;  // stride between the states' accumulators
+  uint32_t* ban = reinterpret_cast<uint32_t*>(A + (MS ? p.nst : 1) * mc);
+  // multi-state extras after the bans: the CTA group's coefficients per
+  // state, c_I per state and the weights w_s
+  double* ms_gc = reinterpret_cast<double*>(ban + (((mc + 31) / 32 + 1) & ~1));
+  double* ms_cI = ms_gc + kGroup * kMaxStates;
+  double* ms_w = ms_cI + kMaxStates;
+  const int nst = MS ? p.nst : 1;
   __shared__ BatchShared<NINT, NT> S;
   const NT* eri_n = numer_eri<NT>(p);
   const NT* h_n = numer_h<NT>(p);
@@ -940,6 +958,13 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
         S.cI = (NT)M->cI;
         S.g = M->g;
         S.slot = slot;
+      }
+      if constexpr (MS) {
+        if (tid < nst) {
+          ms_cI[tid] = p.coefs[(size_t)tid * p.ndet + p.order[M->g]];
+          const double m = __longlong_as_double((long long)p.st_cmax[tid]);
+          ms_w[tid] = 1.0 / (m * m);
+        }
       }
       __syncthreads();
     }
@@ -1021,6 +1046,9 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
     }
     // zero the accumulator, the bans; row sums for H_aa
     for (int c = tid; c < B.nct; c += kThreads) A[c] = 0.0;
+    if constexpr (MS)
+      for (int st = 1; st < nst; st++)
+        for (int c = tid; c < B.nct; c += kThreads) A[st * mc + c] = 0.0;
     if (GRAD)
       for (int x = tid; x < kMaxOrb; x += kThreads) {
         S.rowW2[x] = 0.0;
@@ -1181,6 +1209,8 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
 #pragma unroll
           for (int w = 0; w < NW; w++) S.gJw[tid][w] = rw[(size_t)r * NW + w];
           S.gcj[tid] = (NT)rc[r];
+          if constexpr (MS)
+            for (int st = 0; st < nst; st++) ms_gc[tid * kMaxStates + st] = rc[st * p.rc_stride + r];
           uint32_t xs, ts;
           int nxs, nts;
           excitation_sets<NINT, NT>(B, S, rp[r], rh[r], &xs, &nxs, &ts, &nts);
@@ -1233,6 +1263,9 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
           const int rcode = B.sa * norb + ro;
           const int scode = (B.h == 2) ? B.sb * norb + so : -1;
           double acc = 0.0;
+          double accs[kMaxStates];  // multi-state form: one sum per state
+#pragma unroll
+          for (int st = 0; st < kMaxStates; st++) accs[st] = 0.0;
           for (int j = 0; j < m; j++) {
             bool general = true;
             NT v = NT(0);
@@ -1256,9 +1289,21 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
               }
             }
             if (general) v = element<NINT, NT>(eri_n, h_n, norb, S.gJw[j], S.gX[j], S.gnx[j], S.gT[j], S.gnt[j], rcode, scode);
-            acc += (double)(S.gcj[j] * v);
+            if constexpr (MS) {
+#pragma unroll
+              for (int st = 0; st < kMaxStates; st++)
+                if (st < nst) accs[st] = fma(ms_gc[j * kMaxStates + st], (double)v, accs[st]);
+            } else {
+              acc += (double)(S.gcj[j] * v);
+            }
           }
-          A[cc] += acc;
+          if constexpr (MS) {
+#pragma unroll
+            for (int st = 0; st < kMaxStates; st++)
+              if (st < nst) A[st * mc + cc] += accs[st];
+          } else {
+            A[cc] += acc;
+          }
           con += m;
         }
         __syncthreads();
@@ -1276,6 +1321,11 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
             const int r = S.L1[j];
             const uint64_t* Jw = rw + (size_t)r * NW;
             const NT cj = (NT)rc[r];
+            double cjs[kMaxStates];
+            if constexpr (MS) {
+#pragma unroll
+              for (int st = 0; st < kMaxStates; st++) cjs[st] = st < nst ? rc[st * p.rc_stride + r] : 0.0;
+            }
             const uint64_t part = rp[r];
             uint32_t X, T;
             int nx, nt;
@@ -1287,7 +1337,14 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
               cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
               const int rcode = B.sa * norb + ro;
               const int scode = B.sb * norb + so;
-              atomicAdd(&A[cc], (double)(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode)));
+              if constexpr (MS) {
+                const double v = (double)element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode);
+#pragma unroll
+                for (int st = 0; st < kMaxStates; st++)
+                  if (st < nst) atomicAdd(&A[st * mc + cc], cjs[st] * v);
+              } else {
+                atomicAdd(&A[cc], (double)(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode)));
+              }
               con++;
             });
           } else {
@@ -1298,6 +1355,11 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
               const int r = S.L2[j];
               const uint64_t* Jw = rw + (size_t)r * NW;
               const NT cj = (NT)rc[r];
+              double cjs[kMaxStates];
+              if constexpr (MS) {
+#pragma unroll
+                for (int st = 0; st < kMaxStates; st++) cjs[st] = st < nst ? rc[st * p.rc_stride + r] : 0.0;
+              }
               const uint64_t part = rp[r];
               uint32_t X, T;
               int nx, nt;
@@ -1309,7 +1371,14 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
                 cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
                 const int rcode = B.sa * norb + ro;
                 const int scode = (B.h == 2) ? B.sb * norb + so : -1;
-                atomicAdd(&A[cc], (double)(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode)));
+                if constexpr (MS) {
+                  const double v = (double)element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode);
+#pragma unroll
+                  for (int st = 0; st < kMaxStates; st++)
+                    if (st < nst) atomicAdd(&A[st * mc + cc], cjs[st] * v);
+                } else {
+                  atomicAdd(&A[cc], (double)(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode)));
+                }
                 con++;
               });
             }
@@ -1331,74 +1400,145 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
     const unsigned long long tau = S.tau;
     double acc_e = 0.0, acc_s2 = 0.0;
     unsigned long long acc_na = 0, acc_d0 = 0, acc_d1 = 0, acc_min = 0x7FF0000000000000ull, acc_tiny = 0;
-    for (int cc = tid; cc < B.nct; cc += kThreads) {
-      if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
-      int ro, so, x, y;
-      cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
-      double a = A[cc];
-      if (B.h == 2) {  // the generator's own term c_I <I|H|alpha>
-        NT v;
-        const int a1 = S.iRow[x], b2 = S.iCol[y];
-        if (B.kind == 2) {
-          v = flip_sign(eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)], (a1 ^ b2) < 0);
-        } else {
-          const int a2 = S.iRow[y], b1 = S.iCol[x];
-          v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
-          const int lo = so < B.qb ? so : B.qb, hi = so < B.qb ? B.qb : so;
-          v = flip_sign(v, ((a1 ^ b2) < 0 ? 1 : 0) ^ ((ro > lo && ro < hi) ? 1 : 0));
+    double acc_es[kMaxStates], acc_s2s[kMaxStates];  // multi-state form: sums per state
+#pragma unroll
+    for (int st = 0; st < kMaxStates; st++) acc_es[st] = acc_s2s[st] = 0.0;
+    if constexpr (MS) {
+      for (int cc = tid; cc < B.nct; cc += kThreads) {
+        if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
+        int ro, so, x, y;
+        cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
+        double vI = 0.0;  // <I|H|alpha> for the generator's own term
+        if (B.h == 2) {
+          const int a1 = S.iRow[x], b2 = S.iCol[y];
+          if (B.kind == 2) {
+            vI = (double)flip_sign(eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)], (a1 ^ b2) < 0);
+          } else {
+            const int a2 = S.iRow[y], b1 = S.iCol[x];
+            NT v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
+            const int lo = so < B.qb ? so : B.qb, hi = so < B.qb ? B.qb : so;
+            vI = (double)flip_sign(v, ((a1 ^ b2) < 0 ? 1 : 0) ^ ((ro > lo && ro < hi) ? 1 : 0));
+          }
+          con++;
         }
-        a += (double)(S.cI * v);
-        con++;
+        // E0_s - H_aa = ((E0_s - base) - u0[x]) - rest, as the one-state form
+        double rest = 0.0;
+        if (B.kind == 2) rest = S.u1[y] + p.Jm[ro * norb + so];
+        else if (B.kind == 1) rest = S.u0[y] + (p.Jm[ro * norb + so] - p.Km[ro * norb + so]);
+        double crit = 0.0, a0 = 0.0;
+#pragma unroll
+        for (int st = 0; st < kMaxStates; st++) {
+          if (st >= nst) break;
+          const double a = A[st * mc + cc] + ms_cI[st] * vI;
+          double D = (p.st_e0[st] - S.base) - S.u0[x];
+          if (B.kind != 0) D -= rest;
+          const unsigned long long dex = ((unsigned long long)__double_as_longlong(D) >> 52) & 0x7FFull;
+          const double inv = (dex > 523ull && dex < 1523ull) ? recip_nr<2>(D) : 1.0 / D;
+          const double q = a * inv;
+          const double e = a * q;
+          acc_es[st] += e;
+          acc_s2s[st] += q * q;
+          crit += ms_w[st] * e;  // c_alpha,s A_s / max_I c_Is^2
+          const unsigned long long db = abs_bits(D);
+          acc_min = db < acc_min ? db : acc_min;
+          if (st == 0) a0 = a;
+        }
+        acc_na++;
+        if (abs_bits(a0) < 0x3D06849B86A12B9Bull) acc_tiny++;
+        uint64_t key[NW];
+        const int kwr = B.sa * NINT + (ro >> 6), kws = (B.h == 2) ? B.sb * NINT + (so >> 6) : -1;
+#pragma unroll
+        for (int w = 0; w < NW; w++)
+          key[w] = S.kbase[w] | (w == kwr ? 1ull << (ro & 63) : 0ull) | (w == kws ? 1ull << (so & 63) : 0ull);
+        uint64_t hk = 0;
+#pragma unroll
+        for (int w = 0; w < NW; w++) hk = splitmix64(hk ^ key[w]);
+        acc_d0 += hk;
+        acc_d1 ^= splitmix64(hk ^ 0x243F6A8885A308D3ull);
+        if (p.k > 0) {
+          const unsigned long long eb = abs_bits(crit);
+          if (eb >= tau) {
+            atomicAdd(&p.sel_hist[sel_bin(eb)], 1u);
+            const int pos = atomicAdd(&S.tkcnt, 1);
+            te[pos] = crit;
+            ta[pos] = a0;
+#pragma unroll
+            for (int w = 0; w < NW; w++) tk[(size_t)pos * NW + w] = key[w];
+          }
+        }
       }
-      // D = E0 - H_aa from the per-batch row sums
-      double D = S.dx[x];
-      if (B.kind == 2) D -= S.u1[y] + p.Jm[ro * norb + so];
-      else if (B.kind == 1) D -= S.u0[y] + (p.Jm[ro * norb + so] - p.Km[ro * norb + so]);
-      // |D| in [2^-500, 2^500]: Newton reciprocal; otherwise the division
-      const unsigned long long dex = ((unsigned long long)__double_as_longlong(D) >> 52) & 0x7FFull;
-      const double inv = (dex > 523ull && dex < 1523ull) ? recip_nr<sizeof(NT) == 8 ? 2 : 1>(D) : 1.0 / D;
-      const double q = a * inv;
-      acc_e = fma(a, q, acc_e);  // e = A q
-      acc_s2 += q * q;
-      acc_na++;
-      if (GRAD) {
-        // numerator weight 2A/D for loop 3; (A/D)^2 weights the diagonal
-        A[cc] = 2.0 * q;
-        const double w2 = q * q;
-        atomicAdd(&S.rowW2[x], w2);
-        if (B.kind == 2) atomicAdd(&S.colW2[y], w2);
-        if (B.kind == 1) atomicAdd(&S.rowW2[y], w2);
-        if (B.h == 2) w_grad(p, ro, B.sa, so, B.sb, w2);
-      }
-      // |a| < 1e-14, compared on the bit pattern (no FP64 compare)
-      if (abs_bits(a) < 0x3D06849B86A12B9Bull) acc_tiny++;
-      // |D| and |e| as bit patterns, off the FP64 pipe
-      const unsigned long long db = abs_bits(D);
-      acc_min = db < acc_min ? db : acc_min;
-      uint64_t key[NW];  // alpha's words; selects keep them in registers
-      const int kwr = B.sa * NINT + (ro >> 6), kws = (B.h == 2) ? B.sb * NINT + (so >> 6) : -1;
-#pragma unroll
-      for (int w = 0; w < NW; w++)
-        key[w] = S.kbase[w] | (w == kwr ? 1ull << (ro & 63) : 0ull) | (w == kws ? 1ull << (so & 63) : 0ull);
-      uint64_t hk = 0;
-#pragma unroll
-      for (int w = 0; w < NW; w++) hk = splitmix64(hk ^ key[w]);
-      acc_d0 += hk;
-      acc_d1 ^= splitmix64(hk ^ 0x243F6A8885A308D3ull);
-      // e = A q is formed only when it can reach the threshold: with biased
-      // exponents ea, eq of A and q, |A q| < 2^(ea + eq - 2044), so
-      // ea + eq <= et + 1021 (et: the exponent of tau) puts it below tau
-      const int ea = (int)(abs_bits(a) >> 52), eqx = (int)(abs_bits(q) >> 52);
-      if (p.k > 0 && (tau == 0ull || ea + eqx > (int)(tau >> 52) + 1021)) {
-        const double e = a * q;
-        const unsigned long long eb = abs_bits(e);
-        if (eb >= tau) {
-          atomicAdd(&p.sel_hist[sel_bin(eb)], 1u);
-          const int pos = atomicAdd(&S.tkcnt, 1);
-          te[pos] = e;
-          ta[pos] = a;
-#pragma unroll
-          for (int w = 0; w < NW; w++) tk[(size_t)pos * NW + w] = key[w];
+      acc_e = acc_es[0];
+      acc_s2 = acc_s2s[0];
+    } else {
+      for (int cc = tid; cc < B.nct; cc += kThreads) {
+        if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
+        int ro, so, x, y;
+        cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
+        double a = A[cc];
+        if (B.h == 2) {  // the generator's own term c_I <I|H|alpha>
+          NT v;
+          const int a1 = S.iRow[x], b2 = S.iCol[y];
+          if (B.kind == 2) {
+            v = flip_sign(eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)], (a1 ^ b2) < 0);
+          } else {
+            const int a2 = S.iRow[y], b1 = S.iCol[x];
+            v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
+            const int lo = so < B.qb ? so : B.qb, hi = so < B.qb ? B.qb : so;
+            v = flip_sign(v, ((a1 ^ b2) < 0 ? 1 : 0) ^ ((ro > lo && ro < hi) ? 1 : 0));
+          }
+          a += (double)(S.cI * v);
+          con++;
+        }
+        // D = E0 - H_aa from the per-batch row sums
+        double D = S.dx[x];
+        if (B.kind == 2) D -= S.u1[y] + p.Jm[ro * norb + so];
+        else if (B.kind == 1) D -= S.u0[y] + (p.Jm[ro * norb + so] - p.Km[ro * norb + so]);
+        // |D| in [2^-500, 2^500]: Newton reciprocal; otherwise the division
+        const unsigned long long dex = ((unsigned long long)__double_as_longlong(D) >> 52) & 0x7FFull;
+        const double inv = (dex > 523ull && dex < 1523ull) ? recip_nr<sizeof(NT) == 8 ? 2 : 1>(D) : 1.0 / D;
+        const double q = a * inv;
+        acc_e = fma(a, q, acc_e);  // e = A q
+        acc_s2 += q * q;
+        acc_na++;
+        if (GRAD) {
+          // numerator weight 2A/D for loop 3; (A/D)^2 weights the diagonal
+          A[cc] = 2.0 * q;
+          const double w2 = q * q;
+          atomicAdd(&S.rowW2[x], w2);
+          if (B.kind == 2) atomicAdd(&S.colW2[y], w2);
+          if (B.kind == 1) atomicAdd(&S.rowW2[y], w2);
+          if (B.h == 2) w_grad(p, ro, B.sa, so, B.sb, w2);
+        }
+        // |a| < 1e-14, compared on the bit pattern (no FP64 compare)
+        if (abs_bits(a) < 0x3D06849B86A12B9Bull) acc_tiny++;
+        // |D| and |e| as bit patterns, off the FP64 pipe
+        const unsigned long long db = abs_bits(D);
+        acc_min = db < acc_min ? db : acc_min;
+        uint64_t key[NW];  // alpha's words; selects keep them in registers
+        const int kwr = B.sa * NINT + (ro >> 6), kws = (B.h == 2) ? B.sb * NINT + (so >> 6) : -1;
+  #pragma unroll
+        for (int w = 0; w < NW; w++)
+          key[w] = S.kbase[w] | (w == kwr ? 1ull << (ro & 63) : 0ull) | (w == kws ? 1ull << (so & 63) : 0ull);
+        uint64_t hk = 0;
+  #pragma unroll
+        for (int w = 0; w < NW; w++) hk = splitmix64(hk ^ key[w]);
+        acc_d0 += hk;
+        acc_d1 ^= splitmix64(hk ^ 0x243F6A8885A308D3ull);
+        // e = A q is formed only when it can reach the threshold: with biased
+        // exponents ea, eq of A and q, |A q| < 2^(ea + eq - 2044), so
+        // ea + eq <= et + 1021 (et: the exponent of tau) puts it below tau
+        const int ea = (int)(abs_bits(a) >> 52), eqx = (int)(abs_bits(q) >> 52);
+        if (p.k > 0 && (tau == 0ull || ea + eqx > (int)(tau >> 52) + 1021)) {
+          const double e = a * q;
+          const unsigned long long eb = abs_bits(e);
+          if (eb >= tau) {
+            atomicAdd(&p.sel_hist[sel_bin(eb)], 1u);
+            const int pos = atomicAdd(&S.tkcnt, 1);
+            te[pos] = e;
+            ta[pos] = a;
+  #pragma unroll
+            for (int w = 0; w < NW; w++) tk[(size_t)pos * NW + w] = key[w];
+          }
         }
       }
     }
@@ -1449,6 +1589,29 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
           atomicXor(&p.digest[1], x1);
           atomicMin(p.min_den_bits, m);
           if (tt) atomicAdd(p.n_tiny, tt);
+        }
+      }
+      if constexpr (MS) {  // the other states' eps and s2, one at a time
+#pragma unroll
+        for (int st = 1; st < kMaxStates; st++) {
+          if (st >= nst) break;
+          __syncthreads();
+          S.red_t[0][tid] = acc_es[st];
+          S.red_t[1][tid] = acc_s2s[st];
+          __syncthreads();
+          if (warp == 0) {
+            double ue = 0.0, us = 0.0;
+            for (int i = lane; i < kThreads; i += 32) {
+              ue += S.red_t[0][i];
+              us += S.red_t[1][i];
+            }
+            ue = warp_sum(ue);
+            us = warp_sum(us);
+            if (lane == 0 && (ue != 0.0 || us != 0.0)) {
+              atomicAdd(&p.eps[(size_t)st * p.ndet + g], ue);
+              atomicAdd(&p.s2[(size_t)st * p.ndet + g], us);
+            }
+          }
         }
       }
     }
