@@ -50,8 +50,8 @@ FP64_OPS_PER_PERTURBER = 9
 # lanes per clock per SM: 152 SMs x 2 x 2.07 GHz operations per second
 FP64_PEAK_GOPS = 152 * 2 * 2.07
 # DRAM bytes (read + write) of the sweep kernels over one sweep of the bench
-# workload (prep 1.11 + 5.15 GB, batch 2.86 + 0.25 GB), from one ncu capture
-TRAFFIC_BYTES_PER_SWEEP = 9.37e9
+# workload (prep 1.00 + 5.15 GB, batch 2.85 + 0.25 GB), from one ncu capture
+TRAFFIC_BYTES_PER_SWEEP = 9.24e9
 
 
 def load_workload(name=WORKLOAD):
