@@ -99,7 +99,7 @@ def lib():
         L.or_gradient.restype = I
         L.or_gradient.argtypes = [P, I64, U64P, DP, D, DP, DP, DP, DP, I, I64]
         L.or_states.restype = I
-        L.or_states.argtypes = [P, I64, U64P, I, DP, DP, I64, U64P, DP, DP, DP, DP, C.c_void_p, I]
+        L.or_states.argtypes = [P, I64, U64P, I, DP, DP, I64, U64P, DP, DP, DP, DP, C.c_void_p, I, I, I]
         L.or_max_threads.restype = I
         L.or_set_target.restype = None
         L.or_set_target.argtypes = [P, I, U64P, I, U64P, U64P]
@@ -229,11 +229,12 @@ class Hamiltonian:
         return {"A": float(A[0]), "haa": float(haa[0]), "internal": bool(internal),
                 "gen_rank": int(g[0]), "n_connections": int(nc[0])}
 
-    def states(self, dets, coefs, e0, k, nthreads=0):
+    def states(self, dets, coefs, e0, k, nthreads=0, shard=(0, 0)):
         """Several states: ``coefs`` [nst][ndet], ``e0`` [nst].  Per-state
         E_PT2 and sum A^2/D^2, the shared counts and digest, and the k best
         determinants by the multi-state criterion (``sel_crit``) with A of
-        state 0 (``sel_num``)."""
+        state 0 (``sel_num``).  ``shard`` = (index, count) keeps the
+        perturbers of the generators of rank index mod count."""
         dets = np.ascontiguousarray(dets, dtype=np.uint64)
         coefs = np.ascontiguousarray(np.atleast_2d(coefs), dtype=np.float64)
         e0 = np.ascontiguousarray(np.atleast_1d(e0), dtype=np.float64)
@@ -247,7 +248,8 @@ class Hamiltonian:
         s2 = np.zeros(nst)
         res = Result()
         rc = lib().or_states(self._p, len(dets), _ptr(dets), nst, _ptr(coefs), _ptr(e0), int(k), _ptr(sel),
-                             _ptr(crit), _ptr(num), _ptr(ept2), _ptr(s2), C.byref(res), int(nthreads))
+                             _ptr(crit), _ptr(num), _ptr(ept2), _ptr(s2), C.byref(res), int(nthreads),
+                             int(shard[0]), int(shard[1]))
         if rc != 0:
             raise ValueError(f"oracle states rejected its input (code {rc})")
         out = res.as_dict()

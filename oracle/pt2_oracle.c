@@ -922,17 +922,22 @@ int or_alpha(const or_ham *H, int64_t ndet, const uint64_t *dets, const double *
  * min |E0_k - H_aa| over alpha and k, n_tiny (|A_0| < 1e-14), and e_pt2 /
  * sum_e_over_d of state 0.  The selection (k entries, best first by |e~|,
  * ties by key) goes to sel_dets, sel_crit (e~) and sel_num (A_0).
+ * shard_count > 0 keeps only the alpha whose generator (the lowest-ranked
+ * connected J, ranks by state 0's c^2: the canonical rule of Eqs. calpha and
+ * edetstoch) has a rank equal to shard_index modulo shard_count.
  * Returns 0, -1 (bad sizes, a state with no nonzero coefficient) or a
  * validation code of or_validate.
  */
 int or_states(const or_ham *H, int64_t ndet, const uint64_t *dets, int nst, const double *coefs,
               const double *e0, int64_t k, uint64_t *sel_dets, double *sel_crit, double *sel_num,
-              double *e_pt2, double *sum_e_over_d, or_result *res, int nthreads)
+              double *e_pt2, double *sum_e_over_d, or_result *res, int nthreads, int shard_index,
+              int shard_count)
 {
     int nint = H->nint, nw = 2 * nint;
     memset(res, 0, sizeof(*res));
     res->min_abs_den = INFINITY;
     if (nst < 1 || nst > OR_MAXST || k < 0) return -1;
+    if (shard_count < 0 || (shard_count > 0 && (shard_index < 0 || shard_index >= shard_count))) return -1;
     int rc = or_validate(H, ndet, dets);
     if (rc) return rc;
     for (int s = 0; s < nst; s++) { e_pt2[s] = 0.0; sum_e_over_d[s] = 0.0; }
@@ -971,10 +976,13 @@ int or_states(const or_ham *H, int64_t ndet, const uint64_t *dets, int nst, cons
         if (m != i) memcpy(cand + m * nw, a, sizeof(uint64_t) * nw);
         m++;
     }
-    /* A_k and H_aa per alpha */
+    /* A_k, H_aa and the generator rank per alpha */
     double *A = (double *)calloc((size_t)(m > 0 ? m : 1) * nst, sizeof(double));
     double *haa = (double *)malloc(sizeof(double) * (m > 0 ? m : 1));
     int64_t *nc = (int64_t *)calloc((size_t)(m > 0 ? m : 1), sizeof(int64_t));
+    int64_t *gen = (int64_t *)malloc(sizeof(int64_t) * (m > 0 ? m : 1));
+    int64_t *rank_of = (int64_t *)malloc(sizeof(int64_t) * ndet);
+    or_ranks(ndet, coefs, rank_of);
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
 #endif
@@ -982,17 +990,19 @@ int or_states(const or_ham *H, int64_t ndet, const uint64_t *dets, int nst, cons
         const uint64_t *al = cand + a * nw;
         nsum acc[OR_MAXST];
         for (int s = 0; s < nst; s++) { acc[s].s = 0.0; acc[s].c = 0.0; }
-        int64_t n = 0;
+        int64_t n = 0, g = -1;
         for (int64_t j = 0; j < ndet; j++) {
             const uint64_t *J = dets + j * nw;
             if (or_degree(nint, J, al) > 2) continue;
             double v = or_hij(H, J, al);
             for (int s = 0; s < nst; s++) nsum_add(&acc[s], coefs[(size_t)s * ndet + j] * v);
             n++;
+            if (g < 0 || rank_of[j] < g) g = rank_of[j];
         }
         for (int s = 0; s < nst; s++) A[(size_t)a * nst + s] = nsum_get(&acc[s]);
         haa[a] = or_diag(H, al);
         nc[a] = n;
+        gen[a] = g;
     }
     /* totals and the selection, in alpha order */
     nsum E[OR_MAXST], S2[OR_MAXST];
@@ -1002,6 +1012,7 @@ int or_states(const or_ham *H, int64_t ndet, const uint64_t *dets, int nst, cons
     tk.k = k;
     for (int64_t a = 0; a < m; a++) {
         const uint64_t *al = cand + a * nw;
+        if (shard_count > 0 && gen[a] % shard_count != shard_index) continue;
         double crit = 0.0;
         for (int s = 0; s < nst; s++) {
             double Av = A[(size_t)a * nst + s], D = e0[s] - haa[a];
@@ -1033,7 +1044,7 @@ int or_states(const or_ham *H, int64_t ndet, const uint64_t *dets, int nst, cons
     res->n_selected = tk.n;
     free(ord);
     topk_free(&tk);
-    free(A); free(haa); free(nc); free(cand); free(srt);
+    free(A); free(haa); free(nc); free(gen); free(rank_of); free(cand); free(srt);
     return 0;
 }
 

@@ -8,7 +8,9 @@ edetstoch, which is what the paper's distributed PT2 exploits, Sec.
 * E_PT2, sum A^2/D^2, |A| and the connection count add;
 * the digest words add modulo 2^64 and xor;
 * the selection is the k best of the union of the shards' selections, in the
-  library's order (|e| descending, determinant key ascending).
+  library's order (|e| descending, determinant key ascending);
+* a multi-state sweep's per-state E_PT2 and sum A^2/D^2 add state by state,
+  and its selection (by the multi-state criterion) merges as above.
 """
 from __future__ import annotations
 
@@ -33,6 +35,10 @@ def merge_totals(parts):
         mins.append(p.get("min_abs_den", float("inf")))
     out["digest"] = (d0, d1)
     out["min_abs_den"] = min(mins) if mins else float("inf")
+    if parts and all("e_pt2_states" in p for p in parts):
+        out["e_pt2_states"] = np.sum([np.asarray(p["e_pt2_states"], dtype=np.float64) for p in parts], axis=0)
+        out["sum_e_over_d_states"] = np.sum([np.asarray(p["sum_e_over_d_states"], dtype=np.float64)
+                                             for p in parts], axis=0)
     return out
 
 
@@ -58,8 +64,10 @@ def distributed_merge(dist, res, sel_e, sel_dets, k, device):
     """Exchange step of a sharded sweep: all-gather every rank's partial
     totals and selection, then merge them identically on every rank.
 
-    res: this rank's result dict; sel_e: tensor [n]; sel_dets: tensor
-    [n, 2, nint] (int64 view of the uint64 words).  Returns (totals, e, dets)."""
+    res: this rank's result dict (with ``e_pt2_states`` and
+    ``sum_e_over_d_states`` for a multi-state sweep, the same number of
+    states on every rank); sel_e: tensor [n]; sel_dets: tensor [n, 2, nint]
+    (int64 view of the uint64 words).  Returns (totals, e, dets)."""
     import torch
 
     ws = dist.get_world_size()
@@ -68,7 +76,10 @@ def distributed_merge(dist, res, sel_e, sel_dets, k, device):
     as_i64 = lambda u: u - (1 << 64) if u >= (1 << 63) else u  # noqa: E731
     ints = torch.tensor([int(res["n_perturbers"]), int(res["n_connections"]), int(res.get("n_tiny", 0)),
                          as_i64(d0), as_i64(d1), int(sel_e.numel())], dtype=torch.int64, device=device)
-    flts = torch.tensor([res["e_pt2"], res["sum_e_over_d"], res.get("min_abs_den", float("inf"))],
+    st_e = [float(x) for x in res.get("e_pt2_states", [])]
+    st_s = [float(x) for x in res.get("sum_e_over_d_states", [])]
+    nst = len(st_e)
+    flts = torch.tensor([res["e_pt2"], res["sum_e_over_d"], res.get("min_abs_den", float("inf"))] + st_e + st_s,
                         dtype=torch.float64, device=device)
     gi = [torch.zeros_like(ints) for _ in range(ws)]
     gf = [torch.zeros_like(flts) for _ in range(ws)]
@@ -77,9 +88,13 @@ def distributed_merge(dist, res, sel_e, sel_dets, k, device):
     parts = []
     for a, b in zip(gi, gf):
         a, b = a.cpu().tolist(), b.cpu().tolist()
-        parts.append({"n_perturbers": a[0], "n_connections": a[1], "n_tiny": a[2],
-                      "digest": (a[3] & MASK64, a[4] & MASK64), "e_pt2": b[0], "sum_e_over_d": b[1],
-                      "min_abs_den": b[2], "n_sel": a[5]})
+        part = {"n_perturbers": a[0], "n_connections": a[1], "n_tiny": a[2],
+                "digest": (a[3] & MASK64, a[4] & MASK64), "e_pt2": b[0], "sum_e_over_d": b[1],
+                "min_abs_den": b[2], "n_sel": a[5]}
+        if nst:
+            part["e_pt2_states"] = b[3:3 + nst]
+            part["sum_e_over_d_states"] = b[3 + nst:3 + 2 * nst]
+        parts.append(part)
     m = max(p["n_sel"] for p in parts)
     nw = sel_dets.shape[1] * sel_dets.shape[2] if sel_dets.dim() == 3 else sel_dets.shape[1]
     pe = torch.zeros(max(m, 1), dtype=torch.float64, device=device)

@@ -97,3 +97,52 @@ def test_merge_selection_order():
     # |e| ties (0.5, 0.5) are broken by the key: [4,1] < [5,1]
     assert d.tolist() == [[4, 1], [5, 1], [1, 1], [9, 9]]
     assert e.tolist() == [0.5, -0.5, -0.3, 0.3]
+
+
+def _states_case():
+    import oracle
+    from paper_1902_08154_gb300 import synthetic as S
+
+    ham, dets, c, e0 = _case()
+    c1 = S.random_coefs(len(dets), 64, decay=0.02)
+    return ham, dets, np.stack([c, c1]), [e0, e0 - 0.15]
+
+
+def _states_worker(rank, world, port, k, out_path):
+    import torch
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_1902_08154_gb300.shard import distributed_merge
+
+    ham, dets, C, E0 = _states_case()
+    # this rank's generators (rank r % world), several states at once
+    r = ham.states(dets, C, E0, k=k, nthreads=1, shard=(rank, world))
+    tot, e, d = distributed_merge(dist, r, torch.from_numpy(r["sel_crit"]),
+                                  torch.from_numpy(r["sel_dets"].view(np.int64)), k, "cpu")
+    if rank == 0:
+        np.savez(out_path, e=e, d=d, e_states=tot["e_pt2_states"], s_states=tot["sum_e_over_d_states"],
+                 n=tot["n_perturbers"], nc=tot["n_connections"], d0=np.uint64(tot["digest"][0]),
+                 d1=np.uint64(tot["digest"][1]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_merge_of_a_multi_state_sweep(tmp_path, oracle_mod):
+    import torch.multiprocessing as mp
+
+    k = 30
+    out = str(tmp_path / "merged_states.npz")
+    mp.start_processes(_states_worker, args=(2, _free_port(), k, out), nprocs=2, start_method="spawn", join=True)
+    ham, dets, C, E0 = _states_case()
+    ref = ham.states(dets, C, E0, k=k)
+    m = np.load(out)
+    assert int(m["n"]) == ref["n_perturbers"]
+    assert int(m["nc"]) == ref["n_connections"]
+    assert (int(m["d0"]), int(m["d1"])) == tuple(ref["digest"])
+    np.testing.assert_allclose(m["e_states"], ref["e_pt2_states"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(m["s_states"], ref["sum_e_over_d_states"], rtol=1e-12, atol=0)
+    assert np.array_equal(m["d"], ref["sel_dets"].reshape(k, -1))
+    np.testing.assert_allclose(m["e"], ref["sel_crit"], rtol=1e-12, atol=0)

@@ -141,3 +141,31 @@ def test_states_largest_accumulators(qp, oracle_mod):
     ref = ham.states(dets, C[:3], E0[:3], k=20)
     _check_states(pt2.eval_states(d, _dev(C[:3]), E0[:3], 20), ref)
     pt2.close()
+
+
+def test_states_shards_on_one_gpu(qp, oracle_mod):
+    """Two generator shards of a multi-state sweep (generators of rank i mod 2),
+    run one after the other: each against the oracle's shard, and their merge
+    against the whole sweep."""
+    from paper_1902_08154_gb300.shard import merge_selections, merge_totals
+
+    norb, na, nb = 16, 4, 4
+    h, eri, ham, dets, C, E0 = _states_case(oracle_mod, norb, na, nb, 120, 2, 61)
+    k = 60
+    parts, es, ds = [], [], []
+    for i in range(2):
+        pt2 = qp.PT2(norb, na, nb, _dev(h), _dev(eri), shard_index=i, shard_count=2)
+        got = pt2.eval_states(_dev(dets), _dev(C), E0, k)
+        _check_states(got, ham.states(dets, C, E0, k=k, shard=(i, 2)))
+        parts.append(got)
+        es.append(as_np(got["sel_crit"]))
+        ds.append(as_np(got["sel_dets"]).view(np.uint64).reshape(len(es[-1]), -1))
+        pt2.close()
+    full = ham.states(dets, C, E0, k=k)
+    tot = merge_totals(parts)
+    assert tot["n_perturbers"] == full["n_perturbers"]
+    assert tot["n_connections"] == full["n_connections"]
+    assert tuple(tot["digest"]) == tuple(full["digest"])
+    assert np.abs(tot["e_pt2_states"] - full["e_pt2_states"]).max() <= E_TOL
+    e, d = merge_selections(es, ds, k)
+    check_selection(d, e, full["sel_dets"], full["sel_crit"])

@@ -116,3 +116,28 @@ def test_states_rejects_a_zero_state(oracle_mod):
     c0 = S.random_coefs(len(dets), 46)
     with pytest.raises(ValueError):
         ham.states(dets, np.stack([c0, np.zeros_like(c0)]), [e0, e0], k=5)
+
+
+def test_states_shards_follow_the_generator_rule(oracle_mod):
+    """Shard (i, n) keeps the perturbers of the generators of rank i mod n
+    (Eqs. calpha, edetstoch): with one state its energy is the sum of the
+    one-state sweep's eps over those ranks; the shards add up to the whole."""
+    ham, dets, e0 = _space(oracle_mod)
+    c0 = S.random_coefs(len(dets), 47, decay=0.05)
+    c1 = S.random_coefs(len(dets), 48, decay=0.02)
+    ref = ham.sweep(dets, c0, e0, k=0)
+    n = 3
+    for i in range(n):
+        part = ham.states(dets, c0[None, :], [e0], k=0, shard=(i, n))
+        assert part["e_pt2_states"][0] == pytest.approx(ref["eps_by_rank"][i::n].sum(), abs=1e-12)
+        assert part["n_perturbers"] == int(ref["na_by_rank"][i::n].sum())
+        assert part["n_connections"] == int(ref["ncon_by_rank"][i::n].sum())
+    C, E0 = np.stack([c0, c1]), [e0, e0 - 0.2]
+    full = ham.states(dets, C, E0, k=10**6)
+    parts = [ham.states(dets, C, E0, k=10**6, shard=(i, n)) for i in range(n)]
+    assert sum(p["n_perturbers"] for p in parts) == full["n_perturbers"]
+    assert sum(p["n_connections"] for p in parts) == full["n_connections"]
+    np.testing.assert_allclose(sum(p["e_pt2_states"] for p in parts), full["e_pt2_states"], rtol=0, atol=1e-12)
+    assert (sum(p["digest"][0] for p in parts) % (1 << 64)) == full["digest"][0]
+    keys = sorted(d.tobytes() for p in parts for d in p["sel_dets"])
+    assert keys == sorted(d.tobytes() for d in full["sel_dets"])
