@@ -169,3 +169,41 @@ def test_states_shards_on_one_gpu(qp, oracle_mod):
     assert np.abs(tot["e_pt2_states"] - full["e_pt2_states"]).max() <= E_TOL
     e, d = merge_selections(es, ds, k)
     check_selection(d, e, full["sel_dets"], full["sel_crit"])
+
+
+def test_states_full_size_cfg2_sampled(qp, oracle_mod):
+    """The 64-orbital, 10^4-determinant workload with two states (its stored
+    Psi0, and a seeded second vector with E0 - 0.1): state 0's totals against
+    the oracle's stored sweep, and sampled selected determinants recomputed by
+    the oracle one by one (A_s and H_aa by the Slater-Condon rules, then the
+    multi-state criterion)."""
+    import json
+    import os
+
+    gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    P = np.load(os.path.join(gold, "cfg2_psi0.npz"))
+    E = np.load(os.path.join(gold, "cfg2_expected.npz"))
+    meta = json.loads(str(P["meta"]))
+    summ = json.loads(str(E["summary"]))
+    h, eri = S.hamiltonian(meta["norb"], meta["rank"], meta["seed"])
+    ham = oracle_mod.Hamiltonian(meta["norb"], meta["nalpha"], meta["nbeta"], h, eri)
+    dets = P["dets"]
+    C = np.stack([P["coefs"], S.random_coefs(len(dets), 71, decay=0.001)])
+    E0 = np.array([float(P["e0"]), float(P["e0"]) - 0.1])
+    pt2 = qp.PT2(meta["norb"], meta["nalpha"], meta["nbeta"], _dev(h), _dev(eri))
+    got = pt2.eval_states(_dev(dets), _dev(C), E0, meta["k"])
+    pt2.close()
+    assert got["n_perturbers"] == summ["n_perturbers"]
+    assert got["n_connections"] == summ["n_connections"]
+    assert tuple(got["digest"]) == tuple(int(x) for x in summ["digest"])
+    assert abs(got["e_pt2_states"][0] - summ["e_pt2"]) <= E_TOL
+    sel, crit, num = as_np(got["sel_dets"]).view(np.uint64), as_np(got["sel_crit"]), as_np(got["sel_num"])
+    assert len(crit) == meta["k"]
+    assert np.all(np.abs(crit[:-1]) >= np.abs(crit[1:]))
+    w = 1.0 / np.max(C * C, axis=1)
+    for i in np.random.default_rng(5).choice(len(crit), 24, replace=False):
+        a = [ham.alpha(dets, C[s], sel[i]) for s in range(2)]
+        assert not a[0]["internal"] and a[0]["n_connections"] > 0
+        ref = sum(w[s] * a[s]["A"] ** 2 / (E0[s] - a[s]["haa"]) for s in range(2))
+        assert abs(crit[i] - ref) <= 1e-12 + 1e-10 * abs(ref)
+        assert abs(num[i] - a[0]["A"]) <= 1e-12 + 1e-10 * abs(a[0]["A"])
