@@ -65,6 +65,7 @@ def _check_states(got, ref):
     (40, 3, 3, 80, 100000, 3, 9, None),    # k above the perturber count
     (70, 3, 3, 60, 50, 2, 12, 6),          # two words per spin
     (112, 3, 3, 40, 30, 3, 15, 4),         # opposite-spin batches in two row tiles
+    (64, 2, 2, 60, 50, 2, 16, 6),          # 62 x 62 cells: two accumulators of 31 KB each
 ])
 def test_states_match_oracle(qp, oracle_mod, norb, na, nb, ndet, k, nst, seed, rank):
     h, eri, ham, dets, C, E0 = _states_case(oracle_mod, norb, na, nb, ndet, nst, seed, rank)
