@@ -82,7 +82,7 @@ extern "C" {
 #define QP_ESINGULAR (-4)  /* some |E0 - H_aa| < 1e-12; results still filled */
 #define QP_ENOMEM (-5)     /* device allocation failed */
 #define QP_ECUDA (-6)      /* CUDA runtime error */
-#define QP_ENOTSUP (-8)    /* configuration not supported by this build */
+#define QP_ENOTSUP (-8)    /* configuration not supported by the library */
 #define QP_ENOTCONV (-9)  /* Davidson stopped above its residual tolerance */
 
 #define QP_FP64 0          /* every step in FP64 */

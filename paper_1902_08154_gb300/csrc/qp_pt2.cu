@@ -355,7 +355,7 @@ extern "C" int qp_pt2_create(qp_pt2_ctx** out, int norb, int n_alpha, int n_beta
   if (cfg) c = *cfg;
   if (c.precision != QP_FP64 && c.precision != QP_MIXED) return fail(QP_EINVAL, "unknown precision");
   if (c.threads != 0 && c.threads != sweep_threads())
-    return fail(QP_ENOTSUP, "threads per CTA is fixed at 256 in this build");
+    return fail(QP_ENOTSUP, "threads per CTA is fixed at 256 in this library");
   const int64_t M = (int64_t)norb * (norb + 1) / 2, P = M * (M + 1) / 2;
   // symmetry of h (host copy either way)
   std::vector<double> hh((size_t)norb * norb);
@@ -507,7 +507,7 @@ extern "C" const char* qp_pt2_strerror(int code) {
     case QP_ESINGULAR: return "a denominator E0 - H_aa is below 1e-12 in magnitude";
     case QP_ENOMEM: return "device memory allocation failed";
     case QP_ECUDA: return "CUDA runtime error";
-    case QP_ENOTSUP: return "not supported by this build";
+    case QP_ENOTSUP: return "not supported by the library";
     case QP_ENOTCONV: return "Davidson did not reach the residual tolerance";
     default: return "unknown error";
   }
