@@ -39,19 +39,27 @@ METRIC = "EN-PT2 perturbers/s and generators/s on 1 GB300 vs plain FP64 GPU swee
 UNIT = "perturbers/s"
 L2_FLUSH_BYTES = 256 << 20
 
-# The sweep is bound by the FP64 pipe, the scarce unit of this GPU.  The
-# algorithmic FP64 work (an FMA counted as one operation): per connection
-# (J, alpha) the one FMA of A_alpha += c_J <J|H|alpha>; per perturber the
-# incremental H_aa (3 adds), D = E0 - H_aa, 1/D, q = A/D, e = A q and the two
-# accumulations of e and q^2.
+# The sweep is gather-and-bit work with FP64 arithmetic; on this GPU the FP64
+# pipe is the scarce unit.  Algorithmic FP64 work per unit (an FMA counts as
+# one operation), as the method defines it: per connection (J, alpha) the
+# one FMA of A_alpha += c_J <J|H|alpha>; per perturber the incremental
+# diagonal H_aa (about 20 operations: the Fock-diagonal and two-index terms
+# of the particles and holes), one division and two FMAs (e = A^2/D and the
+# sum of A^2/D^2).  The kernels form H_aa from per-batch row sums in 3 adds
+# and 1/D by a Newton reciprocal; the smallest form the kernels execute,
+# 9 operations per perturber, is reported beside it.
 FP64_OPS_PER_CONNECTION = 1
-FP64_OPS_PER_PERTURBER = 9
-# FP64 peak: 1.25 TFLOP/s nominal (FMA = 2 flops) at 2.07 GHz is 2 FP64
-# lanes per clock per SM: 152 SMs x 2 x 2.07 GHz operations per second
-FP64_PEAK_GOPS = 152 * 2 * 2.07
+FP64_OPS_PER_PERTURBER = 23
+FP64_OPS_PER_PERTURBER_MIN = 9
+# Integer work per unit: about 15 XOR/POPC/add operations per connection
+# (excitation degree and phase) per 64-bit word of a spin string, and
+# 2 x 2 x nint XOR+POPC per pair test of the coarse filter (N_det per
+# generator).
+INT_OPS_PER_CONNECTION_PER_WORD = 15
 # DRAM bytes (read + write) of the sweep kernels over one sweep of the bench
-# workload (prep 1.00 + 5.15 GB, batch 2.85 + 0.25 GB), from one ncu capture
-TRAFFIC_BYTES_PER_SWEEP = 9.24e9
+# workload, from one ncu capture of the current kernels (None when the
+# kernels have changed since the capture).
+TRAFFIC_BYTES_PER_SWEEP = None
 
 
 def load_workload(name=WORKLOAD):
@@ -562,16 +570,33 @@ def run_gb300(args):
     if world == 1 and not args.ndet and not args.no_states:
         states = states_leg(qp, torch, pt2, d_dets, k, flush, stream)
 
-    # roofline of the dominant kernel (the persistent sweep)
+    # roofline of the dominant kernel (the persistent sweep), against the
+    # FP64 and integer rates measured on this GPU in this run
+    from paper_1902_08154_gb300 import peaks
+
+    pk64 = peaks.measure("fp64")
+    pkint = peaks.measure("int")
     ms_sweep = statistics.mean(sweep_ms)
     ops = FP64_OPS_PER_CONNECTION * res["n_connections"] + FP64_OPS_PER_PERTURBER * res["n_perturbers"]
+    ops_min = FP64_OPS_PER_CONNECTION * res["n_connections"] + FP64_OPS_PER_PERTURBER_MIN * res["n_perturbers"]
     achieved = ops / (ms_sweep * 1e-3) / 1e9
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "G FP64 op/s",
-            "frac": achieved / FP64_PEAK_GOPS, "traffic": None if args.ndet else TRAFFIC_BYTES_PER_SWEEP,
+    int_ops = (INT_OPS_PER_CONNECTION_PER_WORD * nint * res["n_connections"]
+               + 4 * nint * float(ndet) * float(ndet) / max(world, 1))
+    int_ach = int_ops / (ms_sweep * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": pk64["gops"], "unit": "G FP64 op/s",
+            "frac": achieved / pk64["gops"], "traffic": None if args.ndet else TRAFFIC_BYTES_PER_SWEEP,
             "kernel": "qp::prep_kernel + qp::batch_kernel (all waves of one sweep)",
             "kernel_ms": ms_sweep, "call_ms": statistics.mean(call_ms),
-            "peak_source": "derived from the nominal FP64 rate: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz",
-            "ops_model": f"{FP64_OPS_PER_CONNECTION} FP64 op/connection + {FP64_OPS_PER_PERTURBER} FP64 op/perturber"}
+            "peak_source": "measured in this run: FP64 FMA throughput kernel (paper_1902_08154_gb300/csrc/peaks.cu), "
+                           f"{pk64['ops_per_sm_clock']:.3f} FMA per SM clock at {pk64['implied_sm_mhz']:.0f} MHz",
+            "ops_model": f"{FP64_OPS_PER_CONNECTION} FP64 op/connection + {FP64_OPS_PER_PERTURBER} FP64 op/perturber",
+            "frac_min_ops": ops_min / (ms_sweep * 1e-3) / 1e9 / pk64["gops"],
+            "min_ops_model": f"{FP64_OPS_PER_CONNECTION} FP64 op/connection + {FP64_OPS_PER_PERTURBER_MIN} "
+                             "FP64 op/perturber (the operations the kernels execute at least)",
+            "int_issue": {"achieved": int_ach, "peak": pkint["gops"], "unit": "G int op/s",
+                          "frac": int_ach / pkint["gops"],
+                          "ops_model": f"{INT_OPS_PER_CONNECTION_PER_WORD} x nint per connection + "
+                                       "4 x nint per coarse-filter pair test"}}
     if rank != 0:
         return 0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

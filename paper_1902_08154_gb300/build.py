@@ -13,6 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 SO = os.path.join(OUT, "libqp_pt2.so")
+# measured pipe throughput (FP64 FMA, integer XOR/POPC/add) for the roofline
+PEAKS_SO = os.path.join(OUT, "libqp_peaks.so")
 UNITS = ["qp_pt2.cu", "sweep.cu", "sweep_mixed.cu", "sweep_grad.cu", "sweep_states.cu", "noalloc.cu",
          "davidson.cu"]
 HEADERS = ["common.cuh", "sweep_impl.cuh"]
@@ -51,8 +53,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose:
             print(r.stdout + r.stderr)
 
-    with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+    peaks_src = os.path.join(SRC, "peaks.cu")
+    if force or _stale(PEAKS_SO, [peaks_src]):
+        jobs.append([nvcc, *ARCH, *FLAGS, "-shared", peaks_src, "-o", PEAKS_SO + f".tmp{os.getpid()}"])
+    with ThreadPoolExecutor(max_workers=len(UNITS) + 1) as ex:
         list(ex.map(run, jobs))
+    if os.path.exists(PEAKS_SO + f".tmp{os.getpid()}"):
+        os.replace(PEAKS_SO + f".tmp{os.getpid()}", PEAKS_SO)
     if force or jobs or _stale(SO, objs):
         tmp = SO + f".tmp{os.getpid()}"
         run([nvcc, *ARCH, "-shared", *objs, "-o", tmp])
