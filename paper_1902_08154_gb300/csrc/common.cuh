@@ -70,6 +70,25 @@ __host__ __device__ inline long long bucket_entries_per_record(int nel) {
   return nel >= 4 ? 6 : (nel == 3 ? 3 : 1);
 }
 
+// Dynamic shared memory of the one-state batch kernel for mc cells: A_alpha
+// as a 96-bit integer per cell (a 64-bit low word and a 32-bit high word; the
+// exact accumulation in sweep_impl.cuh) and one ban bit per cell.
+__host__ __device__ inline size_t sweep_smem(int mc) {
+  const size_t m = (size_t)(mc < 1 ? 1 : mc);
+  return 8 * m + 4 * ((m + 1) & ~(size_t)1) + 4 * ((m + 31) / 32);
+}
+
+struct GenMeta;
+// Device bytes per generator slot of a wave: metadata, nd coarse-filter
+// records (words, nst coefficients, hole mask, particles, flag), bucket
+// offsets, ent_cap self-contained entries (20 bytes), the dead-batch bits and
+// the nper items' FP64 sums (2 per state).
+inline size_t wave_slot_bytes(size_t meta_bytes, int nel, int nbat, int nw, size_t nd, int nst, int nper) {
+  const size_t ent_cap = nd * (size_t)bucket_entries_per_record(nel);
+  return meta_bytes + nd * (8 * (size_t)nw + 8 * (size_t)nst + 8 + 8 + 4) + 4 * (size_t)(nbat + 2) + 20 * ent_cap +
+         4 * (size_t)((nbat + 31) / 32) + 16 * (size_t)nper * (size_t)nst;
+}
+
 // Per-generator data built by the prep kernel and read by the batch kernel.
 struct GenMeta {
   uint64_t I[4];            // generator determinant (2*NINT words used)
@@ -129,9 +148,26 @@ struct SweepParams {
   uint64_t* r_part;               // [slots][ndet]  up to 4 particle codes of J outside I, 16 bits each
   uint32_t* r_flag;               // [slots][ndet]  bit 0: rank(J) < rank(I)
   int* b_ofs;                     // [slots][nbat + 2]  bucket offsets (bucket nbat: J within degree 2)
-  int32_t* b_ent;                 // [slots][ent_cap]   record indices
+  // bucket entries, self-contained so that the batch kernel classifies a
+  // bucket by streaming it: the record's hole mask and particle codes, and
+  // its index with the rank flag (rank(J) < rank(I)) in bit 31
+  uint64_t* e_hm;                 // [slots][ent_cap]
+  uint64_t* e_part;               // [slots][ent_cap]
+  uint32_t* e_rec;                // [slots][ent_cap]
   uint32_t* b_dead;               // [slots][(nbat + 31) / 32]  batches banned as a whole
   int64_t ent_cap;
+
+  // exact accumulation of A_alpha: bits of max_I |c_I| (written by the
+  // validation) and of max |h_pq| and max |(pq|rs)| (the context's), from
+  // which every CTA derives the same fixed-point scale
+  const unsigned long long* cmax_bits;
+  const unsigned long long* hmax_bits;  // [2]: max |h|, max |eri|
+
+  // per-item sums of the wave, reduced per generator in a fixed order:
+  // it_sum[(slot * nper + item) * it_stride + 2 s + {0, 1}] = (e, A^2/D^2)
+  // of state s
+  double* it_sum;
+  int it_stride;
 
   // per-generator outputs, by rank
   double* eps;

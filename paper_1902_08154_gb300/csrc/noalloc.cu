@@ -36,7 +36,8 @@ struct DevResult {
 __global__ void jk_kernel(int norb, const double* eri, double* Jm, double* Km);
 __global__ void validate_kernel(int64_t ndet, int nint, int norb, int na, int nb, const uint64_t* dets,
                             const double* coefs, unsigned long long* hkey, int32_t* hidx,
-                            unsigned long long* rkey, int32_t* ridx, int* err);
+                            unsigned long long* rkey, int32_t* ridx, int* err, unsigned long long* cmax);
+__global__ void absmax_kernel(int64_t n, const double* x, unsigned long long* out);
 __global__ void dup_kernel(int64_t ndet, int nint, const uint64_t* dets, const unsigned long long* hs,
                            const int32_t* hi, int* err);
 __global__ void rank_kernel(int64_t ndet, const int32_t* order, int32_t* rank_of);
@@ -53,7 +54,9 @@ __global__ void select_out_kernel(int n, int nint, const int32_t* perm, const do
 namespace qp {
 cudaError_t launch_prep(int nint, const SweepParams& p, int slots, cudaStream_t st);
 cudaError_t launch_batch(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_reduce_items(const SweepParams& p, cudaStream_t st);
 int batch_blocks_per_sm(int nint, int mixed, size_t smem);
+int report(int code, const char* msg);
 }  // namespace qp
 
 using namespace qp;
@@ -63,14 +66,12 @@ namespace {
 constexpr size_t kScratchBytes = (size_t)64 << 20;  // 64 MiB per device
 constexpr int kMaxDevices = 64;
 
-thread_local std::string g_err;  // message of the last failure (for debugging)
 std::mutex g_mu;
 unsigned char* g_base[kMaxDevices] = {nullptr};
 
-int nfail(int code, const std::string& m) {
-  g_err = m;
-  return code;
-}
+// Failures are reported through the library's error channel, so that
+// qp_pt2_last_error() names them.
+int nfail(int code, const std::string& m) { return qp::report(code, m.c_str()); }
 
 // Symmetry of h, checked on the device (no host copy of h).
 __global__ void sym_kernel(int norb, const double* h, int* err) {
@@ -99,14 +100,17 @@ struct Carve {
   }
 };
 
-bool on_device(const void* p) {
+// Device (or managed) memory that belongs to device dev: memory of another
+// GPU would be reached by peer access, or fault.
+bool on_device(const void* p, int dev) {
   if (!p) return false;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 int cells_max(int norb, int na, int nb) {
@@ -132,6 +136,18 @@ static __device__ __align__(256) unsigned char qp_noalloc_scratch[kScratchBytes]
     if (e_ != cudaSuccess) return nfail(QP_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+// After the first kernel of a call is queued: on a failure, wait for the
+// work already queued, so that no kernel of this call still writes the
+// shared array when the call returns.
+#define NTRY_Q(expr)                                                                   \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      cudaStreamSynchronize(st);                                                       \
+      return nfail(QP_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));      \
+    }                                                                                  \
+  } while (0)
+
 extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const double* h, const double* eri,
                                    int64_t ndet, const uint64_t* dets, const double* coefs, double e0,
                                    int64_t k, uint64_t* sel_dets, double* sel_e, qp_pt2_result* res,
@@ -146,14 +162,14 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   if (ndet >= (1ll << 31)) return nfail(QP_EINVAL, "ndet must be below 2^31");
   if (!std::isfinite(e0)) return nfail(QP_EINVAL, "E0 is not finite");
   if (ndet == 0) return QP_OK;
-  if (!on_device(h) || !on_device(eri) || !on_device(dets) || !on_device(coefs) ||
-      (k > 0 && (!on_device(sel_dets) || !on_device(sel_e))))
-    return nfail(QP_EINVAL, "every array must be device memory of the current device");
   cudaStream_t st = (cudaStream_t)stream;
-
-  // ---- the static array of this device ----
   int dev = 0;
   NTRY(cudaGetDevice(&dev));
+  if (!on_device(h, dev) || !on_device(eri, dev) || !on_device(dets, dev) || !on_device(coefs, dev) ||
+      (k > 0 && (!on_device(sel_dets, dev) || !on_device(sel_e, dev))))
+    return nfail(QP_EINVAL, "every array must be device memory of the current device");
+
+  // ---- the static array of this device ----
   if (dev < 0 || dev >= kMaxDevices) return nfail(QP_ENOTSUP, "device index too large");
   unsigned char* base;
   {
@@ -172,7 +188,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   const int nint = (norb - 1) / 64 + 1, nw = 2 * nint, nel = n_alpha + n_beta;
   const int nbat = nel + nel * (nel - 1) / 2;
   const int max_cells = cells_max(norb, n_alpha, n_beta);
-  const size_t smem = sizeof(double) * max_cells + sizeof(uint32_t) * ((max_cells + 31) / 32);
+  const size_t smem = sweep_smem(max_cells);
   if (batch_blocks_per_sm(nint, 0, smem) < 1) return nfail(QP_ENOTSUP, "batch accumulator exceeds shared memory");
   int nsm = 0;
   NTRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -201,7 +217,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   double* s2 = cv.take<double>(nd);
   unsigned long long* na = cv.take<unsigned long long>(nd);
   unsigned long long* ncon = cv.take<unsigned long long>(nd);
-  unsigned long long* acc = cv.take<unsigned long long>(8);
+  unsigned long long* acc = cv.take<unsigned long long>(9);
   DevResult* dres = cv.take<DevResult>(1);
   int* queues = cv.take<int>(nd + 1);
   double* tk_e = cv.take<double>((size_t)cap * grid);
@@ -209,6 +225,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   uint64_t* tk_key = cv.take<uint64_t>((size_t)cap * grid * nw);
   int* tk_cnt = cv.take<int>(grid);
   unsigned long long* tk_tau = cv.take<unsigned long long>(grid);
+  unsigned long long* d_hmax = cv.take<unsigned long long>(2);
   unsigned int* sel_hist = cv.take<unsigned int>(kSelBins);
   double* cand_e = cv.take<double>(maxc);
   double* cand_a = cv.take<double>(maxc);
@@ -222,9 +239,11 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   const int64_t ent_per = bucket_entries_per_record(nel);
   const int64_t ent_cap = (int64_t)nd * ent_per;
   const size_t dwords = (size_t)(nbat + 31) / 32;
-  const size_t per_slot = sizeof(GenMeta) + nd * (8 * nw + 8 + 8 + 8 + 4) + 4 * (size_t)(nbat + 2) +
-                          4 * (size_t)ent_cap + 4 * dwords + 7 * 256;
-  const size_t left = kScratchBytes > cv.off ? kScratchBytes - cv.off : 0;
+  const int nper = nbat;
+  const size_t per_slot = wave_slot_bytes(sizeof(GenMeta), nel, nbat, nw, nd, 1, nper);
+  // each of the 12 per-slot arrays carved below may start with up to 255
+  // bytes of alignment padding: keep 12 x 256 bytes aside for them
+  const size_t left = kScratchBytes > cv.off + 12 * 256 ? kScratchBytes - cv.off - 12 * 256 : 0;
   int64_t W = (int64_t)(left / per_slot);
   if (W < 1)
     return nfail(QP_EINVAL, "ndet too large for the 64 MiB static scratch of qp_pt2_eval_noalloc");
@@ -239,27 +258,37 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   uint64_t* r_part = cv.take<uint64_t>(nd * wsl);
   uint32_t* r_flag = cv.take<uint32_t>(nd * wsl);
   int* b_ofs = cv.take<int>((size_t)(nbat + 2) * wsl);
-  int32_t* b_ent = cv.take<int32_t>((size_t)ent_cap * wsl);
+  uint64_t* e_hm = cv.take<uint64_t>((size_t)ent_cap * wsl);
+  uint64_t* e_part = cv.take<uint64_t>((size_t)ent_cap * wsl);
+  uint32_t* e_rec = cv.take<uint32_t>((size_t)ent_cap * wsl);
+  double* it_sum = cv.take<double>((size_t)2 * nper * wsl);
   uint32_t* b_dead = cv.take<uint32_t>(dwords * wsl);
   if (!cv.ok) return nfail(QP_EINVAL, "ndet too large for the 64 MiB static scratch of qp_pt2_eval_noalloc");
 
   // ---- clear what must start at zero; integral tables; validation ----
-  static const unsigned long long init[8] = {0, 0, 0x7FF0000000000000ull, 0, 0, 0, 0, 0};
+  // accumulator words: 0, 1 digest, 2 min |D|, 3 tiny, 4 threshold, 6 error
+  // flags, 7 candidates, 8 bits of max |c_I|
+  static const unsigned long long init[9] = {0, 0, 0x7FF0000000000000ull, 0, 0, 0, 0, 0, 0};
   NTRY(cudaMemcpyAsync(acc, init, sizeof(init), cudaMemcpyHostToDevice, st));
   int* d_err = reinterpret_cast<int*>(acc + 6);
   int* d_ncand = reinterpret_cast<int*>(acc + 7);
+  NTRY(cudaMemsetAsync(d_hmax, 0, 2 * sizeof(unsigned long long), st));
   sym_kernel<<<(norb * norb + 255) / 256, 256, 0, st>>>(norb, h, d_err);
+  const int64_t npair = (int64_t)norb * (norb + 1) / 2, P = npair * (npair + 1) / 2;
+  absmax_kernel<<<(norb * norb + 255) / 256, 256, 0, st>>>((int64_t)norb * norb, h, d_hmax);
+  absmax_kernel<<<(unsigned)((P + 255) / 256 < 4096 ? (P + 255) / 256 : 4096), 256, 0, st>>>(P, eri, d_hmax + 1);
   jk_kernel<<<(norb * norb + 255) / 256, 256, 0, st>>>(norb, eri, d_J, d_K);
   const int nb = (int)((ndet + 255) / 256);
-  validate_kernel<<<nb, 256, 0, st>>>(ndet, nint, norb, n_alpha, n_beta, dets, coefs, hkey, hidx, rkey, rank_of, d_err);
-  NTRY(cudaGetLastError());
-  NTRY(cub::DeviceRadixSort::SortPairs(cub_tmp, tmp1, hkey, hkey2, hidx, hidx2, (int)ndet, 0, 64, st));
+  validate_kernel<<<nb, 256, 0, st>>>(ndet, nint, norb, n_alpha, n_beta, dets, coefs, hkey, hidx, rkey, rank_of, d_err,
+                                      acc + 8);
+  NTRY_Q(cudaGetLastError());
+  NTRY_Q(cub::DeviceRadixSort::SortPairs(cub_tmp, tmp1, hkey, hkey2, hidx, hidx2, (int)ndet, 0, 64, st));
   dup_kernel<<<nb, 256, 0, st>>>(ndet, nint, dets, hkey2, hidx2, d_err);
-  NTRY(cub::DeviceRadixSort::SortPairs(cub_tmp, tmp1, rkey, rkey2, rank_of, order, (int)ndet, 0, 64, st));
+  NTRY_Q(cub::DeviceRadixSort::SortPairs(cub_tmp, tmp1, rkey, rkey2, rank_of, order, (int)ndet, 0, 64, st));
   rank_kernel<<<nb, 256, 0, st>>>(ndet, order, rank_of);
   int herr = 0;
-  NTRY(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  NTRY(cudaStreamSynchronize(st));
+  NTRY_Q(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NTRY_Q(cudaStreamSynchronize(st));
   if (herr & 16) return nfail(QP_ESYM, "h is not symmetric");
   if (herr & 1) return nfail(QP_EINVAL, "a determinant has the wrong occupation or bits beyond norb");
   if (herr & 4) return nfail(QP_EINVAL, "a coefficient is not finite");
@@ -281,7 +310,14 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   p.nel = nel;
   p.nbat = nbat;
   p.tile2 = 0;
-  p.nper = nbat;
+  p.nper = nper;
+  p.cmax_bits = acc + 8;
+  p.hmax_bits = d_hmax;
+  p.it_sum = it_sum;
+  p.it_stride = 2;
+  p.e_hm = e_hm;
+  p.e_part = e_part;
+  p.e_rec = e_rec;
   p.ndet = ndet;
   p.dets = dets;
   p.coefs = coefs;
@@ -301,7 +337,6 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   p.r_part = r_part;
   p.r_flag = r_flag;
   p.b_ofs = b_ofs;
-  p.b_ent = b_ent;
   p.b_dead = b_dead;
   p.ent_cap = ent_cap;
   p.eps = eps;
@@ -327,12 +362,14 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
     p.wave_slots = (int)((ngen - w * W) < W ? (ngen - w * W) : W);
     p.last_wave = (w == nwaves - 1);
     p.queue = queues + w;
-    NTRY(launch_prep(nint, p, p.wave_slots, st));
-    NTRY(launch_batch(nint, p, grid, smem, st));
+    NTRY_Q(cudaMemsetAsync(it_sum, 0, sizeof(double) * 2 * (size_t)nper * p.wave_slots, st));
+    NTRY_Q(launch_prep(nint, p, p.wave_slots, st));
+    NTRY_Q(launch_batch(nint, p, grid, smem, st));
+    NTRY_Q(launch_reduce_items(p, st));
   }
   finalize_kernel<<<1, 1024, 0, st>>>(ndet, eps, s2, reinterpret_cast<const long long*>(na),
                                       reinterpret_cast<const long long*>(ncon), dres);
-  NTRY(cudaGetLastError());
+  NTRY_Q(cudaGetLastError());
 
   // ---- selection ----
   int64_t nsel = 0;
@@ -340,8 +377,8 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
     gather_kernel<<<grid, 256, 0, st>>>(grid, nint, cap, tk_cnt, tk_e, tk_a, tk_key, p.tau_bits, cand_e, cand_a,
                                         cand_key, d_ncand, (int64_t)maxc, d_err);
     int ncand = 0;
-    NTRY(cudaMemcpyAsync(&ncand, d_ncand, sizeof(int), cudaMemcpyDeviceToHost, st));
-    NTRY(cudaStreamSynchronize(st));
+    NTRY_Q(cudaMemcpyAsync(&ncand, d_ncand, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NTRY_Q(cudaStreamSynchronize(st));
     if (ncand > 0) {
       const int sb = (ncand + 255) / 256;
       iota_kernel<<<sb, 256, 0, st>>>(ncand, perm);
@@ -349,7 +386,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
       for (int pass = 0; pass <= nw; pass++) {
         const int word = (pass < nw) ? (nw - 1 - pass) : nw;
         sortkey_kernel<<<sb, 256, 0, st>>>(ncand, nint, word, cand_e, cand_key, pa, skey);
-        NTRY(cub::DeviceRadixSort::SortPairs(cub_tmp, tmp2, skey, skey2, pa, pb, ncand, 0, 64, st));
+        NTRY_Q(cub::DeviceRadixSort::SortPairs(cub_tmp, tmp2, skey, skey2, pa, pb, ncand, 0, 64, st));
         int32_t* t = pa;
         pa = pb;
         pb = t;
@@ -357,16 +394,18 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
       nsel = ncand < k ? ncand : k;
       select_out_kernel<<<(int)((nsel + 255) / 256), 256, 0, st>>>((int)nsel, nint, pa, cand_e, cand_a, cand_key,
                                                                  sel_dets, sel_e, nullptr);
-      NTRY(cudaGetLastError());
+      NTRY_Q(cudaGetLastError());
     }
   }
 
   DevResult hres;
-  unsigned long long hacc[8];
-  NTRY(cudaMemcpyAsync(&hres, dres, sizeof(hres), cudaMemcpyDeviceToHost, st));
-  NTRY(cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st));
-  NTRY(cudaStreamSynchronize(st));
+  unsigned long long hacc[9];
+  NTRY_Q(cudaMemcpyAsync(&hres, dres, sizeof(hres), cudaMemcpyDeviceToHost, st));
+  NTRY_Q(cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st));
+  NTRY_Q(cudaStreamSynchronize(st));
   if (reinterpret_cast<int*>(hacc + 6)[0] & 8) return nfail(QP_ECUDA, "internal error: bucket capacity exceeded");
+  if (reinterpret_cast<int*>(hacc + 6)[0] & 64)
+    return nfail(QP_ENOTSUP, "coefficients times integrals beyond 2^93: outside the exact accumulator's range");
   res->e_pt2 = hres.e_pt2;
   res->sum_e_over_d = hres.s2;
   res->n_perturbers = hres.na;

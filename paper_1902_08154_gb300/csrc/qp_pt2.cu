@@ -26,6 +26,7 @@ cudaError_t launch_grad_gen(int nint, const SweepParams& p, int ngen, cudaStream
 size_t states_smem(int max_cells, int nst);
 int batch_blocks_per_sm_states(int nint, size_t smem);
 cudaError_t launch_batch_states(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_reduce_items(const SweepParams& p, cudaStream_t st);
 }  // namespace qp
 
 using namespace qp;
@@ -46,7 +47,10 @@ static int fail(int code, const std::string& msg) {
   } while (0)
 
 // device error flags
-enum : int { kErrOcc = 1, kErrDup = 2, kErrCoef = 4, kErrBucket = 8 };
+// (16 and 32: the no-allocation entry point's symmetry check, the selection's
+// candidate space; 64: coefficients times integrals beyond the exact
+// accumulator's range)
+enum : int { kErrOcc = 1, kErrDup = 2, kErrCoef = 4, kErrBucket = 8, kErrRange = 64 };
 
 // device memory allowed for the per-generator records and buckets of a wave
 static const size_t kWaveBudget = (size_t)4 << 30;
@@ -71,7 +75,7 @@ __global__ void jk_kernel(int norb, const double* eri, double* Jm, double* Km) {
 // the duplicate check; generator sort keys.
 __global__ void validate_kernel(int64_t ndet, int nint, int norb, int na, int nb, const uint64_t* dets,
                             const double* coefs, unsigned long long* hkey, int32_t* hidx,
-                            unsigned long long* rkey, int32_t* ridx, int* err) {
+                            unsigned long long* rkey, int32_t* ridx, int* err, unsigned long long* cmax) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ndet) return;
   const int nw = 2 * nint;
@@ -95,6 +99,7 @@ __global__ void validate_kernel(int64_t ndet, int nint, int norb, int na, int nb
   if (bad) atomicOr(err, kErrOcc);
   const double c = coefs[i];
   if (!isfinite(c)) atomicOr(err, kErrCoef);
+  else atomicMax(cmax, (unsigned long long)__double_as_longlong(fabs(c)));  // max |c_I|, as bits
   hkey[i] = hk;
   hidx[i] = (int32_t)i;
   // decreasing c^2 == increasing ~bits(c*c); the radix sort is stable, so
@@ -102,6 +107,20 @@ __global__ void validate_kernel(int64_t ndet, int nint, int norb, int na, int nb
   const double c2 = c * c;
   rkey[i] = ~(unsigned long long)__double_as_longlong(c2);
   ridx[i] = (int32_t)i;
+}
+
+// Bits of max |x| over n values (non-negative doubles order as their bits).
+__global__ void absmax_kernel(int64_t n, const double* x, unsigned long long* out) {
+  unsigned long long m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(x[i]));
+    m = b > m ? b : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
 __global__ void dup_kernel(int64_t ndet, int nint, const uint64_t* dets, const unsigned long long* hs,
@@ -283,10 +302,11 @@ struct qp_pt2_ctx {
   size_t smem;
   double *d_h = nullptr, *d_eri = nullptr, *d_J = nullptr, *d_K = nullptr;
   float *d_h32 = nullptr, *d_eri32 = nullptr;  // mixed precision only
+  unsigned long long* d_hmax = nullptr;        // bits of max |h|, max |(pq|rs)|
   // workspace
   Buf in_dets, in_coefs, hkey, hkey2, hidx, hidx2, rkey, rkey2, order, rank_of, cub_tmp;
   Buf eps, s2, na, ncon, acc, res;
-  Buf meta, r_words, r_coef, r_hmask, r_part, r_flag, b_ofs, b_ent, b_dead, queues;
+  Buf meta, r_words, r_coef, r_hmask, r_part, r_flag, b_ofs, e_hm, e_part, e_rec, b_dead, queues, it_sum;
   Buf tk_e, tk_a, tk_key, tk_cnt, tk_tau, sel_hist, gen_list, gen_out, st_cmax;
   Buf cand_e, cand_a, cand_key, skey, skey2, perm, perm2, cub_tmp2;
   Buf out_sel, out_e, out_num, out_eps, out_na, out_ncon, out_rank;
@@ -318,7 +338,7 @@ int report(int code, const char* msg) { return fail(code, msg); }
 }  // namespace qp
 
 // accumulator block layout (unsigned long long words)
-enum { kAccDigest0 = 0, kAccDigest1, kAccMinDen, kAccTiny, kAccTau, kAccQueue, kAccErr, kAccNcand, kAccWords };
+enum { kAccDigest0 = 0, kAccDigest1, kAccMinDen, kAccTiny, kAccTau, kAccQueue, kAccErr, kAccNcand, kAccCmax, kAccWords };
 
 static bool is_device_ptr(const void* p) {
   if (!p) return false;
@@ -405,6 +425,12 @@ extern "C" int qp_pt2_create(qp_pt2_ctx** out, int norb, int n_alpha, int n_beta
       cudaMemcpyAsync(x->d_eri, eri, sizeof(double) * P, cudaMemcpyDefault, x->st) != cudaSuccess)
     return bail(QP_ECUDA, "copy of the integrals failed");
   jk_kernel<<<(norb * norb + 255) / 256, 256, 0, x->st>>>(norb, x->d_eri, x->d_J, x->d_K);
+  if (cudaMalloc(&x->d_hmax, 2 * sizeof(unsigned long long)) != cudaSuccess)
+    return bail(QP_ENOMEM, "device allocation failed");
+  if (cudaMemsetAsync(x->d_hmax, 0, 2 * sizeof(unsigned long long), x->st) != cudaSuccess)
+    return bail(QP_ECUDA, "cudaMemsetAsync failed");
+  absmax_kernel<<<(norb * norb + 255) / 256, 256, 0, x->st>>>((int64_t)norb * norb, x->d_h, x->d_hmax);
+  absmax_kernel<<<(unsigned)std::min<int64_t>((P + 255) / 256, 4096), 256, 0, x->st>>>(P, x->d_eri, x->d_hmax + 1);
   if (c.precision == QP_MIXED) {
     if (cudaMalloc(&x->d_h32, sizeof(float) * norb * norb) != cudaSuccess ||
         cudaMalloc(&x->d_eri32, sizeof(float) * P) != cudaSuccess)
@@ -417,7 +443,7 @@ extern "C" int qp_pt2_create(qp_pt2_ctx** out, int norb, int n_alpha, int n_beta
   x->max_cells = cells_max(norb, n_alpha, n_beta);
   if (x->max_cells < 1) x->max_cells = 1;
   x->tile2 = 0;
-  x->smem = sizeof(double) * x->max_cells + sizeof(uint32_t) * ((x->max_cells + 31) / 32);
+  x->smem = sweep_smem(x->max_cells);
   int bps = batch_blocks_per_sm(x->nint, c.precision == QP_MIXED, x->smem);
   if (x->nint == 2 && bps < 2 && n_alpha > 0 && n_beta > 0) {
     // the opposite-spin accumulator fits only once per SM: split those
@@ -432,7 +458,7 @@ extern "C" int qp_pt2_create(qp_pt2_ctx** out, int norb, int n_alpha, int n_beta
     if (m < x->max_cells) {
       x->tile2 = 1;
       x->max_cells = m;
-      x->smem = sizeof(double) * x->max_cells + sizeof(uint32_t) * ((x->max_cells + 31) / 32);
+      x->smem = sweep_smem(x->max_cells);
       bps = batch_blocks_per_sm(x->nint, c.precision == QP_MIXED, x->smem);
     }
   }
@@ -455,10 +481,11 @@ extern "C" void qp_pt2_destroy(qp_pt2_ctx* x) {
   cudaFree(x->d_eri32);
   cudaFree(x->d_J);
   cudaFree(x->d_K);
+  cudaFree(x->d_hmax);
   Buf* all[] = {&x->in_dets, &x->in_coefs, &x->hkey, &x->hkey2, &x->hidx, &x->hidx2, &x->rkey, &x->rkey2,
                 &x->order, &x->rank_of, &x->cub_tmp, &x->eps, &x->s2, &x->na, &x->ncon, &x->acc,
                 &x->res, &x->meta, &x->r_words, &x->r_coef, &x->r_hmask, &x->r_part, &x->r_flag,
-                &x->b_ofs, &x->b_ent, &x->b_dead, &x->queues, &x->tk_e, &x->tk_a, &x->tk_key, &x->tk_cnt, &x->tk_tau, &x->sel_hist, &x->gen_list, &x->gen_out, &x->cand_e, &x->cand_a, &x->cand_key, &x->skey,
+                &x->b_ofs, &x->e_hm, &x->e_part, &x->e_rec, &x->it_sum, &x->b_dead, &x->queues, &x->tk_e, &x->tk_a, &x->tk_key, &x->tk_cnt, &x->tk_tau, &x->sel_hist, &x->gen_list, &x->gen_out, &x->cand_e, &x->cand_a, &x->cand_key, &x->skey,
                 &x->skey2, &x->perm, &x->perm2, &x->cub_tmp2, &x->out_sel, &x->out_e, &x->out_num,
                 &x->out_eps, &x->out_na, &x->out_ncon, &x->out_rank, &x->g_dh, &x->g_deri, &x->g_wF, &x->g_wH};
   for (Buf* b : all) b->release();
@@ -617,7 +644,8 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   const int nb = (int)((ndet + tb - 1) / tb);
   validate_kernel<<<nb, tb, 0, st>>>(ndet, nint, x->norb, x->nalpha, x->nbeta, d_dets, d_coefs,
                                  x->hkey.as<unsigned long long>(), x->hidx.as<int32_t>(),
-                                 x->rkey.as<unsigned long long>(), x->rank_of.as<int32_t>(), d_err);
+                                 x->rkey.as<unsigned long long>(), x->rank_of.as<int32_t>(), d_err,
+                                      acc + kAccCmax);
   x->launches++;
   CUDA_TRY(cudaGetLastError());
   size_t tmp1 = 0;
@@ -679,8 +707,8 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   const int64_t ent_per = bucket_entries_per_record(x->nel);
   const int64_t ent_cap = (int64_t)nd * ent_per;
   const size_t dwords = (size_t)(x->nbat + 31) / 32;
-  const size_t per_slot = sizeof(GenMeta) + nd * (8 * nw + 8 * (size_t)nsts + 8 + 8 + 4) +
-                          4 * (size_t)(x->nbat + 2) + 4 * (size_t)ent_cap + 4 * dwords;
+  const int nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
+  const size_t per_slot = wave_slot_bytes(sizeof(GenMeta), x->nel, x->nbat, nw, nd, nsts, nper);
   int64_t W = (int64_t)(kWaveBudget / per_slot);
   if (W < 1) W = 1;
   if (W > ngen) W = ngen > 0 ? ngen : 1;
@@ -691,7 +719,9 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
       (rc = x->r_words.grow(8 * nd * nw * ws)) || (rc = x->r_coef.grow(8 * nd * ws * nsts)) ||
       (rc = x->r_hmask.grow(8 * nd * ws)) || (rc = x->r_part.grow(8 * nd * ws)) ||
       (rc = x->r_flag.grow(4 * nd * ws)) || (rc = x->b_ofs.grow(4 * (size_t)(x->nbat + 2) * ws)) ||
-      (rc = x->b_ent.grow(4 * (size_t)ent_cap * ws)) || (rc = x->b_dead.grow(4 * dwords * ws)) || (rc = x->queues.grow(4 * (size_t)(nwaves + 1))) ||
+      (rc = x->e_hm.grow(8 * (size_t)ent_cap * ws)) || (rc = x->e_part.grow(8 * (size_t)ent_cap * ws)) ||
+      (rc = x->e_rec.grow(4 * (size_t)ent_cap * ws)) || (rc = x->it_sum.grow(16 * (size_t)nper * nsts * ws)) ||
+      (rc = x->b_dead.grow(4 * dwords * ws)) || (rc = x->queues.grow(4 * (size_t)(nwaves + 1))) ||
       (rc = x->tk_e.grow(8 * (size_t)cap * grid)) || (rc = x->tk_a.grow(8 * (size_t)cap * grid)) ||
       (rc = x->tk_key.grow(8 * (size_t)cap * grid * nw)) || (rc = x->tk_cnt.grow(4 * (size_t)grid)) ||
       (rc = x->tk_tau.grow(8 * (size_t)grid)) || (rc = x->res.grow(sizeof(DevResult) * nsts)) ||
@@ -713,6 +743,13 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   p.nbat = x->nbat;
   p.tile2 = x->tile2;
   p.nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
+  p.hmax_bits = x->d_hmax;
+  p.cmax_bits = acc + kAccCmax;
+  p.it_sum = x->it_sum.as<double>();
+  p.it_stride = 2;
+  p.e_hm = x->e_hm.as<uint64_t>();
+  p.e_part = x->e_part.as<uint64_t>();
+  p.e_rec = x->e_rec.as<uint32_t>();
   p.tgt_on = x->tgt_on;
   p.tgt_max_exc = x->tgt_max_exc;
   for (int w = 0; w < 4; w++) {
@@ -743,7 +780,6 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   p.r_part = x->r_part.as<uint64_t>();
   p.r_flag = x->r_flag.as<uint32_t>();
   p.b_ofs = x->b_ofs.as<int>();
-  p.b_ent = x->b_ent.as<int32_t>();
   p.b_dead = x->b_dead.as<uint32_t>();
   p.ent_cap = ent_cap;
   p.eps = x->eps.as<double>();
@@ -764,6 +800,7 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   p.sel_hist = x->sel_hist.as<unsigned int>();
   p.max_cells = x->max_cells;
   p.err = d_err;
+  p.it_stride = 2 * nsts;
   if (ms) {
     p.nst = nst;
     p.rc_stride = (int64_t)(nd * ws);
@@ -776,10 +813,12 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
     p.wave_slots = (int)((ngen - w * W) < W ? (ngen - w * W) : W);
     p.last_wave = (w == nwaves - 1);
     p.queue = x->queues.as<int>() + w;
+    CUDA_TRY(cudaMemsetAsync(p.it_sum, 0, sizeof(double) * (size_t)p.wave_slots * p.nper * p.it_stride, st));
     CUDA_TRY(launch_prep(nint, p, p.wave_slots, st));
     if (ms) CUDA_TRY(launch_batch_states(nint, p, grid, smem, st));
     else CUDA_TRY(launch_batch(nint, p, grid, smem, st));
-    x->launches += 2;
+    CUDA_TRY(launch_reduce_items(p, st));
+    x->launches += 3;
   }
   CUDA_TRY(cudaEventRecord(x->ev[2], st));
   DevResult* dres = x->res.as<DevResult>();
@@ -878,6 +917,8 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   CUDA_TRY(cudaStreamSynchronize(st));
   x->timed = true;
   if (herr & kErrBucket) return fail(QP_ECUDA, "internal error: bucket capacity exceeded");
+  if (herr & kErrRange)
+    return fail(QP_ENOTSUP, "coefficients times integrals beyond 2^93: outside the exact accumulator's range");
   double md;
   memcpy(&md, &hacc[kAccMinDen], sizeof(md));
   for (int s = 0; s < nsts; s++) {
@@ -999,7 +1040,8 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
   const int nb = (int)((ndet + 255) / 256);
   validate_kernel<<<nb, 256, 0, st>>>(ndet, nint, norb, x->nalpha, x->nbeta, d_dets, d_coefs,
                                       x->hkey.as<unsigned long long>(), x->hidx.as<int32_t>(),
-                                      x->rkey.as<unsigned long long>(), x->rank_of.as<int32_t>(), d_err);
+                                      x->rkey.as<unsigned long long>(), x->rank_of.as<int32_t>(), d_err,
+                                      acc + kAccCmax);
   x->launches++;
   CUDA_TRY(cudaGetLastError());
   size_t tmp1 = 0;
@@ -1031,8 +1073,8 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
   const int64_t ent_per = bucket_entries_per_record(x->nel);
   const int64_t ent_cap = (int64_t)nd * ent_per;
   const size_t dwords = (size_t)(x->nbat + 31) / 32;
-  const size_t per_slot = sizeof(GenMeta) + nd * (8 * nw + 8 + 8 + 8 + 4) + 4 * (size_t)(x->nbat + 2) +
-                          4 * (size_t)ent_cap + 4 * dwords;
+  const int nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
+  const size_t per_slot = wave_slot_bytes(sizeof(GenMeta), x->nel, x->nbat, nw, nd, 1, nper);
   int64_t W = (int64_t)(kWaveBudget / per_slot);
   if (W < 1) W = 1;
   if (W > ngen) W = ngen > 0 ? ngen : 1;
@@ -1043,7 +1085,9 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
       (rc = x->r_words.grow(8 * nd * nw * wsl)) || (rc = x->r_coef.grow(8 * nd * wsl)) ||
       (rc = x->r_hmask.grow(8 * nd * wsl)) || (rc = x->r_part.grow(8 * nd * wsl)) ||
       (rc = x->r_flag.grow(4 * nd * wsl)) || (rc = x->b_ofs.grow(4 * (size_t)(x->nbat + 2) * wsl)) ||
-      (rc = x->b_ent.grow(4 * (size_t)ent_cap * wsl)) || (rc = x->b_dead.grow(4 * dwords * wsl)) ||
+      (rc = x->e_hm.grow(8 * (size_t)ent_cap * wsl)) || (rc = x->e_part.grow(8 * (size_t)ent_cap * wsl)) ||
+      (rc = x->e_rec.grow(4 * (size_t)ent_cap * wsl)) || (rc = x->it_sum.grow(16 * (size_t)nper * wsl)) ||
+      (rc = x->b_dead.grow(4 * dwords * wsl)) ||
       (rc = x->queues.grow(4 * (size_t)(nwaves + 1))) || (rc = x->tk_cnt.grow(4 * (size_t)grid)) ||
       (rc = x->tk_tau.grow(8 * (size_t)grid)) || (rc = x->res.grow(sizeof(DevResult))) ||
       (rc = x->g_wF.grow(8 * nd * 2 * norb)) || (rc = x->g_wH.grow(8 * nd)))
@@ -1065,6 +1109,13 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
   p.nbat = x->nbat;
   p.tile2 = x->tile2;
   p.nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
+  p.hmax_bits = x->d_hmax;
+  p.cmax_bits = acc + kAccCmax;
+  p.it_sum = x->it_sum.as<double>();
+  p.it_stride = 2;
+  p.e_hm = x->e_hm.as<uint64_t>();
+  p.e_part = x->e_part.as<uint64_t>();
+  p.e_rec = x->e_rec.as<uint32_t>();
   p.tgt_on = x->tgt_on;
   p.tgt_max_exc = x->tgt_max_exc;
   for (int w = 0; w < 4; w++) {
@@ -1091,7 +1142,6 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
   p.r_part = x->r_part.as<uint64_t>();
   p.r_flag = x->r_flag.as<uint32_t>();
   p.b_ofs = x->b_ofs.as<int>();
-  p.b_ent = x->b_ent.as<int32_t>();
   p.b_dead = x->b_dead.as<uint32_t>();
   p.ent_cap = ent_cap;
   p.eps = x->eps.as<double>();
@@ -1119,9 +1169,11 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
     p.wave_slots = (int)((ngen - w * W) < W ? (ngen - w * W) : W);
     p.last_wave = (w == nwaves - 1);
     p.queue = x->queues.as<int>() + w;
+    CUDA_TRY(cudaMemsetAsync(p.it_sum, 0, sizeof(double) * (size_t)p.wave_slots * p.nper * p.it_stride, st));
     CUDA_TRY(launch_prep(nint, p, p.wave_slots, st));
     CUDA_TRY(launch_batch_grad(nint, p, grid, x->smem, st));
-    x->launches += 2;
+    CUDA_TRY(launch_reduce_items(p, st));
+    x->launches += 3;
   }
   CUDA_TRY(launch_grad_gen(nint, p, (int)ndet, st));
   x->launches++;
@@ -1151,6 +1203,8 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
   memcpy(&md, &hacc[kAccMinDen], sizeof(md));
   res->min_abs_denominator = md;
   *de0 = -hres.s2;
+  if (((int)(hacc[kAccErr] & 0xffffffffull)) & kErrRange)
+    return fail(QP_ENOTSUP, "coefficients times integrals beyond 2^93: outside the exact accumulator's range");
   if (hres.na > 0 && md < 1e-12) return fail(QP_ESINGULAR, "a denominator E0 - H_aa is below 1e-12");
   return QP_OK;
 }
@@ -1232,8 +1286,8 @@ static int plan_instance(BatchInst& b, size_t wave_budget) {
   const int64_t ent_per = bucket_entries_per_record(x->nel);
   b.ent_cap = (int64_t)nd * ent_per;
   const size_t dwords = (size_t)(x->nbat + 31) / 32;
-  const size_t per_slot = sizeof(GenMeta) + nd * (8 * nw + 8 + 8 + 8 + 4) + 4 * (size_t)(x->nbat + 2) +
-                          4 * (size_t)b.ent_cap + 4 * dwords;
+  const int nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
+  const size_t per_slot = wave_slot_bytes(sizeof(GenMeta), x->nel, x->nbat, nw, nd, 1, nper);
   b.W = (int64_t)(wave_budget / per_slot);
   if (b.W < 1) b.W = 1;
   if (b.W > b.ngen) b.W = b.ngen;
@@ -1254,7 +1308,9 @@ static int plan_instance(BatchInst& b, size_t wave_budget) {
       (rc = x->meta.grow(sizeof(GenMeta) * ws)) || (rc = x->r_words.grow(8 * nd * nw * ws)) ||
       (rc = x->r_coef.grow(8 * nd * ws)) || (rc = x->r_hmask.grow(8 * nd * ws)) ||
       (rc = x->r_part.grow(8 * nd * ws)) || (rc = x->r_flag.grow(4 * nd * ws)) ||
-      (rc = x->b_ofs.grow(4 * (size_t)(x->nbat + 2) * ws)) || (rc = x->b_ent.grow(4 * (size_t)b.ent_cap * ws)) ||
+      (rc = x->b_ofs.grow(4 * (size_t)(x->nbat + 2) * ws)) || (rc = x->e_hm.grow(8 * (size_t)b.ent_cap * ws)) ||
+      (rc = x->e_part.grow(8 * (size_t)b.ent_cap * ws)) || (rc = x->e_rec.grow(4 * (size_t)b.ent_cap * ws)) ||
+      (rc = x->it_sum.grow(16 * (size_t)nper * ws)) ||
       (rc = x->b_dead.grow(4 * dwords * ws)) || (rc = x->queues.grow(4 * (size_t)(b.nwaves + 1))) ||
       (rc = x->tk_e.grow(8 * (size_t)b.cap * grid)) || (rc = x->tk_a.grow(8 * (size_t)b.cap * grid)) ||
       (rc = x->tk_key.grow(8 * (size_t)b.cap * grid * nw)) || (rc = x->tk_cnt.grow(4 * (size_t)grid)) ||
@@ -1282,7 +1338,8 @@ static int enqueue_instance(BatchInst& b, cudaStream_t st) {
   const int nb = (int)((ndet + 255) / 256);
   validate_kernel<<<nb, 256, 0, st>>>(ndet, nint, x->norb, x->nalpha, x->nbeta, b.dets, b.coefs,
                                       x->hkey.as<unsigned long long>(), x->hidx.as<int32_t>(),
-                                      x->rkey.as<unsigned long long>(), x->rank_of.as<int32_t>(), d_err);
+                                      x->rkey.as<unsigned long long>(), x->rank_of.as<int32_t>(), d_err,
+                                      acc + kAccCmax);
   CUDA_TRY(cub::DeviceRadixSort::SortPairs(x->cub_tmp.p, b.tmp1, x->hkey.as<unsigned long long>(),
                                            x->hkey2.as<unsigned long long>(), x->hidx.as<int32_t>(),
                                            x->hidx2.as<int32_t>(), (int)ndet, 0, 64, st));
@@ -1306,6 +1363,13 @@ static int enqueue_instance(BatchInst& b, cudaStream_t st) {
   p.nbat = x->nbat;
   p.tile2 = x->tile2;
   p.nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
+  p.hmax_bits = x->d_hmax;
+  p.cmax_bits = acc + kAccCmax;
+  p.it_sum = x->it_sum.as<double>();
+  p.it_stride = 2;
+  p.e_hm = x->e_hm.as<uint64_t>();
+  p.e_part = x->e_part.as<uint64_t>();
+  p.e_rec = x->e_rec.as<uint32_t>();
   p.tgt_on = x->tgt_on;
   p.tgt_max_exc = x->tgt_max_exc;
   for (int w = 0; w < 4; w++) {
@@ -1335,7 +1399,6 @@ static int enqueue_instance(BatchInst& b, cudaStream_t st) {
   p.r_part = x->r_part.as<uint64_t>();
   p.r_flag = x->r_flag.as<uint32_t>();
   p.b_ofs = x->b_ofs.as<int>();
-  p.b_ent = x->b_ent.as<int32_t>();
   p.b_dead = x->b_dead.as<uint32_t>();
   p.ent_cap = b.ent_cap;
   p.eps = x->eps.as<double>();
@@ -1361,8 +1424,10 @@ static int enqueue_instance(BatchInst& b, cudaStream_t st) {
     p.wave_slots = (int)((b.ngen - w * b.W) < b.W ? (b.ngen - w * b.W) : b.W);
     p.last_wave = (w == b.nwaves - 1);
     p.queue = x->queues.as<int>() + w;
+    CUDA_TRY(cudaMemsetAsync(p.it_sum, 0, sizeof(double) * (size_t)p.wave_slots * p.nper * p.it_stride, st));
     CUDA_TRY(launch_prep(nint, p, p.wave_slots, st));
     CUDA_TRY(launch_batch(nint, p, grid, x->smem, st));
+    CUDA_TRY(launch_reduce_items(p, st));
   }
   finalize_kernel<<<1, 1024, 0, st>>>(ndet, p.eps, p.s2, reinterpret_cast<const long long*>(p.na),
                                       reinterpret_cast<const long long*>(p.ncon), x->res.as<DevResult>());
@@ -1516,6 +1581,7 @@ extern "C" int qp_pt2_batch_run(qp_pt2_batch* B, qp_pt2_result* res, double* ms)
     else if (herr & kErrCoef) code = QP_EINVAL;
     else if (herr & kErrDup) code = QP_EDUP;
     else if (herr & kErrBucket) code = QP_ECUDA;
+    else if (herr & kErrRange) code = QP_ENOTSUP;
     else if (herr & 32) code = QP_ENOMEM;
     r.e_pt2 = hres.e_pt2;
     r.sum_e_over_d = hres.s2;

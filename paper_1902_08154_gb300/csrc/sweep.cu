@@ -5,6 +5,37 @@
 
 namespace qp {
 
+// Per generator of the wave and per state: eps_I and sum A^2/D^2 from the
+// items' slots, added in item order with Neumaier's compensation, so that
+// they are the same bits on every run and every grid size.
+__global__ void reduce_items_kernel(const __grid_constant__ SweepParams p) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nst = p.nst > 1 ? p.nst : 1;
+  if (t >= p.wave_slots * nst) return;
+  const int slot = t / nst, st = t - slot * nst;
+  const int g = p.meta[slot].g;
+  if (g < 0) return;
+  const double* its = p.it_sum + (size_t)slot * p.nper * p.it_stride + 2 * st;
+  double se = 0.0, ce = 0.0, ss = 0.0, cs = 0.0;
+  for (int j = 0; j < p.nper; j++) {
+    const double ve = its[(size_t)j * p.it_stride], vs = its[(size_t)j * p.it_stride + 1];
+    double u = se + ve;
+    ce += (fabs(se) >= fabs(ve)) ? (se - u) + ve : (ve - u) + se;
+    se = u;
+    u = ss + vs;
+    cs += (fabs(ss) >= fabs(vs)) ? (ss - u) + vs : (vs - u) + ss;
+    ss = u;
+  }
+  p.eps[(size_t)st * p.ndet + g] = se + ce;
+  p.s2[(size_t)st * p.ndet + g] = ss + cs;
+}
+
+cudaError_t launch_reduce_items(const SweepParams& p, cudaStream_t st) {
+  const int n = p.wave_slots * (p.nst > 1 ? p.nst : 1);
+  if (n > 0) reduce_items_kernel<<<(n + 127) / 128, 128, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
 template __global__ void prep_kernel<1>(const __grid_constant__ SweepParams);
 template __global__ void prep_kernel<2>(const __grid_constant__ SweepParams);
 template __global__ void batch_kernel<1, double>(const __grid_constant__ SweepParams);

@@ -151,6 +151,133 @@ __device__ __forceinline__ float flip_sign(float v, bool neg) {
   return __int_as_float(__float_as_int(v) ^ ((int)neg << 31));
 }
 
+// ---------------------------------------------------------------------------
+// Exact accumulation of the numerator A_alpha = sum_J c_J <J|H|alpha> in the
+// one-state sweep.  Each product (FP64, or FP32 in the mixed form) is
+// converted, with one rounding at 2^-F, to a 96-bit two's-complement integer
+// in units of 2^-F and added with integer arithmetic, so that A_alpha does
+// not depend on the order of the additions: the J of a batch reach a cell
+// from different warps, and integer sums give the same bits on every run
+// and every grid.  F is the same for a whole sweep: with
+// B = max_I |c_I| * N_det * Hmax, where Hmax bounds every |<J|H|alpha>|
+// (max |h| + 2 (n_el + 1) max |(pq|rs)|), |A_alpha| <= B < 2^(94 - F), so no
+// sum leaves the 95-bit range and every product lies below 2^94 * 2^-F.  The
+// sum is rounded once to FP64 in the cells pass; it keeps everything above
+// 2^-F (about 1e-21 on the workloads here), more than an FP64 sum of the
+// same products keeps.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int fix_scale(const SweepParams& p) {
+  const double cmax = __longlong_as_double((long long)*p.cmax_bits);
+  const double hmx = __longlong_as_double((long long)p.hmax_bits[0]);
+  const double emx = __longlong_as_double((long long)p.hmax_bits[1]);
+  const double hmax = hmx + 2.0 * (double)(p.nel + 1) * emx;
+  const double bound = cmax * (double)p.ndet * hmax;
+  if (!(bound > 0.0)) return 100;
+  // floor(log2(bound)) from the exponent field; 2^(e+1) > bound
+  const int e = (int)((((unsigned long long)__double_as_longlong(bound)) >> 52) & 0x7FF) - 1023;
+  int F = 93 - e;
+  if (F > 126) F = 126;
+  if (F < 0) {  // coefficients times integrals beyond 2^93: not representable
+    atomicOr(p.err, 64);
+    F = 0;
+  }
+  return F;
+}
+
+// m * 2^sh as a 96-bit integer (lo, hi), negated when neg; m < 2^53 and
+// m * 2^sh < 2^94; for sh < 0 the bits below 2^0 are rounded (half up).
+__device__ __forceinline__ void fix_of_mant(unsigned long long m, int sh, bool neg, unsigned long long& lo,
+                                            int& hi) {
+  unsigned long long l;
+  unsigned int h;
+  if (sh >= 64) {
+    l = 0ull;
+    h = (unsigned int)(m << (sh - 64));
+  } else if (sh > 0) {
+    l = m << sh;
+    h = (unsigned int)(m >> (64 - sh));
+  } else if (sh == 0) {
+    l = m;
+    h = 0u;
+  } else {
+    const int r = -sh;
+    l = (r < 64) ? (m >> r) + ((m >> (r - 1)) & 1ull) : 0ull;
+    h = 0u;
+  }
+  if (neg) {
+    l = ~l + 1ull;
+    h = ~h + (l == 0ull ? 1u : 0u);
+  }
+  lo = l;
+  hi = (int)h;
+}
+
+__device__ __forceinline__ void fix_of(double x, int F, unsigned long long& lo, int& hi) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) {  // zero, or below 2^-1022: nothing at 2^-F (F <= 126)
+    lo = 0ull;
+    hi = 0;
+    return;
+  }
+  fix_of_mant((b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull, e - 1075 + F, (b >> 63) != 0ull, lo, hi);
+}
+
+__device__ __forceinline__ void fix_of(float x, int F, unsigned long long& lo, int& hi) {
+  const unsigned int b = (unsigned int)__float_as_int(x);
+  const int e = (int)((b >> 23) & 0xFF);
+  if (e == 0) {
+    lo = 0ull;
+    hi = 0;
+    return;
+  }
+  fix_of_mant((unsigned long long)((b & 0x7FFFFFu) | 0x800000u), e - 150 + F, (b >> 31) != 0u, lo, hi);
+}
+
+__device__ __forceinline__ void fix_add(unsigned long long& lo, int& hi, unsigned long long l2, int h2) {
+  lo += l2;
+  hi += h2 + (lo < l2 ? 1 : 0);
+}
+
+// Adds (l, h) into the shared-memory accumulator of cell cc: the low words
+// add modulo 2^64 and each carry out of them is added to the high word, so
+// the total is exact whatever the order of the atomics.
+__device__ __forceinline__ void fix_atomic_add(unsigned long long* Alo, int* Ahi, int cc, unsigned long long l,
+                                               int h) {
+  const unsigned long long old = atomicAdd(&Alo[cc], l);
+  const int dh = h + ((old + l < old) ? 1 : 0);
+  if (dh) atomicAdd(&Ahi[cc], dh);
+}
+
+// (lo, hi) * 2^-F rounded to FP64 (nearest, ties away from zero): the top
+// 53 bits of the magnitude, with integer operations only.
+__device__ __forceinline__ double fix_to_double(unsigned long long lo, int hi, int F) {
+  const bool neg = hi < 0;
+  if (neg) {
+    lo = ~lo + 1ull;
+    hi = (int)(~(unsigned int)hi + (lo == 0ull ? 1u : 0u));
+  }
+  int n;  // bit length of the magnitude
+  if (hi) n = 96 - __clz(hi);
+  else if (lo) n = 64 - __clzll((long long)lo);
+  else return 0.0;
+  unsigned long long mant;
+  if (n <= 53) {
+    mant = lo << (53 - n);
+  } else {
+    const int s = n - 53;  // 1 .. 42
+    const unsigned long long q = (lo >> s) | ((unsigned long long)(unsigned int)hi << (64 - s));
+    mant = q + ((lo >> (s - 1)) & 1ull);
+    if (mant >> 53) {
+      mant >>= 1;
+      n++;
+    }
+  }
+  const unsigned long long ex = (unsigned long long)(n - 1 - F + 1023);
+  return __longlong_as_double((long long)((neg ? 0x8000000000000000ull : 0ull) | (ex << 52) |
+                                          (mant & 0x000FFFFFFFFFFFFFull)));
+}
+
 __device__ __forceinline__ int pair_batch(int nel, int i, int j) {  // i < j
   return nel + j * (j - 1) / 2 + i;
 }
@@ -320,13 +447,22 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(const __grid_constant__ 
   int* ofs = p.b_ofs + (size_t)slot * (nbat + 2);
   for (int b = tid; b <= nbat + 1; b += kThreads) ofs[b] = s_cnt[b];
   __syncthreads();
-  int32_t* ent = p.b_ent + (size_t)slot * (size_t)p.ent_cap;
+  uint64_t* e_hm = p.e_hm + (size_t)slot * (size_t)p.ent_cap;
+  uint64_t* e_part = p.e_part + (size_t)slot * (size_t)p.ent_cap;
+  uint32_t* e_rec = p.e_rec + (size_t)slot * (size_t)p.ent_cap;
   const long long cap = p.ent_cap;
-  for (int r = tid; r < nrec; r += kThreads)
-    for_buckets(rh[r], nel, nbat, [&](int b) {
+  for (int r = tid; r < nrec; r += kThreads) {
+    const uint64_t hm = rh[r], pt = rp[r];
+    const uint32_t rec = (uint32_t)r | ((rf[r] & 1u) << 31);
+    for_buckets(hm, nel, nbat, [&](int b) {
       const int o = atomicAdd(&s_cnt[b], 1);
-      if (o < cap) ent[o] = r;
+      if (o < cap) {
+        e_hm[o] = hm;
+        e_part[o] = pt;
+        e_rec[o] = rec;
+      }
     });
+  }
 
   // ---- batches banned as a whole: a J ranked before I with t <= 1 (one
   // hole) or t = 0 (two holes) reaches every cell.  Only J with d <= 2 can:
@@ -380,7 +516,15 @@ struct BatchShared {
   uint64_t kbase[2 * NINT];  // I with the batch's holes removed
   int g, slot;
   long long item;
-  int L0[kChunk], L1[kChunk], L2[kChunk];
+  // storage of one phase of a work item at a time: the J lists of loops 2
+  // and 3, the selection histogram, the per-thread sums of the reduction
+  union {
+    struct {
+      int L0[kChunk], L1[kChunk], L2[kChunk];
+    } l;
+    int hist[256];
+    double red_t[2][kThreads];  // per-thread e and (A/D)^2 sums of the item
+  } u;
   int n0, n1, n2;
   int cnext;  // next row-reaching J (then subset block) to draw
   // a group of J reaching every cell, processed by the whole CTA
@@ -390,21 +534,31 @@ struct BatchShared {
   int gnx[kGroup], gnt[kGroup];
   // two-hole batches: J = K + {x1, x2}; per particle orbital of each slot the
   // pair index tri(x, r) with the phase parity in bit 31
-  int gRow[kGroup][kMaxOrb], gCol[kGroup][kMaxOrb];
+  // (loop 2); the gradient's per-orbital weights use the same storage in
+  // the cells pass and after loop 3
+  union {
+    struct {
+      int gRow[kGroup][kMaxOrb], gCol[kGroup][kMaxOrb];
+    } g;
+    struct {
+      double rowW2[kMaxOrb], colW2[kMaxOrb];  // sums of (A/D)^2 over the cells of each particle orbital
+    } w;
+    // loop 1: flags of the rows (rowm) and columns (colm) of cells that J
+    // ranked before I reach as a whole (by virtual orbital index)
+    struct {
+      uint32_t rowm[kMaxOrb], colm[kMaxOrb];
+    } m;
+  } v;
   int gx1[kGroup], gx2[kGroup], gsr[kGroup], gsc[kGroup];
   int wsum[kWarps];
   // selection
   int tkcnt;
   unsigned long long tau;
-  int hist[256];
   uint64_t pw[1 + 2 * NINT];
   uint64_t thr[1 + 2 * NINT];
   int need, group, found_w, found_sh;
   // reductions
-  double red_t[2][kThreads];  // per-thread e and (A/D)^2 sums of the item
   unsigned long long red_u[kWarps][6];
-  // gradient: sums of (A/D)^2 over the cells of each particle orbital
-  double rowW2[kMaxOrb], colW2[kMaxOrb];
   double sw2;
 };
 
@@ -502,6 +656,21 @@ __device__ __forceinline__ void for_subset_cells(const Batch& B, const BatchShar
     for (int i = 0; i < na; i++)
       for (int j = 0; j < nb; j++) fn(S.vidx[0][pk(Pa, i)] * S.nv[1] + S.vidx[1][pk(Pb, j)]);
   }
+}
+
+// True when some cell inside the particles of J lies in this item's tile and
+// is not banned: a J with t = 2 that reaches no such cell adds nothing and is
+// dropped at classification (most of them: their one cell is usually banned
+// by an earlier generator, or its spins do not match the batch's).
+template <int NINT, typename NT>
+__device__ __forceinline__ bool subset_live(const Batch& B, const BatchShared<NINT, NT>& S, int norb,
+                                            uint64_t part, const uint32_t* ban) {
+  bool live = false;
+  for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
+    const int cc = c - B.clo;
+    live |= (unsigned)cc < (unsigned)B.nct && !((ban[cc >> 5] >> (cc & 31)) & 1u);
+  });
+  return live;
 }
 
 // Cells touching the particles of J (two-hole batch, t = 1): visited by the
@@ -784,23 +953,23 @@ __device__ __noinline__ void compact_selection(const SweepParams& p, BatchShared
   bool done = false;
   for (int w = 0; w < NW && !done; w++) {
     for (int sh = 56; sh >= 0; sh -= 8) {
-      for (int b = tid; b < 256; b += kThreads) S.hist[b] = 0;
+      for (int b = tid; b < 256; b += kThreads) S.u.hist[b] = 0;
       __syncthreads();
       for (int i = tid; i < n; i += kThreads)
         if (prefix_match<NINT>(te, tk, i, S.pw, w, sh + 8))
-          atomicAdd(&S.hist[(composite_word<NINT>(te, tk, i, w) >> sh) & 255], 1);
+          atomicAdd(&S.u.hist[(composite_word<NINT>(te, tk, i, w) >> sh) & 255], 1);
       __syncthreads();
       if (tid == 0) {
         int c = 0, d = 255;
         for (int b = 0; b < 256; b++) {
-          if (c + S.hist[b] >= S.need) {
+          if (c + S.u.hist[b] >= S.need) {
             d = b;
             break;
           }
-          c += S.hist[b];
+          c += S.u.hist[b];
         }
         S.need -= c;
-        S.group = S.hist[d];
+        S.group = S.u.hist[d];
         S.pw[w] |= (uint64_t)d << sh;
         S.found_w = w;
         S.found_sh = sh;
@@ -880,9 +1049,14 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
   static_assert(!MS || sizeof(NT) == 8, "the multi-state form is FP64");
   constexpr int NW = 2 * NINT;
   extern __shared__ __align__(16) unsigned char dyn[];
-  double* A = reinterpret_cast<double*>(dyn);
   const int mc = p.max_cells;  // stride between the states' accumulators
-  uint32_t* ban = reinterpret_cast<uint32_t*>(A + (MS ? p.nst : 1) * mc);
+  // multi-state form: one FP64 accumulator per state; one-state form: the
+  // exact 96-bit accumulators (low words, then high words)
+  double* A = reinterpret_cast<double*>(dyn);
+  unsigned long long* Alo = reinterpret_cast<unsigned long long*>(dyn);
+  int* Ahi = reinterpret_cast<int*>(Alo + mc);
+  uint32_t* ban =
+      MS ? reinterpret_cast<uint32_t*>(A + p.nst * mc) : reinterpret_cast<uint32_t*>(Ahi + ((mc + 1) & ~1));
   // multi-state extras after the bans: the CTA group's coefficients per
   // state, c_I per state and the weights w_s
   double* ms_gc = reinterpret_cast<double*>(ban + (((mc + 31) / 32 + 1) & ~1));
@@ -906,6 +1080,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
     S.tau = p.tk_tau[blockIdx.x];
     S.slot = -1;
   }
+  const int F = MS ? 0 : fix_scale(p);  // fixed-point scale of A_alpha (units of 2^-F)
 
   for (;;) {
     __syncthreads();
@@ -1015,7 +1190,6 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
 
     // bucket lists: this batch's bucket, then the shared bucket (degree <= 2)
     const int* ofs = p.b_ofs + (size_t)slot * (nbat + 2);
-    const int32_t* ent = p.b_ent + (size_t)slot * (size_t)p.ent_cap;
     // entries: the batch's own bucket (one-hole batch {a}: the d = 3 records
     // holding a; two-hole batch: the d = 4 records holding both holes), then
     // for a two-hole batch {a, b} the d = 3 lists of a and of b (a record
@@ -1028,11 +1202,13 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
     const size_t rb = (size_t)slot * (size_t)p.ndet;
     const uint64_t* rw = p.r_words + rb * NW;
     const double* rc = p.r_coef + rb;
-    const uint64_t* rh = p.r_hmask + rb;
-    const uint64_t* rp = p.r_part + rb;
-    const uint32_t* rf = p.r_flag + rb;
+    const size_t eb = (size_t)slot * (size_t)p.ent_cap;
+    const uint64_t* ehm = p.e_hm + eb;
+    const uint64_t* epart = p.e_part + eb;
+    const uint32_t* erec = p.e_rec + eb;
+    // position of the i-th entry of this batch in the slot's entry arrays
     auto entry = [&](int i) {
-      return i < s1 ? ent[ob + i] : (i < s2 ? ent[o1 + i - s1] : (i < s3 ? ent[o2 + i - s2] : ent[oa + i - s3]));
+      return i < s1 ? ob + i : (i < s2 ? o1 + i - s1 : (i < s3 ? o2 + i - s2 : oa + i - s3));
     };
     // a d = 3 record of b's list that also holds a was taken from a's list
     auto dup = [&](int i, uint64_t hm) { return i >= s2 && i < s3 && ((hm >> B.ia) & 1ull); };
@@ -1045,15 +1221,15 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
       if (B.h == 2) S.kbase[B.sb * NINT + (B.qb >> 6)] &= ~(1ull << (B.qb & 63));
     }
     // zero the accumulator, the bans; row sums for H_aa
-    for (int c = tid; c < B.nct; c += kThreads) A[c] = 0.0;
-    if constexpr (MS)
-      for (int st = 1; st < nst; st++)
+    if constexpr (MS) {
+      for (int st = 0; st < nst; st++)
         for (int c = tid; c < B.nct; c += kThreads) A[st * mc + c] = 0.0;
-    if (GRAD)
-      for (int x = tid; x < kMaxOrb; x += kThreads) {
-        S.rowW2[x] = 0.0;
-        S.colW2[x] = 0.0;
+    } else {
+      for (int c = tid; c < B.nct; c += kThreads) {
+        Alo[c] = 0ull;
+        Ahi[c] = 0;
       }
+    }
     for (int c = tid; c < (B.nct + 31) / 32; c += kThreads) ban[c] = 0u;
     {
       auto W = [&](int x, int sx, int y, int sy) {
@@ -1122,29 +1298,41 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
       }
     }
 
-    // ---- loop 1: bans ----
+    // ---- loop 1: bans.  J ranked before I that reach a whole row or column
+    // of cells (two-hole batch, t = 1) flag it in rowm / colm; the flags are
+    // turned into cell bans after the loop ----
+    for (int x = tid; x < kMaxOrb; x += kThreads) {
+      S.v.m.rowm[x] = 0u;
+      S.v.m.colm[x] = 0u;
+    }
+    __syncthreads();
     bool dead = false;
     for (int c0 = 0; c0 < total; c0 += kChunk) {
-      if (tid == 0) S.n1 = 0;
-      __syncthreads();
       bool dl = false;
       const int c1 = min(c0 + kChunk, total);
       for (int i = c0 + tid; i < c1; i += kThreads) {
-        const int r = entry(i);
-        const uint64_t hm = rh[r];
+        const int o = entry(i);
+        const uint64_t hm = ehm[o];
         if (dup(i, hm)) continue;
         const int t = __popcll(hm & ~B.hm);
         if (t > 2) continue;
-        if (rf[r] & 1u) {
+        if (erec[o] >> 31) {
           if ((B.h == 1 && t <= 1) || (B.h == 2 && t == 0)) {
             dl = true;
           } else if (B.h == 2 && t == 1) {
-            S.L1[atomicAdd(&S.n1, 1)] = r;
+            const uint64_t part = epart[o];
+            int na_, nb_;
+            const uint32_t Pa = particles_of_spin(part, norb, B.kind == 2 ? 0 : B.sa, &na_);
+            for (int q = 0; q < na_; q++) S.v.m.rowm[S.vidx[B.kind == 2 ? 0 : B.sa][pk(Pa, q)]] = 1u;
+            if (B.kind == 2) {
+              const uint32_t Pb = particles_of_spin(part, norb, 1, &nb_);
+              for (int q = 0; q < nb_; q++) S.v.m.colm[S.vidx[1][pk(Pb, q)]] = 1u;
+            }
           } else {  // t == 2
-            for_subset_cells<NINT, NT>(B, S, norb, rp[r], [&](int c) { ban_cell(ban, B, c); });
+            for_subset_cells<NINT, NT>(B, S, norb, epart[o], [&](int c) { ban_cell(ban, B, c); });
           }
         } else if (t == 0 && hm == B.hm) {  // J = I - H + X with X a cell: alpha is internal
-          const uint64_t part = rp[r];
+          const uint64_t part = epart[o];
           int n0, n1, c;
           if (B.kind == 0) {
             const uint32_t P0 = particles_of_spin(part, norb, B.sa, &n0);
@@ -1164,14 +1352,26 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
         dead = true;
         break;
       }
-      for (int j = warp; j < S.n1; j += kWarps)
-        for_row_cells<NINT, NT>(B, S, norb, rp[S.L1[j]], lane,
-                            [&](int c) { ban_cell(ban, B, c); });
-      __syncthreads();
     }
     if (dead) continue;
+    if (B.h == 2) {  // flagged rows and columns: one ban word per warp and round
+      for (int c0 = 0; c0 < B.nct; c0 += kThreads) {
+        const int cc = c0 + tid;
+        bool bn = false;
+        if (cc < B.nct) {
+          int ro, so, x, y;
+          cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
+          bn = (S.v.m.rowm[x] | (B.kind == 2 ? S.v.m.colm[y] : S.v.m.rowm[y])) != 0u;
+        }
+        const unsigned bw = __ballot_sync(kFull, bn);
+        if (lane == 0 && bw) ban[(c0 >> 5) + warp] |= bw;
+      }
+      __syncthreads();
+    }
 
-    // ---- loop 2: A(R) += c_J <J|H|I - H + R> over J ranked at or after I ----
+    // ---- loop 2: A(R) += c_J <J|H|I - H + R> over J ranked at or after I.
+    // In the one-state form every term goes into the exact accumulator, so
+    // the order in which J are listed and cells are reached does not matter ----
     unsigned long long con = 0;
     for (int c0 = 0; c0 < total; c0 += kChunk) {
       if (tid == 0) {
@@ -1183,17 +1383,17 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
       __syncthreads();
       const int c1 = min(c0 + kChunk, total);
       for (int i = c0 + tid; i < c1; i += kThreads) {
-        const int r = entry(i);
-        if (rf[r] & 1u) continue;
-        const uint64_t hmr = rh[r];
+        const int o = entry(i);
+        if (erec[o] >> 31) continue;
+        const uint64_t hmr = ehm[o];
         if (dup(i, hmr)) continue;
         if (B.h == 2 && hmr == 0ull) continue;  // J = I: added in the cells pass
         const int t = __popcll(hmr & ~B.hm);
         if (t > 2) continue;
         const bool all = (B.h == 1) ? (t <= 1) : (t == 0);
-        if (all) S.L0[atomicAdd(&S.n0, 1)] = r;
-        else if (t == 1) S.L1[atomicAdd(&S.n1, 1)] = r;
-        else S.L2[atomicAdd(&S.n2, 1)] = r;
+        if (all) S.u.l.L0[atomicAdd(&S.n0, 1)] = o;
+        else if (t == 1) S.u.l.L1[atomicAdd(&S.n1, 1)] = o;
+        else if (subset_live<NINT, NT>(B, S, norb, epart[o], ban)) S.u.l.L2[atomicAdd(&S.n2, 1)] = o;
       }
       __syncthreads();
       // J reaching every cell: the whole CTA, kGroup of them per pass.
@@ -1205,7 +1405,8 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
       for (int g0 = 0; g0 < n0; g0 += kGroup) {
         const int m = min(kGroup, n0 - g0);
         if (tid < m) {
-          const int r = S.L0[g0 + tid];
+          const int o = S.u.l.L0[g0 + tid];
+          const int r = (int)(erec[o] & 0x7FFFFFFFu);
 #pragma unroll
           for (int w = 0; w < NW; w++) S.gJw[tid][w] = rw[(size_t)r * NW + w];
           S.gcj[tid] = (NT)rc[r];
@@ -1213,7 +1414,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
             for (int st = 0; st < nst; st++) ms_gc[tid * kMaxStates + st] = rc[st * p.rc_stride + r];
           uint32_t xs, ts;
           int nxs, nts;
-          excitation_sets<NINT, NT>(B, S, rp[r], rh[r], &xs, &nxs, &ts, &nts);
+          excitation_sets<NINT, NT>(B, S, epart[o], ehm[o], &xs, &nxs, &ts, &nts);
           S.gX[tid] = xs;
           S.gT[tid] = ts;
           S.gnx[tid] = nxs;
@@ -1242,7 +1443,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
               const int r = S.vir[sl1][v];
               int par = 0;
               if (r != x1) par = count_between<NINT>(Jw + sl1 * NINT, r < x1 ? r : x1, r < x1 ? x1 : r) & 1;
-              S.gRow[j][v] = tri(x1, r) | (par << 31);
+              S.v.g.gRow[j][v] = tri(x1, r) | (par << 31);
             } else {
               const int sv = S.vir[sl2][v - nva];
               int par = 0;
@@ -1251,7 +1452,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
                 const int lo = sv < x2 ? sv : x2, hi = sv < x2 ? x2 : sv;
                 par ^= (x1 > lo && x1 < hi) ? 1 : 0;
               }
-              S.gCol[j][v - nva] = tri(x2, sv) | (par << 31);
+              S.v.g.gCol[j][v - nva] = tri(x2, sv) | (par << 31);
             }
           }
           __syncthreads();
@@ -1262,7 +1463,8 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
           cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
           const int rcode = B.sa * norb + ro;
           const int scode = (B.h == 2) ? B.sb * norb + so : -1;
-          double acc = 0.0;
+          unsigned long long acc_lo = 0ull;  // exact sum of this group's products
+          int acc_hi = 0;
           double accs[kMaxStates];  // multi-state form: one sum per state
 #pragma unroll
           for (int st = 0; st < kMaxStates; st++) accs[st] = 0.0;
@@ -1273,13 +1475,13 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
               const int sr = S.gsr[j], sc = S.gsc[j];
               if (B.kind == 2) {
                 if (x != sr && y != sc) {
-                  const int rt = S.gRow[j][x], ct = S.gCol[j][y];
+                  const int rt = S.v.g.gRow[j][x], ct = S.v.g.gCol[j][y];
                   v = flip_sign(eri_n[tri(rt & 0x7fffffff, ct & 0x7fffffff)], (rt ^ ct) < 0);
                   general = false;
                 }
               } else if (x != sr && x != sc && y != sr && y != sc) {
-                const int a1 = S.gRow[j][x], b2 = S.gCol[j][y];
-                const int a2 = S.gRow[j][y], b1 = S.gCol[j][x];
+                const int a1 = S.v.g.gRow[j][x], b2 = S.v.g.gCol[j][y];
+                const int a2 = S.v.g.gRow[j][y], b1 = S.v.g.gCol[j][x];
                 v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
                 const int x2 = S.gx2[j] - B.sa * norb;
                 const int lo = so < x2 ? so : x2, hi = so < x2 ? x2 : so;
@@ -1294,7 +1496,10 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
               for (int st = 0; st < kMaxStates; st++)
                 if (st < nst) accs[st] = fma(ms_gc[j * kMaxStates + st], (double)v, accs[st]);
             } else {
-              acc += (double)(S.gcj[j] * v);
+              unsigned long long l;
+              int hh;
+              fix_of(S.gcj[j] * v, F, l, hh);
+              fix_add(acc_lo, acc_hi, l, hh);
             }
           }
           if constexpr (MS) {
@@ -1302,7 +1507,11 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
             for (int st = 0; st < kMaxStates; st++)
               if (st < nst) A[st * mc + cc] += accs[st];
           } else {
-            A[cc] += acc;
+            unsigned long long lo = Alo[cc];
+            int hi = Ahi[cc];
+            fix_add(lo, hi, acc_lo, acc_hi);
+            Alo[cc] = lo;
+            Ahi[cc] = hi;
           }
           con += m;
         }
@@ -1318,7 +1527,8 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
           jd = __shfl_sync(kFull, jd, 0);
           if (jd < n1) {
             const int j = jd;
-            const int r = S.L1[j];
+            const int o = S.u.l.L1[j];
+            const int r = (int)(erec[o] & 0x7FFFFFFFu);
             const uint64_t* Jw = rw + (size_t)r * NW;
             const NT cj = (NT)rc[r];
             double cjs[kMaxStates];
@@ -1326,10 +1536,10 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
 #pragma unroll
               for (int st = 0; st < kMaxStates; st++) cjs[st] = st < nst ? rc[st * p.rc_stride + r] : 0.0;
             }
-            const uint64_t part = rp[r];
+            const uint64_t part = epart[o];
             uint32_t X, T;
             int nx, nt;
-            excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
+            excitation_sets<NINT, NT>(B, S, part, ehm[o], &X, &nx, &T, &nt);
             for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
               const int cc = c - B.clo;
               if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
@@ -1343,7 +1553,10 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
                 for (int st = 0; st < kMaxStates; st++)
                   if (st < nst) atomicAdd(&A[st * mc + cc], cjs[st] * v);
               } else {
-                atomicAdd(&A[cc], (double)(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode)));
+                unsigned long long l;
+                int hh;
+                fix_of(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode), F, l, hh);
+                fix_atomic_add(Alo, Ahi, cc, l, hh);
               }
               con++;
             });
@@ -1352,7 +1565,8 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
             if (j0 >= n2) break;
             const int j = j0 + lane;
             if (j < n2) {
-              const int r = S.L2[j];
+              const int o = S.u.l.L2[j];
+            const int r = (int)(erec[o] & 0x7FFFFFFFu);
               const uint64_t* Jw = rw + (size_t)r * NW;
               const NT cj = (NT)rc[r];
               double cjs[kMaxStates];
@@ -1360,10 +1574,10 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
 #pragma unroll
                 for (int st = 0; st < kMaxStates; st++) cjs[st] = st < nst ? rc[st * p.rc_stride + r] : 0.0;
               }
-              const uint64_t part = rp[r];
+              const uint64_t part = epart[o];
               uint32_t X, T;
               int nx, nt;
-              excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
+              excitation_sets<NINT, NT>(B, S, part, ehm[o], &X, &nx, &T, &nt);
               for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
                 const int cc = c - B.clo;
                 if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
@@ -1377,7 +1591,10 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
                   for (int st = 0; st < kMaxStates; st++)
                     if (st < nst) atomicAdd(&A[st * mc + cc], cjs[st] * v);
                 } else {
-                  atomicAdd(&A[cc], (double)(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode)));
+                  unsigned long long l;
+                  int hh;
+                  fix_of(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode), F, l, hh);
+                  fix_atomic_add(Alo, Ahi, cc, l, hh);
                 }
                 con++;
               });
@@ -1389,6 +1606,13 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
     }
 
     // ---- cells: the perturbers of I in this batch ----
+    if (GRAD) {  // loop 2 is over: the pair tables' storage takes the weights
+      for (int x = tid; x < kMaxOrb; x += kThreads) {
+        S.v.w.rowW2[x] = 0.0;
+        S.v.w.colW2[x] = 0.0;
+      }
+      __syncthreads();
+    }
     if (p.k > 0) {
       if (S.tkcnt + B.nct > p.cap) compact_selection<NINT, NT>(p, S, te, ta, tk);
       if (tid == 0) {
@@ -1474,7 +1698,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
         if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
         int ro, so, x, y;
         cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
-        double a = A[cc];
+        double a = fix_to_double(Alo[cc], Ahi[cc], F);
         if (B.h == 2) {  // the generator's own term c_I <I|H|alpha>
           NT v;
           const int a1 = S.iRow[x], b2 = S.iCol[y];
@@ -1504,9 +1728,9 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
           // numerator weight 2A/D for loop 3; (A/D)^2 weights the diagonal
           A[cc] = 2.0 * q;
           const double w2 = q * q;
-          atomicAdd(&S.rowW2[x], w2);
-          if (B.kind == 2) atomicAdd(&S.colW2[y], w2);
-          if (B.kind == 1) atomicAdd(&S.rowW2[y], w2);
+          atomicAdd(&S.v.w.rowW2[x], w2);
+          if (B.kind == 2) atomicAdd(&S.v.w.colW2[y], w2);
+          if (B.kind == 1) atomicAdd(&S.v.w.rowW2[y], w2);
           if (B.h == 2) w_grad(p, ro, B.sa, so, B.sb, w2);
         }
         // |a| < 1e-14, compared on the bit pattern (no FP64 compare)
@@ -1546,8 +1770,8 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
     {
       // FP64 sums through shared memory and one warp: a shuffle tree in every
       // warp would spend five FP64 adds per lane per quantity
-      S.red_t[0][tid] = acc_e;
-      S.red_t[1][tid] = acc_s2;
+      S.u.red_t[0][tid] = acc_e;
+      S.u.red_t[1][tid] = acc_s2;
       const unsigned long long na = warp_sum_u(acc_na), nc = warp_sum_u(con), d0 = warp_sum_u(acc_d0);
       const unsigned long long d1 = warp_xor_u(acc_d1), mn = warp_min_u(acc_min), tiny = warp_sum_u(acc_tiny);
       if (lane == 0) {
@@ -1562,8 +1786,8 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
       double se = 0.0, ss = 0.0;
       if (warp == 0) {
         for (int i = lane; i < kThreads; i += 32) {
-          se += S.red_t[0][i];
-          ss += S.red_t[1][i];
+          se += S.u.red_t[0][i];
+          ss += S.u.red_t[1][i];
         }
         se = warp_sum(se);
         ss = warp_sum(ss);
@@ -1580,9 +1804,14 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
           tt += S.red_u[w][5];
         }
         S.sw2 = ts;
+        // the item's FP64 sums go to its own slot; the generator's eps_I
+        // and sum A^2/D^2 are reduced from the slots in item order after the
+        // wave (reduce_items_kernel), so they do not depend on which CTA
+        // finished first
+        double* its = p.it_sum + ((size_t)slot * nper + j) * p.it_stride;
+        its[0] = te_;
+        its[1] = ts;
         if (tn) {
-          atomicAdd(&p.eps[g], te_);
-          atomicAdd(&p.s2[g], ts);
           atomicAdd(&p.na[g], tn);
           atomicAdd(&p.ncon[g], tc);
           atomicAdd(&p.digest[0], x0);
@@ -1596,20 +1825,21 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
         for (int st = 1; st < kMaxStates; st++) {
           if (st >= nst) break;
           __syncthreads();
-          S.red_t[0][tid] = acc_es[st];
-          S.red_t[1][tid] = acc_s2s[st];
+          S.u.red_t[0][tid] = acc_es[st];
+          S.u.red_t[1][tid] = acc_s2s[st];
           __syncthreads();
           if (warp == 0) {
             double ue = 0.0, us = 0.0;
             for (int i = lane; i < kThreads; i += 32) {
-              ue += S.red_t[0][i];
-              us += S.red_t[1][i];
+              ue += S.u.red_t[0][i];
+              us += S.u.red_t[1][i];
             }
             ue = warp_sum(ue);
             us = warp_sum(us);
-            if (lane == 0 && (ue != 0.0 || us != 0.0)) {
-              atomicAdd(&p.eps[(size_t)st * p.ndet + g], ue);
-              atomicAdd(&p.s2[(size_t)st * p.ndet + g], us);
+            if (lane == 0) {
+              double* its = p.it_sum + ((size_t)slot * nper + j) * p.it_stride;
+              its[2 * st] = ue;
+              its[2 * st + 1] = us;
             }
           }
         }
@@ -1628,24 +1858,26 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
         __syncthreads();
         const int c1 = min(c0 + kChunk, total);
         for (int i = c0 + tid; i < c1; i += kThreads) {
-          const int r = entry(i);
-          if (rf[r] & 1u) continue;
-          if (dup(i, rh[r])) continue;
-          const int t = __popcll(rh[r] & ~B.hm);
+          const int o = entry(i);
+          if (erec[o] >> 31) continue;
+          const uint64_t hmr = ehm[o];
+          if (dup(i, hmr)) continue;
+          const int t = __popcll(hmr & ~B.hm);
           if (t > 2) continue;
           const bool all = (B.h == 1) ? (t <= 1) : (t == 0);
-          if (all) S.L0[atomicAdd(&S.n0, 1)] = r;
-          else if (t == 1) S.L1[atomicAdd(&S.n1, 1)] = r;
-          else S.L2[atomicAdd(&S.n2, 1)] = r;
+          if (all) S.u.l.L0[atomicAdd(&S.n0, 1)] = o;
+          else if (t == 1) S.u.l.L1[atomicAdd(&S.n1, 1)] = o;
+          else if (subset_live<NINT, NT>(B, S, norb, epart[o], ban)) S.u.l.L2[atomicAdd(&S.n2, 1)] = o;
         }
         __syncthreads();
         for (int j = 0; j < S.n0; j++) {
-          const int r = S.L0[j];
+          const int o = S.u.l.L0[j];
+          const int r = (int)(erec[o] & 0x7FFFFFFFu);
           const uint64_t* Jw = rw + (size_t)r * NW;
           const double cj = rc[r];
           uint32_t X, T;
           int nx, nt;
-          excitation_sets<NINT, NT>(B, S, rp[r], rh[r], &X, &nx, &T, &nt);
+          excitation_sets<NINT, NT>(B, S, epart[o], ehm[o], &X, &nx, &T, &nt);
           for (int cc = tid; cc < B.nct; cc += kThreads) {
             if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
             int ro, so, x, y;
@@ -1661,13 +1893,14 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
             jd = __shfl_sync(kFull, jd, 0);
             if (jd < n1) {
               const int j = jd;
-              const int r = S.L1[j];
+              const int o = S.u.l.L1[j];
+              const int r = (int)(erec[o] & 0x7FFFFFFFu);
               const uint64_t* Jw = rw + (size_t)r * NW;
               const double cj = rc[r];
-              const uint64_t part = rp[r];
+              const uint64_t part = epart[o];
               uint32_t X, T;
               int nx, nt;
-              excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
+              excitation_sets<NINT, NT>(B, S, part, ehm[o], &X, &nx, &T, &nt);
               for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
                 const int cc = c - B.clo;
                 if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
@@ -1680,13 +1913,14 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
               if (j0 >= n2) break;
               const int j = j0 + lane;
               if (j < n2) {
-                const int r = S.L2[j];
+                const int o = S.u.l.L2[j];
+                const int r = (int)(erec[o] & 0x7FFFFFFFu);
                 const uint64_t* Jw = rw + (size_t)r * NW;
                 const double cj = rc[r];
-                const uint64_t part = rp[r];
+                const uint64_t part = epart[o];
                 uint32_t X, T;
                 int nx, nt;
-                excitation_sets<NINT, NT>(B, S, part, rh[r], &X, &nx, &T, &nt);
+                excitation_sets<NINT, NT>(B, S, part, ehm[o], &X, &nx, &T, &nt);
                 for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
                   const int cc = c - B.clo;
                   if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
@@ -1707,7 +1941,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
       double* wF = p.g_wF + (size_t)g * 2 * norb;
       const int s1 = B.sa, s2 = (B.h == 2) ? B.sb : B.sa;
       for (int x = tid; x < S.nv[s1]; x += kThreads) {
-        const double wr = S.rowW2[x];
+        const double wr = S.v.w.rowW2[x];
         if (wr == 0.0) continue;
         const int r = S.vir[s1][x];
         atomicAdd(&wF[s1 * norb + r], wr);
@@ -1716,7 +1950,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
       }
       if (B.kind == 2)
         for (int y = tid; y < S.nv[s2]; y += kThreads) {
-          const double wc = S.colW2[y];
+          const double wc = S.v.w.colW2[y];
           if (wc == 0.0) continue;
           const int sv = S.vir[s2][y];
           atomicAdd(&wF[s2 * norb + sv], wc);

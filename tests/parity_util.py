@@ -69,3 +69,27 @@ def check_selection(got_dets, got_e, ref_dets, ref_e, rel=1e-9):
     # best-first order
     a = np.abs(ge)
     assert np.all(a[:-1] >= a[1:] * (1 - 1e-12) - 1e-300)
+
+
+def variational(ham, dets):
+    """Lowest eigenpair of H over the determinant set (dense, from the
+    oracle's matrix elements): a unit-norm Psi0 with a variational E0, as
+    the CIPSI workloads have, for the small random test spaces."""
+    n = len(dets)
+    H = np.array([[ham.hij(dets[i], dets[j]) for j in range(n)] for i in range(n)])
+    w, v = np.linalg.eigh(H)
+    c = v[:, 0] * (1.0 if v[0, 0] >= 0 else -1.0)
+    return np.ascontiguousarray(c), float(w[0])
+
+
+def cipsi_space(oracle_mod, ham, norb, na, nb, ndet, doublings=2):
+    """A small Psi0 grown by the oracle's CIPSI rule (seed space of
+    ndet / 2^doublings determinants, then doublings), with its coefficients
+    and variational E0: the shape of the workloads (Sec. "The basic
+    algorithm"), at sizes the oracle grows in a fraction of a second."""
+    from oracle import psi0
+
+    from paper_1902_08154_gb300 import synthetic as S
+
+    dets, c, e0, _ = psi0.cipsi_grow(ham, S.hf_det(norb, na, nb), ndet, doublings=doublings)
+    return np.ascontiguousarray(dets), np.ascontiguousarray(c), float(e0)

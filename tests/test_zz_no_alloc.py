@@ -28,7 +28,13 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("norb,na,nb,ndet,k,seed", [(16, 4, 4, 300, 200, 71), (70, 3, 3, 80, 50, 72)])
+# The last case needs several waves of generator slots inside the fixed
+# array: one slot of 64 orbitals, 10+10 electrons and 1000 determinants holds
+# 1000 coarse-filter records (44 bytes each) and up to 6000 bucket entries
+# (20 bytes each), about 164 KB, so the 64 MiB array holds fewer than 410
+# slots for the 1000 generators.
+@pytest.mark.parametrize("norb,na,nb,ndet,k,seed", [(16, 4, 4, 300, 200, 71), (70, 3, 3, 80, 50, 72),
+                                                    (64, 10, 10, 1000, 1000, 76)])
 def test_noalloc_matches_eval_twice(norb, na, nb, ndet, k, seed):
     import torch
 
@@ -76,6 +82,12 @@ def test_noalloc_refuses_host_memory_and_oversize():
     # host arrays are refused: the entry point copies nothing
     rc, _ = qp.qp_pt2_eval_noalloc(norb, na, nb, h, eri, 20, dets, c, -10.0, 0)
     assert rc == qp.QP_EINVAL
+    assert b"device memory" in qp.load().qp_pt2_last_error()
+    # so is page-locked host memory, which the GPU could reach but which is
+    # not memory of the current device
+    hp = torch.from_numpy(h).pin_memory()
+    rc, _ = qp.qp_pt2_eval_noalloc(norb, na, nb, hp, _dev(eri), 20, _dev(dets), _dev(c), -10.0, 0)
+    assert rc == qp.QP_EINVAL
     # a selection that cannot fit in the fixed scratch is refused cleanly
     hd, ed, dd, cd = _dev(h), _dev(eri), _dev(dets), _dev(c)
     k = 10**7
@@ -83,3 +95,4 @@ def test_noalloc_refuses_host_memory_and_oversize():
     sel_e = torch.zeros(1, dtype=torch.float64, device="cuda")
     rc, _ = qp.qp_pt2_eval_noalloc(norb, na, nb, hd, ed, 20, dd, cd, -10.0, k, sel, sel_e)
     assert rc == qp.QP_EINVAL
+    assert b"too large" in qp.load().qp_pt2_last_error()
