@@ -415,7 +415,7 @@ def run_gb300(args):
             flush.zero_()
             res = step()
             if dist:
-                distributed_merge(dist, res, sel_e[: res["n_selected"]], sel[: res["n_selected"]], k, device)
+                distributed_merge(dist, res, sel_e[: res["n_selected"]], sel[: res["n_selected"]], k, device, e0)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -432,7 +432,7 @@ def run_gb300(args):
             res = step()
             if dist:
                 tot, _, _ = distributed_merge(dist, res, sel_e[: res["n_selected"]], sel[: res["n_selected"]],
-                                              k, device)
+                                              k, device, e0)
                 units = int(tot["n_perturbers"])
             else:
                 units = res["n_perturbers"]

@@ -61,6 +61,14 @@
  * and qp_pt2_eval_noalloc takes device arrays only.  Calls run on the stream of the context's configuration and
  * return after the stream has finished the call's work.
  *
+ * Reproducibility: in the one-state sweeps (qp_pt2_eval, _eval_ex,
+ * _eval_gens, _grad, the batch and qp_pt2_eval_noalloc) the products
+ * c_J <J|H|alpha> are summed exactly (96-bit integers in units of 2^-F, F
+ * fixed per call from max |c_I|, N_det and the integrals' size) and rounded
+ * once, the sums of a generator are reduced in a fixed order and E_PT2 in
+ * rank order: the same inputs give the same bits on every run, every grid
+ * size and every work-queue order.
+ *
  * Errors: every entry point returns QP_OK (0) or a negative code; no call
  * aborts, traps or throws.  qp_pt2_strerror() names a code;
  * qp_pt2_last_error() gives the message of the last failing call of this
@@ -82,14 +90,16 @@ extern "C" {
 #define QP_ESINGULAR (-4)  /* some |E0 - H_aa| < 1e-12; results still filled */
 #define QP_ENOMEM (-5)     /* device allocation failed */
 #define QP_ECUDA (-6)      /* CUDA runtime error */
+#define QP_ETIMEOUT (-7)   /* the device watchdog stopped the sweep (cfg timeout_s); results partial */
 #define QP_ENOTSUP (-8)    /* configuration not supported by the library */
 #define QP_ENOTCONV (-9)  /* Davidson stopped above its residual tolerance */
 
 #define QP_FP64 0          /* every step in FP64 */
 #define QP_MIXED 1         /* numerator <J|H|alpha> gathers and products c_J<J|H|alpha> in
-                              FP32 (FP32 copies of h and eri); each product is added into
-                              an FP64 accumulator A_alpha; denominators E0 - H_aa, e_alpha
-                              and every reduction in FP64.  Error bound per result: about
+                              FP32 (FP32 copies of h and eri); the products are summed
+                              exactly into A_alpha (as in QP_FP64, below) and A_alpha is
+                              rounded once to FP64; denominators E0 - H_aa, e_alpha and
+                              every reduction in FP64.  Error bound per result: about
                               2^-24 * sum_alpha 2|A_alpha| sum_J |c_J H_Jalpha| / |D_alpha|. */
 
 typedef struct qp_pt2_ctx qp_pt2_ctx; /* opaque, library-owned */
@@ -102,6 +112,17 @@ typedef struct {
     int shard_index;    /* generator sharding across processes: this call   */
     int shard_count;    /* sweeps the generators of rank r with              */
                         /* r % shard_count == shard_index (0, 0: all of them) */
+    int work_chunk;     /* work items (generator x hole-set batch) a CTA takes from
+                           the queue per draw; 0 = 1 */
+    int tile;           /* tiles of rows each opposite-spin two-hole batch is split
+                           into (its accumulator shrinks by that factor, so more
+                           CTAs share an SM); 0 = chosen by the library (2 when
+                           the whole accumulator fits only once per SM, else 1) */
+    double timeout_s;   /* device watchdog: 0 = none; otherwise CTAs stop taking
+                           work items once timeout_s seconds of device time have
+                           passed since the call's sweep started, and the call
+                           returns QP_ETIMEOUT with the partial results of the
+                           items done (the context stays usable) */
 } qp_pt2_config;
 
 typedef struct {
@@ -118,6 +139,9 @@ typedef struct {
                                     splitmix64(hk ^ 0x243F6A8885A308D3) over the
                                     key hashes hk, hk = fold of splitmix64 over
                                     the 2*nint key words starting from 0 */
+    double z;                   /* renormalisation factor Z = 1/(1 + sum_e_over_d) (Sec.
+                                   "Renormalized PT2", Eq. Z) */
+    double e_rpt2;              /* E0 + Z E_PT2: the renormalised second-order energy */
 } qp_pt2_result;
 
 /* Create a context for norb orbitals and n_alpha + n_beta electrons.
@@ -313,6 +337,15 @@ int qp_pt2_last_timings(const qp_pt2_ctx *ctx, double *ms);
 int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const double *h, const double *eri,
                         int64_t ndet, const uint64_t *dets, const double *coefs, double e0, int64_t k,
                         uint64_t *sel_dets, double *sel_e, qp_pt2_result *res, void *stream);
+
+/* Merge of the partial results of n generator shards of one sweep (the
+ * exchange step of a sharded sweep, Sec. "Parallelism"): E_PT2, sum A^2/D^2,
+ * the counts and n_tiny add, the digest words add modulo 2^64 and xor, the
+ * minimum denominator is the minimum, n_selected is left 0 (the selection is
+ * merged separately), and z, e_rpt2 are recomputed from the merged sums with
+ * e0.  parts and out are host memory; out may alias parts[0].  QP_EINVAL if
+ * n < 1 or a pointer is NULL. */
+int qp_pt2_merge_results(int n, const qp_pt2_result *parts, double e0, qp_pt2_result *out);
 
 /* Release the context and its device memory.  NULL is accepted. */
 void qp_pt2_destroy(qp_pt2_ctx *ctx);

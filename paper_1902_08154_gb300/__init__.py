@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SO = os.path.join(HERE, "_build", "libqp_pt2.so")
 
 QP_OK, QP_EINVAL, QP_EDUP, QP_ESYM, QP_ESINGULAR, QP_ENOMEM, QP_ECUDA, QP_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -8
-QP_ENOTCONV = -9
+QP_ETIMEOUT, QP_ENOTCONV = -7, -9
 QP_FP64 = 0
 QP_MIXED = 1
 
@@ -36,6 +36,7 @@ EXPORTS = (
     "qp_pt2_strerror",
     "qp_pt2_last_error",
     "qp_pt2_eval_noalloc",
+    "qp_pt2_merge_results",
     "qp_pt2_grad",
     "qp_pt2_batch_create",
     "qp_pt2_batch_run",
@@ -45,7 +46,8 @@ EXPORTS = (
 
 class Config(C.Structure):
     _fields_ = [("precision", C.c_int), ("stream", C.c_void_p), ("blocks_per_sm", C.c_int), ("threads", C.c_int),
-                ("shard_index", C.c_int), ("shard_count", C.c_int)]
+                ("shard_index", C.c_int), ("shard_count", C.c_int), ("work_chunk", C.c_int), ("tile", C.c_int),
+                ("timeout_s", C.c_double)]
 
 
 class Result(C.Structure):
@@ -58,6 +60,8 @@ class Result(C.Structure):
         ("n_selected", C.c_int64),
         ("n_tiny", C.c_int64),
         ("perturber_digest", C.c_uint64 * 2),
+        ("z", C.c_double),
+        ("e_rpt2", C.c_double),
     ]
 
     def as_dict(self):
@@ -70,15 +74,36 @@ class Result(C.Structure):
             "n_selected": self.n_selected,
             "n_tiny": self.n_tiny,
             "digest": (int(self.perturber_digest[0]), int(self.perturber_digest[1])),
+            "z": self.z,
+            "e_rpt2": self.e_rpt2,
         }
 
 
-def rpt2(res, e0):
-    """Renormalised PT2 (Sec. "Renormalized PT2"): with
-    dSigma/dE at E0 = -sum_alpha A^2/D^2 (returned by every sweep),
-    Z = 1 / (1 + sum A^2/D^2) lies in (0, 1] and E = E0 + Z E_PT2."""
-    z = 1.0 / (1.0 + res["sum_e_over_d"])
-    return {"z": z, "e_rpt2": float(e0) + z * res["e_pt2"]}
+def rpt2(res, e0=None):
+    """Renormalised PT2 (Sec. "Renormalized PT2") of a result dict: Z and
+    E0 + Z E_PT2, as the library computed them."""
+    return {"z": res["z"], "e_rpt2": res["e_rpt2"]}
+
+
+def merge_results(parts, e0):
+    """Merge of the partial results of generator shards (dicts as returned
+    by the sweeps) through qp_pt2_merge_results: sums and counts add, the
+    digest words add modulo 2^64 and xor, Z and E_rPT2 are recomputed."""
+    n = len(parts)
+    arr = (Result * n)()
+    for i, p in enumerate(parts):
+        r = arr[i]
+        r.e_pt2 = float(p["e_pt2"])
+        r.sum_e_over_d = float(p["sum_e_over_d"])
+        r.min_abs_denominator = float(p.get("min_abs_den", float("inf")))
+        r.n_perturbers = int(p["n_perturbers"])
+        r.n_connections = int(p["n_connections"])
+        r.n_tiny = int(p.get("n_tiny", 0))
+        r.perturber_digest[0] = int(p["digest"][0]) & ((1 << 64) - 1)
+        r.perturber_digest[1] = int(p["digest"][1]) & ((1 << 64) - 1)
+    out = Result()
+    _check(load().qp_pt2_merge_results(n, arr, float(e0), C.byref(out)))
+    return out.as_dict()
 
 
 class DavidsonInfo(C.Structure):
@@ -135,6 +160,8 @@ def load(path: str = SO):
     L.qp_pt2_last_error.argtypes = []
     L.qp_pt2_grad.restype = C.c_int
     L.qp_pt2_grad.argtypes = [vp, i64, vp, vp, dbl, vp, vp, vp, C.POINTER(Result)]
+    L.qp_pt2_merge_results.restype = C.c_int
+    L.qp_pt2_merge_results.argtypes = [C.c_int, C.c_void_p, C.c_double, C.POINTER(Result)]
     L.qp_pt2_eval_noalloc.restype = C.c_int
     L.qp_pt2_eval_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, i64, vp, vp, dbl, i64, vp, vp,
                                       C.POINTER(Result), vp]
@@ -160,10 +187,11 @@ def _check(rc):
 
 
 def qp_pt2_create(norb, n_alpha, n_beta, h, eri, stream=None, blocks_per_sm=0, precision=QP_FP64,
-                  shard_index=0, shard_count=0):
+                  shard_index=0, shard_count=0, work_chunk=0, tile=0, timeout_s=0.0):
     """Create a context; h and eri are float64 numpy arrays or CUDA tensors."""
     L = load()
-    cfg = Config(precision, stream or None, blocks_per_sm, 0, shard_index, shard_count)
+    cfg = Config(precision, stream or None, blocks_per_sm, 0, shard_index, shard_count, work_chunk, tile,
+                 float(timeout_s))
     out = C.c_void_p()
     _check(L.qp_pt2_create(C.byref(out), norb, n_alpha, n_beta, _ptr(h), _ptr(eri), C.byref(cfg)))
     return out
@@ -269,11 +297,12 @@ class PT2:
     """Owning wrapper: one context per (Hamiltonian, electron count)."""
 
     def __init__(self, norb, n_alpha, n_beta, h, eri, stream=None, blocks_per_sm=0, shard_index=0,
-                 shard_count=0, precision=QP_FP64):
+                 shard_count=0, precision=QP_FP64, work_chunk=0, tile=0, timeout_s=0.0):
         self.norb, self.n_alpha, self.n_beta = norb, n_alpha, n_beta
         self.nint = (norb - 1) // 64 + 1
         self.ctx = qp_pt2_create(norb, n_alpha, n_beta, h, eri, stream, blocks_per_sm, precision=precision,
-                                 shard_index=shard_index, shard_count=shard_count)
+                                 shard_index=shard_index, shard_count=shard_count, work_chunk=work_chunk,
+                                 tile=tile, timeout_s=timeout_s)
 
     def close(self):
         if getattr(self, "ctx", None) is not None and _lib is not None:
@@ -315,7 +344,6 @@ class PT2:
                                  sn if k else None, eps, na, nc, rk, check=check)
         out = res.as_dict()
         out["rc"] = rc
-        out.update(rpt2(out, e0))
         m = res.n_selected
         out.update(sel_dets=sel[:m], sel_e=se[:m], sel_num=sn[:m])
         if per_generator:

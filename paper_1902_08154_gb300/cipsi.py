@@ -30,3 +30,15 @@ def grow(pt2, dets, coefs, e0, doublings, tol=1e-10, log=None):
         if log:
             log(f"  doubling {it + 1}: ndet={len(dets)} e0={e0:.12f}")
     return dets, coefs, e0, info
+
+
+def grow_from_seed(pt2, seed_dets, doublings, tol=1e-10, log=None):
+    """The growth from a seed space: the lowest eigenpair of H over the seed
+    (Davidson), then ``doublings`` doublings as in ``grow``.  seed_dets: host
+    array.  Returns (dets, coefs, e0, info); info starts with the seed's
+    record."""
+    seed_dets = np.ascontiguousarray(seed_dets, dtype=np.uint64)
+    e0, coefs, dinfo = pt2.davidson(seed_dets, tol=tol)
+    dets, coefs, e0, info = grow(pt2, seed_dets, coefs, e0, doublings, tol=tol, log=log)
+    info[0].update(residual=dinfo["residual"], davidson_ms=dinfo["build_ms"] + dinfo["solve_ms"])
+    return dets, coefs, e0, info

@@ -102,10 +102,18 @@ struct GenMeta {
 
 struct SweepParams {
   int norb, nalpha, nbeta, nel, nbat;
-  // tile2 = 1: every opposite-spin two-hole batch is split into two work
-  // items over halves of its rows (its accumulator would not fit twice in an
-  // SM's shared memory); nper = work items per generator
-  int tile2, nper;
+  // ntile > 1: every opposite-spin two-hole batch is split into ntile work
+  // items over consecutive blocks of ceil(nv_up / ntile) rows (so that its
+  // accumulator fits, or fits more than once, in an SM's shared memory);
+  // nper = work items per generator = nbat + (ntile - 1) n_alpha n_beta
+  int ntile, nper;
+  // work items taken from the queue per draw (>= 1)
+  int chunk;
+  // watchdog: with timeout_ns > 0 a CTA stops taking work items once
+  // timeout_ns nanoseconds (device global timer) have passed since *t_start,
+  // the time the first CTA of the call started, and sets error flag 128
+  unsigned long long timeout_ns;
+  unsigned long long* t_start;
   int64_t ndet;
   const uint64_t* dets;   // [ndet][2][NINT]
   const double* coefs;    // [ndet]

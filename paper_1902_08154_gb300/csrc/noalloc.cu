@@ -309,7 +309,10 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   p.nbeta = n_beta;
   p.nel = nel;
   p.nbat = nbat;
-  p.tile2 = 0;
+  p.ntile = 1;
+  p.chunk = 1;
+  p.timeout_ns = 0ull;
+  p.t_start = nullptr;
   p.nper = nper;
   p.cmax_bits = acc + 8;
   p.hmax_bits = d_hmax;
@@ -417,6 +420,8 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   double md;
   memcpy(&md, &hacc[2], sizeof(md));
   res->min_abs_denominator = md;
+  res->z = 1.0 / (1.0 + res->sum_e_over_d);  // renormalised PT2 (Sec. "Renormalized PT2")
+  res->e_rpt2 = e0 + res->z * res->e_pt2;
   if (hres.na > 0 && md < 1e-12) return nfail(QP_ESINGULAR, "a denominator E0 - H_aa is below 1e-12");
   return QP_OK;
 }

@@ -50,7 +50,7 @@ static int fail(int code, const std::string& msg) {
 // (16 and 32: the no-allocation entry point's symmetry check, the selection's
 // candidate space; 64: coefficients times integrals beyond the exact
 // accumulator's range)
-enum : int { kErrOcc = 1, kErrDup = 2, kErrCoef = 4, kErrBucket = 8, kErrRange = 64 };
+enum : int { kErrOcc = 1, kErrDup = 2, kErrCoef = 4, kErrBucket = 8, kErrRange = 64, kErrTimeout = 128 };
 
 // device memory allowed for the per-generator records and buckets of a wave
 static const size_t kWaveBudget = (size_t)4 << 30;
@@ -296,7 +296,7 @@ struct qp_pt2_ctx {
   cudaStream_t st;
   int device, nsm;
   int max_cells, bps, grid;
-  int tile2;  // opposite-spin batches split in two row tiles
+  int ntile;  // row tiles of the opposite-spin batches (1: not split)
   int tgt_on = 0, tgt_max_exc = -1;  // target space (qp_pt2_set_target)
   uint64_t tgt_ref[4] = {0, 0, 0, 0}, tgt_core[4] = {0, 0, 0, 0}, tgt_del[4] = {0, 0, 0, 0};
   size_t smem;
@@ -337,8 +337,15 @@ int ctx_view(const qp_pt2_ctx* x, CtxView* v) {
 int report(int code, const char* msg) { return fail(code, msg); }
 }  // namespace qp
 
+// Renormalised PT2 (Sec. "Renormalized PT2"): with sum_e_over_d = sum A^2/D^2
+// = -dSigma/dE at E0, Z = 1/(1 + sum_e_over_d) and E = E0 + Z E_PT2.
+static void set_rpt2(qp_pt2_result& r, double e0) {
+  r.z = 1.0 / (1.0 + r.sum_e_over_d);
+  r.e_rpt2 = e0 + r.z * r.e_pt2;
+}
+
 // accumulator block layout (unsigned long long words)
-enum { kAccDigest0 = 0, kAccDigest1, kAccMinDen, kAccTiny, kAccTau, kAccQueue, kAccErr, kAccNcand, kAccCmax, kAccWords };
+enum { kAccDigest0 = 0, kAccDigest1, kAccMinDen, kAccTiny, kAccTau, kAccQueue, kAccErr, kAccNcand, kAccCmax, kAccT0, kAccWords };
 
 static bool is_device_ptr(const void* p) {
   if (!p) return false;
@@ -348,18 +355,6 @@ static bool is_device_ptr(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-static int cells_max(int norb, int na, int nb) {
-  const int va = norb - na, vb = norb - nb;
-  int m = va > vb ? va : vb;
-  int t = va * (va - 1) / 2;
-  m = t > m ? t : m;
-  t = vb * (vb - 1) / 2;
-  m = t > m ? t : m;
-  t = va * vb;
-  m = t > m ? t : m;
-  return m;
 }
 
 extern "C" int qp_pt2_create(qp_pt2_ctx** out, int norb, int n_alpha, int n_beta, const double* h,
@@ -440,27 +435,32 @@ extern "C" int qp_pt2_create(qp_pt2_ctx** out, int norb, int n_alpha, int n_beta
   }
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(x->st) != cudaSuccess)
     return bail(QP_ECUDA, "integral tables failed");
-  x->max_cells = cells_max(norb, n_alpha, n_beta);
-  if (x->max_cells < 1) x->max_cells = 1;
-  x->tile2 = 0;
+  if (c.tile < 0) return bail(QP_EINVAL, "tile must be >= 0");
+  if (c.work_chunk < 0) return bail(QP_EINVAL, "work_chunk must be >= 0");
+  if (!(c.timeout_s >= 0.0)) return bail(QP_EINVAL, "timeout_s must be >= 0");
+  // cells of the largest work item when the opposite-spin batches are split
+  // into t tiles of rows
+  const int va = norb - n_alpha, vb = norb - n_beta;
+  auto cells_tiled = [&](int t) {
+    int m = (n_alpha > 0 && n_beta > 0) ? ((va + t - 1) / t) * vb : 0;
+    const int others[4] = {va, vb, va * (va - 1) / 2, vb * (vb - 1) / 2};
+    for (int o : others) m = o > m ? o : m;
+    return m < 1 ? 1 : m;
+  };
+  x->ntile = 1;
+  if (c.tile > 0) {
+    x->ntile = (n_alpha > 0 && n_beta > 0) ? std::min(c.tile, std::max(va, 1)) : 1;
+  }
+  x->max_cells = cells_tiled(x->ntile);
   x->smem = sweep_smem(x->max_cells);
   int bps = batch_blocks_per_sm(x->nint, c.precision == QP_MIXED, x->smem);
-  if (x->nint == 2 && bps < 2 && n_alpha > 0 && n_beta > 0) {
+  if (c.tile == 0 && x->nint == 2 && bps < 2 && n_alpha > 0 && n_beta > 0 && cells_tiled(2) < x->max_cells) {
     // the opposite-spin accumulator fits only once per SM: split those
     // batches in two tiles of rows, so that two CTAs share the SM
-    const int va = norb - n_alpha, vb = norb - n_beta;
-    int m = cells_max(norb, n_alpha, n_beta);
-    if (m == va * vb) {
-      m = ((va + 1) / 2) * vb;
-      const int others[4] = {va, vb, va * (va - 1) / 2, vb * (vb - 1) / 2};
-      for (int o : others) m = o > m ? o : m;
-    }
-    if (m < x->max_cells) {
-      x->tile2 = 1;
-      x->max_cells = m;
-      x->smem = sweep_smem(x->max_cells);
-      bps = batch_blocks_per_sm(x->nint, c.precision == QP_MIXED, x->smem);
-    }
+    x->ntile = 2;
+    x->max_cells = cells_tiled(2);
+    x->smem = sweep_smem(x->max_cells);
+    bps = batch_blocks_per_sm(x->nint, c.precision == QP_MIXED, x->smem);
   }
   if (bps < 1) return bail(QP_ENOTSUP, "the batch accumulator does not fit in shared memory");
   if (c.blocks_per_sm > 0 && c.blocks_per_sm < bps) bps = c.blocks_per_sm;
@@ -536,11 +536,33 @@ extern "C" const char* qp_pt2_strerror(int code) {
     case QP_ECUDA: return "CUDA runtime error";
     case QP_ENOTSUP: return "not supported by the library";
     case QP_ENOTCONV: return "Davidson did not reach the residual tolerance";
+    case QP_ETIMEOUT: return "the device watchdog stopped the sweep";
     default: return "unknown error";
   }
 }
 
 extern "C" const char* qp_pt2_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int qp_pt2_merge_results(int n, const qp_pt2_result* parts, double e0, qp_pt2_result* out) {
+  if (n < 1 || !parts || !out) return fail(QP_EINVAL, "n < 1 or a NULL pointer");
+  qp_pt2_result m;
+  memset(&m, 0, sizeof(m));
+  m.min_abs_denominator = INFINITY;
+  for (int i = 0; i < n; i++) {
+    const qp_pt2_result& r = parts[i];
+    m.e_pt2 += r.e_pt2;
+    m.sum_e_over_d += r.sum_e_over_d;
+    m.n_perturbers += r.n_perturbers;
+    m.n_connections += r.n_connections;
+    m.n_tiny += r.n_tiny;
+    m.perturber_digest[0] += r.perturber_digest[0];  // modulo 2^64
+    m.perturber_digest[1] ^= r.perturber_digest[1];
+    if (r.min_abs_denominator < m.min_abs_denominator) m.min_abs_denominator = r.min_abs_denominator;
+  }
+  set_rpt2(m, e0);
+  *out = m;
+  return QP_OK;
+}
 
 // Stage a caller array on the device: returns the device pointer to use.
 template <typename T>
@@ -707,7 +729,7 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   const int64_t ent_per = bucket_entries_per_record(x->nel);
   const int64_t ent_cap = (int64_t)nd * ent_per;
   const size_t dwords = (size_t)(x->nbat + 31) / 32;
-  const int nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
+  const int nper = x->nbat + (x->ntile - 1) * x->nalpha * x->nbeta;
   const size_t per_slot = wave_slot_bytes(sizeof(GenMeta), x->nel, x->nbat, nw, nd, nsts, nper);
   int64_t W = (int64_t)(kWaveBudget / per_slot);
   if (W < 1) W = 1;
@@ -741,8 +763,11 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   p.nbeta = x->nbeta;
   p.nel = x->nel;
   p.nbat = x->nbat;
-  p.tile2 = x->tile2;
-  p.nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
+  p.ntile = x->ntile;
+  p.nper = x->nbat + (x->ntile - 1) * x->nalpha * x->nbeta;
+  p.chunk = x->cfg.work_chunk > 0 ? x->cfg.work_chunk : 1;
+  p.timeout_ns = (unsigned long long)(x->cfg.timeout_s * 1e9);
+  p.t_start = acc + kAccT0;
   p.hmax_bits = x->d_hmax;
   p.cmax_bits = acc + kAccCmax;
   p.it_sum = x->it_sum.as<double>();
@@ -931,7 +956,9 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
     res[s].perturber_digest[0] = hacc[kAccDigest0];
     res[s].perturber_digest[1] = hacc[kAccDigest1];
     res[s].min_abs_denominator = md;
+    set_rpt2(res[s], ms ? e0s[s] : e0);
   }
+  if (herr & kErrTimeout) return fail(QP_ETIMEOUT, "the device watchdog stopped the sweep (timeout_s)");
   if (hres[0].na > 0 && md < 1e-12) return fail(QP_ESINGULAR, "a denominator E0 - H_aa is below 1e-12");
   return QP_OK;
 }
@@ -1073,7 +1100,7 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
   const int64_t ent_per = bucket_entries_per_record(x->nel);
   const int64_t ent_cap = (int64_t)nd * ent_per;
   const size_t dwords = (size_t)(x->nbat + 31) / 32;
-  const int nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
+  const int nper = x->nbat + (x->ntile - 1) * x->nalpha * x->nbeta;
   const size_t per_slot = wave_slot_bytes(sizeof(GenMeta), x->nel, x->nbat, nw, nd, 1, nper);
   int64_t W = (int64_t)(kWaveBudget / per_slot);
   if (W < 1) W = 1;
@@ -1107,8 +1134,11 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
   p.nbeta = x->nbeta;
   p.nel = x->nel;
   p.nbat = x->nbat;
-  p.tile2 = x->tile2;
-  p.nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
+  p.ntile = x->ntile;
+  p.nper = x->nbat + (x->ntile - 1) * x->nalpha * x->nbeta;
+  p.chunk = x->cfg.work_chunk > 0 ? x->cfg.work_chunk : 1;
+  p.timeout_ns = (unsigned long long)(x->cfg.timeout_s * 1e9);
+  p.t_start = acc + kAccT0;
   p.hmax_bits = x->d_hmax;
   p.cmax_bits = acc + kAccCmax;
   p.it_sum = x->it_sum.as<double>();
@@ -1203,8 +1233,11 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
   memcpy(&md, &hacc[kAccMinDen], sizeof(md));
   res->min_abs_denominator = md;
   *de0 = -hres.s2;
+  set_rpt2(*res, e0);
   if (((int)(hacc[kAccErr] & 0xffffffffull)) & kErrRange)
     return fail(QP_ENOTSUP, "coefficients times integrals beyond 2^93: outside the exact accumulator's range");
+  if (((int)(hacc[kAccErr] & 0xffffffffull)) & kErrTimeout)
+    return fail(QP_ETIMEOUT, "the device watchdog stopped the sweep (timeout_s)");
   if (hres.na > 0 && md < 1e-12) return fail(QP_ESINGULAR, "a denominator E0 - H_aa is below 1e-12");
   return QP_OK;
 }
@@ -1286,7 +1319,7 @@ static int plan_instance(BatchInst& b, size_t wave_budget) {
   const int64_t ent_per = bucket_entries_per_record(x->nel);
   b.ent_cap = (int64_t)nd * ent_per;
   const size_t dwords = (size_t)(x->nbat + 31) / 32;
-  const int nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
+  const int nper = x->nbat + (x->ntile - 1) * x->nalpha * x->nbeta;
   const size_t per_slot = wave_slot_bytes(sizeof(GenMeta), x->nel, x->nbat, nw, nd, 1, nper);
   b.W = (int64_t)(wave_budget / per_slot);
   if (b.W < 1) b.W = 1;
@@ -1361,8 +1394,11 @@ static int enqueue_instance(BatchInst& b, cudaStream_t st) {
   p.nbeta = x->nbeta;
   p.nel = x->nel;
   p.nbat = x->nbat;
-  p.tile2 = x->tile2;
-  p.nper = x->nbat + (x->tile2 ? x->nalpha * x->nbeta : 0);
+  p.ntile = x->ntile;
+  p.nper = x->nbat + (x->ntile - 1) * x->nalpha * x->nbeta;
+  p.chunk = x->cfg.work_chunk > 0 ? x->cfg.work_chunk : 1;
+  p.timeout_ns = (unsigned long long)(x->cfg.timeout_s * 1e9);
+  p.t_start = acc + kAccT0;
   p.hmax_bits = x->d_hmax;
   p.cmax_bits = acc + kAccCmax;
   p.it_sum = x->it_sum.as<double>();
@@ -1582,6 +1618,7 @@ extern "C" int qp_pt2_batch_run(qp_pt2_batch* B, qp_pt2_result* res, double* ms)
     else if (herr & kErrDup) code = QP_EDUP;
     else if (herr & kErrBucket) code = QP_ECUDA;
     else if (herr & kErrRange) code = QP_ENOTSUP;
+    else if (herr & kErrTimeout) code = QP_ETIMEOUT;
     else if (herr & 32) code = QP_ENOMEM;
     r.e_pt2 = hres.e_pt2;
     r.sum_e_over_d = hres.s2;
@@ -1594,6 +1631,7 @@ extern "C" int qp_pt2_batch_run(qp_pt2_batch* B, qp_pt2_result* res, double* ms)
     double md;
     memcpy(&md, &hacc[kAccMinDen], sizeof(md));
     r.min_abs_denominator = md;
+    set_rpt2(r, b.e0);
     if (code == QP_OK && hres.na > 0 && md < 1e-12) code = QP_ESINGULAR;
     if (res) res[i] = r;
     if (code != QP_OK && worst == QP_OK) {

@@ -135,6 +135,13 @@ __device__ __forceinline__ double recip_nr(double d) {
   return r;
 }
 
+// Nanoseconds of the device's global timer.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Bit pattern of |x|.  The mask is applied in inline PTX: written in C++ the
 // compiler recognises it as fabs and issues it on the FP64 pipe.
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
@@ -515,7 +522,7 @@ struct BatchShared {
   float inv_nv1;
   uint64_t kbase[2 * NINT];  // I with the batch's holes removed
   int g, slot;
-  long long item;
+  long long item, inext, iend;
   // storage of one phase of a work item at a time: the J lists of loops 2
   // and 3, the selection histogram, the per-thread sums of the reduction
   union {
@@ -1079,24 +1086,39 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
     S.tkcnt = p.tk_cnt[blockIdx.x];
     S.tau = p.tk_tau[blockIdx.x];
     S.slot = -1;
+    S.inext = S.iend = 0;
+    if (p.timeout_ns) atomicCAS(p.t_start, 0ull, global_ns());
   }
   const int F = MS ? 0 : fix_scale(p);  // fixed-point scale of A_alpha (units of 2^-F)
 
   for (;;) {
     __syncthreads();
-    if (tid == 0) S.item = atomicAdd(p.queue, 1);
+    if (tid == 0) {  // the next work item: p.chunk of them per draw from the queue
+      if (S.inext >= S.iend) {
+        const long long b0 = atomicAdd(p.queue, p.chunk);
+        S.inext = b0;
+        S.iend = b0 + p.chunk;
+      }
+      S.item = S.inext++;
+      if (p.timeout_ns && global_ns() - *((volatile unsigned long long*)p.t_start) > p.timeout_ns) {
+        atomicOr(p.err, 128);  // watchdog: stop taking work, report the timeout
+        S.item = nitems;
+      }
+    }
     __syncthreads();
     const long long item = S.item;
     if (item >= nitems) break;
     const int slot = (int)(item / nper), j = (int)(item - (long long)slot * nper);
-    // item j < nbat: batch j (the first tile of a split batch); j >= nbat:
-    // the second tile of the (j - nbat)-th opposite-spin batch
+    // item j < nbat: batch j (the first row tile of a split batch); j >= nbat:
+    // row tile 1 + (j - nbat) / (n_alpha n_beta) of opposite-spin batch
+    // (j - nbat) % (n_alpha n_beta)
     int b = j, tile = 0;
     if (j >= nbat) {
-      const int k = j - nbat, na = p.nalpha;
+      const int na = p.nalpha, nab = p.nalpha * p.nbeta;
+      const int k = (j - nbat) % nab;
+      tile = 1 + (j - nbat) / nab;
       const int ia = k % na, ib = na + k / na;
       b = nel + ib * (ib - 1) / 2 + ia;
-      tile = 1;
     }
     const GenMeta* M = p.meta + slot;
     if (M->g < 0) continue;
@@ -1181,10 +1203,11 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
     }
     B.clo = 0;
     B.nct = B.ncell;
-    if (p.tile2 && B.kind == 2) {  // rows [0, h) or [h, nv0)
-      const int h = (S.nv[0] + 1) / 2;
-      B.clo = tile ? h * S.nv[1] : 0;
-      B.nct = (tile ? S.nv[0] - h : h) * S.nv[1];
+    if (p.ntile > 1 && B.kind == 2) {  // rows [tile h, min((tile + 1) h, nv0))
+      const int h = (S.nv[0] + p.ntile - 1) / p.ntile;
+      const int r0 = tile * h, r1 = min(r0 + h, S.nv[0]);
+      B.clo = r0 * S.nv[1];
+      B.nct = (r1 - r0) * S.nv[1];
     }
     if (B.nct <= 0) continue;
 

@@ -5,8 +5,9 @@ generators are independent under the canonical rule of Eqs. calpha and
 edetstoch, which is what the paper's distributed PT2 exploits, Sec.
 "Parallelism").  The partial results combine exactly:
 
-* E_PT2, sum A^2/D^2, |A| and the connection count add;
-* the digest words add modulo 2^64 and xor;
+* E_PT2, sum A^2/D^2, |A| and the connection count add, the digest words
+  add modulo 2^64 and xor, and Z and E_rPT2 follow from the merged sums: the
+  library's ``qp_pt2_merge_results`` does this arithmetic;
 * the selection is the k best of the union of the shards' selections, in the
   library's order (|e| descending, determinant key ascending);
 * a multi-state sweep's per-state E_PT2 and sum A^2/D^2 add state by state,
@@ -19,22 +20,12 @@ import numpy as np
 MASK64 = (1 << 64) - 1
 
 
-def merge_totals(parts):
-    """parts: list of result dicts (as returned by ``PT2.eval``)."""
-    out = {"e_pt2": 0.0, "sum_e_over_d": 0.0, "n_perturbers": 0, "n_connections": 0, "n_tiny": 0}
-    d0, d1 = 0, 0
-    mins = []
-    for p in parts:
-        out["e_pt2"] += p["e_pt2"]
-        out["sum_e_over_d"] += p["sum_e_over_d"]
-        out["n_perturbers"] += int(p["n_perturbers"])
-        out["n_connections"] += int(p["n_connections"])
-        out["n_tiny"] += int(p.get("n_tiny", 0))
-        d0 = (d0 + int(p["digest"][0])) & MASK64
-        d1 ^= int(p["digest"][1])
-        mins.append(p.get("min_abs_den", float("inf")))
-    out["digest"] = (d0, d1)
-    out["min_abs_den"] = min(mins) if mins else float("inf")
+def merge_totals(parts, e0=0.0):
+    """parts: list of result dicts (as returned by ``PT2.eval``), in shard
+    order; e0: the E0 of the sweep (for Z and E_rPT2)."""
+    from . import merge_results
+
+    out = merge_results(parts, e0)
     if parts and all("e_pt2_states" in p for p in parts):
         out["e_pt2_states"] = np.sum([np.asarray(p["e_pt2_states"], dtype=np.float64) for p in parts], axis=0)
         out["sum_e_over_d_states"] = np.sum([np.asarray(p["sum_e_over_d_states"], dtype=np.float64)
@@ -60,7 +51,7 @@ def merge_selections(e_lists, det_lists, k):
     return e[order], d[order]
 
 
-def distributed_merge(dist, res, sel_e, sel_dets, k, device):
+def distributed_merge(dist, res, sel_e, sel_dets, k, device, e0=0.0):
     """Exchange step of a sharded sweep: all-gather every rank's partial
     totals and selection, then merge them identically on every rank.
 
@@ -109,6 +100,6 @@ def distributed_merge(dist, res, sel_e, sel_dets, k, device):
     dist.all_gather(gd, pd)
     e_all = [g[: p["n_sel"]].cpu().numpy() for g, p in zip(ge, parts)]
     d_all = [d[: p["n_sel"]].cpu().numpy().view(np.uint64) for d, p in zip(gd, parts)]
-    totals = merge_totals(parts)
+    totals = merge_totals(parts, e0)
     e, d = merge_selections(e_all, d_all, k)
     return totals, e, d

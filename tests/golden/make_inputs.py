@@ -22,6 +22,13 @@ not available; shapes follow the paper's CAS-sized active spaces):
   cfg3r: the first 10 determinants of the 128-orbital workload
         (``synthetic.cfg3_instance``; 14+14 electrons, Cholesky rank 192),
         expected sweep with k = 20 (totals and per-generator arrays).
+  cfg3seed: the seed space of the CIPSI growth of the 128-orbital workload
+        (norb 128, 14+14 electrons, Cholesky rank 192, seed 2): HF plus the
+        12,499 single and double substitutions of HF with the lowest diagonal
+        energy, ties by key.  Only the determinants are stored; the three
+        doublings to 10^5 determinants (Davidson, then the top-|e_alpha|
+        selection, Sec. "The basic algorithm") are run from them by the
+        consumer.
 
 Files: ``<cfg>_psi0.npz`` (dets, coefs, e0 and metadata) and
 ``<cfg>_expected.npz`` (totals, per-generator arrays by rank, selection).
@@ -49,6 +56,9 @@ CONFIGS = {
     "cfg4": dict(norb=48, nalpha=8, nbeta=8, rank=72, seed=3, ndet=20000, k=40000, grow=True, gradient=True),
     # the head (10 determinants) of the 128-orbital workload's Psi0
     "cfg3r": dict(norb=128, nalpha=14, nbeta=14, rank=192, seed=2, ndet=10, k=20, grow=False, instance="cfg3"),
+    # the seed space (N_det / 8) of the 128-orbital workload's CIPSI growth
+    "cfg3seed": dict(norb=128, nalpha=14, nbeta=14, rank=192, seed=2, ndet=12500, final_ndet=100000,
+                     doublings=3, grow=False, instance="cfg3seed"),
 }
 
 
@@ -69,6 +79,16 @@ def make_cfg3r(name, cfg):
                         summary=json.dumps(summary), meta=json.dumps(cfg))
 
 
+def make_cfg3seed(name, cfg):
+    t0 = time.time()
+    h, eri = S.hamiltonian_fast(cfg["norb"], cfg["rank"], cfg["seed"])
+    ham = oracle.Hamiltonian(cfg["norb"], cfg["nalpha"], cfg["nbeta"], h, eri)
+    hf = S.hf_det(cfg["norb"], cfg["nalpha"], cfg["nbeta"])
+    dets = psi0.seed_space(ham, hf, cfg["ndet"])
+    log(f"{name}: seed space of {len(dets)} dets in {time.time() - t0:.1f}s")
+    np.savez_compressed(os.path.join(HERE, f"{name}.npz"), dets=dets, meta=json.dumps(cfg))
+
+
 def log(msg):
     print(msg, flush=True)
 
@@ -77,6 +97,8 @@ def make(name, mem_budget=12 << 30):
     cfg = CONFIGS[name]
     if cfg.get("instance") == "cfg3":
         return make_cfg3r(name, cfg)
+    if cfg.get("instance") == "cfg3seed":
+        return make_cfg3seed(name, cfg)
     t0 = time.time()
     h, eri = S.hamiltonian(cfg["norb"], cfg["rank"], cfg["seed"])
     ham = oracle.Hamiltonian(cfg["norb"], cfg["nalpha"], cfg["nbeta"], h, eri)

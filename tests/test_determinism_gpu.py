@@ -167,3 +167,64 @@ def test_one_state_shards_match_oracle(qp, oracle_mod, nshard):
     keys = [tuple(int(w) for w in row) for row in d]
     order = sorted(range(len(e)), key=lambda i: (-abs(e[i]), keys[i]))[:k]
     check_selection(d[order].reshape(len(order), 2, -1), e[order], ref["sel_dets"], ref["sel_e"])
+
+
+def test_work_chunk_and_row_tiles(qp, oracle_mod):
+    """Runtime launch parameters: items drawn 4 per queue draw, and the
+    opposite-spin batches split into 1, 2 or 3 tiles of rows; every setting
+    matches the oracle, and the draw size does not change a single bit."""
+    norb, na, nb = 20, 4, 4
+    h, eri = S.hamiltonian(norb, 22, 91)
+    ham = oracle_mod.Hamiltonian(norb, na, nb, h, eri)
+    dets = S.random_excited_dets(norb, na, nb, 140, 92)
+    c = S.random_coefs(len(dets), 93, decay=0.05)
+    c /= np.linalg.norm(c)
+    e0 = min(ham.diag(d) for d in dets) - 1.0
+    ref = ham.sweep(dets, c, e0, k=100)
+    for tile in (1, 2, 3):
+        outs = []
+        for chunk in (1, 4):
+            pt2 = qp.PT2(norb, na, nb, _dev(h), _dev(eri), work_chunk=chunk, tile=tile)
+            outs.append(pt2.eval(_dev(dets), _dev(c), e0, 100, per_generator=True))
+            pt2.close()
+        check_totals(outs[0], ref)
+        check_per_generator(outs[0], ref)
+        check_selection(outs[0]["sel_dets"], outs[0]["sel_e"], ref["sel_dets"], ref["sel_e"])
+        _same(outs[0], outs[1])
+
+
+def test_watchdog_timeout(qp):
+    """A watchdog limit far below the sweep's time: the call returns
+    QP_ETIMEOUT with partial totals, and the GPU and library stay usable (a
+    context without the limit then gives the whole sweep)."""
+    meta, h, eri, dets, c, e0 = _cfg2_head(2500)
+    full = qp.PT2(meta["norb"], meta["nalpha"], meta["nbeta"], _dev(h), _dev(eri))
+    ref = full.eval(_dev(dets), _dev(c), e0, 100)
+    short = qp.PT2(meta["norb"], meta["nalpha"], meta["nbeta"], _dev(h), _dev(eri), timeout_s=1e-6)
+    for _ in range(2):
+        got = short.eval(_dev(dets), _dev(c), e0, 100, check=False)
+        assert got["rc"] == qp.QP_ETIMEOUT
+        assert got["n_perturbers"] < ref["n_perturbers"]
+    assert b"watchdog" in qp.load().qp_pt2_last_error()
+    again = full.eval(_dev(dets), _dev(c), e0, 100)
+    assert again["rc"] == qp.QP_OK and again["e_pt2"] == ref["e_pt2"]
+    short.close()
+    full.close()
+
+
+def test_rpt2_fields(qp, oracle_mod):
+    """Z = 1/(1 + sum A^2/D^2) and E0 + Z E_PT2 come with every result."""
+    norb, na, nb = 12, 3, 3
+    h, eri = S.hamiltonian(norb, 14, 95)
+    ham = oracle_mod.Hamiltonian(norb, na, nb, h, eri)
+    dets = S.random_excited_dets(norb, na, nb, 40, 96)
+    c = S.random_coefs(len(dets), 97, decay=0.05)
+    c /= np.linalg.norm(c)
+    e0 = min(ham.diag(d) for d in dets) - 1.0
+    ref = ham.sweep(dets, c, e0, k=0)
+    pt2 = qp.PT2(norb, na, nb, h, eri)
+    got = pt2.eval(dets, c, e0, 0)
+    z = 1.0 / (1.0 + ref["sum_e_over_d"])
+    assert got["z"] == pytest.approx(z, rel=1e-12)
+    assert got["e_rpt2"] == pytest.approx(e0 + z * ref["e_pt2"], abs=1e-10)
+    pt2.close()

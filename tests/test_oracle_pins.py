@@ -430,7 +430,12 @@ def test_gradient_matches_central_differences(grad_case):
 # ---------------------------------------------------------------------------
 def test_rpt2_self_energy_derivative_and_z(small_case):
     """Sigma(E) = sum A^2/(E - H_aa): Sigma(E0) = E_PT2, dSigma/dE at E0 =
-    -sum A^2/D^2 (central difference), and Z = 1/(1 + sum A^2/D^2) in (0, 1]."""
+    -sum A^2/D^2 (central difference), and Z = 1/(1 + sum A^2/D^2) in (0, 1].
+    Z and E_rPT2 are the library's (qp_pt2_merge_results of the oracle's
+    totals, no GPU needed), checked against the definition."""
+    from paper_1902_08154_gb300 import build
+
+    build.build()
     import paper_1902_08154_gb300 as qp
 
     ham, h, eri, dets, c, e0 = small_case
@@ -439,7 +444,20 @@ def test_rpt2_self_energy_derivative_and_z(small_case):
     sp = ham.sweep(dets, c, e0 + d, k=0)["e_pt2"]
     sm = ham.sweep(dets, c, e0 - d, k=0)["e_pt2"]
     assert (sp - sm) / (2 * d) == pytest.approx(-base["sum_e_over_d"], rel=1e-7)
-    r = qp.rpt2(base, e0)
+    r = qp.merge_results([base], e0)
     assert 0.0 < r["z"] <= 1.0
+    assert r["z"] == pytest.approx(1.0 / (1.0 + base["sum_e_over_d"]), rel=1e-15)
     assert r["e_rpt2"] == pytest.approx(e0 + r["z"] * base["e_pt2"], abs=1e-14)
     assert abs(r["e_rpt2"] - e0) <= abs(base["e_pt2"])  # rPT2 damps the correction
+    # merging shards: sums and counts add, digests add modulo 2^64 and xor
+    half = [dict(base, e_pt2=base["e_pt2"] / 2, sum_e_over_d=base["sum_e_over_d"] / 2,
+                 n_perturbers=base["n_perturbers"] // 2, n_connections=base["n_connections"] // 2,
+                 digest=(base["digest"][0], 0)),
+            dict(base, e_pt2=base["e_pt2"] / 2, sum_e_over_d=base["sum_e_over_d"] / 2,
+                 n_perturbers=base["n_perturbers"] - base["n_perturbers"] // 2,
+                 n_connections=base["n_connections"] - base["n_connections"] // 2,
+                 digest=((1 << 64) - 1, base["digest"][1]))]
+    m = qp.merge_results(half, e0)
+    assert m["n_perturbers"] == base["n_perturbers"] and m["n_connections"] == base["n_connections"]
+    assert m["digest"] == ((base["digest"][0] - 1) % (1 << 64), base["digest"][1])
+    assert m["e_pt2"] == pytest.approx(base["e_pt2"], abs=1e-15) and m["z"] == pytest.approx(r["z"], rel=1e-15)

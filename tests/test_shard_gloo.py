@@ -61,15 +61,25 @@ def _worker(rank, world, port, k, out_path):
     res["digest"] = (d0, d1)
     le, ld = merge_selections(es, ds, k)  # this shard's own k best
     tot, e, d = distributed_merge(dist, res, torch.from_numpy(le),
-                                  torch.from_numpy(ld.view(np.int64).reshape(len(le), 2, -1)), k, "cpu")
+                                  torch.from_numpy(ld.view(np.int64).reshape(len(le), 2, -1)), k, "cpu", e0)
     if rank == 0:
         np.savez(out_path, e=e, d=d, e_pt2=tot["e_pt2"], n=tot["n_perturbers"], nc=tot["n_connections"],
-                 d0=np.uint64(tot["digest"][0]), d1=np.uint64(tot["digest"][1]))
+                 d0=np.uint64(tot["digest"][0]), d1=np.uint64(tot["digest"][1]), z=tot["z"],
+                 e_rpt2=tot["e_rpt2"], s2=tot["sum_e_over_d"])
     dist.barrier()
     dist.destroy_process_group()
 
 
-def test_two_rank_merge_matches_full_sweep(tmp_path, oracle_mod):
+@pytest.fixture(scope="module")
+def library():
+    """The exchange step's arithmetic is the library's (qp_pt2_merge_results,
+    no GPU needed): build it before the ranks start."""
+    from paper_1902_08154_gb300 import build
+
+    build.build()
+
+
+def test_two_rank_merge_matches_full_sweep(tmp_path, oracle_mod, library):
     import torch.multiprocessing as mp
 
     k = 25
@@ -82,6 +92,9 @@ def test_two_rank_merge_matches_full_sweep(tmp_path, oracle_mod):
     assert int(m["nc"]) == ref["n_connections"]
     assert (int(m["d0"]), int(m["d1"])) == tuple(ref["digest"])
     assert abs(float(m["e_pt2"]) - ref["e_pt2"]) < 1e-12
+    # Z and E_rPT2 of the merged sums (Sec. "Renormalized PT2")
+    assert float(m["z"]) == pytest.approx(1.0 / (1.0 + ref["sum_e_over_d"]), rel=1e-12)
+    assert float(m["e_rpt2"]) == pytest.approx(e0 + float(m["z"]) * ref["e_pt2"], abs=1e-12)
     assert np.array_equal(m["d"], ref["sel_dets"].reshape(k, -1))
     assert np.allclose(m["e"], ref["sel_e"], rtol=1e-12, atol=1e-15)
 
@@ -130,7 +143,7 @@ def _states_worker(rank, world, port, k, out_path):
     dist.destroy_process_group()
 
 
-def test_two_rank_merge_of_a_multi_state_sweep(tmp_path, oracle_mod):
+def test_two_rank_merge_of_a_multi_state_sweep(tmp_path, oracle_mod, library):
     import torch.multiprocessing as mp
 
     k = 30
