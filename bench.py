@@ -288,7 +288,12 @@ def wide_leg(qp, torch, device, flush):
     grow_ctx.close()
     dd, cd = torch.from_numpy(dets.view(np.int64)).to(device), torch.from_numpy(coefs).to(device)
     n = len(dets)
-    out = {"workload": f"norb {spec['norb']}, {spec['nalpha']}+{spec['nbeta']} electrons, Cholesky rank "
+    hctx = qp.PT2(spec["norb"], spec["nalpha"], spec["nbeta"], hd, ed)
+    h_strings = hctx.hamiltonian(dd, search=0)[4]
+    h_all = hctx.hamiltonian(dd, search=1)[4]
+    hctx.close()
+    out = {"h_build_ms_strings": h_strings, "h_build_ms_all_pairs": h_all,
+           "workload": f"norb {spec['norb']}, {spec['nalpha']}+{spec['nbeta']} electrons, Cholesky rank "
                        f"{spec['rank']}, seed {spec['seed']}, N_det {n} grown from 12,500 by 3 CIPSI doublings, "
                        "k = N_det",
            "inputs_seconds": t_in, "growth_seconds": t_grow,
@@ -566,9 +571,15 @@ def run_gb300(args):
     dav = None
     if world == 1 and not args.ndet and not args.no_davidson:
         e0d, _, di = pt2.davidson(d_dets, tol=1e-10)
+        # the pair search of the H build: through the spin strings (used by
+        # Davidson) against the test of every pair
+        hs = pt2.hamiltonian(d_dets, search=0)
+        ha = pt2.hamiltonian(d_dets, search=1)
         dav = {"ms": di["build_ms"] + di["solve_ms"], "build_ms": di["build_ms"], "solve_ms": di["solve_ms"],
                "iterations": di["iterations"], "nnz": di["nnz"], "e0": e0d,
-               "abs_err_vs_oracle_e0": abs(e0d - e0)}
+               "abs_err_vs_oracle_e0": abs(e0d - e0),
+               "h_build_ms_strings": hs[4], "h_build_ms_all_pairs": ha[4],
+               "same_matrix": bool(np.array_equal(hs[1], ha[1]) and np.array_equal(hs[2], ha[2]))}
 
     # several states of the same Psi0: one multi-state sweep against two
     # one-state sweeps

@@ -257,6 +257,23 @@ int qp_pt2_sigma(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, int nvec, 
 int qp_pt2_davidson(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, const double *guess, double tol,
                     int max_iter, double *coefs, double *e0, qp_pt2_davidson_info *info);
 
+/* The Hamiltonian over Psi0 as it is built for qp_pt2_sigma and
+ * qp_pt2_davidson: the off-diagonal elements of the pairs at excitation
+ * degree 1 or 2 in CSR form, columns ascending within each row, and the
+ * diagonal.  search 0: connected pairs found through the spin-up and
+ * spin-down strings (Appendix "Davidson diagonalization": Psi0 = sum C_IJ
+ * |I_up J_dn>, same-spin excitations along a row or a column of C,
+ * opposite-spin doubles by a spin-up single excitation then a spin-down one;
+ * the work per row is the length of its string lists, O(N_det^(3/2)) in all);
+ * search 1: every pair tested, O(N_det^2).  Both give the same matrix.
+ * *nnz (host) receives the number of stored off-diagonal elements; rowptr
+ * [ndet+1] (int64), cols [nnz], vals [nnz] and diag [ndet] are written when
+ * not NULL (host or device memory), so a first call with cols = vals = NULL
+ * gives the sizes.  *build_ms (may be NULL): device time of the build.
+ * Psi0 is validated as for qp_pt2_eval (QP_EINVAL, QP_EDUP). */
+int qp_pt2_hamiltonian(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, int search, int64_t *nnz,
+                       int64_t *rowptr, int32_t *cols, double *vals, double *diag, double *build_ms);
+
 /* Gradient of E_PT2 (adjoint of the sweep), with Psi0's coefficients and E0
  * held fixed.  Every matrix element is linear in h and the integrals (Eqs.
  * Hij), so with A_alpha = <Psi0|H|alpha> and D_alpha = E0 - <alpha|H|alpha>

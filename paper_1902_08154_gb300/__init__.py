@@ -30,6 +30,7 @@ EXPORTS = (
     "qp_pt2_sigma",
     "qp_pt2_set_target",
     "qp_pt2_davidson",
+    "qp_pt2_hamiltonian",
     "qp_pt2_last_launches",
     "qp_pt2_last_timings",
     "qp_pt2_destroy",
@@ -144,6 +145,9 @@ def load(path: str = SO):
     L.qp_pt2_sigma.argtypes = [vp, i64, vp, C.c_int, vp, vp]
     L.qp_pt2_davidson.restype = C.c_int
     L.qp_pt2_davidson.argtypes = [vp, i64, vp, vp, dbl, C.c_int, vp, vp, C.POINTER(DavidsonInfo)]
+    L.qp_pt2_hamiltonian.restype = C.c_int
+    L.qp_pt2_hamiltonian.argtypes = [vp, i64, vp, C.c_int, C.POINTER(C.c_int64), vp, vp, vp, vp,
+                                     C.POINTER(C.c_double)]
     L.qp_pt2_eval_gens.restype = C.c_int
     L.qp_pt2_eval_gens.argtypes = [vp, i64, vp, vp, dbl, i64, vp, i64, vp, vp, vp, vp, vp, C.POINTER(Result)]
     L.qp_pt2_eval_states.restype = C.c_int
@@ -378,6 +382,23 @@ class PT2:
             c = torch.zeros(len(dets), dtype=torch.float64, device=dets.device)
         _, e0, info = qp_pt2_davidson(self.ctx, len(dets), dets, c, guess, tol, max_iter)
         return e0, c, info
+
+    def hamiltonian(self, dets, search=0):
+        """H over Psi0: (rowptr, cols, vals, diag, build ms) as host arrays;
+        search 0 = through the spin strings, 1 = every pair."""
+        L = load()
+        nnz = C.c_int64()
+        ms = C.c_double()
+        _check(L.qp_pt2_hamiltonian(self.ctx, len(dets), _ptr(dets), int(search), C.byref(nnz), None, None, None,
+                                    None, None))
+        n = len(dets)
+        rowptr = np.zeros(n + 1, dtype=np.int64)
+        cols = np.zeros(max(nnz.value, 1), dtype=np.int32)
+        vals = np.zeros(max(nnz.value, 1))
+        diag = np.zeros(n)
+        _check(L.qp_pt2_hamiltonian(self.ctx, n, _ptr(dets), int(search), C.byref(nnz), _ptr(rowptr), _ptr(cols),
+                                    _ptr(vals), _ptr(diag), C.byref(ms)))
+        return rowptr, cols[: nnz.value], vals[: nnz.value], diag, ms.value
 
     def eval_states(self, dets, coefs, e0, k, check=True):
         """Several states of one internal space (``coefs`` [nstates, ndet],

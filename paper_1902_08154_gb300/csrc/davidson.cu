@@ -5,8 +5,10 @@
 //
 //   * H is built once per call as a CSR matrix of the pairs (I, J) at
 //     excitation degree 1 or 2 (Slater-Condon rules, Eqs. Hij), plus its
-//     diagonal.  Pairs are found by a tiled all-pairs test (each CTA keeps a
-//     tile of rows in shared memory and streams every determinant once),
+//     diagonal.  Pairs are found through the spin-up and spin-down strings
+//     of the determinants (the paper's DISCIUS-like search, see below), or,
+//     as a cross-check, by a tiled all-pairs test (each CTA keeps a tile of
+//     rows in shared memory and streams every determinant once); they are
 //     written in any order and then sorted by column within each row, so that
 //     the products below add in a fixed order.
 //   * sigma = H u by one warp per row.
@@ -17,6 +19,7 @@
 //     eigensolver (Golub & Van Loan, Sec. 8.5) diagonalises it.
 #include <cuda_runtime.h>
 
+#include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 #include <cub/device/device_segmented_radix_sort.cuh>
 #include <cmath>
@@ -174,6 +177,151 @@ __global__ void pairs_kernel(int64_t n, const uint64_t* dets, int norb, const do
   }
 }
 
+// ---------------------------------------------------------------------------
+// Connected pairs through the alpha and beta strings (Appendix "Davidson
+// diagonalization": Psi0 = sum C_IJ |I_up J_dn>, same-spin excitations found
+// along a row or a column of C, opposite-spin doubles by a spin-up single
+// excitation followed by a spin-down one).  The determinants are grouped by
+// their spin-up string and by their spin-down string; for row I:
+//   (a) J with the spin-down string of I: spin-up excitation of degree 1 or 2;
+//   (b) J with the spin-up string of I: spin-down excitation of degree 1 or 2;
+//   (c) J whose spin-up string is a single excitation of I's (the string
+//       neighbour lists) and whose spin-down string is a single excitation of
+//       I's: the opposite-spin doubles.
+// Every connected pair is met exactly once, and the work per row is the
+// length of its lists instead of N_det.
+// ---------------------------------------------------------------------------
+struct SpinStrings {
+  int nu = 0;             // distinct strings
+  int* sid = nullptr;     // [n] string index of each determinant
+  int* ptr = nullptr;     // [nu + 1] offsets into grp
+  int* grp = nullptr;     // [n] determinants ordered by string
+  uint64_t* ukey = nullptr;  // [nu][nint] the distinct strings
+  int* nb_ptr = nullptr;  // [nu + 1] single-excitation neighbours (spin-up strings only)
+  int* nb = nullptr;
+};
+
+__global__ void str_key_kernel(int64_t n, int nw, int off, const uint64_t* dets, const int* perm,
+                               unsigned long long* key, int* val) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int j = perm ? perm[i] : (int)i;
+  key[i] = dets[(size_t)j * nw + off];
+  val[i] = j;
+}
+
+template <int NINT>
+__global__ void str_flag_kernel(int64_t n, int spin, const uint64_t* dets, const int* grp, int* flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int f = (i == 0);
+  if (i > 0) {
+    const uint64_t* a = dets + (size_t)grp[i] * 2 * NINT + spin * NINT;
+    const uint64_t* b = dets + (size_t)grp[i - 1] * 2 * NINT + spin * NINT;
+#pragma unroll
+    for (int w = 0; w < NINT; w++) f |= (a[w] != b[w]);
+  }
+  flag[i] = f;
+}
+
+template <int NINT>
+__global__ void str_index_kernel(int64_t n, int spin, const uint64_t* dets, const int* grp, const int* flag,
+                                 const int* incl, int* sid, int* ptr, uint64_t* ukey) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int id = incl[i] - 1;
+  sid[grp[i]] = id;
+  if (flag[i]) {
+    ptr[id] = (int)i;
+#pragma unroll
+    for (int w = 0; w < NINT; w++) ukey[(size_t)id * NINT + w] = dets[(size_t)grp[i] * 2 * NINT + spin * NINT + w];
+  }
+}
+
+// Single-excitation neighbours among the distinct strings (count, then fill).
+template <int NINT, bool COUNT>
+__global__ void str_nb_kernel(int nu, const uint64_t* ukey, int* cnt, const int* nb_ptr, int* nb) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= nu) return;
+  uint64_t a[NINT];
+#pragma unroll
+  for (int w = 0; w < NINT; w++) a[w] = ukey[(size_t)u * NINT + w];
+  int c = 0;
+  for (int v = 0; v < nu; v++) {
+    int d = 0;
+#pragma unroll
+    for (int w = 0; w < NINT; w++) d += __popcll(a[w] ^ ukey[(size_t)v * NINT + w]);
+    if (d == 2) {
+      if (!COUNT) nb[nb_ptr[u] + c] = v;
+      c++;
+    }
+  }
+  if (COUNT) cnt[u] = c;
+}
+
+template <int NINT>
+__device__ __forceinline__ int spin_degree(const uint64_t* I, const uint64_t* J, int spin) {
+  int d = 0;
+#pragma unroll
+  for (int w = 0; w < NINT; w++) d += __popcll(I[spin * NINT + w] ^ J[spin * NINT + w]);
+  return d >> 1;
+}
+
+// One warp per row I: COUNT writes the number of connected J, otherwise the
+// (column, <I|H|J>) pairs go to the row's next free slots.
+template <int NINT, bool COUNT>
+__global__ void str_pairs_kernel(int64_t n, const uint64_t* dets, int norb, const double* h, const double* eri,
+                                 const int* aid, const int* aptr, const int* agrp, const int* anb_ptr,
+                                 const int* anb, const int* bid, const int* bptr, const int* bgrp, int* rowcnt,
+                                 const int64_t* rowptr, int* cursor, int* cols, double* vals, int* err) {
+  constexpr int NW = 2 * NINT;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  uint64_t I[NW];
+#pragma unroll
+  for (int w = 0; w < NW; w++) I[w] = dets[(size_t)row * NW + w];
+  int cnt = 0;
+  auto emit = [&](int j) {
+    if (COUNT) {
+      cnt++;
+    } else {
+      const int64_t pos = rowptr[row] + atomicAdd(&cursor[row], 1);
+      cols[pos] = j;
+      vals[pos] = hij_pair<NINT>(I, dets + (size_t)j * NW, norb, h, eri);
+    }
+  };
+  {  // (a) the same spin-down string: spin-up excitations
+    const int b = bid[row];
+    for (int k = bptr[b] + lane; k < bptr[b + 1]; k += 32) {
+      const int j = bgrp[k];
+      if (j == (int)row) continue;
+      const int d = spin_degree<NINT>(I, dets + (size_t)j * NW, 0);
+      if (d == 0) atomicOr(err, 1);  // a repeated determinant
+      else if (d <= 2) emit(j);
+    }
+  }
+  const int a = aid[row];
+  for (int k = aptr[a] + lane; k < aptr[a + 1]; k += 32) {  // (b) the same spin-up string
+    const int j = agrp[k];
+    if (j == (int)row) continue;
+    const int d = spin_degree<NINT>(I, dets + (size_t)j * NW, 1);
+    if (d >= 1 && d <= 2) emit(j);
+  }
+  for (int q = anb_ptr[a]; q < anb_ptr[a + 1]; q++) {  // (c) spin-up single, then spin-down single
+    const int a2 = anb[q];
+    for (int k = aptr[a2] + lane; k < aptr[a2 + 1]; k += 32) {
+      const int j = agrp[k];
+      if (spin_degree<NINT>(I, dets + (size_t)j * NW, 1) == 1) emit(j);
+    }
+  }
+  if (COUNT) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) rowcnt[row] = cnt;
+  }
+}
+
 // Y[k] = H X[k] for nvec vectors of length n: one warp per row.
 __global__ void spmv_kernel(int64_t n, int nvec, const int64_t* rowptr, const int* cols, const double* vals,
                             const double* diag, const double* X, double* Y) {
@@ -298,7 +446,74 @@ struct HMat {
   double *vals = nullptr, *diag = nullptr;
 };
 
-int build_h(const CtxView& c, int64_t n, const uint64_t* d_dets, DevMem& mem, HMat* H) {
+// The determinants grouped by their string of one spin (radix sort of the
+// string words, least significant word first), the distinct strings, and
+// for the spin-up strings their single-excitation neighbours.
+int build_strings(const CtxView& c, int64_t n, const uint64_t* d_dets, int spin, bool neighbours, DevMem& mem,
+                  SpinStrings* S) {
+  cudaStream_t st = c.st;
+  const int nint = c.nint, nw = 2 * nint;
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  unsigned long long* key = mem.alloc<unsigned long long>(n);
+  unsigned long long* key2 = mem.alloc<unsigned long long>(n);
+  int* val = mem.alloc<int>(n);
+  int* perm = mem.alloc<int>(n);
+  int* flag = mem.alloc<int>(n);
+  int* incl = mem.alloc<int>(n);
+  S->sid = mem.alloc<int>(n);
+  S->grp = perm;
+  if (!key || !key2 || !val || !perm || !flag || !incl || !S->sid)
+    return report(QP_ENOMEM, "device allocation for the spin strings failed");
+  size_t tmp = 0, tmp2 = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, tmp, key, key2, val, perm, (int)n, 0, 64, st);
+  cub::DeviceScan::InclusiveSum(nullptr, tmp2, flag, incl, (int)n, st);
+  void* d_tmp = mem.alloc<unsigned char>(tmp > tmp2 ? tmp : tmp2);
+  if (!d_tmp) return report(QP_ENOMEM, "device allocation for the spin strings failed");
+  for (int w = nint - 1; w >= 0; w--) {  // least significant word first; the sorts are stable
+    str_key_kernel<<<nb, 256, 0, st>>>(n, nw, spin * nint + w, d_dets, w == nint - 1 ? nullptr : perm, key, val);
+    DV_TRY(cub::DeviceRadixSort::SortPairs(d_tmp, tmp, key, key2, val, perm, (int)n, 0, 64, st));
+  }
+  if (nint == 1) str_flag_kernel<1><<<nb, 256, 0, st>>>(n, spin, d_dets, perm, flag);
+  else str_flag_kernel<2><<<nb, 256, 0, st>>>(n, spin, d_dets, perm, flag);
+  DV_TRY(cub::DeviceScan::InclusiveSum(d_tmp, tmp2, flag, incl, (int)n, st));
+  int nu = 0;
+  DV_TRY(cudaMemcpyAsync(&nu, incl + (n - 1), sizeof(int), cudaMemcpyDeviceToHost, st));
+  DV_TRY(cudaStreamSynchronize(st));
+  S->nu = nu;
+  S->ptr = mem.alloc<int>((size_t)nu + 1);
+  S->ukey = mem.alloc<uint64_t>((size_t)nu * nint);
+  if (!S->ptr || !S->ukey) return report(QP_ENOMEM, "device allocation for the spin strings failed");
+  if (nint == 1) str_index_kernel<1><<<nb, 256, 0, st>>>(n, spin, d_dets, perm, flag, incl, S->sid, S->ptr, S->ukey);
+  else str_index_kernel<2><<<nb, 256, 0, st>>>(n, spin, d_dets, perm, flag, incl, S->sid, S->ptr, S->ukey);
+  const int nn = (int)n;
+  DV_TRY(cudaMemcpyAsync(S->ptr + nu, &nn, sizeof(int), cudaMemcpyHostToDevice, st));
+  if (!neighbours) return QP_OK;
+  int* cnt = mem.alloc<int>((size_t)nu + 1);
+  S->nb_ptr = mem.alloc<int>((size_t)nu + 1);
+  if (!cnt || !S->nb_ptr) return report(QP_ENOMEM, "device allocation for the spin strings failed");
+  DV_TRY(cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)nu + 1), st));
+  const unsigned nbu = (unsigned)((nu + 127) / 128);
+  if (nint == 1) str_nb_kernel<1, true><<<nbu, 128, 0, st>>>(nu, S->ukey, cnt, nullptr, nullptr);
+  else str_nb_kernel<2, true><<<nbu, 128, 0, st>>>(nu, S->ukey, cnt, nullptr, nullptr);
+  size_t tmp3 = 0;
+  cub::DeviceScan::ExclusiveSum(nullptr, tmp3, cnt, S->nb_ptr, nu + 1, st);
+  void* d_tmp3 = mem.alloc<unsigned char>(tmp3);
+  if (!d_tmp3) return report(QP_ENOMEM, "device allocation for the spin strings failed");
+  DV_TRY(cub::DeviceScan::ExclusiveSum(d_tmp3, tmp3, cnt, S->nb_ptr, nu + 1, st));
+  int tot = 0;
+  DV_TRY(cudaMemcpyAsync(&tot, S->nb_ptr + nu, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DV_TRY(cudaStreamSynchronize(st));
+  S->nb = mem.alloc<int>((size_t)tot);
+  if (!S->nb) return report(QP_ENOMEM, "device allocation for the spin strings failed");
+  if (nint == 1) str_nb_kernel<1, false><<<nbu, 128, 0, st>>>(nu, S->ukey, nullptr, S->nb_ptr, S->nb);
+  else str_nb_kernel<2, false><<<nbu, 128, 0, st>>>(nu, S->ukey, nullptr, S->nb_ptr, S->nb);
+  DV_TRY(cudaGetLastError());
+  return QP_OK;
+}
+
+// search: kSearchStrings (default) or kSearchAllPairs (the tiled test of
+// every pair, O(N_det^2), kept as a cross-check)
+int build_h(const CtxView& c, int64_t n, const uint64_t* d_dets, DevMem& mem, HMat* H, int search = 0) {
   cudaStream_t st = c.st;
   H->n = n;
   int* rowcnt = mem.alloc<int>(n + 1);
@@ -313,15 +528,54 @@ int build_h(const CtxView& c, int64_t n, const uint64_t* d_dets, DevMem& mem, HM
   DV_TRY(cudaMemsetAsync(rowcnt, 0, sizeof(int) * (n + 1), st));
   DV_TRY(cudaMemsetAsync(cursor, 0, sizeof(int) * n, st));
   const unsigned tiles = (unsigned)((n + kRows - 1) / kRows), nb = (unsigned)((n + 255) / 256);
-  if (c.nint == 1) {
-    diag_kernel<1><<<nb, 256, 0, st>>>(n, d_dets, c.norb, c.h, c.Jm, c.Km, H->diag);
-    pairs_kernel<1, true><<<tiles, 256, 0, st>>>(n, d_dets, c.norb, c.h, c.eri, rowcnt, nullptr, nullptr, nullptr,
-                                                 nullptr, err);
-  } else {
-    diag_kernel<2><<<nb, 256, 0, st>>>(n, d_dets, c.norb, c.h, c.Jm, c.Km, H->diag);
-    pairs_kernel<2, true><<<tiles, 256, 0, st>>>(n, d_dets, c.norb, c.h, c.eri, rowcnt, nullptr, nullptr, nullptr,
-                                                 nullptr, err);
+  const unsigned nwarp = (unsigned)((n * 32 + 255) / 256);
+  SpinStrings SA, SB;
+  int rc;
+  if (search == 0) {
+    if ((rc = build_strings(c, n, d_dets, 0, true, mem, &SA)) || (rc = build_strings(c, n, d_dets, 1, false, mem, &SB)))
+      return rc;
   }
+  // one pass of the pair search: COUNT (row counts) or fill
+  auto pairs = [&](bool count, const int64_t* rowptr, int* cols, double* vals) {
+    if (search == 0) {
+      if (c.nint == 1) {
+        if (count)
+          str_pairs_kernel<1, true><<<nwarp, 256, 0, st>>>(n, d_dets, c.norb, c.h, c.eri, SA.sid, SA.ptr, SA.grp,
+                                                           SA.nb_ptr, SA.nb, SB.sid, SB.ptr, SB.grp, rowcnt, rowptr,
+                                                           cursor, cols, vals, err);
+        else
+          str_pairs_kernel<1, false><<<nwarp, 256, 0, st>>>(n, d_dets, c.norb, c.h, c.eri, SA.sid, SA.ptr, SA.grp,
+                                                            SA.nb_ptr, SA.nb, SB.sid, SB.ptr, SB.grp, rowcnt, rowptr,
+                                                            cursor, cols, vals, err);
+      } else {
+        if (count)
+          str_pairs_kernel<2, true><<<nwarp, 256, 0, st>>>(n, d_dets, c.norb, c.h, c.eri, SA.sid, SA.ptr, SA.grp,
+                                                           SA.nb_ptr, SA.nb, SB.sid, SB.ptr, SB.grp, rowcnt, rowptr,
+                                                           cursor, cols, vals, err);
+        else
+          str_pairs_kernel<2, false><<<nwarp, 256, 0, st>>>(n, d_dets, c.norb, c.h, c.eri, SA.sid, SA.ptr, SA.grp,
+                                                            SA.nb_ptr, SA.nb, SB.sid, SB.ptr, SB.grp, rowcnt, rowptr,
+                                                            cursor, cols, vals, err);
+      }
+    } else if (c.nint == 1) {
+      if (count)
+        pairs_kernel<1, true><<<tiles, 256, 0, st>>>(n, d_dets, c.norb, c.h, c.eri, rowcnt, nullptr, nullptr, nullptr,
+                                                     nullptr, err);
+      else
+        pairs_kernel<1, false><<<tiles, 256, 0, st>>>(n, d_dets, c.norb, c.h, c.eri, nullptr, rowptr, cursor, cols,
+                                                      vals, err);
+    } else {
+      if (count)
+        pairs_kernel<2, true><<<tiles, 256, 0, st>>>(n, d_dets, c.norb, c.h, c.eri, rowcnt, nullptr, nullptr, nullptr,
+                                                     nullptr, err);
+      else
+        pairs_kernel<2, false><<<tiles, 256, 0, st>>>(n, d_dets, c.norb, c.h, c.eri, nullptr, rowptr, cursor, cols,
+                                                      vals, err);
+    }
+  };
+  if (c.nint == 1) diag_kernel<1><<<nb, 256, 0, st>>>(n, d_dets, c.norb, c.h, c.Jm, c.Km, H->diag);
+  else diag_kernel<2><<<nb, 256, 0, st>>>(n, d_dets, c.norb, c.h, c.Jm, c.Km, H->diag);
+  pairs(true, nullptr, nullptr, nullptr);
   DV_TRY(cudaGetLastError());
   // row counts (int) -> 64-bit exclusive offsets
   std::vector<int> hc((size_t)n);
@@ -339,12 +593,7 @@ int build_h(const CtxView& c, int64_t n, const uint64_t* d_dets, DevMem& mem, HM
   int* cols2 = mem.alloc<int>(H->nnz);
   double* vals2 = mem.alloc<double>(H->nnz);
   if (!H->cols || !H->vals || !cols2 || !vals2) return report(QP_ENOMEM, "device allocation for the Hamiltonian failed");
-  if (c.nint == 1)
-    pairs_kernel<1, false><<<tiles, 256, 0, st>>>(n, d_dets, c.norb, c.h, c.eri, nullptr, H->rowptr, cursor, cols2,
-                                                  vals2, err);
-  else
-    pairs_kernel<2, false><<<tiles, 256, 0, st>>>(n, d_dets, c.norb, c.h, c.eri, nullptr, H->rowptr, cursor, cols2,
-                                                  vals2, err);
+  pairs(false, H->rowptr, cols2, vals2);
   DV_TRY(cudaGetLastError());
   if (H->nnz > 0) {  // columns ascending within each row: a fixed order of the sums
     if (H->nnz >= (1ll << 31) || n >= (1ll << 31)) return report(QP_ENOTSUP, "Hamiltonian above 2^31 entries");
@@ -431,6 +680,41 @@ extern "C" int qp_pt2_sigma(qp_pt2_ctx* ctx, int64_t ndet, const uint64_t* dets,
                                                                      d_u, d_s);
   DV_TRY(cudaGetLastError());
   DV_TRY(cudaMemcpyAsync(S, d_s, sizeof(double) * ndet * nvec, cudaMemcpyDefault, c.st));
+  DV_TRY(cudaStreamSynchronize(c.st));
+  return QP_OK;
+}
+
+extern "C" int qp_pt2_hamiltonian(qp_pt2_ctx* ctx, int64_t ndet, const uint64_t* dets, int search, int64_t* nnz,
+                                  int64_t* rowptr, int32_t* cols, double* vals, double* diag, double* build_ms) {
+  CtxView c;
+  int rc = ctx_view(ctx, &c);
+  if (rc) return rc;
+  if ((rc = check_inputs(c, ndet, dets))) return rc;
+  if (!nnz) return report(QP_EINVAL, "nnz is NULL");
+  if (search != 0 && search != 1) return report(QP_EINVAL, "search must be 0 (spin strings) or 1 (all pairs)");
+  DevMem mem;
+  const uint64_t* d_dets;
+  if ((rc = to_device(dets, (size_t)ndet * 2 * c.nint, c.st, mem, &d_dets))) return rc;
+  if ((rc = validate(c, ndet, d_dets))) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, c.st);
+  HMat H;
+  rc = build_h(c, ndet, d_dets, mem, &H, search);
+  cudaEventRecord(e1, c.st);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  *nnz = H.nnz;
+  if (build_ms) *build_ms = ms;
+  if (rowptr) DV_TRY(cudaMemcpyAsync(rowptr, H.rowptr, sizeof(int64_t) * (ndet + 1), cudaMemcpyDefault, c.st));
+  if (cols && H.nnz) DV_TRY(cudaMemcpyAsync(cols, H.cols, sizeof(int) * H.nnz, cudaMemcpyDefault, c.st));
+  if (vals && H.nnz) DV_TRY(cudaMemcpyAsync(vals, H.vals, sizeof(double) * H.nnz, cudaMemcpyDefault, c.st));
+  if (diag) DV_TRY(cudaMemcpyAsync(diag, H.diag, sizeof(double) * ndet, cudaMemcpyDefault, c.st));
   DV_TRY(cudaStreamSynchronize(c.st));
   return QP_OK;
 }

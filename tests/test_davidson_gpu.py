@@ -141,3 +141,68 @@ def test_davidson_two_words_per_spin(qp, oracle_mod):
     pt2.close()
     assert e0 == pytest.approx(w[0], abs=1e-10)
     assert abs(abs(np.dot(c.cpu().numpy(), v[:, 0])) - 1.0) <= 1e-12
+
+
+def _csr_dense(n, rowptr, cols, vals, diag):
+    H = np.zeros((n, n))
+    for i in range(n):
+        H[i, cols[rowptr[i]:rowptr[i + 1]]] = vals[rowptr[i]:rowptr[i + 1]]
+    H[np.arange(n), np.arange(n)] = diag
+    return H
+
+
+@pytest.mark.parametrize("norb,na,nb,ndet,seed,rank", [(12, 3, 3, 150, 71, 14), (16, 4, 4, 300, 72, 18),
+                                                       (70, 3, 3, 120, 73, 6), (128, 2, 2, 80, 74, 3)])
+def test_string_search_matches_all_pairs_and_oracle(qp, oracle_mod, norb, na, nb, ndet, seed, rank):
+    """The pair search through the spin strings (Appendix "Davidson
+    diagonalization") gives the same CSR matrix, element for element, as the
+    test of every pair, and the same matrix as the oracle's."""
+    from oracle import psi0
+
+    h, eri = S.hamiltonian(norb, rank, seed)
+    ham = oracle_mod.Hamiltonian(norb, na, nb, h, eri)
+    dets = S.random_excited_dets(norb, na, nb, ndet, seed + 1)
+    pt2 = qp.PT2(norb, na, nb, _dev(h), _dev(eri))
+    a = pt2.hamiltonian(_dev(dets), search=0)
+    b = pt2.hamiltonian(dets, search=1)
+    pt2.close()
+    for x, y in zip(a[:4], b[:4]):
+        assert np.array_equal(x, y)
+    ref = psi0.hamiltonian_matrix(ham, dets).toarray()
+    got = _csr_dense(len(dets), *a[:4])
+    assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def test_string_search_full_ci_and_duplicates(qp, oracle_mod):
+    """Every determinant of a full CI space: each one meets all of its
+    singles and doubles; a repeated determinant is refused (QP_EDUP)."""
+    norb, na, nb = 7, 3, 2
+    h, eri = S.hamiltonian(norb, 9, 75)
+    fci = S.all_dets(norb, na, nb)
+    pt2 = qp.PT2(norb, na, nb, h, eri)
+    rowptr, cols, vals, diag, _ = pt2.hamiltonian(fci, search=0)
+    deg = lambda a, b: int(sum(bin(int(x) ^ int(y)).count("1") for x, y in zip(a.ravel(), b.ravel()))) // 2
+    for i in range(0, len(fci), 7):
+        expect = sorted(j for j in range(len(fci)) if j != i and deg(fci[i], fci[j]) <= 2)
+        assert list(cols[rowptr[i]:rowptr[i + 1]]) == expect
+    dup = np.concatenate([fci[:20], fci[5:6]])
+    with pytest.raises(qp.QPError) as ei:
+        pt2.hamiltonian(dup, search=0)
+    assert ei.value.code == qp.QP_EDUP
+    pt2.close()
+
+
+def test_string_search_on_the_cfg2_psi0(qp):
+    """The 10^4-determinant workload: the string search and the all-pairs
+    test build the same matrix, bit for bit."""
+    P = np.load(os.path.join(GOLDEN, "cfg2_psi0.npz"))
+    meta = json.loads(str(P["meta"]))
+    h, eri = S.hamiltonian(meta["norb"], meta["rank"], meta["seed"])
+    pt2 = qp.PT2(meta["norb"], meta["nalpha"], meta["nbeta"], _dev(h), _dev(eri))
+    d = _dev(P["dets"])
+    a = pt2.hamiltonian(d, search=0)
+    b = pt2.hamiltonian(d, search=1)
+    pt2.close()
+    for x, y in zip(a[:4], b[:4]):
+        assert np.array_equal(x, y)
+    print(f"cfg2 H build: strings {a[4]:.2f} ms, all pairs {b[4]:.2f} ms, nnz {len(a[1])}")
