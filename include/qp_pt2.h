@@ -196,14 +196,26 @@ int qp_pt2_set_target(qp_pt2_ctx *ctx, const uint64_t *ref, int max_exc, const u
  * (rank 0 = largest c_I^2, ties by input index); only those generators are
  * swept.  gen_eps / gen_na / gen_ncon (each may be NULL; host or device)
  * receive eps_I, |A_I| and the connection count of each listed generator, in
- * list order.  *res holds the totals over the listed generators and the
+ * list order, and gen_s2 (may be NULL) their sums A^2/D^2.  *res holds the
+ * totals over the listed generators and the
  * selection is the best min(k, ...) of their perturbers.  The list overrides
  * sharding.  QP_EINVAL for a rank out of range, a repeated rank or a device
  * pointer for ranks. */
 int qp_pt2_eval_gens(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, const double *coefs,
                      double e0, int64_t ngen, const int32_t *ranks, int64_t k, uint64_t *sel_dets,
-                     double *sel_e, double *gen_eps, int64_t *gen_na, int64_t *gen_ncon,
+                     double *sel_e, double *gen_eps, double *gen_s2, int64_t *gen_na, int64_t *gen_ncon,
                      qp_pt2_result *res);
+
+/* E_PT2 from per-generator values by rank, reduced exactly as a whole sweep
+ * reduces them (Eq. edetstoch: E_PT2 = sum over generators of eps_I, in rank
+ * order, with the library's fixed-order compensated sum): a sweep assembled
+ * from subset sweeps (a checkpointed or distributed one) gets the same bits
+ * as one qp_pt2_eval.  eps[n], s2[n] (sum A^2/D^2 of each generator), na[n],
+ * ncon[n]: host or device arrays indexed by rank.  Fills e_pt2,
+ * sum_e_over_d, n_perturbers, n_connections, z and e_rpt2 of *res (the
+ * other fields: 0, min_abs_denominator inf). */
+int qp_pt2_reduce_ranks(qp_pt2_ctx *ctx, int64_t n, const double *eps, const double *s2, const int64_t *na,
+                        const int64_t *ncon, double e0, qp_pt2_result *res);
 
 /* Several states at once (Sec. "Selected CI": one PT2 calculation per
  * state, and the selection criterion of Angeli et al.):

@@ -38,6 +38,7 @@ EXPORTS = (
     "qp_pt2_last_error",
     "qp_pt2_eval_noalloc",
     "qp_pt2_merge_results",
+    "qp_pt2_reduce_ranks",
     "qp_pt2_grad",
     "qp_pt2_batch_create",
     "qp_pt2_batch_run",
@@ -149,7 +150,9 @@ def load(path: str = SO):
     L.qp_pt2_hamiltonian.argtypes = [vp, i64, vp, C.c_int, C.POINTER(C.c_int64), vp, vp, vp, vp,
                                      C.POINTER(C.c_double)]
     L.qp_pt2_eval_gens.restype = C.c_int
-    L.qp_pt2_eval_gens.argtypes = [vp, i64, vp, vp, dbl, i64, vp, i64, vp, vp, vp, vp, vp, C.POINTER(Result)]
+    L.qp_pt2_eval_gens.argtypes = [vp, i64, vp, vp, dbl, i64, vp, i64, vp, vp, vp, vp, vp, vp, C.POINTER(Result)]
+    L.qp_pt2_reduce_ranks.restype = C.c_int
+    L.qp_pt2_reduce_ranks.argtypes = [vp, i64, vp, vp, vp, vp, dbl, C.POINTER(Result)]
     L.qp_pt2_eval_states.restype = C.c_int
     L.qp_pt2_eval_states.argtypes = [vp, i64, vp, C.c_int, vp, vp, i64, vp, vp, vp, C.POINTER(Result)]
     L.qp_pt2_last_launches.restype = i64
@@ -224,13 +227,13 @@ def qp_pt2_eval_ex(ctx, ndet, dets, coefs, e0, k, sel_dets=None, sel_e=None, sel
 
 
 def qp_pt2_eval_gens(ctx, ndet, dets, coefs, e0, ranks, k=0, sel_dets=None, sel_e=None, gen_eps=None, gen_na=None,
-                     gen_ncon=None, check=True):
+                     gen_ncon=None, check=True, gen_s2=None):
     """Sweep of the listed generator ranks only (``ranks``: host int32 array)."""
     ranks = np.ascontiguousarray(ranks, dtype=np.int32)
     res = Result()
     rc = load().qp_pt2_eval_gens(ctx, ndet, _ptr(dets), _ptr(coefs), float(e0), len(ranks), _ptr(ranks), k,
-                                 _ptr(sel_dets), _ptr(sel_e), _ptr(gen_eps), _ptr(gen_na), _ptr(gen_ncon),
-                                 C.byref(res))
+                                 _ptr(sel_dets), _ptr(sel_e), _ptr(gen_eps), _ptr(gen_s2), _ptr(gen_na),
+                                 _ptr(gen_ncon), C.byref(res))
     if check:
         _check(rc)
     return rc, res
@@ -437,6 +440,7 @@ class PT2:
         ranks = np.ascontiguousarray(ranks, dtype=np.int32)
         n = len(ranks)
         eps = np.zeros(max(n, 1))
+        s2 = np.zeros(max(n, 1))
         na = np.zeros(max(n, 1), dtype=np.int64)
         nc = np.zeros(max(n, 1), dtype=np.int64)
         if isinstance(dets, np.ndarray):
@@ -448,11 +452,21 @@ class PT2:
             sel = torch.zeros((max(k, 1), 2, self.nint), dtype=torch.int64, device=dets.device)
             se = torch.zeros(max(k, 1), dtype=torch.float64, device=dets.device)
         _, res = qp_pt2_eval_gens(self.ctx, len(dets), dets, coefs, e0, ranks, k, sel if k else None,
-                                  se if k else None, eps, na, nc)
+                                  se if k else None, eps, na, nc, gen_s2=s2)
         out = res.as_dict()
         m = res.n_selected
-        out.update(eps=eps[:n], na=na[:n], ncon=nc[:n], sel_dets=sel[:m], sel_e=se[:m])
+        out.update(eps=eps[:n], s2=s2[:n], na=na[:n], ncon=nc[:n], sel_dets=sel[:m], sel_e=se[:m])
         return out
+
+    def reduce_ranks(self, eps, s2, na, ncon, e0):
+        """E_PT2, sum A^2/D^2, counts, Z and E_rPT2 from per-rank arrays,
+        reduced exactly as a whole sweep reduces them (qp_pt2_reduce_ranks)."""
+        arrs = [np.ascontiguousarray(a, dtype=t) for a, t in
+                ((eps, np.float64), (s2, np.float64), (na, np.int64), (ncon, np.int64))]
+        res = Result()
+        _check(load().qp_pt2_reduce_ranks(self.ctx, len(arrs[0]), *[_ptr(a) for a in arrs], float(e0),
+                                          C.byref(res)))
+        return res.as_dict()
 
 
 def pt2_energy(h, eri, dets, coefs, e0, n_alpha, n_beta, stream=None):

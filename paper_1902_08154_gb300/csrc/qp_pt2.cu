@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/qp_pt2.h"
 #include "common.cuh"
 
@@ -337,6 +339,18 @@ int ctx_view(const qp_pt2_ctx* x, CtxView* v) {
 int report(int code, const char* msg) { return fail(code, msg); }
 }  // namespace qp
 
+// NVTX range over one phase of a call (validation, a wave of the sweep, the
+// selection merge), visible on the CPU timeline of a profiler; it costs
+// nothing when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  void next(const char* name) {  // close this phase, open the next one
+    nvtxRangePop();
+    nvtxRangePushA(name);
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 // Renormalised PT2 (Sec. "Renormalized PT2"): with sum_e_over_d = sum A^2/D^2
 // = -dSigma/dE at E0, Z = 1/(1 + sum_e_over_d) and E = E0 + Z E_PT2.
 static void set_rpt2(qp_pt2_result& r, double e0) {
@@ -595,13 +609,14 @@ static int out_target(Buf& b, T* user, size_t count, T** dst, bool* copy_back) {
 }
 
 // eps, |A_I| and connections of the listed generators (by rank).
-__global__ void gather_gen_kernel(int64_t n, const int32_t* ranks, const double* eps, const unsigned long long* na,
-                                  const unsigned long long* ncon, double* out_eps, int64_t* out_na,
-                                  int64_t* out_ncon) {
+__global__ void gather_gen_kernel(int64_t n, const int32_t* ranks, const double* eps, const double* s2,
+                                  const unsigned long long* na, const unsigned long long* ncon, double* out_eps,
+                                  double* out_s2, int64_t* out_na, int64_t* out_ncon) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int r = ranks[i];
   out_eps[i] = eps[r];
+  out_s2[i] = s2[r];
   out_na[i] = (int64_t)na[r];
   out_ncon[i] = (int64_t)ncon[r];
 }
@@ -617,7 +632,7 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
                      int64_t k, uint64_t* sel_dets, double* sel_e, double* sel_num, double* eps_by_rank,
                      int64_t* na_by_rank, int64_t* ncon_by_rank, int32_t* rank_of_out, qp_pt2_result* res,
                      const int32_t* gen_ranks, int64_t ngen_list, double* gen_eps, int64_t* gen_na,
-                     int64_t* gen_ncon, int nst = 0, const double* e0s = nullptr) {
+                     int64_t* gen_ncon, int nst = 0, const double* e0s = nullptr, double* gen_s2 = nullptr) {
   const bool ms = nst > 0;
   const int nsts = ms ? nst : 1;
   if (!x || !res) return fail(QP_EINVAL, "ctx or res is NULL");
@@ -649,8 +664,10 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   if ((rc = stage_in(x, x->in_dets, dets, (size_t)ndet * nw, &d_dets))) return rc;
   if ((rc = stage_in(x, x->in_coefs, coefs, (size_t)ndet * nsts, &d_coefs))) return rc;
 
+  NvtxRange nvtx_call("qp_pt2 sweep");
   // ---- validation and generator order ----
   const size_t nd = (size_t)ndet;
+  NvtxRange nvtx_phase("qp_pt2 validate and rank");
   if ((rc = x->hkey.grow(8 * nd)) || (rc = x->hkey2.grow(8 * nd)) || (rc = x->hidx.grow(4 * nd)) ||
       (rc = x->hidx2.grow(4 * nd)) || (rc = x->rkey.grow(8 * nd)) || (rc = x->rkey2.grow(8 * nd)) ||
       (rc = x->order.grow(4 * nd)) || (rc = x->rank_of.grow(4 * nd)) || (rc = x->acc.grow(8 * kAccWords)))
@@ -706,6 +723,7 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
     if (hcmax[s] == 0ull) return fail(QP_EINVAL, "a state has no nonzero coefficient");
 
   // ---- sweep: waves of generator slots, prep + batch kernels ----
+  nvtx_phase.next("qp_pt2 waves");
   size_t smem = x->smem;
   int grid = x->grid;
   if (ms) {  // nst accumulators per CTA: fewer CTAs per SM may fit
@@ -721,7 +739,7 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
                                  : (ndet > shard_index) ? (ndet - shard_index + shard_count - 1) / shard_count : 0;
   if (gen_ranks) {
     if ((rc = x->gen_list.grow(4 * (size_t)(ngen > 0 ? ngen : 1))) ||
-        (rc = x->gen_out.grow(24 * (size_t)(ngen > 0 ? ngen : 1))))
+        (rc = x->gen_out.grow(32 * (size_t)(ngen > 0 ? ngen : 1))))
       return rc;
     if (ngen > 0)
       CUDA_TRY(cudaMemcpyAsync(x->gen_list.p, gen_ranks, 4 * (size_t)ngen, cudaMemcpyHostToDevice, st));
@@ -856,6 +874,7 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   CUDA_TRY(cudaGetLastError());
 
   // ---- selection merge ----
+  nvtx_phase.next("qp_pt2 selection merge");
   int64_t nsel = 0;
   if (k > 0) {
     const size_t maxc = (size_t)grid * (size_t)k;
@@ -922,14 +941,15 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
     return rc;
   if (gen_ranks && ngen > 0) {
     double* ge = x->gen_out.as<double>();
-    int64_t* gn = reinterpret_cast<int64_t*>(ge + ngen);
+    double* gs = ge + ngen;
+    int64_t* gn = reinterpret_cast<int64_t*>(gs + ngen);
     int64_t* gc = gn + ngen;
-    gather_gen_kernel<<<(unsigned)((ngen + 255) / 256), 256, 0, st>>>(ngen, x->gen_list.as<int32_t>(), p.eps, p.na,
-                                                                       p.ncon, ge, gn, gc);
+    gather_gen_kernel<<<(unsigned)((ngen + 255) / 256), 256, 0, st>>>(ngen, x->gen_list.as<int32_t>(), p.eps, p.s2,
+                                                                       p.na, p.ncon, ge, gs, gn, gc);
     x->launches++;
     CUDA_TRY(cudaGetLastError());
     if ((rc = copy_out(gen_eps, ge, 8 * (size_t)ngen)) || (rc = copy_out(gen_na, gn, 8 * (size_t)ngen)) ||
-        (rc = copy_out(gen_ncon, gc, 8 * (size_t)ngen)))
+        (rc = copy_out(gen_ncon, gc, 8 * (size_t)ngen)) || (rc = copy_out(gen_s2, gs, 8 * (size_t)ngen)))
       return rc;
   }
 
@@ -963,6 +983,34 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   return QP_OK;
 }
 
+extern "C" int qp_pt2_reduce_ranks(qp_pt2_ctx* x, int64_t n, const double* eps, const double* s2, const int64_t* na,
+                                   const int64_t* ncon, double e0, qp_pt2_result* res) {
+  if (!x || !res || !eps || !s2 || !na || !ncon) return fail(QP_EINVAL, "a NULL argument");
+  if (n < 1 || n >= (1ll << 31)) return fail(QP_EINVAL, "n must lie in [1, 2^31)");
+  memset(res, 0, sizeof(*res));
+  res->min_abs_denominator = INFINITY;
+  cudaStream_t st = x->st;
+  int rc;
+  const double *d_eps, *d_s2;
+  const int64_t *d_na, *d_nc;
+  if ((rc = stage_in(x, x->eps, eps, (size_t)n, &d_eps)) || (rc = stage_in(x, x->s2, s2, (size_t)n, &d_s2)) ||
+      (rc = stage_in(x, x->na, na, (size_t)n, &d_na)) || (rc = stage_in(x, x->ncon, ncon, (size_t)n, &d_nc)) ||
+      (rc = x->res.grow(sizeof(DevResult))))
+    return rc;
+  finalize_kernel<<<1, 1024, 0, st>>>(n, d_eps, d_s2, reinterpret_cast<const long long*>(d_na),
+                                      reinterpret_cast<const long long*>(d_nc), x->res.as<DevResult>());
+  CUDA_TRY(cudaGetLastError());
+  DevResult h;
+  CUDA_TRY(cudaMemcpyAsync(&h, x->res.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  res->e_pt2 = h.e_pt2;
+  res->sum_e_over_d = h.s2;
+  res->n_perturbers = h.na;
+  res->n_connections = h.ncon;
+  set_rpt2(*res, e0);
+  return QP_OK;
+}
+
 extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const double* coefs,
                               double e0, int64_t k, uint64_t* sel_dets, double* sel_e, double* sel_num,
                               double* eps_by_rank, int64_t* na_by_rank, int64_t* ncon_by_rank,
@@ -973,7 +1021,7 @@ extern "C" int qp_pt2_eval_ex(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets,
 
 extern "C" int qp_pt2_eval_gens(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const double* coefs,
                                 double e0, int64_t ngen, const int32_t* ranks, int64_t k, uint64_t* sel_dets,
-                                double* sel_e, double* gen_eps, int64_t* gen_na, int64_t* gen_ncon,
+                                double* sel_e, double* gen_eps, double* gen_s2, int64_t* gen_na, int64_t* gen_ncon,
                                 qp_pt2_result* res) {
   if (!x || !res) return fail(QP_EINVAL, "ctx or res is NULL");
   if (ngen < 0 || (ngen > 0 && !ranks)) return fail(QP_EINVAL, "ngen is negative or ranks is NULL");
@@ -988,7 +1036,7 @@ extern "C" int qp_pt2_eval_gens(qp_pt2_ctx* x, int64_t ndet, const uint64_t* det
     }
   }
   return eval_core(x, ndet, dets, coefs, e0, k, sel_dets, sel_e, nullptr, nullptr, nullptr, nullptr, nullptr, res,
-                   ranks, ngen, gen_eps, gen_na, gen_ncon);
+                   ranks, ngen, gen_eps, gen_na, gen_ncon, 0, nullptr, gen_s2);
 }
 
 extern "C" int qp_pt2_eval_states(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, int nstates,
