@@ -99,6 +99,11 @@ extern "C" int qp_peak_measure(int kind, int iters, int reps, double* out) {
     cudaFree(sink);
     return -5;
   }
+  if (cudaMemset(cyc, 0, 8) != cudaSuccess) {
+    cudaFree(sink);
+    cudaFree(cyc);
+    return -6;
+  }
   double ms = 0.0;
   int rc;
   if (kind == 0) {
