@@ -320,12 +320,45 @@ int qp_pt2_grad(qp_pt2_ctx *ctx, int64_t ndet, const uint64_t *dets, const doubl
  *   ndet[n], dets[n], coefs[n], e0[n], k[n]: as in qp_pt2_eval, device memory
  *   sel_dets[n], sel_e[n]: device outputs (may be NULL where k[i] = 0)
  *   grid[n]      persistent CTAs of each instance's sweep (NULL or 0: the
- *                context's default); chosen by the package's autotuner */
+ *                context's default); chosen by the package's autotuner
+ * qp_pt2_batch_create is qp_pt2_batch_create_ex with fused = 0 and the
+ * given max_streams. */
 typedef struct qp_pt2_batch qp_pt2_batch;
 int qp_pt2_batch_create(qp_pt2_batch **out, int n, qp_pt2_ctx *const *ctxs, const int64_t *ndet,
                         const uint64_t *const *dets, const double *const *coefs, const double *e0,
                         const int64_t *k, uint64_t *const *sel_dets, double *const *sel_e, const int *grid,
                         int max_streams, void *stream);
+
+/* Launch shape of a batch (qp_pt2_batch_create_ex).
+ *   fused = 1: the instances are grouped by words per spin and precision; the
+ *     sweeps of a group run as one persistent launch per wave whose work
+ *     queue spans the (instance, generator, hole-set batch) items of all its
+ *     instances, instance after instance (the instance with the largest
+ *     work items first), and every CTA may take items of every instance.
+ *     The instances' waves are planned together so that all of a group's
+ *     instances finish in about the same number of waves.  The groups run
+ *     on concurrent streams; validation, ranking and the selection merge of
+ *     each instance run on up to max_streams concurrent streams.
+ *   fused = 0: each instance's sweep keeps launches of its own, on up to
+ *     max_streams concurrent streams (grid[] applies in this form only).
+ *   work_chunk    fused: items per draw from the shared queue (0: 1)
+ *   tile          fused: row tiles of the opposite-spin batches, applied to
+ *                 every instance (0: each context's own choice)
+ *   blocks_per_sm fused: persistent CTAs per SM (0: as many as fit)
+ *   wave_gb       fused: device memory for the records and buckets of one
+ *                 wave of all instances, in GiB (0: 24) */
+typedef struct {
+    int fused;
+    int max_streams;
+    int work_chunk;
+    int tile;
+    int blocks_per_sm;
+    double wave_gb;
+} qp_pt2_batch_options;
+int qp_pt2_batch_create_ex(qp_pt2_batch **out, int n, qp_pt2_ctx *const *ctxs, const int64_t *ndet,
+                           const uint64_t *const *dets, const double *const *coefs, const double *e0,
+                           const int64_t *k, uint64_t *const *sel_dets, double *const *sel_e, const int *grid,
+                           const qp_pt2_batch_options *opt, void *stream);
 int qp_pt2_batch_run(qp_pt2_batch *batch, qp_pt2_result *res, double *ms);
 void qp_pt2_batch_destroy(qp_pt2_batch *batch);
 

@@ -41,6 +41,7 @@ EXPORTS = (
     "qp_pt2_reduce_ranks",
     "qp_pt2_grad",
     "qp_pt2_batch_create",
+    "qp_pt2_batch_create_ex",
     "qp_pt2_batch_run",
     "qp_pt2_batch_destroy",
 )
@@ -503,14 +504,26 @@ def pt2_energy(h, eri, dets, coefs, e0, n_alpha, n_beta, stream=None):
     return _PT2Energy.apply(h, eri, e0)
 
 
+class BatchOptions(C.Structure):
+    _fields_ = [("fused", C.c_int), ("max_streams", C.c_int), ("work_chunk", C.c_int), ("tile", C.c_int),
+                ("blocks_per_sm", C.c_int), ("wave_gb", C.c_double)]
+
+
 class Batch:
     """Many independent sweeps captured into one CUDA graph (see
-    qp_pt2_batch_create in include/qp_pt2.h).
+    qp_pt2_batch_create_ex in include/qp_pt2.h).
 
     instances: list of dicts with keys pt2 (a PT2 context), dets, coefs (CUDA
-    tensors), e0 (float), k (int).  Output tensors are allocated here."""
+    tensors), e0 (float), k (int).  Output tensors are allocated here.
+    fused=True: one persistent launch per wave over all instances of a word
+    count and precision, with work_chunk items per draw of its queue, tile
+    row tiles applied to every instance (0: each context's own) and
+    blocks_per_sm CTAs per SM (0: as many as fit); fused=False: each
+    instance's own launches on up to max_streams streams, with grid[i]
+    persistent CTAs (None: the context's default)."""
 
-    def __init__(self, instances, grid=None, max_streams=0, stream=None):
+    def __init__(self, instances, grid=None, max_streams=0, stream=None, fused=True, work_chunk=0, tile=0,
+                 blocks_per_sm=0, wave_gb=0.0):
         import torch
 
         L = load()
@@ -532,18 +545,22 @@ class Batch:
         sel = VP(*[t.data_ptr() for t in self.sel])
         se = VP(*[t.data_ptr() for t in self.sel_e])
         g = (C.c_int * n)(*(grid or [0] * n))
-        self._keep = (ctxs, ndet, dets, coefs, e0, ks, sel, se, g)
-        L.qp_pt2_batch_create.restype = C.c_int
-        L.qp_pt2_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
-                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                          C.c_int, C.c_void_p]
+        opt = BatchOptions(int(bool(fused)), int(max_streams), int(work_chunk), int(tile), int(blocks_per_sm),
+                           float(wave_gb))
+        self.options = {"fused": bool(fused), "max_streams": max_streams, "work_chunk": work_chunk, "tile": tile,
+                        "blocks_per_sm": blocks_per_sm, "wave_gb": wave_gb}
+        self._keep = (ctxs, ndet, dets, coefs, e0, ks, sel, se, g, opt)
+        L.qp_pt2_batch_create_ex.restype = C.c_int
+        L.qp_pt2_batch_create_ex.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p, C.POINTER(BatchOptions), C.c_void_p]
         L.qp_pt2_batch_run.restype = C.c_int
         L.qp_pt2_batch_run.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]
         L.qp_pt2_batch_destroy.restype = None
         L.qp_pt2_batch_destroy.argtypes = [C.c_void_p]
         self.handle = C.c_void_p()
-        _check(L.qp_pt2_batch_create(C.byref(self.handle), n, ctxs, ndet, dets, coefs, e0, ks, sel, se, g,
-                                     max_streams, stream or None))
+        _check(L.qp_pt2_batch_create_ex(C.byref(self.handle), n, ctxs, ndet, dets, coefs, e0, ks, sel, se, g,
+                                        C.byref(opt), stream or None))
 
     def run(self):
         """Run the graph once: (list of result dicts, device ms)."""

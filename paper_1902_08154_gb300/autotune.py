@@ -1,11 +1,13 @@
 """Autotuner for batched sweeps.
 
-For a batch of instances it times a small set of launch shapes of the one
-CUDA graph -- the persistent CTAs given to each instance's sweep and the
-number of concurrent streams the instances are spread over -- and keeps the
-fastest.  Results are cached in a JSON file keyed by the batch's shape
-(orbitals, electrons, determinants, k, precision of every instance), so a
-batch of the same shape is tuned once per machine.
+For a batch of instances it times launch shapes of the fused batch (one
+persistent launch per wave whose queue spans all instances' work items) and
+keeps the fastest: the work items a CTA takes per draw from the shared queue
+(``work_chunk``), the row tiles of the opposite-spin batches (``tile``; 0
+keeps each context's own choice) and the persistent CTAs per SM.  Results are
+cached in a JSON file keyed by the batch's shape (orbitals, electrons,
+determinants, k, precision of every instance), so a batch of the same shape
+is tuned once per machine.
 """
 from __future__ import annotations
 
@@ -16,36 +18,37 @@ import os
 CACHE = os.environ.get("QP_PT2_TUNE_CACHE",
                        os.path.join(os.path.expanduser("~"), ".cache", "qp_pt2", "autotune.json"))
 
+CHUNKS = (1, 2, 4, 8)
+TILES = (0, 2)
+
 
 def signature(instances) -> str:
     rows = [(i["pt2"].norb, i["pt2"].n_alpha, i["pt2"].n_beta, len(i["dets"]), i["k"], i.get("precision", 0))
             for i in instances]
-    return hashlib.sha256(json.dumps(rows).encode()).hexdigest()[:20]
+    return hashlib.sha256(json.dumps(["fused"] + rows).encode()).hexdigest()[:20]
 
 
-def candidates(instances, nsm):
-    """Launch shapes tried: (name, per-instance CTA counts, streams)."""
-    work = []
-    for i in instances:
-        p = i["pt2"]
-        nel = p.n_alpha + p.n_beta
-        work.append(len(i["dets"]) * (nel + nel * (nel - 1) // 2))
-    tot = float(sum(work)) or 1.0
-    full = [3 * nsm] * len(instances)
-    prop = [max(nsm // 4, min(3 * nsm, int(round(3 * nsm * len(instances) * w / tot / 4)))) for w in work]
-    shapes = []
-    for streams in (8, 16):
-        shapes.append(("full", full, streams))
-        shapes.append(("one_per_sm", [nsm] * len(instances), streams))
-        shapes.append(("proportional", prop, streams))
-    return shapes
+def candidates(instances, nsm=None):
+    """Launch shapes tried first: dicts of Batch keyword arguments, every
+    (work_chunk, tile) pair with as many CTAs per SM as fit.  ``tune`` then
+    tries the best pair with two CTAs per SM."""
+    return [{"work_chunk": c, "tile": t, "blocks_per_sm": 0} for t in TILES for c in CHUNKS]
 
 
-def tune(instances, nsm, repeats=2, cache=CACHE, log=None):
-    """Return (grid list, streams, record); times every candidate shape
-    unless the cache holds this batch's shape."""
+def _time(instances, shape, repeats, max_streams):
     from . import Batch
 
+    b = Batch(instances, fused=True, max_streams=max_streams, **shape)
+    b.run()
+    t = min(b.run()[1] for _ in range(repeats))
+    b.close()
+    return t
+
+
+def tune(instances, nsm, repeats=2, cache=CACHE, log=None, max_streams=16):
+    """Return (shape, record): the fastest shape (Batch keyword arguments)
+    and the timings of every shape tried.  Times the candidates unless the
+    cache holds this batch's shape."""
     sig = signature(instances)
     table = {}
     if cache and os.path.exists(cache):
@@ -55,24 +58,29 @@ def tune(instances, nsm, repeats=2, cache=CACHE, log=None):
             table = {}
     if sig in table:
         rec = table[sig]
-        return rec["grid"], rec["streams"], rec
-    best = None
+        return rec["shape"], rec
     tried = []
-    for name, grid, streams in candidates(instances, nsm):
-        b = Batch(instances, grid=grid, max_streams=streams)
-        b.run()
-        t = min(b.run()[1] for _ in range(repeats))
-        b.close()
-        tried.append({"name": name, "streams": streams, "ms": t})
+    best = None
+    for shape in candidates(instances, nsm):
+        t = _time(instances, shape, repeats, max_streams)
+        tried.append(dict(shape, ms=t))
         if log:
-            log(f"autotune {name:13s} streams={streams:2d}: {t:.2f} ms")
+            log(f"autotune work_chunk={shape['work_chunk']} tile={shape['tile']}: {t:.2f} ms")
         if best is None or t < best[0]:
-            best = (t, name, grid, streams)
-    rec = {"grid": best[2], "streams": best[3], "policy": best[1], "ms": best[0], "tried": tried}
+            best = (t, shape)
+    # the best pair with two CTAs per SM (fewer CTAs share each SM's L1)
+    shape = dict(best[1], blocks_per_sm=2)
+    t = _time(instances, shape, repeats, max_streams)
+    tried.append(dict(shape, ms=t))
+    if log:
+        log(f"autotune work_chunk={shape['work_chunk']} tile={shape['tile']} blocks_per_sm=2: {t:.2f} ms")
+    if t < best[0]:
+        best = (t, shape)
+    rec = {"shape": best[1], "ms": best[0], "tried": tried}
     if cache:
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         table[sig] = rec
         tmp = cache + f".tmp{os.getpid()}"
         json.dump(table, open(tmp, "w"))
         os.replace(tmp, cache)
-    return rec["grid"], rec["streams"], rec
+    return rec["shape"], rec

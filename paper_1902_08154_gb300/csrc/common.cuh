@@ -208,4 +208,19 @@ struct SweepParams {
   double* g_wH;                  // [ndet]           weight of dH_II per generator rank
 };
 
+// One wave of several instances' sweeps in one launch: ps[i] holds instance
+// i's parameters for the wave; slot_ofs / item_ofs number the instances'
+// generator slots / work items one instance after the other.
+struct MultiWave {
+  const SweepParams* ps;       // [n]
+  const int* slot_ofs;         // [n + 1]
+  const long long* item_ofs;   // [n + 1]
+  int n;
+  int chunk;                   // work items per draw from the shared queue
+  unsigned long long* queue;   // the wave's item counter
+  unsigned long long timeout_ns;
+  unsigned long long* t_start;
+  int* err;                    // flag 128: the watchdog stopped the launch
+};
+
 }  // namespace qp

@@ -29,6 +29,11 @@ size_t states_smem(int max_cells, int nst);
 int batch_blocks_per_sm_states(int nint, size_t smem);
 cudaError_t launch_batch_states(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_reduce_items(const SweepParams& p, cudaStream_t st);
+cudaError_t launch_reduce_items_multi(const SweepParams* ps, int n, int max_slots, cudaStream_t st);
+cudaError_t launch_wave_multi(int nint, int mixed, const MultiWave& m, int total_slots, int grid, size_t smem,
+                              cudaStream_t st);
+cudaError_t launch_compact_multi(int nint, int mixed, const SweepParams* ps, int n, int grid, cudaStream_t st);
+int batch_multi_blocks_per_sm(int nint, int mixed, size_t smem);
 }  // namespace qp
 
 using namespace qp;
@@ -371,6 +376,16 @@ static bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Cells of the largest work item when the opposite-spin batches are split
+// into t tiles of rows.
+static int cells_for_tile(int norb, int n_alpha, int n_beta, int t) {
+  const int va = norb - n_alpha, vb = norb - n_beta;
+  int m = (n_alpha > 0 && n_beta > 0) ? ((va + t - 1) / t) * vb : 0;
+  const int others[4] = {va, vb, va * (va - 1) / 2, vb * (vb - 1) / 2};
+  for (int o : others) m = o > m ? o : m;
+  return m < 1 ? 1 : m;
+}
+
 extern "C" int qp_pt2_create(qp_pt2_ctx** out, int norb, int n_alpha, int n_beta, const double* h,
                              const double* eri, const qp_pt2_config* cfg) {
   if (!out) return fail(QP_EINVAL, "out is NULL");
@@ -454,13 +469,8 @@ extern "C" int qp_pt2_create(qp_pt2_ctx** out, int norb, int n_alpha, int n_beta
   if (!(c.timeout_s >= 0.0)) return bail(QP_EINVAL, "timeout_s must be >= 0");
   // cells of the largest work item when the opposite-spin batches are split
   // into t tiles of rows
-  const int va = norb - n_alpha, vb = norb - n_beta;
-  auto cells_tiled = [&](int t) {
-    int m = (n_alpha > 0 && n_beta > 0) ? ((va + t - 1) / t) * vb : 0;
-    const int others[4] = {va, vb, va * (va - 1) / 2, vb * (vb - 1) / 2};
-    for (int o : others) m = o > m ? o : m;
-    return m < 1 ? 1 : m;
-  };
+  const int va = norb - n_alpha;
+  auto cells_tiled = [&](int t) { return cells_for_tile(norb, n_alpha, n_beta, t); };
   x->ntile = 1;
   if (c.tile > 0) {
     x->ntile = (n_alpha > 0 && n_beta > 0) ? std::min(c.tile, std::max(va, 1)) : 1;
@@ -1337,13 +1347,37 @@ struct BatchInst {
   uint64_t* sel;
   double* se;
   int grid;
+  int ntile, nper, max_cells;  // launch shape of this instance's work items
+  size_t smem;
   int64_t W, nwaves, ngen, ent_cap, cap;
   size_t maxc, tmp1, tmp2;
   double work;
+  int group;        // fused form: the instance's group
+  SweepParams p;    // the sweep's parameters (the wave fields are set per wave)
+};
+
+// Fused form: the instances of one word count and precision, swept by one
+// persistent launch per wave.
+struct FusedGroup {
+  int nint = 1, mixed = 0;
+  std::vector<int> members;  // instance indices, largest work items first
+  int grid = 0, nwaves = 0, chunk = 1;
+  size_t smem = 0;
+  unsigned long long timeout_ns = 0;
+  std::vector<int> nact, slots, max_slots;  // per wave
+  SweepParams* d_ps = nullptr;    // [nwaves + 1][nm]: the wave's active instances; row nwaves: all members
+  int* d_slot_ofs = nullptr;      // [nwaves][nm + 1]
+  long long* d_item_ofs = nullptr;  // [nwaves][nm + 1]
+  unsigned long long* d_words = nullptr;  // [nwaves] item counters, then the watchdog's start time
+  int* d_err = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr;
 };
 
 struct qp_pt2_batch {
   std::vector<BatchInst> inst;
+  std::vector<FusedGroup> groups;
+  bool fused = false;
   cudaStream_t main = nullptr;
   bool own_main = false;
   std::vector<cudaStream_t> br;
@@ -1353,23 +1387,30 @@ struct qp_pt2_batch {
   cudaGraphExec_t exec = nullptr;
 };
 
-static int plan_instance(BatchInst& b, size_t wave_budget) {
+// Device bytes of one generator slot of instance b's waves.
+static size_t inst_slot_bytes(const BatchInst& b) {
+  const qp_pt2_ctx* x = b.x;
+  return wave_slot_bytes(sizeof(GenMeta), x->nel, x->nbat, 2 * x->nint, (size_t)b.ndet, 1, b.nper);
+}
+
+// Workspaces of instance b: W slots per wave (W_fixed > 0) or as many as
+// wave_budget bytes hold.
+static int plan_instance(BatchInst& b, size_t wave_budget, int64_t W_fixed) {
   qp_pt2_ctx* x = b.x;
   const int nint = x->nint, nw = 2 * nint;
   const size_t nd = (size_t)b.ndet;
   int rc;
   if (b.grid <= 0) b.grid = x->grid;
   const int grid = b.grid;
-  b.cap = b.k > 0 ? b.k + x->max_cells : 1;
+  b.cap = b.k > 0 ? b.k + b.max_cells : 1;
   // every CTA may hold up to k candidates when no CTA has filled its buffer
   b.maxc = (size_t)grid * (size_t)(b.k > 0 ? b.k : 1);
   b.ngen = b.ndet;
   const int64_t ent_per = bucket_entries_per_record(x->nel);
   b.ent_cap = (int64_t)nd * ent_per;
   const size_t dwords = (size_t)(x->nbat + 31) / 32;
-  const int nper = x->nbat + (x->ntile - 1) * x->nalpha * x->nbeta;
-  const size_t per_slot = wave_slot_bytes(sizeof(GenMeta), x->nel, x->nbat, nw, nd, 1, nper);
-  b.W = (int64_t)(wave_budget / per_slot);
+  const int nper = b.nper;
+  b.W = W_fixed > 0 ? W_fixed : (int64_t)(wave_budget / inst_slot_bytes(b));
   if (b.W < 1) b.W = 1;
   if (b.W > b.ngen) b.W = b.ngen;
   b.nwaves = (b.ngen + b.W - 1) / b.W;
@@ -1400,50 +1441,22 @@ static int plan_instance(BatchInst& b, size_t wave_budget) {
       (rc = x->cand_key.grow(8 * b.maxc * nw)) || (rc = x->skey.grow(8 * b.maxc)) ||
       (rc = x->skey2.grow(8 * b.maxc)) || (rc = x->perm.grow(4 * b.maxc)) || (rc = x->perm2.grow(4 * b.maxc)))
     return rc;
-  b.work = (double)b.ndet * (double)(x->nel + x->nel * (x->nel - 1) / 2) * (double)x->max_cells;
+  b.work = (double)b.ndet * (double)(x->nel + x->nel * (x->nel - 1) / 2) * (double)b.max_cells;
   return QP_OK;
 }
 
-// All of one instance's sweep on stream st, without host synchronisation.
-static int enqueue_instance(BatchInst& b, cudaStream_t st) {
+// The sweep's parameters of instance b (after plan_instance).
+static void make_params(BatchInst& b) {
   qp_pt2_ctx* x = b.x;
-  const int nint = x->nint, nw = 2 * nint;
-  const int64_t ndet = b.ndet;
-  const size_t nd = (size_t)ndet;
-  const int grid = b.grid;
   unsigned long long* acc = x->acc.as<unsigned long long>();
-  int* d_err = reinterpret_cast<int*>(acc + kAccErr);
-  int* d_ncand = reinterpret_cast<int*>(acc + kAccNcand);
-  init_acc_kernel<<<1, 32, 0, st>>>(acc);
-  CUDA_TRY(cudaMemsetAsync(x->sel_hist.p, 0, 4 * (size_t)kSelBins, st));
-  const int nb = (int)((ndet + 255) / 256);
-  validate_kernel<<<nb, 256, 0, st>>>(ndet, nint, x->norb, x->nalpha, x->nbeta, b.dets, b.coefs,
-                                      x->hkey.as<unsigned long long>(), x->hidx.as<int32_t>(),
-                                      x->rkey.as<unsigned long long>(), x->rank_of.as<int32_t>(), d_err,
-                                      acc + kAccCmax);
-  CUDA_TRY(cub::DeviceRadixSort::SortPairs(x->cub_tmp.p, b.tmp1, x->hkey.as<unsigned long long>(),
-                                           x->hkey2.as<unsigned long long>(), x->hidx.as<int32_t>(),
-                                           x->hidx2.as<int32_t>(), (int)ndet, 0, 64, st));
-  dup_kernel<<<nb, 256, 0, st>>>(ndet, nint, b.dets, x->hkey2.as<unsigned long long>(), x->hidx2.as<int32_t>(), d_err);
-  CUDA_TRY(cub::DeviceRadixSort::SortPairs(x->cub_tmp.p, b.tmp1, x->rkey.as<unsigned long long>(),
-                                           x->rkey2.as<unsigned long long>(), x->rank_of.as<int32_t>(),
-                                           x->order.as<int32_t>(), (int)ndet, 0, 64, st));
-  rank_kernel<<<nb, 256, 0, st>>>(ndet, x->order.as<int32_t>(), x->rank_of.as<int32_t>());
-  CUDA_TRY(cudaMemsetAsync(x->eps.p, 0, 8 * nd, st));
-  CUDA_TRY(cudaMemsetAsync(x->s2.p, 0, 8 * nd, st));
-  CUDA_TRY(cudaMemsetAsync(x->na.p, 0, 8 * nd, st));
-  CUDA_TRY(cudaMemsetAsync(x->ncon.p, 0, 8 * nd, st));
-  CUDA_TRY(cudaMemsetAsync(x->queues.p, 0, 4 * (size_t)(b.nwaves + 1), st));
-  CUDA_TRY(cudaMemsetAsync(x->tk_cnt.p, 0, 4 * (size_t)grid, st));
-  CUDA_TRY(cudaMemsetAsync(x->tk_tau.p, 0, 8 * (size_t)grid, st));
   SweepParams p{};
   p.norb = x->norb;
   p.nalpha = x->nalpha;
   p.nbeta = x->nbeta;
   p.nel = x->nel;
   p.nbat = x->nbat;
-  p.ntile = x->ntile;
-  p.nper = x->nbat + (x->ntile - 1) * x->nalpha * x->nbeta;
+  p.ntile = b.ntile;
+  p.nper = b.nper;
   p.chunk = x->cfg.work_chunk > 0 ? x->cfg.work_chunk : 1;
   p.timeout_ns = (unsigned long long)(x->cfg.timeout_s * 1e9);
   p.t_start = acc + kAccT0;
@@ -1461,7 +1474,7 @@ static int enqueue_instance(BatchInst& b, cudaStream_t st) {
     p.tgt_core[w] = x->tgt_core[w];
     p.tgt_del[w] = x->tgt_del[w];
   }
-  p.ndet = ndet;
+  p.ndet = b.ndet;
   p.dets = b.dets;
   p.coefs = b.coefs;
   p.order = x->order.as<int32_t>();
@@ -1501,19 +1514,74 @@ static int enqueue_instance(BatchInst& b, cudaStream_t st) {
   p.tk_tau = x->tk_tau.as<unsigned long long>();
   p.tau_bits = acc + kAccTau;
   p.sel_hist = x->sel_hist.as<unsigned int>();
-  p.max_cells = x->max_cells;
-  p.err = d_err;
+  p.max_cells = b.max_cells;
+  p.err = reinterpret_cast<int*>(acc + kAccErr);
+  b.p = p;
+}
+
+// Validation, ranking and the zeroing of the sums, on stream st.
+static int enqueue_pre(BatchInst& b, cudaStream_t st) {
+  qp_pt2_ctx* x = b.x;
+  const int nint = x->nint;
+  const int64_t ndet = b.ndet;
+  const size_t nd = (size_t)ndet;
+  unsigned long long* acc = x->acc.as<unsigned long long>();
+  int* d_err = reinterpret_cast<int*>(acc + kAccErr);
+  init_acc_kernel<<<1, 32, 0, st>>>(acc);
+  CUDA_TRY(cudaMemsetAsync(x->sel_hist.p, 0, 4 * (size_t)kSelBins, st));
+  const int nb = (int)((ndet + 255) / 256);
+  validate_kernel<<<nb, 256, 0, st>>>(ndet, nint, x->norb, x->nalpha, x->nbeta, b.dets, b.coefs,
+                                      x->hkey.as<unsigned long long>(), x->hidx.as<int32_t>(),
+                                      x->rkey.as<unsigned long long>(), x->rank_of.as<int32_t>(), d_err,
+                                      acc + kAccCmax);
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(x->cub_tmp.p, b.tmp1, x->hkey.as<unsigned long long>(),
+                                           x->hkey2.as<unsigned long long>(), x->hidx.as<int32_t>(),
+                                           x->hidx2.as<int32_t>(), (int)ndet, 0, 64, st));
+  dup_kernel<<<nb, 256, 0, st>>>(ndet, nint, b.dets, x->hkey2.as<unsigned long long>(), x->hidx2.as<int32_t>(), d_err);
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(x->cub_tmp.p, b.tmp1, x->rkey.as<unsigned long long>(),
+                                           x->rkey2.as<unsigned long long>(), x->rank_of.as<int32_t>(),
+                                           x->order.as<int32_t>(), (int)ndet, 0, 64, st));
+  rank_kernel<<<nb, 256, 0, st>>>(ndet, x->order.as<int32_t>(), x->rank_of.as<int32_t>());
+  CUDA_TRY(cudaMemsetAsync(x->eps.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->s2.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->na.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->ncon.p, 0, 8 * nd, st));
+  CUDA_TRY(cudaMemsetAsync(x->queues.p, 0, 4 * (size_t)(b.nwaves + 1), st));
+  CUDA_TRY(cudaMemsetAsync(x->tk_cnt.p, 0, 4 * (size_t)b.grid, st));
+  CUDA_TRY(cudaMemsetAsync(x->tk_tau.p, 0, 8 * (size_t)b.grid, st));
+  // the per-item slots of the first wave (the multi-instance reduction
+  // clears them for the next one)
+  CUDA_TRY(cudaMemsetAsync(x->it_sum.p, 0, 16 * (size_t)b.nper * (size_t)b.W, st));
+  return QP_OK;
+}
+
+// The waves of instance b's own sweep, on stream st.
+static int enqueue_waves(BatchInst& b, cudaStream_t st) {
+  qp_pt2_ctx* x = b.x;
+  SweepParams p = b.p;
   for (int64_t w = 0; w < b.nwaves; w++) {
     p.wave_start = (int)(w * b.W);
     p.wave_slots = (int)((b.ngen - w * b.W) < b.W ? (b.ngen - w * b.W) : b.W);
     p.last_wave = (w == b.nwaves - 1);
     p.queue = x->queues.as<int>() + w;
     CUDA_TRY(cudaMemsetAsync(p.it_sum, 0, sizeof(double) * (size_t)p.wave_slots * p.nper * p.it_stride, st));
-    CUDA_TRY(launch_prep(nint, p, p.wave_slots, st));
-    CUDA_TRY(launch_batch(nint, p, grid, x->smem, st));
+    CUDA_TRY(launch_prep(x->nint, p, p.wave_slots, st));
+    CUDA_TRY(launch_batch(x->nint, p, b.grid, b.smem, st));
     CUDA_TRY(launch_reduce_items(p, st));
   }
-  finalize_kernel<<<1, 1024, 0, st>>>(ndet, p.eps, p.s2, reinterpret_cast<const long long*>(p.na),
+  return QP_OK;
+}
+
+// The totals and the merge of the CTAs' selection buffers, on stream st.
+static int enqueue_post(BatchInst& b, cudaStream_t st) {
+  qp_pt2_ctx* x = b.x;
+  const int nint = x->nint, nw = 2 * nint;
+  const int grid = b.grid;
+  const SweepParams& p = b.p;
+  unsigned long long* acc = x->acc.as<unsigned long long>();
+  int* d_err = reinterpret_cast<int*>(acc + kAccErr);
+  int* d_ncand = reinterpret_cast<int*>(acc + kAccNcand);
+  finalize_kernel<<<1, 1024, 0, st>>>(b.ndet, p.eps, p.s2, reinterpret_cast<const long long*>(p.na),
                                       reinterpret_cast<const long long*>(p.ncon), x->res.as<DevResult>());
   if (b.k > 0) {
     gather_kernel<<<grid, 256, 0, st>>>(grid, nint, b.cap, p.tk_cnt, p.tk_e, p.tk_a, p.tk_key, p.tau_bits,
@@ -1543,12 +1611,152 @@ static int enqueue_instance(BatchInst& b, cudaStream_t st) {
   return QP_OK;
 }
 
+// Fused form: group the instances by word count and precision, size their
+// waves together (the same number of waves for all, wave_budget bytes of
+// records and buckets per wave over all instances), and write each group's
+// per-wave tables of parameters and slot / item offsets to the device.
+static int plan_fused(qp_pt2_batch* B, const qp_pt2_batch_options& o, size_t wave_budget) {
+  const int n = (int)B->inst.size();
+  for (int i = 0; i < n; i++) {
+    BatchInst& b = B->inst[i];
+    const int mixed = b.x->cfg.precision == QP_MIXED;
+    int g = -1;
+    for (size_t j = 0; j < B->groups.size(); j++)
+      if (B->groups[j].nint == b.x->nint && B->groups[j].mixed == mixed) g = (int)j;
+    if (g < 0) {
+      B->groups.emplace_back();
+      g = (int)B->groups.size() - 1;
+      B->groups[g].nint = b.x->nint;
+      B->groups[g].mixed = mixed;
+    }
+    b.group = g;
+    B->groups[g].members.push_back(i);
+  }
+  double total = 0.0;
+  for (auto& b : B->inst) total += (double)inst_slot_bytes(b) * (double)b.ngen;
+  int64_t R = (int64_t)std::ceil(total / (double)wave_budget);
+  if (R < 1) R = 1;
+  for (auto& G : B->groups) {
+    qp_pt2_ctx* x0 = B->inst[G.members[0]].x;
+    G.smem = 0;
+    for (int i : G.members) G.smem = std::max(G.smem, B->inst[i].smem);
+    int bps = batch_multi_blocks_per_sm(G.nint, G.mixed, G.smem);
+    if (bps < 1) return fail(QP_ENOTSUP, "the batch accumulator does not fit in shared memory");
+    if (o.blocks_per_sm > 0 && o.blocks_per_sm < bps) bps = o.blocks_per_sm;
+    G.grid = bps * x0->nsm;
+    G.chunk = o.work_chunk > 0 ? o.work_chunk : 1;
+    // the instance with the largest work items first: the queue's tail is made
+    // of the smallest items
+    std::stable_sort(G.members.begin(), G.members.end(), [&](int a, int c) {
+      const BatchInst &ba = B->inst[a], &bc = B->inst[c];
+      return ba.max_cells != bc.max_cells ? ba.max_cells > bc.max_cells : ba.ndet > bc.ndet;
+    });
+    G.nwaves = 0;
+    G.timeout_ns = 0;
+    for (int i : G.members) {
+      BatchInst& b = B->inst[i];
+      b.grid = G.grid;
+      const int64_t W = (b.ndet + R - 1) / R;
+      int rc = plan_instance(b, 0, W);
+      if (rc) return rc;
+      make_params(b);
+      G.nwaves = std::max(G.nwaves, (int)b.nwaves);
+      const unsigned long long t = b.p.timeout_ns;
+      if (t && (G.timeout_ns == 0 || t < G.timeout_ns)) G.timeout_ns = t;
+    }
+    const int nm = (int)G.members.size();
+    std::vector<SweepParams> hp((size_t)(G.nwaves + 1) * nm);
+    std::vector<int> hs((size_t)G.nwaves * (nm + 1), 0);
+    std::vector<long long> hi((size_t)G.nwaves * (nm + 1), 0);
+    G.nact.assign(G.nwaves, 0);
+    G.slots.assign(G.nwaves, 0);
+    G.max_slots.assign(G.nwaves, 0);
+    for (int r = 0; r < G.nwaves; r++) {
+      int a = 0;
+      int* so = hs.data() + (size_t)r * (nm + 1);
+      long long* io = hi.data() + (size_t)r * (nm + 1);
+      for (int i : G.members) {
+        const BatchInst& b = B->inst[i];
+        if (r >= b.nwaves) continue;
+        SweepParams p = b.p;
+        p.wave_start = (int)(r * b.W);
+        p.wave_slots = (int)std::min<int64_t>(b.W, b.ngen - r * b.W);
+        p.last_wave = 0;  // compact_multi_kernel keeps the k best after the last wave
+        p.queue = nullptr;
+        hp[(size_t)r * nm + a] = p;
+        so[a + 1] = so[a] + p.wave_slots;
+        io[a + 1] = io[a] + (long long)p.wave_slots * p.nper;
+        G.max_slots[r] = std::max(G.max_slots[r], p.wave_slots);
+        a++;
+      }
+      G.nact[r] = a;
+      G.slots[r] = so[a];
+    }
+    for (int m = 0; m < nm; m++) hp[(size_t)G.nwaves * nm + m] = B->inst[G.members[m]].p;
+    if (cudaMalloc(&G.d_ps, sizeof(SweepParams) * hp.size()) != cudaSuccess ||
+        cudaMalloc(&G.d_slot_ofs, sizeof(int) * hs.size()) != cudaSuccess ||
+        cudaMalloc(&G.d_item_ofs, sizeof(long long) * hi.size()) != cudaSuccess ||
+        cudaMalloc(&G.d_words, sizeof(unsigned long long) * (G.nwaves + 1)) != cudaSuccess ||
+        cudaMalloc(&G.d_err, sizeof(int)) != cudaSuccess)
+      return fail(QP_ENOMEM, "device allocation of the batch tables failed");
+    if (cudaMemcpy(G.d_ps, hp.data(), sizeof(SweepParams) * hp.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(G.d_slot_ofs, hs.data(), sizeof(int) * hs.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(G.d_item_ofs, hi.data(), sizeof(long long) * hi.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(G.d_err, 0, sizeof(int)) != cudaSuccess)
+      return fail(QP_ECUDA, "copy of the batch tables failed");
+    if (cudaStreamCreateWithFlags(&G.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming) != cudaSuccess)
+      return fail(QP_ECUDA, "stream creation failed");
+  }
+  return QP_OK;
+}
+
+// One group's waves on its stream: per wave the prep and batch launches over
+// all active instances and the per-generator reduction; then the compaction
+// of the candidate buffers.
+static int enqueue_group(FusedGroup& G) {
+  const int nm = (int)G.members.size();
+  CUDA_TRY(cudaMemsetAsync(G.d_words, 0, sizeof(unsigned long long) * (G.nwaves + 1), G.st));
+  CUDA_TRY(cudaMemsetAsync(G.d_err, 0, sizeof(int), G.st));
+  for (int r = 0; r < G.nwaves; r++) {
+    MultiWave m{};
+    m.ps = G.d_ps + (size_t)r * nm;
+    m.slot_ofs = G.d_slot_ofs + (size_t)r * (nm + 1);
+    m.item_ofs = G.d_item_ofs + (size_t)r * (nm + 1);
+    m.n = G.nact[r];
+    m.chunk = G.chunk;
+    m.queue = G.d_words + r;
+    m.timeout_ns = G.timeout_ns;
+    m.t_start = G.d_words + G.nwaves;
+    m.err = G.d_err;
+    CUDA_TRY(launch_wave_multi(G.nint, G.mixed, m, G.slots[r], G.grid, G.smem, G.st));
+    CUDA_TRY(launch_reduce_items_multi(m.ps, G.nact[r], G.max_slots[r], G.st));
+  }
+  CUDA_TRY(launch_compact_multi(G.nint, G.mixed, G.d_ps + (size_t)G.nwaves * nm, nm, G.grid, G.st));
+  return QP_OK;
+}
+
 extern "C" int qp_pt2_batch_create(qp_pt2_batch** out, int n, qp_pt2_ctx* const* ctxs, const int64_t* ndet,
                                    const uint64_t* const* dets, const double* const* coefs, const double* e0,
                                    const int64_t* k, uint64_t* const* sel_dets, double* const* sel_e,
                                    const int* grid, int max_streams, void* stream) {
+  qp_pt2_batch_options o{};
+  o.fused = 0;
+  o.max_streams = max_streams;
+  return qp_pt2_batch_create_ex(out, n, ctxs, ndet, dets, coefs, e0, k, sel_dets, sel_e, grid, &o, stream);
+}
+
+extern "C" int qp_pt2_batch_create_ex(qp_pt2_batch** out, int n, qp_pt2_ctx* const* ctxs, const int64_t* ndet,
+                                      const uint64_t* const* dets, const double* const* coefs, const double* e0,
+                                      const int64_t* k, uint64_t* const* sel_dets, double* const* sel_e,
+                                      const int* grid, const qp_pt2_batch_options* opt, void* stream) {
   if (!out || n < 1 || !ctxs || !ndet || !dets || !coefs || !e0 || !k) return fail(QP_EINVAL, "bad batch arguments");
   *out = nullptr;
+  qp_pt2_batch_options o{};
+  o.fused = 1;
+  if (opt) o = *opt;
+  if (o.work_chunk < 0 || o.tile < 0 || o.blocks_per_sm < 0 || !(o.wave_gb >= 0.0))
+    return fail(QP_EINVAL, "bad batch options");
   qp_pt2_batch* B = new (std::nothrow) qp_pt2_batch();
   if (!B) return fail(QP_ENOMEM, "host allocation failed");
   auto bail = [&](int code, const std::string& m) {
@@ -1556,6 +1764,7 @@ extern "C" int qp_pt2_batch_create(qp_pt2_batch** out, int n, qp_pt2_ctx* const*
     return fail(code, m);
   };
   B->main = (cudaStream_t)stream;
+  B->fused = o.fused != 0;
   for (int i = 0; i < n; i++) {
     BatchInst b{};
     b.x = ctxs[i];
@@ -1566,7 +1775,7 @@ extern "C" int qp_pt2_batch_create(qp_pt2_batch** out, int n, qp_pt2_ctx* const*
     b.e0 = e0[i];
     b.sel = sel_dets ? sel_dets[i] : nullptr;
     b.se = sel_e ? sel_e[i] : nullptr;
-    b.grid = grid ? grid[i] : 0;
+    b.grid = (grid && !B->fused) ? grid[i] : 0;
     if (!b.x || b.ndet < 1 || b.k < 0 || b.ndet >= (1ll << 31) || !std::isfinite(b.e0))
       return bail(QP_EINVAL, "bad instance " + std::to_string(i));
     if (b.x->cfg.shard_count > 1) return bail(QP_EINVAL, "sharded contexts cannot be batched");
@@ -1574,15 +1783,35 @@ extern "C" int qp_pt2_batch_create(qp_pt2_batch** out, int n, qp_pt2_ctx* const*
       return bail(QP_EINVAL, "batched inputs and outputs must be device memory (instance " + std::to_string(i) + ")");
     for (int j = 0; j < i; j++)
       if (B->inst[j].x == b.x) return bail(QP_EINVAL, "each instance needs its own context");
-    // all instances' workspaces stay allocated together: share the wave budget
-    size_t budget = (size_t)(16ull << 30) / (size_t)n;
-    if (budget > kWaveBudget) budget = kWaveBudget;
-    if (budget < ((size_t)64 << 20)) budget = (size_t)64 << 20;
-    int rc = plan_instance(b, budget);
-    if (rc) return bail(rc, "planning instance " + std::to_string(i) + ": " + g_last_error);
+    qp_pt2_ctx* x = b.x;
+    b.ntile = x->ntile;
+    b.max_cells = x->max_cells;
+    b.smem = x->smem;
+    if (B->fused && o.tile > 0) {
+      const int va = x->norb - x->nalpha;
+      b.ntile = (x->nalpha > 0 && x->nbeta > 0) ? std::min(o.tile, std::max(va, 1)) : 1;
+      b.max_cells = cells_for_tile(x->norb, x->nalpha, x->nbeta, b.ntile);
+      b.smem = sweep_smem(b.max_cells);
+    }
+    b.nper = x->nbat + (b.ntile - 1) * x->nalpha * x->nbeta;
+    b.ngen = b.ndet;
+    if (!B->fused) {
+      // all instances' workspaces stay allocated together: share the wave budget
+      size_t budget = (size_t)(16ull << 30) / (size_t)n;
+      if (budget > kWaveBudget) budget = kWaveBudget;
+      if (budget < ((size_t)64 << 20)) budget = (size_t)64 << 20;
+      int rc = plan_instance(b, budget, 0);
+      if (rc) return bail(rc, "planning instance " + std::to_string(i) + ": " + g_last_error);
+      make_params(b);
+    }
     B->inst.push_back(b);
   }
-  int ns = max_streams > 0 ? max_streams : 16;
+  if (B->fused) {
+    const double gb = o.wave_gb > 0.0 ? o.wave_gb : 24.0;
+    int rc = plan_fused(B, o, (size_t)(gb * (double)(1ull << 30)));
+    if (rc) return bail(rc, "planning the batch: " + g_last_error);
+  }
+  int ns = o.max_streams > 0 ? o.max_streams : 16;
   if (ns > n) ns = n;
   B->br.resize(ns);
   B->ev.resize(ns);
@@ -1618,9 +1847,29 @@ extern "C" int qp_pt2_batch_create(qp_pt2_batch** out, int n, qp_pt2_ctx* const*
   cudaEventRecord(B->fork, cap);
   for (int s = 0; s < ns; s++) cudaStreamWaitEvent(B->br[s], B->fork, 0);
   int erc = QP_OK;
-  for (int i : order) {
-    erc = enqueue_instance(B->inst[i], B->br[branch[i]]);
-    if (erc) break;
+  if (!B->fused) {
+    for (int i : order) {
+      BatchInst& b = B->inst[i];
+      cudaStream_t st = B->br[branch[i]];
+      if ((erc = enqueue_pre(b, st)) || (erc = enqueue_waves(b, st)) || (erc = enqueue_post(b, st))) break;
+    }
+  } else {
+    for (int i : order)
+      if ((erc = enqueue_pre(B->inst[i], B->br[branch[i]]))) break;
+    // every group's waves start when all instances are validated and ranked
+    for (int s = 0; s < ns && !erc; s++) cudaEventRecord(B->ev[s], B->br[s]);
+    for (auto& G : B->groups) {
+      if (erc) break;
+      for (int s = 0; s < ns; s++) cudaStreamWaitEvent(G.st, B->ev[s], 0);
+      erc = enqueue_group(G);
+      cudaEventRecord(G.done, G.st);
+    }
+    for (int s = 0; s < ns && !erc; s++)
+      for (auto& G : B->groups) cudaStreamWaitEvent(B->br[s], G.done, 0);
+    for (int i : order) {
+      if (erc) break;
+      erc = enqueue_post(B->inst[i], B->br[branch[i]]);
+    }
   }
   for (int s = 0; s < ns; s++) {
     cudaEventRecord(B->ev[s], B->br[s]);
@@ -1668,6 +1917,11 @@ extern "C" int qp_pt2_batch_run(qp_pt2_batch* B, qp_pt2_result* res, double* ms)
     else if (herr & kErrRange) code = QP_ENOTSUP;
     else if (herr & kErrTimeout) code = QP_ETIMEOUT;
     else if (herr & 32) code = QP_ENOMEM;
+    if (code == QP_OK && B->fused) {  // the group's launch stopped by its watchdog
+      int gerr = 0;
+      CUDA_TRY(cudaMemcpy(&gerr, B->groups[b.group].d_err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (gerr & kErrTimeout) code = QP_ETIMEOUT;
+    }
     r.e_pt2 = hres.e_pt2;
     r.sum_e_over_d = hres.s2;
     r.n_perturbers = hres.na;
@@ -1694,6 +1948,15 @@ extern "C" void qp_pt2_batch_destroy(qp_pt2_batch* B) {
   if (!B) return;
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
+  for (auto& G : B->groups) {
+    if (G.d_ps) cudaFree(G.d_ps);
+    if (G.d_slot_ofs) cudaFree(G.d_slot_ofs);
+    if (G.d_item_ofs) cudaFree(G.d_item_ofs);
+    if (G.d_words) cudaFree(G.d_words);
+    if (G.d_err) cudaFree(G.d_err);
+    if (G.st) cudaStreamDestroy(G.st);
+    if (G.done) cudaEventDestroy(G.done);
+  }
   for (auto s : B->br) if (s) cudaStreamDestroy(s);
   for (auto e : B->ev) if (e) cudaEventDestroy(e);
   if (B->fork) cudaEventDestroy(B->fork);

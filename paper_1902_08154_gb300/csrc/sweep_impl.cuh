@@ -315,14 +315,14 @@ __device__ __forceinline__ void for_buckets(uint64_t hm, int nel, int nbat, Fn&&
 // prep kernel: one CTA per generator slot of the wave
 // ---------------------------------------------------------------------------
 template <int NINT>
-__global__ void __launch_bounds__(kThreads) prep_kernel(const __grid_constant__ SweepParams p) {
+__device__ __forceinline__ void prep_slot(const SweepParams& p, const int slot) {
   constexpr int NW = 2 * NINT;
   __shared__ int s_cnt[kMaxBatch + 2];
   __shared__ uint32_t s_dead[(kMaxBatch + 31) / 32];
   __shared__ int s_wsum[kWarps];
   __shared__ uint64_t sI[NW];
   __shared__ int s_occ[kMaxElec];
-  const int slot = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const int norb = p.norb, nel = p.nel, nbat = p.nbat;
   GenMeta* M = p.meta + slot;
   const long long t = (long long)p.wave_start + slot;
@@ -499,6 +499,51 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(const __grid_constant__ 
   __syncthreads();
   uint32_t* dead = p.b_dead + (size_t)slot * dw;
   for (int w = tid; w < dw; w += kThreads) dead[w] = s_dead[w];
+}
+
+// One CTA per generator slot of the wave.
+template <int NINT>
+__global__ void __launch_bounds__(kThreads) prep_kernel(const __grid_constant__ SweepParams p) {
+  prep_slot<NINT>(p, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Several instances in one launch (a wave of each of their sweeps).  ps[i] is
+// instance i's parameters for this wave; slot_ofs / item_ofs number the
+// instances' generator slots / work items one instance after the other.
+// ---------------------------------------------------------------------------
+static_assert(sizeof(SweepParams) % 8 == 0, "parameters are copied by 8-byte words");
+
+// Copy the parameters of instance i to shared memory (all threads).
+__device__ __forceinline__ void load_params(SweepParams& dst, const SweepParams* ps, int i) {
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(ps + i);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(&dst);
+  for (int w = threadIdx.x; w < (int)(sizeof(SweepParams) / 8); w += blockDim.x) d[w] = src[w];
+}
+
+// The last instance whose first slot (item) is at or below x.
+template <typename T>
+__device__ __forceinline__ int instance_of(const T* ofs, int n, long long x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((long long)ofs[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One CTA per generator slot of every instance of the wave.
+template <int NINT>
+__global__ void __launch_bounds__(kThreads) prep_multi_kernel(const __grid_constant__ MultiWave m) {
+  __shared__ SweepParams Ps;
+  __shared__ int s_inst;
+  if (threadIdx.x == 0) s_inst = instance_of(m.slot_ofs, m.n, blockIdx.x);
+  __syncthreads();
+  const int i = s_inst;
+  load_params(Ps, m.ps, i);
+  __syncthreads();
+  prep_slot<NINT>(Ps, (int)blockIdx.x - m.slot_ofs[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1039,6 +1084,946 @@ __device__ __noinline__ void compact_selection(const SweepParams& p, BatchShared
   __syncthreads();
 }
 
+// The CTA's dynamic shared memory for the sweep of p and the sweep's sizes,
+// formed by the kernel once (once per instance in the multi-instance kernel)
+// and kept across work items.  Multi-state form: one FP64 accumulator per
+// state (stride mc), then the ban bits, the CTA group's coefficients per
+// state, c_I per state and the weights w_s; one-state form: the exact 96-bit
+// accumulators (low words, then high words), then the ban bits.
+struct ItemEnv {
+  double* A;
+  unsigned long long* Alo;
+  int* Ahi;
+  uint32_t* ban;
+  double *ms_gc, *ms_cI, *ms_w;
+  int mc, nst, norb, nel, nbat, nper;
+};
+
+template <bool MS>
+__device__ __forceinline__ ItemEnv item_env(const SweepParams& p) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  ItemEnv E;
+  E.mc = p.max_cells;
+  E.A = reinterpret_cast<double*>(dyn);
+  E.Alo = reinterpret_cast<unsigned long long*>(dyn);
+  E.Ahi = reinterpret_cast<int*>(E.Alo + E.mc);
+  E.ban = MS ? reinterpret_cast<uint32_t*>(E.A + p.nst * E.mc) : reinterpret_cast<uint32_t*>(E.Ahi + ((E.mc + 1) & ~1));
+  E.ms_gc = reinterpret_cast<double*>(E.ban + (((E.mc + 31) / 32 + 1) & ~1));
+  E.ms_cI = E.ms_gc + kGroup * kMaxStates;
+  E.ms_w = E.ms_cI + kMaxStates;
+  E.nst = MS ? p.nst : 1;
+  E.norb = p.norb;
+  E.nel = p.nel;
+  E.nbat = p.nbat;
+  E.nper = p.nper;
+  return E;
+}
+
+// One work item of the sweep of p (a generator slot's hole-set batch, or a
+// row tile of one): bans, the accumulation of A_alpha, the cells pass and the
+// item's sums.  Used by the kernel of one sweep and by the kernel whose queue
+// spans the waves of several instances.
+template <int NINT, typename NT, bool GRAD, bool MS>
+__device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NINT, NT>& S, const long long item,
+                                           const int F, double* te, double* ta, uint64_t* tk, const ItemEnv& E,
+                                           const NT* eri_n, const NT* h_n) {
+  constexpr int NW = 2 * NINT;
+  double* A = E.A;
+  unsigned long long* Alo = E.Alo;
+  int* Ahi = E.Ahi;
+  uint32_t* ban = E.ban;
+  double* ms_gc = E.ms_gc;
+  double* ms_cI = E.ms_cI;
+  double* ms_w = E.ms_w;
+  const int mc = E.mc, nst = E.nst;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int norb = E.norb, nel = E.nel, nbat = E.nbat;
+  const int nper = E.nper;
+
+  const int slot = (int)(item / nper), j = (int)(item - (long long)slot * nper);
+  // item j < nbat: batch j (the first row tile of a split batch); j >= nbat:
+  // row tile 1 + (j - nbat) / (n_alpha n_beta) of opposite-spin batch
+  // (j - nbat) % (n_alpha n_beta)
+  int b = j, tile = 0;
+  if (j >= nbat) {
+    const int na = p.nalpha, nab = p.nalpha * p.nbeta;
+    const int k = (j - nbat) % nab;
+    tile = 1 + (j - nbat) / nab;
+    const int ia = k % na, ib = na + k / na;
+    b = nel + ib * (ib - 1) / 2 + ia;
+  }
+  const GenMeta* M = p.meta + slot;
+  if (M->g < 0) return;
+  if ((p.b_dead[(size_t)slot * ((nbat + 31) / 32) + (b >> 5)] >> (b & 31)) & 1u) return;
+  if (slot != S.slot) {  // load the generator
+    __syncthreads();
+    if (tid < NW) S.I[tid] = M->I[tid];
+    if (tid < nel) S.occ[tid] = M->occ[tid];
+    for (int x = tid; x < 2 * norb; x += kThreads) S.F[x / norb][x % norb] = M->F[x / norb][x % norb];
+    __syncthreads();
+    for (int x = tid; x < 2 * norb; x += kThreads) {
+      const int s = x / norb, q = x - s * norb;
+      const uint64_t* sw = S.I + s * NINT;
+      const bool occ = (sw[q >> 6] >> (q & 63)) & 1ull;
+      int below = 0;  // occupied orbitals of spin s below q
+#pragma unroll
+      for (int w = 0; w < NINT; w++) {
+        const int lim = q - 64 * w;
+        if (lim >= 64) below += __popcll(sw[w]);
+        else if (lim > 0) below += __popcll(sw[w] & ((1ull << lim) - 1));
+      }
+      const int v = q - below;
+      S.vidx[s][q] = occ ? -1 : v;
+      if (!occ) S.vir[s][v] = q;
+    }
+    if (tid < 2) {
+      int n = 0;
+#pragma unroll
+      for (int w = 0; w < NINT; w++) n += __popcll(S.I[tid * NINT + w]);
+      S.nv[tid] = norb - n;
+    }
+    if (tid == 0) {
+      S.hii = M->hii;
+      S.cI = (NT)M->cI;
+      S.g = M->g;
+      S.slot = slot;
+    }
+    if constexpr (MS) {
+      if (tid < nst) {
+        ms_cI[tid] = p.coefs[(size_t)tid * p.ndet + p.order[M->g]];
+        const double m = __longlong_as_double((long long)p.st_cmax[tid]);
+        ms_w[tid] = 1.0 / (m * m);
+      }
+    }
+    __syncthreads();
+  }
+  const int g = S.g;
+
+  // ---- batch geometry ----
+  Batch B;
+  if (b < nel) {
+    B.h = 1;
+    B.ia = b;
+    B.ib = -1;
+  } else {
+    const int t = b - nel;
+    int y = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
+    while (y * (y - 1) / 2 > t) y--;
+    while ((y + 1) * y / 2 <= t) y++;
+    B.h = 2;
+    B.ib = y;
+    B.ia = t - y * (y - 1) / 2;
+  }
+  B.ca = S.occ[B.ia];
+  B.sa = B.ca >= norb;
+  B.qa = B.ca - B.sa * norb;
+  B.hm = 1ull << B.ia;
+  if (B.h == 2) {
+    B.cb = S.occ[B.ib];
+    B.sb = B.cb >= norb;
+    B.qb = B.cb - B.sb * norb;
+    B.hm |= 1ull << B.ib;
+    B.kind = (B.sa == B.sb) ? 1 : 2;
+    const int nv = S.nv[B.sa];
+    B.ncell = (B.kind == 1) ? nv * (nv - 1) / 2 : S.nv[0] * S.nv[1];
+  } else {
+    B.cb = -1;
+    B.sb = -1;
+    B.qb = -1;
+    B.kind = 0;
+    B.ncell = S.nv[B.sa];
+  }
+  B.clo = 0;
+  B.nct = B.ncell;
+  if (p.ntile > 1 && B.kind == 2) {  // rows [tile h, min((tile + 1) h, nv0))
+    const int h = (S.nv[0] + p.ntile - 1) / p.ntile;
+    const int r0 = tile * h, r1 = min(r0 + h, S.nv[0]);
+    B.clo = r0 * S.nv[1];
+    B.nct = (r1 - r0) * S.nv[1];
+  }
+  if (B.nct <= 0) return;
+
+  // bucket lists: this batch's bucket, then the shared bucket (degree <= 2)
+  const int* ofs = p.b_ofs + (size_t)slot * (nbat + 2);
+  // entries: the batch's own bucket (one-hole batch {a}: the d = 3 records
+  // holding a; two-hole batch: the d = 4 records holding both holes), then
+  // for a two-hole batch {a, b} the d = 3 lists of a and of b (a record
+  // holding both is taken from a's list only), then the shared bucket
+  const int ob = ofs[b], nb_ = ofs[b + 1] - ob, oa = ofs[nbat], na_ = ofs[nbat + 1] - oa;
+  const int o1 = (B.h == 2) ? ofs[B.ia] : 0, n1_ = (B.h == 2) ? ofs[B.ia + 1] - o1 : 0;
+  const int o2 = (B.h == 2) ? ofs[B.ib] : 0, n2_ = (B.h == 2) ? ofs[B.ib + 1] - o2 : 0;
+  const int s1 = nb_, s2 = s1 + n1_, s3 = s2 + n2_;
+  const int total = s3 + na_;
+  const size_t rb = (size_t)slot * (size_t)p.ndet;
+  const uint64_t* rw = p.r_words + rb * NW;
+  const double* rc = p.r_coef + rb;
+  const size_t eb = (size_t)slot * (size_t)p.ent_cap;
+  const uint64_t* ehm = p.e_hm + eb;
+  const uint64_t* epart = p.e_part + eb;
+  const uint32_t* erec = p.e_rec + eb;
+  // position of the i-th entry of this batch in the slot's entry arrays
+  auto entry = [&](int i) {
+    return i < s1 ? ob + i : (i < s2 ? o1 + i - s1 : (i < s3 ? o2 + i - s2 : oa + i - s3));
+  };
+  // a d = 3 record of b's list that also holds a was taken from a's list
+  auto dup = [&](int i, uint64_t hm) { return i >= s2 && i < s3 && ((hm >> B.ia) & 1ull); };
+
+  if (tid == 0) {
+    S.inv_nv1 = S.nv[1] > 0 ? 1.0f / (float)S.nv[1] : 0.0f;
+#pragma unroll
+    for (int w = 0; w < NW; w++) S.kbase[w] = S.I[w];
+    S.kbase[B.sa * NINT + (B.qa >> 6)] &= ~(1ull << (B.qa & 63));
+    if (B.h == 2) S.kbase[B.sb * NINT + (B.qb >> 6)] &= ~(1ull << (B.qb & 63));
+  }
+  // zero the accumulator, the bans; row sums for H_aa
+  if constexpr (MS) {
+    for (int st = 0; st < nst; st++)
+      for (int c = tid; c < B.nct; c += kThreads) A[st * mc + c] = 0.0;
+  } else {
+    for (int c = tid; c < B.nct; c += kThreads) {
+      Alo[c] = 0ull;
+      Ahi[c] = 0;
+    }
+  }
+  for (int c = tid; c < (B.nct + 31) / 32; c += kThreads) ban[c] = 0u;
+  {
+    auto W = [&](int x, int sx, int y, int sy) {
+      double v = p.Jm[x * norb + y];
+      if (sx == sy) v -= p.Km[x * norb + y];
+      return v;
+    };
+    if (B.kind == 0) {
+      const int s = B.sa;
+      for (int x = tid; x < S.nv[s]; x += kThreads) {
+        const int r = S.vir[s][x];
+        S.u0[x] = S.F[s][r] - W(r, s, B.qa, s);
+      }
+      if (tid == 0) S.base = S.hii - S.F[s][B.qa];
+    } else {
+      const int s1 = B.sa, s2 = B.sb;
+      for (int x = tid; x < S.nv[s1]; x += kThreads) {
+        const int r = S.vir[s1][x];
+        S.u0[x] = S.F[s1][r] - W(r, s1, B.qa, s1) - W(r, s1, B.qb, s2);
+      }
+      if (B.kind == 2)
+        for (int y = tid; y < S.nv[s2]; y += kThreads) {
+          const int s = S.vir[s2][y];
+          S.u1[y] = S.F[s2][s] - W(s, s2, B.qa, s1) - W(s, s2, B.qb, s2);
+        }
+      if (tid == 0) S.base = S.hii - S.F[s1][B.qa] - S.F[s2][B.qb] + W(B.qa, s1, B.qb, s2);
+      // pair tables of J = I: rows tri(qa, r) and columns tri(qb, s) with
+      // the phases of qa -> r and qb -> s on I's strings
+      const int sl2 = (B.kind == 2) ? 1 : s1;
+      const int nva = S.nv[s1];
+      for (int v = tid; v < nva + S.nv[sl2]; v += kThreads) {
+        if (v < nva) {
+          const int r = S.vir[s1][v];
+          const int par = count_between<NINT>(S.I + s1 * NINT, r < B.qa ? r : B.qa, r < B.qa ? B.qa : r) & 1;
+          S.iRow[v] = tri(B.qa, r) | (par << 31);
+        } else {
+          const int sv = S.vir[sl2][v - nva];
+          int par = count_between<NINT>(S.I + sl2 * NINT, sv < B.qb ? sv : B.qb, sv < B.qb ? B.qb : sv) & 1;
+          if (B.kind == 1) {
+            const int lo = sv < B.qb ? sv : B.qb, hi = sv < B.qb ? B.qb : sv;
+            par ^= (B.qa > lo && B.qa < hi) ? 1 : 0;
+          }
+          S.iCol[v - nva] = tri(B.qb, sv) | (par << 31);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int x = tid; x < S.nv[B.sa]; x += kThreads) S.dx[x] = (p.e0 - S.base) - S.u0[x];
+  if (p.tgt_on) {  // cells outside the target space contribute nothing: ban them
+    for (int cc = tid; cc < B.nct; cc += kThreads) {
+      int ro, so, x, y;
+      cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
+      const int kwr = B.sa * NINT + (ro >> 6), kws = (B.h == 2) ? B.sb * NINT + (so >> 6) : -1;
+      bool ok = true;
+      int moved = 0;
+#pragma unroll
+      for (int w = 0; w < NW; w++) {
+        const uint64_t k = S.kbase[w] | (w == kwr ? 1ull << (ro & 63) : 0ull) | (w == kws ? 1ull << (so & 63) : 0ull);
+        ok &= (k & p.tgt_core[w]) == p.tgt_core[w];
+        ok &= (k & p.tgt_del[w]) == 0ull;
+        moved += __popcll(k ^ p.tgt_ref[w]);
+      }
+      if (p.tgt_max_exc >= 0) ok &= (moved >> 1) <= p.tgt_max_exc;
+      if (!ok) atomicOr(&ban[cc >> 5], 1u << (cc & 31));
+    }
+  }
+
+  // ---- loop 1: bans.  J ranked before I that reach a whole row or column
+  // of cells (two-hole batch, t = 1) flag it in rowm / colm; the flags are
+  // turned into cell bans after the loop ----
+  for (int x = tid; x < kMaxOrb; x += kThreads) {
+    S.v.m.rowm[x] = 0u;
+    S.v.m.colm[x] = 0u;
+  }
+  __syncthreads();
+  bool dead = false;
+  for (int c0 = 0; c0 < total; c0 += kChunk) {
+    bool dl = false;
+    const int c1 = min(c0 + kChunk, total);
+    for (int i = c0 + tid; i < c1; i += kThreads) {
+      const int o = entry(i);
+      const uint64_t hm = ehm[o];
+      if (dup(i, hm)) continue;
+      const int t = __popcll(hm & ~B.hm);
+      if (t > 2) continue;
+      if (erec[o] >> 31) {
+        if ((B.h == 1 && t <= 1) || (B.h == 2 && t == 0)) {
+          dl = true;
+        } else if (B.h == 2 && t == 1) {
+          const uint64_t part = epart[o];
+          int na_, nb_;
+          const uint32_t Pa = particles_of_spin(part, norb, B.kind == 2 ? 0 : B.sa, &na_);
+          for (int q = 0; q < na_; q++) S.v.m.rowm[S.vidx[B.kind == 2 ? 0 : B.sa][pk(Pa, q)]] = 1u;
+          if (B.kind == 2) {
+            const uint32_t Pb = particles_of_spin(part, norb, 1, &nb_);
+            for (int q = 0; q < nb_; q++) S.v.m.colm[S.vidx[1][pk(Pb, q)]] = 1u;
+          }
+        } else {  // t == 2
+          for_subset_cells<NINT, NT>(B, S, norb, epart[o], [&](int c) { ban_cell(ban, B, c); });
+        }
+      } else if (t == 0 && hm == B.hm) {  // J = I - H + X with X a cell: alpha is internal
+        const uint64_t part = epart[o];
+        int n0, n1, c;
+        if (B.kind == 0) {
+          const uint32_t P0 = particles_of_spin(part, norb, B.sa, &n0);
+          c = S.vidx[B.sa][pk(P0, 0)];
+        } else if (B.kind == 1) {
+          const uint32_t P0 = particles_of_spin(part, norb, B.sa, &n0);
+          c = pair_cell(S.vidx[B.sa][pk(P0, 0)], S.vidx[B.sa][pk(P0, 1)]);
+        } else {
+          const uint32_t P0 = particles_of_spin(part, norb, 0, &n0);
+          const uint32_t P1 = particles_of_spin(part, norb, 1, &n1);
+          c = S.vidx[0][pk(P0, 0)] * S.nv[1] + S.vidx[1][pk(P1, 0)];
+        }
+        ban_cell(ban, B, c);
+      }
+    }
+    if (__syncthreads_or(dl)) {
+      dead = true;
+      break;
+    }
+  }
+  if (dead) return;
+  if (B.h == 2) {  // flagged rows and columns: one ban word per warp and round
+    for (int c0 = 0; c0 < B.nct; c0 += kThreads) {
+      const int cc = c0 + tid;
+      bool bn = false;
+      if (cc < B.nct) {
+        int ro, so, x, y;
+        cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
+        bn = (S.v.m.rowm[x] | (B.kind == 2 ? S.v.m.colm[y] : S.v.m.rowm[y])) != 0u;
+      }
+      const unsigned bw = __ballot_sync(kFull, bn);
+      if (lane == 0 && bw) ban[(c0 >> 5) + warp] |= bw;
+    }
+    __syncthreads();
+  }
+
+  // ---- loop 2: A(R) += c_J <J|H|I - H + R> over J ranked at or after I.
+  // In the one-state form every term goes into the exact accumulator, so
+  // the order in which J are listed and cells are reached does not matter ----
+  unsigned long long con = 0;
+  for (int c0 = 0; c0 < total; c0 += kChunk) {
+    if (tid == 0) {
+      S.n0 = 0;
+      S.n1 = 0;
+      S.n2 = 0;
+      S.cnext = 0;
+    }
+    __syncthreads();
+    const int c1 = min(c0 + kChunk, total);
+    for (int i = c0 + tid; i < c1; i += kThreads) {
+      const int o = entry(i);
+      if (erec[o] >> 31) continue;
+      const uint64_t hmr = ehm[o];
+      if (dup(i, hmr)) continue;
+      if (B.h == 2 && hmr == 0ull) continue;  // J = I: added in the cells pass
+      const int t = __popcll(hmr & ~B.hm);
+      if (t > 2) continue;
+      const bool all = (B.h == 1) ? (t <= 1) : (t == 0);
+      if (all) S.u.l.L0[atomicAdd(&S.n0, 1)] = o;
+      else if (t == 1) S.u.l.L1[atomicAdd(&S.n1, 1)] = o;
+      else if (subset_live<NINT, NT>(B, S, norb, epart[o], ban)) S.u.l.L2[atomicAdd(&S.n2, 1)] = o;
+    }
+    __syncthreads();
+    // J reaching every cell: the whole CTA, kGroup of them per pass.
+    // In a two-hole batch such a J is K + {x1, x2}; for a cell R disjoint
+    // from {x1, x2} the element is a double substitution x1 x2 -> R whose
+    // pair indices and phase split into a row part and a column part,
+    // precomputed once per J (cells meeting {x1, x2} take the general path).
+    const int n0 = S.n0;
+    for (int g0 = 0; g0 < n0; g0 += kGroup) {
+      const int m = min(kGroup, n0 - g0);
+      if (tid < m) {
+        const int o = S.u.l.L0[g0 + tid];
+        const int r = (int)(erec[o] & 0x7FFFFFFFu);
+#pragma unroll
+        for (int w = 0; w < NW; w++) S.gJw[tid][w] = rw[(size_t)r * NW + w];
+        S.gcj[tid] = (NT)rc[r];
+        if constexpr (MS)
+          for (int st = 0; st < nst; st++) ms_gc[tid * kMaxStates + st] = rc[st * p.rc_stride + r];
+        uint32_t xs, ts;
+        int nxs, nts;
+        excitation_sets<NINT, NT>(B, S, epart[o], ehm[o], &xs, &nxs, &ts, &nts);
+        S.gX[tid] = xs;
+        S.gT[tid] = ts;
+        S.gnx[tid] = nxs;
+        S.gnt[tid] = nts;
+        if (B.h == 2) {
+          const int a = pk(xs, 0), bb = pk(xs, 1);
+          const int x1 = a < bb ? a : bb, x2 = a < bb ? bb : a;
+          S.gx1[tid] = x1;
+          S.gx2[tid] = x2;
+          const int s1 = x1 >= norb, s2 = x2 >= norb;
+          S.gsr[tid] = S.vidx[s1][x1 - s1 * norb];
+          S.gsc[tid] = S.vidx[s2][x2 - s2 * norb];
+        }
+      }
+      __syncthreads();
+      const int sl1 = B.sa, sl2 = (B.kind == 2) ? 1 : B.sa;
+      const int nva = S.nv[sl1], nvb = S.nv[sl2];
+      if (B.h == 2) {
+        const int per = nva + nvb;
+        for (int idx = tid; idx < m * per; idx += kThreads) {
+          const int j = idx / per;
+          const int v = idx - j * per;
+          const uint64_t* Jw = S.gJw[j];
+          const int x1 = S.gx1[j] - sl1 * norb, x2 = S.gx2[j] - sl2 * norb;
+          if (v < nva) {
+            const int r = S.vir[sl1][v];
+            int par = 0;
+            if (r != x1) par = count_between<NINT>(Jw + sl1 * NINT, r < x1 ? r : x1, r < x1 ? x1 : r) & 1;
+            S.v.g.gRow[j][v] = tri(x1, r) | (par << 31);
+          } else {
+            const int sv = S.vir[sl2][v - nva];
+            int par = 0;
+            if (sv != x2) par = count_between<NINT>(Jw + sl2 * NINT, sv < x2 ? sv : x2, sv < x2 ? x2 : sv) & 1;
+            if (B.kind == 1) {
+              const int lo = sv < x2 ? sv : x2, hi = sv < x2 ? x2 : sv;
+              par ^= (x1 > lo && x1 < hi) ? 1 : 0;
+            }
+            S.v.g.gCol[j][v - nva] = tri(x2, sv) | (par << 31);
+          }
+        }
+        __syncthreads();
+      }
+      for (int cc = tid; cc < B.nct; cc += kThreads) {
+        if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
+        int ro, so, x, y;
+        cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
+        const int rcode = B.sa * norb + ro;
+        const int scode = (B.h == 2) ? B.sb * norb + so : -1;
+        unsigned long long acc_lo = 0ull;  // exact sum of this group's products
+        int acc_hi = 0;
+        double accs[kMaxStates];  // multi-state form: one sum per state
+#pragma unroll
+        for (int st = 0; st < kMaxStates; st++) accs[st] = 0.0;
+        for (int j = 0; j < m; j++) {
+          bool general = true;
+          NT v = NT(0);
+          if (B.h == 2) {
+            const int sr = S.gsr[j], sc = S.gsc[j];
+            if (B.kind == 2) {
+              if (x != sr && y != sc) {
+                const int rt = S.v.g.gRow[j][x], ct = S.v.g.gCol[j][y];
+                v = flip_sign(eri_n[tri(rt & 0x7fffffff, ct & 0x7fffffff)], (rt ^ ct) < 0);
+                general = false;
+              }
+            } else if (x != sr && x != sc && y != sr && y != sc) {
+              const int a1 = S.v.g.gRow[j][x], b2 = S.v.g.gCol[j][y];
+              const int a2 = S.v.g.gRow[j][y], b1 = S.v.g.gCol[j][x];
+              v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
+              const int x2 = S.gx2[j] - B.sa * norb;
+              const int lo = so < x2 ? so : x2, hi = so < x2 ? x2 : so;
+              const int par = ((a1 ^ b2) < 0 ? 1 : 0) ^ ((ro > lo && ro < hi) ? 1 : 0);
+              v = flip_sign(v, par);
+              general = false;
+            }
+          }
+          if (general) v = element<NINT, NT>(eri_n, h_n, norb, S.gJw[j], S.gX[j], S.gnx[j], S.gT[j], S.gnt[j], rcode, scode);
+          if constexpr (MS) {
+#pragma unroll
+            for (int st = 0; st < kMaxStates; st++)
+              if (st < nst) accs[st] = fma(ms_gc[j * kMaxStates + st], (double)v, accs[st]);
+          } else {
+            unsigned long long l;
+            int hh;
+            fix_of(S.gcj[j] * v, F, l, hh);
+            fix_add(acc_lo, acc_hi, l, hh);
+          }
+        }
+        if constexpr (MS) {
+#pragma unroll
+          for (int st = 0; st < kMaxStates; st++)
+            if (st < nst) A[st * mc + cc] += accs[st];
+        } else {
+          unsigned long long lo = Alo[cc];
+          int hi = Ahi[cc];
+          fix_add(lo, hi, acc_lo, acc_hi);
+          Alo[cc] = lo;
+          Ahi[cc] = hi;
+        }
+        con += m;
+      }
+      __syncthreads();
+    }
+    // J reaching a row of cells (one warp each), then J reaching a few
+    // cells (one lane each, 32 per draw), drawn by the warps as they free up
+    {
+      const int n1 = S.n1, n2 = S.n2;
+      for (;;) {
+        int jd = 0;
+        if (lane == 0) jd = atomicAdd(&S.cnext, 1);
+        jd = __shfl_sync(kFull, jd, 0);
+        if (jd < n1) {
+          const int j = jd;
+          const int o = S.u.l.L1[j];
+          const int r = (int)(erec[o] & 0x7FFFFFFFu);
+          const uint64_t* Jw = rw + (size_t)r * NW;
+          const NT cj = (NT)rc[r];
+          double cjs[kMaxStates];
+          if constexpr (MS) {
+#pragma unroll
+            for (int st = 0; st < kMaxStates; st++) cjs[st] = st < nst ? rc[st * p.rc_stride + r] : 0.0;
+          }
+          const uint64_t part = epart[o];
+          uint32_t X, T;
+          int nx, nt;
+          excitation_sets<NINT, NT>(B, S, part, ehm[o], &X, &nx, &T, &nt);
+          for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
+            const int cc = c - B.clo;
+            if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
+            int ro, so, x, y;
+            cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
+            const int rcode = B.sa * norb + ro;
+            const int scode = B.sb * norb + so;
+            if constexpr (MS) {
+              const double v = (double)element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode);
+#pragma unroll
+              for (int st = 0; st < kMaxStates; st++)
+                if (st < nst) atomicAdd(&A[st * mc + cc], cjs[st] * v);
+            } else {
+              unsigned long long l;
+              int hh;
+              fix_of(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode), F, l, hh);
+              fix_atomic_add(Alo, Ahi, cc, l, hh);
+            }
+            con++;
+          });
+        } else {
+          const int j0 = (jd - n1) * 32;
+          if (j0 >= n2) break;
+          const int j = j0 + lane;
+          if (j < n2) {
+            const int o = S.u.l.L2[j];
+          const int r = (int)(erec[o] & 0x7FFFFFFFu);
+            const uint64_t* Jw = rw + (size_t)r * NW;
+            const NT cj = (NT)rc[r];
+            double cjs[kMaxStates];
+            if constexpr (MS) {
+#pragma unroll
+              for (int st = 0; st < kMaxStates; st++) cjs[st] = st < nst ? rc[st * p.rc_stride + r] : 0.0;
+            }
+            const uint64_t part = epart[o];
+            uint32_t X, T;
+            int nx, nt;
+            excitation_sets<NINT, NT>(B, S, part, ehm[o], &X, &nx, &T, &nt);
+            for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
+              const int cc = c - B.clo;
+              if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
+              int ro, so, x, y;
+              cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
+              const int rcode = B.sa * norb + ro;
+              const int scode = (B.h == 2) ? B.sb * norb + so : -1;
+              if constexpr (MS) {
+                const double v = (double)element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode);
+#pragma unroll
+                for (int st = 0; st < kMaxStates; st++)
+                  if (st < nst) atomicAdd(&A[st * mc + cc], cjs[st] * v);
+              } else {
+                unsigned long long l;
+                int hh;
+                fix_of(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode), F, l, hh);
+                fix_atomic_add(Alo, Ahi, cc, l, hh);
+              }
+              con++;
+            });
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- cells: the perturbers of I in this batch ----
+  if (GRAD) {  // loop 2 is over: the pair tables' storage takes the weights
+    for (int x = tid; x < kMaxOrb; x += kThreads) {
+      S.v.w.rowW2[x] = 0.0;
+      S.v.w.colW2[x] = 0.0;
+    }
+    __syncthreads();
+  }
+  if (p.k > 0) {
+    if (S.tkcnt + B.nct > p.cap) compact_selection<NINT, NT>(p, S, te, ta, tk);
+    if (tid == 0) {
+      const unsigned long long gt = *((volatile unsigned long long*)p.tau_bits);
+      if (gt > S.tau) S.tau = gt;
+    }
+    __syncthreads();
+  }
+  const unsigned long long tau = S.tau;
+  double acc_e = 0.0, acc_s2 = 0.0;
+  unsigned long long acc_na = 0, acc_d0 = 0, acc_d1 = 0, acc_min = 0x7FF0000000000000ull, acc_tiny = 0;
+  double acc_es[kMaxStates], acc_s2s[kMaxStates];  // multi-state form: sums per state
+#pragma unroll
+  for (int st = 0; st < kMaxStates; st++) acc_es[st] = acc_s2s[st] = 0.0;
+  if constexpr (MS) {
+    for (int cc = tid; cc < B.nct; cc += kThreads) {
+      if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
+      int ro, so, x, y;
+      cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
+      double vI = 0.0;  // <I|H|alpha> for the generator's own term
+      if (B.h == 2) {
+        const int a1 = S.iRow[x], b2 = S.iCol[y];
+        if (B.kind == 2) {
+          vI = (double)flip_sign(eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)], (a1 ^ b2) < 0);
+        } else {
+          const int a2 = S.iRow[y], b1 = S.iCol[x];
+          NT v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
+          const int lo = so < B.qb ? so : B.qb, hi = so < B.qb ? B.qb : so;
+          vI = (double)flip_sign(v, ((a1 ^ b2) < 0 ? 1 : 0) ^ ((ro > lo && ro < hi) ? 1 : 0));
+        }
+        con++;
+      }
+      // E0_s - H_aa = ((E0_s - base) - u0[x]) - rest, as the one-state form
+      double rest = 0.0;
+      if (B.kind == 2) rest = S.u1[y] + p.Jm[ro * norb + so];
+      else if (B.kind == 1) rest = S.u0[y] + (p.Jm[ro * norb + so] - p.Km[ro * norb + so]);
+      double crit = 0.0, a0 = 0.0;
+#pragma unroll
+      for (int st = 0; st < kMaxStates; st++) {
+        if (st >= nst) break;
+        const double a = A[st * mc + cc] + ms_cI[st] * vI;
+        double D = (p.st_e0[st] - S.base) - S.u0[x];
+        if (B.kind != 0) D -= rest;
+        const unsigned long long dex = ((unsigned long long)__double_as_longlong(D) >> 52) & 0x7FFull;
+        const double inv = (dex > 523ull && dex < 1523ull) ? recip_nr<2>(D) : 1.0 / D;
+        const double q = a * inv;
+        const double e = a * q;
+        acc_es[st] += e;
+        acc_s2s[st] += q * q;
+        crit += ms_w[st] * e;  // c_alpha,s A_s / max_I c_Is^2
+        const unsigned long long db = abs_bits(D);
+        acc_min = db < acc_min ? db : acc_min;
+        if (st == 0) a0 = a;
+      }
+      acc_na++;
+      if (abs_bits(a0) < 0x3D06849B86A12B9Bull) acc_tiny++;
+      uint64_t key[NW];
+      const int kwr = B.sa * NINT + (ro >> 6), kws = (B.h == 2) ? B.sb * NINT + (so >> 6) : -1;
+#pragma unroll
+      for (int w = 0; w < NW; w++)
+        key[w] = S.kbase[w] | (w == kwr ? 1ull << (ro & 63) : 0ull) | (w == kws ? 1ull << (so & 63) : 0ull);
+      uint64_t hk = 0;
+#pragma unroll
+      for (int w = 0; w < NW; w++) hk = splitmix64(hk ^ key[w]);
+      acc_d0 += hk;
+      acc_d1 ^= splitmix64(hk ^ 0x243F6A8885A308D3ull);
+      if (p.k > 0) {
+        const unsigned long long eb = abs_bits(crit);
+        if (eb >= tau) {
+          atomicAdd(&p.sel_hist[sel_bin(eb)], 1u);
+          const int pos = atomicAdd(&S.tkcnt, 1);
+          te[pos] = crit;
+          ta[pos] = a0;
+#pragma unroll
+          for (int w = 0; w < NW; w++) tk[(size_t)pos * NW + w] = key[w];
+        }
+      }
+    }
+    acc_e = acc_es[0];
+    acc_s2 = acc_s2s[0];
+  } else {
+    for (int cc = tid; cc < B.nct; cc += kThreads) {
+      if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
+      int ro, so, x, y;
+      cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
+      double a = fix_to_double(Alo[cc], Ahi[cc], F);
+      if (B.h == 2) {  // the generator's own term c_I <I|H|alpha>
+        NT v;
+        const int a1 = S.iRow[x], b2 = S.iCol[y];
+        if (B.kind == 2) {
+          v = flip_sign(eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)], (a1 ^ b2) < 0);
+        } else {
+          const int a2 = S.iRow[y], b1 = S.iCol[x];
+          v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
+          const int lo = so < B.qb ? so : B.qb, hi = so < B.qb ? B.qb : so;
+          v = flip_sign(v, ((a1 ^ b2) < 0 ? 1 : 0) ^ ((ro > lo && ro < hi) ? 1 : 0));
+        }
+        a += (double)(S.cI * v);
+        con++;
+      }
+      // D = E0 - H_aa from the per-batch row sums
+      double D = S.dx[x];
+      if (B.kind == 2) D -= S.u1[y] + p.Jm[ro * norb + so];
+      else if (B.kind == 1) D -= S.u0[y] + (p.Jm[ro * norb + so] - p.Km[ro * norb + so]);
+      // |D| in [2^-500, 2^500]: Newton reciprocal; otherwise the division
+      const unsigned long long dex = ((unsigned long long)__double_as_longlong(D) >> 52) & 0x7FFull;
+      const double inv = (dex > 523ull && dex < 1523ull) ? recip_nr<sizeof(NT) == 8 ? 2 : 1>(D) : 1.0 / D;
+      const double q = a * inv;
+      acc_e = fma(a, q, acc_e);  // e = A q
+      acc_s2 += q * q;
+      acc_na++;
+      if (GRAD) {
+        // numerator weight 2A/D for loop 3; (A/D)^2 weights the diagonal
+        A[cc] = 2.0 * q;
+        const double w2 = q * q;
+        atomicAdd(&S.v.w.rowW2[x], w2);
+        if (B.kind == 2) atomicAdd(&S.v.w.colW2[y], w2);
+        if (B.kind == 1) atomicAdd(&S.v.w.rowW2[y], w2);
+        if (B.h == 2) w_grad(p, ro, B.sa, so, B.sb, w2);
+      }
+      // |a| < 1e-14, compared on the bit pattern (no FP64 compare)
+      if (abs_bits(a) < 0x3D06849B86A12B9Bull) acc_tiny++;
+      // |D| and |e| as bit patterns, off the FP64 pipe
+      const unsigned long long db = abs_bits(D);
+      acc_min = db < acc_min ? db : acc_min;
+      uint64_t key[NW];  // alpha's words; selects keep them in registers
+      const int kwr = B.sa * NINT + (ro >> 6), kws = (B.h == 2) ? B.sb * NINT + (so >> 6) : -1;
+#pragma unroll
+      for (int w = 0; w < NW; w++)
+        key[w] = S.kbase[w] | (w == kwr ? 1ull << (ro & 63) : 0ull) | (w == kws ? 1ull << (so & 63) : 0ull);
+      uint64_t hk = 0;
+#pragma unroll
+      for (int w = 0; w < NW; w++) hk = splitmix64(hk ^ key[w]);
+      acc_d0 += hk;
+      acc_d1 ^= splitmix64(hk ^ 0x243F6A8885A308D3ull);
+      // e = A q is formed only when it can reach the threshold: with biased
+      // exponents ea, eq of A and q, |A q| < 2^(ea + eq - 2044), so
+      // ea + eq <= et + 1021 (et: the exponent of tau) puts it below tau
+      const int ea = (int)(abs_bits(a) >> 52), eqx = (int)(abs_bits(q) >> 52);
+      if (p.k > 0 && (tau == 0ull || ea + eqx > (int)(tau >> 52) + 1021)) {
+        const double e = a * q;
+        const unsigned long long eb = abs_bits(e);
+        if (eb >= tau) {
+          atomicAdd(&p.sel_hist[sel_bin(eb)], 1u);
+          const int pos = atomicAdd(&S.tkcnt, 1);
+          te[pos] = e;
+          ta[pos] = a;
+#pragma unroll
+          for (int w = 0; w < NW; w++) tk[(size_t)pos * NW + w] = key[w];
+        }
+      }
+    }
+  }
+  // ---- per-item reduction into the generator's totals ----
+  {
+    // FP64 sums through shared memory and one warp: a shuffle tree in every
+    // warp would spend five FP64 adds per lane per quantity
+    S.u.red_t[0][tid] = acc_e;
+    S.u.red_t[1][tid] = acc_s2;
+    const unsigned long long na = warp_sum_u(acc_na), nc = warp_sum_u(con), d0 = warp_sum_u(acc_d0);
+    const unsigned long long d1 = warp_xor_u(acc_d1), mn = warp_min_u(acc_min), tiny = warp_sum_u(acc_tiny);
+    if (lane == 0) {
+      S.red_u[warp][0] = na;
+      S.red_u[warp][1] = nc;
+      S.red_u[warp][2] = d0;
+      S.red_u[warp][3] = d1;
+      S.red_u[warp][4] = mn;
+      S.red_u[warp][5] = tiny;
+    }
+    __syncthreads();
+    double se = 0.0, ss = 0.0;
+    if (warp == 0) {
+      for (int i = lane; i < kThreads; i += 32) {
+        se += S.u.red_t[0][i];
+        ss += S.u.red_t[1][i];
+      }
+      se = warp_sum(se);
+      ss = warp_sum(ss);
+    }
+    if (tid == 0) {
+      const double te_ = se, ts = ss;
+      unsigned long long tn = 0, tc = 0, x0 = 0, x1 = 0, m = 0x7FF0000000000000ull, tt = 0;
+      for (int w = 0; w < kWarps; w++) {
+        tn += S.red_u[w][0];
+        tc += S.red_u[w][1];
+        x0 += S.red_u[w][2];
+        x1 ^= S.red_u[w][3];
+        m = S.red_u[w][4] < m ? S.red_u[w][4] : m;
+        tt += S.red_u[w][5];
+      }
+      S.sw2 = ts;
+      // the item's FP64 sums go to its own slot; the generator's eps_I
+      // and sum A^2/D^2 are reduced from the slots in item order after the
+      // wave (reduce_items_kernel), so they do not depend on which CTA
+      // finished first
+      double* its = p.it_sum + ((size_t)slot * nper + j) * p.it_stride;
+      its[0] = te_;
+      its[1] = ts;
+      if (tn) {
+        atomicAdd(&p.na[g], tn);
+        atomicAdd(&p.ncon[g], tc);
+        atomicAdd(&p.digest[0], x0);
+        atomicXor(&p.digest[1], x1);
+        atomicMin(p.min_den_bits, m);
+        if (tt) atomicAdd(p.n_tiny, tt);
+      }
+    }
+    if constexpr (MS) {  // the other states' eps and s2, one at a time
+#pragma unroll
+      for (int st = 1; st < kMaxStates; st++) {
+        if (st >= nst) break;
+        __syncthreads();
+        S.u.red_t[0][tid] = acc_es[st];
+        S.u.red_t[1][tid] = acc_s2s[st];
+        __syncthreads();
+        if (warp == 0) {
+          double ue = 0.0, us = 0.0;
+          for (int i = lane; i < kThreads; i += 32) {
+            ue += S.u.red_t[0][i];
+            us += S.u.red_t[1][i];
+          }
+          ue = warp_sum(ue);
+          us = warp_sum(us);
+          if (lane == 0) {
+            double* its = p.it_sum + ((size_t)slot * nper + j) * p.it_stride;
+            its[2 * st] = ue;
+            its[2 * st + 1] = us;
+          }
+        }
+      }
+    }
+  }
+  if (GRAD) {
+    __syncthreads();
+    // ---- loop 3: c_J (2A/D) d<J|H|alpha> over the same (J, cell) pairs ----
+    for (int c0 = 0; c0 < total; c0 += kChunk) {
+      if (tid == 0) {
+        S.n0 = 0;
+        S.n1 = 0;
+        S.n2 = 0;
+        S.cnext = 0;
+      }
+      __syncthreads();
+      const int c1 = min(c0 + kChunk, total);
+      for (int i = c0 + tid; i < c1; i += kThreads) {
+        const int o = entry(i);
+        if (erec[o] >> 31) continue;
+        const uint64_t hmr = ehm[o];
+        if (dup(i, hmr)) continue;
+        const int t = __popcll(hmr & ~B.hm);
+        if (t > 2) continue;
+        const bool all = (B.h == 1) ? (t <= 1) : (t == 0);
+        if (all) S.u.l.L0[atomicAdd(&S.n0, 1)] = o;
+        else if (t == 1) S.u.l.L1[atomicAdd(&S.n1, 1)] = o;
+        else if (subset_live<NINT, NT>(B, S, norb, epart[o], ban)) S.u.l.L2[atomicAdd(&S.n2, 1)] = o;
+      }
+      __syncthreads();
+      for (int j = 0; j < S.n0; j++) {
+        const int o = S.u.l.L0[j];
+        const int r = (int)(erec[o] & 0x7FFFFFFFu);
+        const uint64_t* Jw = rw + (size_t)r * NW;
+        const double cj = rc[r];
+        uint32_t X, T;
+        int nx, nt;
+        excitation_sets<NINT, NT>(B, S, epart[o], ehm[o], &X, &nx, &T, &nt);
+        for (int cc = tid; cc < B.nct; cc += kThreads) {
+          if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
+          int ro, so, x, y;
+          cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
+          element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, (B.h == 2) ? B.sb * norb + so : -1, cj * A[cc]);
+        }
+      }
+      {  // row-reaching J (a warp each), then subset-reaching J (32 per draw), drawn dynamically
+        const int n1 = S.n1, n2 = S.n2;
+        for (;;) {
+          int jd = 0;
+          if (lane == 0) jd = atomicAdd(&S.cnext, 1);
+          jd = __shfl_sync(kFull, jd, 0);
+          if (jd < n1) {
+            const int j = jd;
+            const int o = S.u.l.L1[j];
+            const int r = (int)(erec[o] & 0x7FFFFFFFu);
+            const uint64_t* Jw = rw + (size_t)r * NW;
+            const double cj = rc[r];
+            const uint64_t part = epart[o];
+            uint32_t X, T;
+            int nx, nt;
+            excitation_sets<NINT, NT>(B, S, part, ehm[o], &X, &nx, &T, &nt);
+            for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
+              const int cc = c - B.clo;
+              if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
+              int ro, so, x, y;
+              cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
+              element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, B.sb * norb + so, cj * A[cc]);
+            });
+          } else {
+            const int j0 = (jd - n1) * 32;
+            if (j0 >= n2) break;
+            const int j = j0 + lane;
+            if (j < n2) {
+              const int o = S.u.l.L2[j];
+              const int r = (int)(erec[o] & 0x7FFFFFFFu);
+              const uint64_t* Jw = rw + (size_t)r * NW;
+              const double cj = rc[r];
+              const uint64_t part = epart[o];
+              uint32_t X, T;
+              int nx, nt;
+              excitation_sets<NINT, NT>(B, S, part, ehm[o], &X, &nx, &T, &nt);
+              for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
+                const int cc = c - B.clo;
+                if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
+                int ro, so, x, y;
+                cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
+                element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, (B.h == 2) ? B.sb * norb + so : -1,
+                                   cj * A[cc]);
+              });
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // ---- diagonal: H_aa = H_II - F(a) [- F(b) + W(a,b)] + F(r) [+ F(s)]
+    //      - W(r,a) [- W(r,b) - W(s,a) - W(s,b) + W(r,s)]; the W(r,s) terms
+    //      were scattered per cell, the rest goes by row sums ----
+    double* wF = p.g_wF + (size_t)g * 2 * norb;
+    const int s1 = B.sa, s2 = (B.h == 2) ? B.sb : B.sa;
+    for (int x = tid; x < S.nv[s1]; x += kThreads) {
+      const double wr = S.v.w.rowW2[x];
+      if (wr == 0.0) continue;
+      const int r = S.vir[s1][x];
+      atomicAdd(&wF[s1 * norb + r], wr);
+      w_grad(p, r, s1, B.qa, B.sa, -wr);
+      if (B.h == 2) w_grad(p, r, s1, B.qb, B.sb, -wr);
+    }
+    if (B.kind == 2)
+      for (int y = tid; y < S.nv[s2]; y += kThreads) {
+        const double wc = S.v.w.colW2[y];
+        if (wc == 0.0) continue;
+        const int sv = S.vir[s2][y];
+        atomicAdd(&wF[s2 * norb + sv], wc);
+        w_grad(p, sv, s2, B.qa, B.sa, -wc);
+        w_grad(p, sv, s2, B.qb, B.sb, -wc);
+      }
+    if (tid == 0 && S.sw2 != 0.0) {
+      const double sw = S.sw2;
+      atomicAdd(&p.g_wH[g], sw);
+      atomicAdd(&wF[B.sa * norb + B.qa], -sw);
+      if (B.h == 2) {
+        atomicAdd(&wF[B.sb * norb + B.qb], -sw);
+        w_grad(p, B.qa, B.sa, B.qb, B.sb, sw);
+      }
+    }
+  }
+}
+
 // Three CTAs per SM for one word per spin; two words per spin come with
 // larger accumulators (at most two CTAs fit in shared memory), so those
 // kernels take the registers of two CTAs and do not spill.
@@ -1055,32 +2040,15 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
   static_assert(!(MS && GRAD), "the gradient is a one-state form");
   static_assert(!MS || sizeof(NT) == 8, "the multi-state form is FP64");
   constexpr int NW = 2 * NINT;
-  extern __shared__ __align__(16) unsigned char dyn[];
-  const int mc = p.max_cells;  // stride between the states' accumulators
-  // multi-state form: one FP64 accumulator per state; one-state form: the
-  // exact 96-bit accumulators (low words, then high words)
-  double* A = reinterpret_cast<double*>(dyn);
-  unsigned long long* Alo = reinterpret_cast<unsigned long long*>(dyn);
-  int* Ahi = reinterpret_cast<int*>(Alo + mc);
-  uint32_t* ban =
-      MS ? reinterpret_cast<uint32_t*>(A + p.nst * mc) : reinterpret_cast<uint32_t*>(Ahi + ((mc + 1) & ~1));
-  // multi-state extras after the bans: the CTA group's coefficients per
-  // state, c_I per state and the weights w_s
-  double* ms_gc = reinterpret_cast<double*>(ban + (((mc + 31) / 32 + 1) & ~1));
-  double* ms_cI = ms_gc + kGroup * kMaxStates;
-  double* ms_w = ms_cI + kMaxStates;
-  const int nst = MS ? p.nst : 1;
   __shared__ BatchShared<NINT, NT> S;
-  const NT* eri_n = numer_eri<NT>(p);
-  const NT* h_n = numer_h<NT>(p);
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int norb = p.norb, nel = p.nel, nbat = p.nbat;
+  const int tid = threadIdx.x;
+  const long long nitems = (long long)p.wave_slots * p.nper;
   double* te = p.tk_e + (size_t)blockIdx.x * (size_t)p.cap;
   double* ta = p.tk_a + (size_t)blockIdx.x * (size_t)p.cap;
   uint64_t* tk = p.tk_key + (size_t)blockIdx.x * (size_t)p.cap * NW;
-  const int nper = p.nper;
-  const long long nitems = (long long)p.wave_slots * nper;
+  const ItemEnv E = item_env<MS>(p);
+  const NT* eri_n = numer_eri<NT>(p);
+  const NT* h_n = numer_h<NT>(p);
 
   if (tid == 0) {
     S.tkcnt = p.tk_cnt[blockIdx.x];
@@ -1108,888 +2076,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
     __syncthreads();
     const long long item = S.item;
     if (item >= nitems) break;
-    const int slot = (int)(item / nper), j = (int)(item - (long long)slot * nper);
-    // item j < nbat: batch j (the first row tile of a split batch); j >= nbat:
-    // row tile 1 + (j - nbat) / (n_alpha n_beta) of opposite-spin batch
-    // (j - nbat) % (n_alpha n_beta)
-    int b = j, tile = 0;
-    if (j >= nbat) {
-      const int na = p.nalpha, nab = p.nalpha * p.nbeta;
-      const int k = (j - nbat) % nab;
-      tile = 1 + (j - nbat) / nab;
-      const int ia = k % na, ib = na + k / na;
-      b = nel + ib * (ib - 1) / 2 + ia;
-    }
-    const GenMeta* M = p.meta + slot;
-    if (M->g < 0) continue;
-    if ((p.b_dead[(size_t)slot * ((nbat + 31) / 32) + (b >> 5)] >> (b & 31)) & 1u) continue;
-    if (slot != S.slot) {  // load the generator
-      __syncthreads();
-      if (tid < NW) S.I[tid] = M->I[tid];
-      if (tid < nel) S.occ[tid] = M->occ[tid];
-      for (int x = tid; x < 2 * norb; x += kThreads) S.F[x / norb][x % norb] = M->F[x / norb][x % norb];
-      __syncthreads();
-      for (int x = tid; x < 2 * norb; x += kThreads) {
-        const int s = x / norb, q = x - s * norb;
-        const uint64_t* sw = S.I + s * NINT;
-        const bool occ = (sw[q >> 6] >> (q & 63)) & 1ull;
-        int below = 0;  // occupied orbitals of spin s below q
-#pragma unroll
-        for (int w = 0; w < NINT; w++) {
-          const int lim = q - 64 * w;
-          if (lim >= 64) below += __popcll(sw[w]);
-          else if (lim > 0) below += __popcll(sw[w] & ((1ull << lim) - 1));
-        }
-        const int v = q - below;
-        S.vidx[s][q] = occ ? -1 : v;
-        if (!occ) S.vir[s][v] = q;
-      }
-      if (tid < 2) {
-        int n = 0;
-#pragma unroll
-        for (int w = 0; w < NINT; w++) n += __popcll(S.I[tid * NINT + w]);
-        S.nv[tid] = norb - n;
-      }
-      if (tid == 0) {
-        S.hii = M->hii;
-        S.cI = (NT)M->cI;
-        S.g = M->g;
-        S.slot = slot;
-      }
-      if constexpr (MS) {
-        if (tid < nst) {
-          ms_cI[tid] = p.coefs[(size_t)tid * p.ndet + p.order[M->g]];
-          const double m = __longlong_as_double((long long)p.st_cmax[tid]);
-          ms_w[tid] = 1.0 / (m * m);
-        }
-      }
-      __syncthreads();
-    }
-    const int g = S.g;
-
-    // ---- batch geometry ----
-    Batch B;
-    if (b < nel) {
-      B.h = 1;
-      B.ia = b;
-      B.ib = -1;
-    } else {
-      const int t = b - nel;
-      int y = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
-      while (y * (y - 1) / 2 > t) y--;
-      while ((y + 1) * y / 2 <= t) y++;
-      B.h = 2;
-      B.ib = y;
-      B.ia = t - y * (y - 1) / 2;
-    }
-    B.ca = S.occ[B.ia];
-    B.sa = B.ca >= norb;
-    B.qa = B.ca - B.sa * norb;
-    B.hm = 1ull << B.ia;
-    if (B.h == 2) {
-      B.cb = S.occ[B.ib];
-      B.sb = B.cb >= norb;
-      B.qb = B.cb - B.sb * norb;
-      B.hm |= 1ull << B.ib;
-      B.kind = (B.sa == B.sb) ? 1 : 2;
-      const int nv = S.nv[B.sa];
-      B.ncell = (B.kind == 1) ? nv * (nv - 1) / 2 : S.nv[0] * S.nv[1];
-    } else {
-      B.cb = -1;
-      B.sb = -1;
-      B.qb = -1;
-      B.kind = 0;
-      B.ncell = S.nv[B.sa];
-    }
-    B.clo = 0;
-    B.nct = B.ncell;
-    if (p.ntile > 1 && B.kind == 2) {  // rows [tile h, min((tile + 1) h, nv0))
-      const int h = (S.nv[0] + p.ntile - 1) / p.ntile;
-      const int r0 = tile * h, r1 = min(r0 + h, S.nv[0]);
-      B.clo = r0 * S.nv[1];
-      B.nct = (r1 - r0) * S.nv[1];
-    }
-    if (B.nct <= 0) continue;
-
-    // bucket lists: this batch's bucket, then the shared bucket (degree <= 2)
-    const int* ofs = p.b_ofs + (size_t)slot * (nbat + 2);
-    // entries: the batch's own bucket (one-hole batch {a}: the d = 3 records
-    // holding a; two-hole batch: the d = 4 records holding both holes), then
-    // for a two-hole batch {a, b} the d = 3 lists of a and of b (a record
-    // holding both is taken from a's list only), then the shared bucket
-    const int ob = ofs[b], nb_ = ofs[b + 1] - ob, oa = ofs[nbat], na_ = ofs[nbat + 1] - oa;
-    const int o1 = (B.h == 2) ? ofs[B.ia] : 0, n1_ = (B.h == 2) ? ofs[B.ia + 1] - o1 : 0;
-    const int o2 = (B.h == 2) ? ofs[B.ib] : 0, n2_ = (B.h == 2) ? ofs[B.ib + 1] - o2 : 0;
-    const int s1 = nb_, s2 = s1 + n1_, s3 = s2 + n2_;
-    const int total = s3 + na_;
-    const size_t rb = (size_t)slot * (size_t)p.ndet;
-    const uint64_t* rw = p.r_words + rb * NW;
-    const double* rc = p.r_coef + rb;
-    const size_t eb = (size_t)slot * (size_t)p.ent_cap;
-    const uint64_t* ehm = p.e_hm + eb;
-    const uint64_t* epart = p.e_part + eb;
-    const uint32_t* erec = p.e_rec + eb;
-    // position of the i-th entry of this batch in the slot's entry arrays
-    auto entry = [&](int i) {
-      return i < s1 ? ob + i : (i < s2 ? o1 + i - s1 : (i < s3 ? o2 + i - s2 : oa + i - s3));
-    };
-    // a d = 3 record of b's list that also holds a was taken from a's list
-    auto dup = [&](int i, uint64_t hm) { return i >= s2 && i < s3 && ((hm >> B.ia) & 1ull); };
-
-    if (tid == 0) {
-      S.inv_nv1 = S.nv[1] > 0 ? 1.0f / (float)S.nv[1] : 0.0f;
-#pragma unroll
-      for (int w = 0; w < NW; w++) S.kbase[w] = S.I[w];
-      S.kbase[B.sa * NINT + (B.qa >> 6)] &= ~(1ull << (B.qa & 63));
-      if (B.h == 2) S.kbase[B.sb * NINT + (B.qb >> 6)] &= ~(1ull << (B.qb & 63));
-    }
-    // zero the accumulator, the bans; row sums for H_aa
-    if constexpr (MS) {
-      for (int st = 0; st < nst; st++)
-        for (int c = tid; c < B.nct; c += kThreads) A[st * mc + c] = 0.0;
-    } else {
-      for (int c = tid; c < B.nct; c += kThreads) {
-        Alo[c] = 0ull;
-        Ahi[c] = 0;
-      }
-    }
-    for (int c = tid; c < (B.nct + 31) / 32; c += kThreads) ban[c] = 0u;
-    {
-      auto W = [&](int x, int sx, int y, int sy) {
-        double v = p.Jm[x * norb + y];
-        if (sx == sy) v -= p.Km[x * norb + y];
-        return v;
-      };
-      if (B.kind == 0) {
-        const int s = B.sa;
-        for (int x = tid; x < S.nv[s]; x += kThreads) {
-          const int r = S.vir[s][x];
-          S.u0[x] = S.F[s][r] - W(r, s, B.qa, s);
-        }
-        if (tid == 0) S.base = S.hii - S.F[s][B.qa];
-      } else {
-        const int s1 = B.sa, s2 = B.sb;
-        for (int x = tid; x < S.nv[s1]; x += kThreads) {
-          const int r = S.vir[s1][x];
-          S.u0[x] = S.F[s1][r] - W(r, s1, B.qa, s1) - W(r, s1, B.qb, s2);
-        }
-        if (B.kind == 2)
-          for (int y = tid; y < S.nv[s2]; y += kThreads) {
-            const int s = S.vir[s2][y];
-            S.u1[y] = S.F[s2][s] - W(s, s2, B.qa, s1) - W(s, s2, B.qb, s2);
-          }
-        if (tid == 0) S.base = S.hii - S.F[s1][B.qa] - S.F[s2][B.qb] + W(B.qa, s1, B.qb, s2);
-        // pair tables of J = I: rows tri(qa, r) and columns tri(qb, s) with
-        // the phases of qa -> r and qb -> s on I's strings
-        const int sl2 = (B.kind == 2) ? 1 : s1;
-        const int nva = S.nv[s1];
-        for (int v = tid; v < nva + S.nv[sl2]; v += kThreads) {
-          if (v < nva) {
-            const int r = S.vir[s1][v];
-            const int par = count_between<NINT>(S.I + s1 * NINT, r < B.qa ? r : B.qa, r < B.qa ? B.qa : r) & 1;
-            S.iRow[v] = tri(B.qa, r) | (par << 31);
-          } else {
-            const int sv = S.vir[sl2][v - nva];
-            int par = count_between<NINT>(S.I + sl2 * NINT, sv < B.qb ? sv : B.qb, sv < B.qb ? B.qb : sv) & 1;
-            if (B.kind == 1) {
-              const int lo = sv < B.qb ? sv : B.qb, hi = sv < B.qb ? B.qb : sv;
-              par ^= (B.qa > lo && B.qa < hi) ? 1 : 0;
-            }
-            S.iCol[v - nva] = tri(B.qb, sv) | (par << 31);
-          }
-        }
-      }
-    }
-    __syncthreads();
-    for (int x = tid; x < S.nv[B.sa]; x += kThreads) S.dx[x] = (p.e0 - S.base) - S.u0[x];
-    if (p.tgt_on) {  // cells outside the target space contribute nothing: ban them
-      for (int cc = tid; cc < B.nct; cc += kThreads) {
-        int ro, so, x, y;
-        cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
-        const int kwr = B.sa * NINT + (ro >> 6), kws = (B.h == 2) ? B.sb * NINT + (so >> 6) : -1;
-        bool ok = true;
-        int moved = 0;
-#pragma unroll
-        for (int w = 0; w < NW; w++) {
-          const uint64_t k = S.kbase[w] | (w == kwr ? 1ull << (ro & 63) : 0ull) | (w == kws ? 1ull << (so & 63) : 0ull);
-          ok &= (k & p.tgt_core[w]) == p.tgt_core[w];
-          ok &= (k & p.tgt_del[w]) == 0ull;
-          moved += __popcll(k ^ p.tgt_ref[w]);
-        }
-        if (p.tgt_max_exc >= 0) ok &= (moved >> 1) <= p.tgt_max_exc;
-        if (!ok) atomicOr(&ban[cc >> 5], 1u << (cc & 31));
-      }
-    }
-
-    // ---- loop 1: bans.  J ranked before I that reach a whole row or column
-    // of cells (two-hole batch, t = 1) flag it in rowm / colm; the flags are
-    // turned into cell bans after the loop ----
-    for (int x = tid; x < kMaxOrb; x += kThreads) {
-      S.v.m.rowm[x] = 0u;
-      S.v.m.colm[x] = 0u;
-    }
-    __syncthreads();
-    bool dead = false;
-    for (int c0 = 0; c0 < total; c0 += kChunk) {
-      bool dl = false;
-      const int c1 = min(c0 + kChunk, total);
-      for (int i = c0 + tid; i < c1; i += kThreads) {
-        const int o = entry(i);
-        const uint64_t hm = ehm[o];
-        if (dup(i, hm)) continue;
-        const int t = __popcll(hm & ~B.hm);
-        if (t > 2) continue;
-        if (erec[o] >> 31) {
-          if ((B.h == 1 && t <= 1) || (B.h == 2 && t == 0)) {
-            dl = true;
-          } else if (B.h == 2 && t == 1) {
-            const uint64_t part = epart[o];
-            int na_, nb_;
-            const uint32_t Pa = particles_of_spin(part, norb, B.kind == 2 ? 0 : B.sa, &na_);
-            for (int q = 0; q < na_; q++) S.v.m.rowm[S.vidx[B.kind == 2 ? 0 : B.sa][pk(Pa, q)]] = 1u;
-            if (B.kind == 2) {
-              const uint32_t Pb = particles_of_spin(part, norb, 1, &nb_);
-              for (int q = 0; q < nb_; q++) S.v.m.colm[S.vidx[1][pk(Pb, q)]] = 1u;
-            }
-          } else {  // t == 2
-            for_subset_cells<NINT, NT>(B, S, norb, epart[o], [&](int c) { ban_cell(ban, B, c); });
-          }
-        } else if (t == 0 && hm == B.hm) {  // J = I - H + X with X a cell: alpha is internal
-          const uint64_t part = epart[o];
-          int n0, n1, c;
-          if (B.kind == 0) {
-            const uint32_t P0 = particles_of_spin(part, norb, B.sa, &n0);
-            c = S.vidx[B.sa][pk(P0, 0)];
-          } else if (B.kind == 1) {
-            const uint32_t P0 = particles_of_spin(part, norb, B.sa, &n0);
-            c = pair_cell(S.vidx[B.sa][pk(P0, 0)], S.vidx[B.sa][pk(P0, 1)]);
-          } else {
-            const uint32_t P0 = particles_of_spin(part, norb, 0, &n0);
-            const uint32_t P1 = particles_of_spin(part, norb, 1, &n1);
-            c = S.vidx[0][pk(P0, 0)] * S.nv[1] + S.vidx[1][pk(P1, 0)];
-          }
-          ban_cell(ban, B, c);
-        }
-      }
-      if (__syncthreads_or(dl)) {
-        dead = true;
-        break;
-      }
-    }
-    if (dead) continue;
-    if (B.h == 2) {  // flagged rows and columns: one ban word per warp and round
-      for (int c0 = 0; c0 < B.nct; c0 += kThreads) {
-        const int cc = c0 + tid;
-        bool bn = false;
-        if (cc < B.nct) {
-          int ro, so, x, y;
-          cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
-          bn = (S.v.m.rowm[x] | (B.kind == 2 ? S.v.m.colm[y] : S.v.m.rowm[y])) != 0u;
-        }
-        const unsigned bw = __ballot_sync(kFull, bn);
-        if (lane == 0 && bw) ban[(c0 >> 5) + warp] |= bw;
-      }
-      __syncthreads();
-    }
-
-    // ---- loop 2: A(R) += c_J <J|H|I - H + R> over J ranked at or after I.
-    // In the one-state form every term goes into the exact accumulator, so
-    // the order in which J are listed and cells are reached does not matter ----
-    unsigned long long con = 0;
-    for (int c0 = 0; c0 < total; c0 += kChunk) {
-      if (tid == 0) {
-        S.n0 = 0;
-        S.n1 = 0;
-        S.n2 = 0;
-        S.cnext = 0;
-      }
-      __syncthreads();
-      const int c1 = min(c0 + kChunk, total);
-      for (int i = c0 + tid; i < c1; i += kThreads) {
-        const int o = entry(i);
-        if (erec[o] >> 31) continue;
-        const uint64_t hmr = ehm[o];
-        if (dup(i, hmr)) continue;
-        if (B.h == 2 && hmr == 0ull) continue;  // J = I: added in the cells pass
-        const int t = __popcll(hmr & ~B.hm);
-        if (t > 2) continue;
-        const bool all = (B.h == 1) ? (t <= 1) : (t == 0);
-        if (all) S.u.l.L0[atomicAdd(&S.n0, 1)] = o;
-        else if (t == 1) S.u.l.L1[atomicAdd(&S.n1, 1)] = o;
-        else if (subset_live<NINT, NT>(B, S, norb, epart[o], ban)) S.u.l.L2[atomicAdd(&S.n2, 1)] = o;
-      }
-      __syncthreads();
-      // J reaching every cell: the whole CTA, kGroup of them per pass.
-      // In a two-hole batch such a J is K + {x1, x2}; for a cell R disjoint
-      // from {x1, x2} the element is a double substitution x1 x2 -> R whose
-      // pair indices and phase split into a row part and a column part,
-      // precomputed once per J (cells meeting {x1, x2} take the general path).
-      const int n0 = S.n0;
-      for (int g0 = 0; g0 < n0; g0 += kGroup) {
-        const int m = min(kGroup, n0 - g0);
-        if (tid < m) {
-          const int o = S.u.l.L0[g0 + tid];
-          const int r = (int)(erec[o] & 0x7FFFFFFFu);
-#pragma unroll
-          for (int w = 0; w < NW; w++) S.gJw[tid][w] = rw[(size_t)r * NW + w];
-          S.gcj[tid] = (NT)rc[r];
-          if constexpr (MS)
-            for (int st = 0; st < nst; st++) ms_gc[tid * kMaxStates + st] = rc[st * p.rc_stride + r];
-          uint32_t xs, ts;
-          int nxs, nts;
-          excitation_sets<NINT, NT>(B, S, epart[o], ehm[o], &xs, &nxs, &ts, &nts);
-          S.gX[tid] = xs;
-          S.gT[tid] = ts;
-          S.gnx[tid] = nxs;
-          S.gnt[tid] = nts;
-          if (B.h == 2) {
-            const int a = pk(xs, 0), bb = pk(xs, 1);
-            const int x1 = a < bb ? a : bb, x2 = a < bb ? bb : a;
-            S.gx1[tid] = x1;
-            S.gx2[tid] = x2;
-            const int s1 = x1 >= norb, s2 = x2 >= norb;
-            S.gsr[tid] = S.vidx[s1][x1 - s1 * norb];
-            S.gsc[tid] = S.vidx[s2][x2 - s2 * norb];
-          }
-        }
-        __syncthreads();
-        const int sl1 = B.sa, sl2 = (B.kind == 2) ? 1 : B.sa;
-        const int nva = S.nv[sl1], nvb = S.nv[sl2];
-        if (B.h == 2) {
-          const int per = nva + nvb;
-          for (int idx = tid; idx < m * per; idx += kThreads) {
-            const int j = idx / per;
-            const int v = idx - j * per;
-            const uint64_t* Jw = S.gJw[j];
-            const int x1 = S.gx1[j] - sl1 * norb, x2 = S.gx2[j] - sl2 * norb;
-            if (v < nva) {
-              const int r = S.vir[sl1][v];
-              int par = 0;
-              if (r != x1) par = count_between<NINT>(Jw + sl1 * NINT, r < x1 ? r : x1, r < x1 ? x1 : r) & 1;
-              S.v.g.gRow[j][v] = tri(x1, r) | (par << 31);
-            } else {
-              const int sv = S.vir[sl2][v - nva];
-              int par = 0;
-              if (sv != x2) par = count_between<NINT>(Jw + sl2 * NINT, sv < x2 ? sv : x2, sv < x2 ? x2 : sv) & 1;
-              if (B.kind == 1) {
-                const int lo = sv < x2 ? sv : x2, hi = sv < x2 ? x2 : sv;
-                par ^= (x1 > lo && x1 < hi) ? 1 : 0;
-              }
-              S.v.g.gCol[j][v - nva] = tri(x2, sv) | (par << 31);
-            }
-          }
-          __syncthreads();
-        }
-        for (int cc = tid; cc < B.nct; cc += kThreads) {
-          if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
-          int ro, so, x, y;
-          cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
-          const int rcode = B.sa * norb + ro;
-          const int scode = (B.h == 2) ? B.sb * norb + so : -1;
-          unsigned long long acc_lo = 0ull;  // exact sum of this group's products
-          int acc_hi = 0;
-          double accs[kMaxStates];  // multi-state form: one sum per state
-#pragma unroll
-          for (int st = 0; st < kMaxStates; st++) accs[st] = 0.0;
-          for (int j = 0; j < m; j++) {
-            bool general = true;
-            NT v = NT(0);
-            if (B.h == 2) {
-              const int sr = S.gsr[j], sc = S.gsc[j];
-              if (B.kind == 2) {
-                if (x != sr && y != sc) {
-                  const int rt = S.v.g.gRow[j][x], ct = S.v.g.gCol[j][y];
-                  v = flip_sign(eri_n[tri(rt & 0x7fffffff, ct & 0x7fffffff)], (rt ^ ct) < 0);
-                  general = false;
-                }
-              } else if (x != sr && x != sc && y != sr && y != sc) {
-                const int a1 = S.v.g.gRow[j][x], b2 = S.v.g.gCol[j][y];
-                const int a2 = S.v.g.gRow[j][y], b1 = S.v.g.gCol[j][x];
-                v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
-                const int x2 = S.gx2[j] - B.sa * norb;
-                const int lo = so < x2 ? so : x2, hi = so < x2 ? x2 : so;
-                const int par = ((a1 ^ b2) < 0 ? 1 : 0) ^ ((ro > lo && ro < hi) ? 1 : 0);
-                v = flip_sign(v, par);
-                general = false;
-              }
-            }
-            if (general) v = element<NINT, NT>(eri_n, h_n, norb, S.gJw[j], S.gX[j], S.gnx[j], S.gT[j], S.gnt[j], rcode, scode);
-            if constexpr (MS) {
-#pragma unroll
-              for (int st = 0; st < kMaxStates; st++)
-                if (st < nst) accs[st] = fma(ms_gc[j * kMaxStates + st], (double)v, accs[st]);
-            } else {
-              unsigned long long l;
-              int hh;
-              fix_of(S.gcj[j] * v, F, l, hh);
-              fix_add(acc_lo, acc_hi, l, hh);
-            }
-          }
-          if constexpr (MS) {
-#pragma unroll
-            for (int st = 0; st < kMaxStates; st++)
-              if (st < nst) A[st * mc + cc] += accs[st];
-          } else {
-            unsigned long long lo = Alo[cc];
-            int hi = Ahi[cc];
-            fix_add(lo, hi, acc_lo, acc_hi);
-            Alo[cc] = lo;
-            Ahi[cc] = hi;
-          }
-          con += m;
-        }
-        __syncthreads();
-      }
-      // J reaching a row of cells (one warp each), then J reaching a few
-      // cells (one lane each, 32 per draw), drawn by the warps as they free up
-      {
-        const int n1 = S.n1, n2 = S.n2;
-        for (;;) {
-          int jd = 0;
-          if (lane == 0) jd = atomicAdd(&S.cnext, 1);
-          jd = __shfl_sync(kFull, jd, 0);
-          if (jd < n1) {
-            const int j = jd;
-            const int o = S.u.l.L1[j];
-            const int r = (int)(erec[o] & 0x7FFFFFFFu);
-            const uint64_t* Jw = rw + (size_t)r * NW;
-            const NT cj = (NT)rc[r];
-            double cjs[kMaxStates];
-            if constexpr (MS) {
-#pragma unroll
-              for (int st = 0; st < kMaxStates; st++) cjs[st] = st < nst ? rc[st * p.rc_stride + r] : 0.0;
-            }
-            const uint64_t part = epart[o];
-            uint32_t X, T;
-            int nx, nt;
-            excitation_sets<NINT, NT>(B, S, part, ehm[o], &X, &nx, &T, &nt);
-            for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
-              const int cc = c - B.clo;
-              if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
-              int ro, so, x, y;
-              cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-              const int rcode = B.sa * norb + ro;
-              const int scode = B.sb * norb + so;
-              if constexpr (MS) {
-                const double v = (double)element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode);
-#pragma unroll
-                for (int st = 0; st < kMaxStates; st++)
-                  if (st < nst) atomicAdd(&A[st * mc + cc], cjs[st] * v);
-              } else {
-                unsigned long long l;
-                int hh;
-                fix_of(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode), F, l, hh);
-                fix_atomic_add(Alo, Ahi, cc, l, hh);
-              }
-              con++;
-            });
-          } else {
-            const int j0 = (jd - n1) * 32;
-            if (j0 >= n2) break;
-            const int j = j0 + lane;
-            if (j < n2) {
-              const int o = S.u.l.L2[j];
-            const int r = (int)(erec[o] & 0x7FFFFFFFu);
-              const uint64_t* Jw = rw + (size_t)r * NW;
-              const NT cj = (NT)rc[r];
-              double cjs[kMaxStates];
-              if constexpr (MS) {
-#pragma unroll
-                for (int st = 0; st < kMaxStates; st++) cjs[st] = st < nst ? rc[st * p.rc_stride + r] : 0.0;
-              }
-              const uint64_t part = epart[o];
-              uint32_t X, T;
-              int nx, nt;
-              excitation_sets<NINT, NT>(B, S, part, ehm[o], &X, &nx, &T, &nt);
-              for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
-                const int cc = c - B.clo;
-                if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
-                int ro, so, x, y;
-                cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-                const int rcode = B.sa * norb + ro;
-                const int scode = (B.h == 2) ? B.sb * norb + so : -1;
-                if constexpr (MS) {
-                  const double v = (double)element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode);
-#pragma unroll
-                  for (int st = 0; st < kMaxStates; st++)
-                    if (st < nst) atomicAdd(&A[st * mc + cc], cjs[st] * v);
-                } else {
-                  unsigned long long l;
-                  int hh;
-                  fix_of(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode), F, l, hh);
-                  fix_atomic_add(Alo, Ahi, cc, l, hh);
-                }
-                con++;
-              });
-            }
-          }
-        }
-      }
-      __syncthreads();
-    }
-
-    // ---- cells: the perturbers of I in this batch ----
-    if (GRAD) {  // loop 2 is over: the pair tables' storage takes the weights
-      for (int x = tid; x < kMaxOrb; x += kThreads) {
-        S.v.w.rowW2[x] = 0.0;
-        S.v.w.colW2[x] = 0.0;
-      }
-      __syncthreads();
-    }
-    if (p.k > 0) {
-      if (S.tkcnt + B.nct > p.cap) compact_selection<NINT, NT>(p, S, te, ta, tk);
-      if (tid == 0) {
-        const unsigned long long gt = *((volatile unsigned long long*)p.tau_bits);
-        if (gt > S.tau) S.tau = gt;
-      }
-      __syncthreads();
-    }
-    const unsigned long long tau = S.tau;
-    double acc_e = 0.0, acc_s2 = 0.0;
-    unsigned long long acc_na = 0, acc_d0 = 0, acc_d1 = 0, acc_min = 0x7FF0000000000000ull, acc_tiny = 0;
-    double acc_es[kMaxStates], acc_s2s[kMaxStates];  // multi-state form: sums per state
-#pragma unroll
-    for (int st = 0; st < kMaxStates; st++) acc_es[st] = acc_s2s[st] = 0.0;
-    if constexpr (MS) {
-      for (int cc = tid; cc < B.nct; cc += kThreads) {
-        if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
-        int ro, so, x, y;
-        cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
-        double vI = 0.0;  // <I|H|alpha> for the generator's own term
-        if (B.h == 2) {
-          const int a1 = S.iRow[x], b2 = S.iCol[y];
-          if (B.kind == 2) {
-            vI = (double)flip_sign(eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)], (a1 ^ b2) < 0);
-          } else {
-            const int a2 = S.iRow[y], b1 = S.iCol[x];
-            NT v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
-            const int lo = so < B.qb ? so : B.qb, hi = so < B.qb ? B.qb : so;
-            vI = (double)flip_sign(v, ((a1 ^ b2) < 0 ? 1 : 0) ^ ((ro > lo && ro < hi) ? 1 : 0));
-          }
-          con++;
-        }
-        // E0_s - H_aa = ((E0_s - base) - u0[x]) - rest, as the one-state form
-        double rest = 0.0;
-        if (B.kind == 2) rest = S.u1[y] + p.Jm[ro * norb + so];
-        else if (B.kind == 1) rest = S.u0[y] + (p.Jm[ro * norb + so] - p.Km[ro * norb + so]);
-        double crit = 0.0, a0 = 0.0;
-#pragma unroll
-        for (int st = 0; st < kMaxStates; st++) {
-          if (st >= nst) break;
-          const double a = A[st * mc + cc] + ms_cI[st] * vI;
-          double D = (p.st_e0[st] - S.base) - S.u0[x];
-          if (B.kind != 0) D -= rest;
-          const unsigned long long dex = ((unsigned long long)__double_as_longlong(D) >> 52) & 0x7FFull;
-          const double inv = (dex > 523ull && dex < 1523ull) ? recip_nr<2>(D) : 1.0 / D;
-          const double q = a * inv;
-          const double e = a * q;
-          acc_es[st] += e;
-          acc_s2s[st] += q * q;
-          crit += ms_w[st] * e;  // c_alpha,s A_s / max_I c_Is^2
-          const unsigned long long db = abs_bits(D);
-          acc_min = db < acc_min ? db : acc_min;
-          if (st == 0) a0 = a;
-        }
-        acc_na++;
-        if (abs_bits(a0) < 0x3D06849B86A12B9Bull) acc_tiny++;
-        uint64_t key[NW];
-        const int kwr = B.sa * NINT + (ro >> 6), kws = (B.h == 2) ? B.sb * NINT + (so >> 6) : -1;
-#pragma unroll
-        for (int w = 0; w < NW; w++)
-          key[w] = S.kbase[w] | (w == kwr ? 1ull << (ro & 63) : 0ull) | (w == kws ? 1ull << (so & 63) : 0ull);
-        uint64_t hk = 0;
-#pragma unroll
-        for (int w = 0; w < NW; w++) hk = splitmix64(hk ^ key[w]);
-        acc_d0 += hk;
-        acc_d1 ^= splitmix64(hk ^ 0x243F6A8885A308D3ull);
-        if (p.k > 0) {
-          const unsigned long long eb = abs_bits(crit);
-          if (eb >= tau) {
-            atomicAdd(&p.sel_hist[sel_bin(eb)], 1u);
-            const int pos = atomicAdd(&S.tkcnt, 1);
-            te[pos] = crit;
-            ta[pos] = a0;
-#pragma unroll
-            for (int w = 0; w < NW; w++) tk[(size_t)pos * NW + w] = key[w];
-          }
-        }
-      }
-      acc_e = acc_es[0];
-      acc_s2 = acc_s2s[0];
-    } else {
-      for (int cc = tid; cc < B.nct; cc += kThreads) {
-        if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
-        int ro, so, x, y;
-        cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
-        double a = fix_to_double(Alo[cc], Ahi[cc], F);
-        if (B.h == 2) {  // the generator's own term c_I <I|H|alpha>
-          NT v;
-          const int a1 = S.iRow[x], b2 = S.iCol[y];
-          if (B.kind == 2) {
-            v = flip_sign(eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)], (a1 ^ b2) < 0);
-          } else {
-            const int a2 = S.iRow[y], b1 = S.iCol[x];
-            v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
-            const int lo = so < B.qb ? so : B.qb, hi = so < B.qb ? B.qb : so;
-            v = flip_sign(v, ((a1 ^ b2) < 0 ? 1 : 0) ^ ((ro > lo && ro < hi) ? 1 : 0));
-          }
-          a += (double)(S.cI * v);
-          con++;
-        }
-        // D = E0 - H_aa from the per-batch row sums
-        double D = S.dx[x];
-        if (B.kind == 2) D -= S.u1[y] + p.Jm[ro * norb + so];
-        else if (B.kind == 1) D -= S.u0[y] + (p.Jm[ro * norb + so] - p.Km[ro * norb + so]);
-        // |D| in [2^-500, 2^500]: Newton reciprocal; otherwise the division
-        const unsigned long long dex = ((unsigned long long)__double_as_longlong(D) >> 52) & 0x7FFull;
-        const double inv = (dex > 523ull && dex < 1523ull) ? recip_nr<sizeof(NT) == 8 ? 2 : 1>(D) : 1.0 / D;
-        const double q = a * inv;
-        acc_e = fma(a, q, acc_e);  // e = A q
-        acc_s2 += q * q;
-        acc_na++;
-        if (GRAD) {
-          // numerator weight 2A/D for loop 3; (A/D)^2 weights the diagonal
-          A[cc] = 2.0 * q;
-          const double w2 = q * q;
-          atomicAdd(&S.v.w.rowW2[x], w2);
-          if (B.kind == 2) atomicAdd(&S.v.w.colW2[y], w2);
-          if (B.kind == 1) atomicAdd(&S.v.w.rowW2[y], w2);
-          if (B.h == 2) w_grad(p, ro, B.sa, so, B.sb, w2);
-        }
-        // |a| < 1e-14, compared on the bit pattern (no FP64 compare)
-        if (abs_bits(a) < 0x3D06849B86A12B9Bull) acc_tiny++;
-        // |D| and |e| as bit patterns, off the FP64 pipe
-        const unsigned long long db = abs_bits(D);
-        acc_min = db < acc_min ? db : acc_min;
-        uint64_t key[NW];  // alpha's words; selects keep them in registers
-        const int kwr = B.sa * NINT + (ro >> 6), kws = (B.h == 2) ? B.sb * NINT + (so >> 6) : -1;
-  #pragma unroll
-        for (int w = 0; w < NW; w++)
-          key[w] = S.kbase[w] | (w == kwr ? 1ull << (ro & 63) : 0ull) | (w == kws ? 1ull << (so & 63) : 0ull);
-        uint64_t hk = 0;
-  #pragma unroll
-        for (int w = 0; w < NW; w++) hk = splitmix64(hk ^ key[w]);
-        acc_d0 += hk;
-        acc_d1 ^= splitmix64(hk ^ 0x243F6A8885A308D3ull);
-        // e = A q is formed only when it can reach the threshold: with biased
-        // exponents ea, eq of A and q, |A q| < 2^(ea + eq - 2044), so
-        // ea + eq <= et + 1021 (et: the exponent of tau) puts it below tau
-        const int ea = (int)(abs_bits(a) >> 52), eqx = (int)(abs_bits(q) >> 52);
-        if (p.k > 0 && (tau == 0ull || ea + eqx > (int)(tau >> 52) + 1021)) {
-          const double e = a * q;
-          const unsigned long long eb = abs_bits(e);
-          if (eb >= tau) {
-            atomicAdd(&p.sel_hist[sel_bin(eb)], 1u);
-            const int pos = atomicAdd(&S.tkcnt, 1);
-            te[pos] = e;
-            ta[pos] = a;
-  #pragma unroll
-            for (int w = 0; w < NW; w++) tk[(size_t)pos * NW + w] = key[w];
-          }
-        }
-      }
-    }
-    // ---- per-item reduction into the generator's totals ----
-    {
-      // FP64 sums through shared memory and one warp: a shuffle tree in every
-      // warp would spend five FP64 adds per lane per quantity
-      S.u.red_t[0][tid] = acc_e;
-      S.u.red_t[1][tid] = acc_s2;
-      const unsigned long long na = warp_sum_u(acc_na), nc = warp_sum_u(con), d0 = warp_sum_u(acc_d0);
-      const unsigned long long d1 = warp_xor_u(acc_d1), mn = warp_min_u(acc_min), tiny = warp_sum_u(acc_tiny);
-      if (lane == 0) {
-        S.red_u[warp][0] = na;
-        S.red_u[warp][1] = nc;
-        S.red_u[warp][2] = d0;
-        S.red_u[warp][3] = d1;
-        S.red_u[warp][4] = mn;
-        S.red_u[warp][5] = tiny;
-      }
-      __syncthreads();
-      double se = 0.0, ss = 0.0;
-      if (warp == 0) {
-        for (int i = lane; i < kThreads; i += 32) {
-          se += S.u.red_t[0][i];
-          ss += S.u.red_t[1][i];
-        }
-        se = warp_sum(se);
-        ss = warp_sum(ss);
-      }
-      if (tid == 0) {
-        const double te_ = se, ts = ss;
-        unsigned long long tn = 0, tc = 0, x0 = 0, x1 = 0, m = 0x7FF0000000000000ull, tt = 0;
-        for (int w = 0; w < kWarps; w++) {
-          tn += S.red_u[w][0];
-          tc += S.red_u[w][1];
-          x0 += S.red_u[w][2];
-          x1 ^= S.red_u[w][3];
-          m = S.red_u[w][4] < m ? S.red_u[w][4] : m;
-          tt += S.red_u[w][5];
-        }
-        S.sw2 = ts;
-        // the item's FP64 sums go to its own slot; the generator's eps_I
-        // and sum A^2/D^2 are reduced from the slots in item order after the
-        // wave (reduce_items_kernel), so they do not depend on which CTA
-        // finished first
-        double* its = p.it_sum + ((size_t)slot * nper + j) * p.it_stride;
-        its[0] = te_;
-        its[1] = ts;
-        if (tn) {
-          atomicAdd(&p.na[g], tn);
-          atomicAdd(&p.ncon[g], tc);
-          atomicAdd(&p.digest[0], x0);
-          atomicXor(&p.digest[1], x1);
-          atomicMin(p.min_den_bits, m);
-          if (tt) atomicAdd(p.n_tiny, tt);
-        }
-      }
-      if constexpr (MS) {  // the other states' eps and s2, one at a time
-#pragma unroll
-        for (int st = 1; st < kMaxStates; st++) {
-          if (st >= nst) break;
-          __syncthreads();
-          S.u.red_t[0][tid] = acc_es[st];
-          S.u.red_t[1][tid] = acc_s2s[st];
-          __syncthreads();
-          if (warp == 0) {
-            double ue = 0.0, us = 0.0;
-            for (int i = lane; i < kThreads; i += 32) {
-              ue += S.u.red_t[0][i];
-              us += S.u.red_t[1][i];
-            }
-            ue = warp_sum(ue);
-            us = warp_sum(us);
-            if (lane == 0) {
-              double* its = p.it_sum + ((size_t)slot * nper + j) * p.it_stride;
-              its[2 * st] = ue;
-              its[2 * st + 1] = us;
-            }
-          }
-        }
-      }
-    }
-    if (GRAD) {
-      __syncthreads();
-      // ---- loop 3: c_J (2A/D) d<J|H|alpha> over the same (J, cell) pairs ----
-      for (int c0 = 0; c0 < total; c0 += kChunk) {
-        if (tid == 0) {
-          S.n0 = 0;
-          S.n1 = 0;
-          S.n2 = 0;
-          S.cnext = 0;
-        }
-        __syncthreads();
-        const int c1 = min(c0 + kChunk, total);
-        for (int i = c0 + tid; i < c1; i += kThreads) {
-          const int o = entry(i);
-          if (erec[o] >> 31) continue;
-          const uint64_t hmr = ehm[o];
-          if (dup(i, hmr)) continue;
-          const int t = __popcll(hmr & ~B.hm);
-          if (t > 2) continue;
-          const bool all = (B.h == 1) ? (t <= 1) : (t == 0);
-          if (all) S.u.l.L0[atomicAdd(&S.n0, 1)] = o;
-          else if (t == 1) S.u.l.L1[atomicAdd(&S.n1, 1)] = o;
-          else if (subset_live<NINT, NT>(B, S, norb, epart[o], ban)) S.u.l.L2[atomicAdd(&S.n2, 1)] = o;
-        }
-        __syncthreads();
-        for (int j = 0; j < S.n0; j++) {
-          const int o = S.u.l.L0[j];
-          const int r = (int)(erec[o] & 0x7FFFFFFFu);
-          const uint64_t* Jw = rw + (size_t)r * NW;
-          const double cj = rc[r];
-          uint32_t X, T;
-          int nx, nt;
-          excitation_sets<NINT, NT>(B, S, epart[o], ehm[o], &X, &nx, &T, &nt);
-          for (int cc = tid; cc < B.nct; cc += kThreads) {
-            if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
-            int ro, so, x, y;
-            cell_orbitals<NINT, NT>(B, S, B.clo + cc, &ro, &so, &x, &y);
-            element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, (B.h == 2) ? B.sb * norb + so : -1, cj * A[cc]);
-          }
-        }
-        {  // row-reaching J (a warp each), then subset-reaching J (32 per draw), drawn dynamically
-          const int n1 = S.n1, n2 = S.n2;
-          for (;;) {
-            int jd = 0;
-            if (lane == 0) jd = atomicAdd(&S.cnext, 1);
-            jd = __shfl_sync(kFull, jd, 0);
-            if (jd < n1) {
-              const int j = jd;
-              const int o = S.u.l.L1[j];
-              const int r = (int)(erec[o] & 0x7FFFFFFFu);
-              const uint64_t* Jw = rw + (size_t)r * NW;
-              const double cj = rc[r];
-              const uint64_t part = epart[o];
-              uint32_t X, T;
-              int nx, nt;
-              excitation_sets<NINT, NT>(B, S, part, ehm[o], &X, &nx, &T, &nt);
-              for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
-                const int cc = c - B.clo;
-                if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
-                int ro, so, x, y;
-                cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-                element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, B.sb * norb + so, cj * A[cc]);
-              });
-            } else {
-              const int j0 = (jd - n1) * 32;
-              if (j0 >= n2) break;
-              const int j = j0 + lane;
-              if (j < n2) {
-                const int o = S.u.l.L2[j];
-                const int r = (int)(erec[o] & 0x7FFFFFFFu);
-                const uint64_t* Jw = rw + (size_t)r * NW;
-                const double cj = rc[r];
-                const uint64_t part = epart[o];
-                uint32_t X, T;
-                int nx, nt;
-                excitation_sets<NINT, NT>(B, S, part, ehm[o], &X, &nx, &T, &nt);
-                for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
-                  const int cc = c - B.clo;
-                  if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
-                  int ro, so, x, y;
-                  cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-                  element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, (B.h == 2) ? B.sb * norb + so : -1,
-                                     cj * A[cc]);
-                });
-              }
-            }
-          }
-        }
-        __syncthreads();
-      }
-      // ---- diagonal: H_aa = H_II - F(a) [- F(b) + W(a,b)] + F(r) [+ F(s)]
-      //      - W(r,a) [- W(r,b) - W(s,a) - W(s,b) + W(r,s)]; the W(r,s) terms
-      //      were scattered per cell, the rest goes by row sums ----
-      double* wF = p.g_wF + (size_t)g * 2 * norb;
-      const int s1 = B.sa, s2 = (B.h == 2) ? B.sb : B.sa;
-      for (int x = tid; x < S.nv[s1]; x += kThreads) {
-        const double wr = S.v.w.rowW2[x];
-        if (wr == 0.0) continue;
-        const int r = S.vir[s1][x];
-        atomicAdd(&wF[s1 * norb + r], wr);
-        w_grad(p, r, s1, B.qa, B.sa, -wr);
-        if (B.h == 2) w_grad(p, r, s1, B.qb, B.sb, -wr);
-      }
-      if (B.kind == 2)
-        for (int y = tid; y < S.nv[s2]; y += kThreads) {
-          const double wc = S.v.w.colW2[y];
-          if (wc == 0.0) continue;
-          const int sv = S.vir[s2][y];
-          atomicAdd(&wF[s2 * norb + sv], wc);
-          w_grad(p, sv, s2, B.qa, B.sa, -wc);
-          w_grad(p, sv, s2, B.qb, B.sb, -wc);
-        }
-      if (tid == 0 && S.sw2 != 0.0) {
-        const double sw = S.sw2;
-        atomicAdd(&p.g_wH[g], sw);
-        atomicAdd(&wF[B.sa * norb + B.qa], -sw);
-        if (B.h == 2) {
-          atomicAdd(&wF[B.sb * norb + B.qb], -sw);
-          w_grad(p, B.qa, B.sa, B.qb, B.sb, sw);
-        }
-      }
-    }
+    batch_item<NINT, NT, GRAD, MS>(p, S, item, F, te, ta, tk, E, eri_n, h_n);
   }
   if (p.k > 0 && p.last_wave) compact_selection<NINT, NT>(p, S, te, ta, tk);
   __syncthreads();
@@ -1997,6 +2084,143 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
     p.tk_cnt[blockIdx.x] = S.tkcnt;
     p.tk_tau[blockIdx.x] = S.tau;
   }
+}
+
+// The work items of one wave of several instances' sweeps (one word count
+// and precision) from one queue: instance after instance, in the order of
+// m.ps, `m.chunk` items per draw.  A CTA that moves to another instance
+// stores its selection state (candidate count and threshold) for the
+// instance it leaves, copies the parameters of the one it enters to shared
+// memory and loads that instance's state; the dynamic shared memory is sized
+// for the largest accumulator of the instances.  Every instance has its own
+// candidate buffers for each CTA of the launch; they are compacted to k
+// entries by compact_multi_kernel after the last wave.
+template <int NINT, typename NT>
+__global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_multi_kernel(const __grid_constant__ MultiWave m) {
+  constexpr int NW = 2 * NINT;
+  __shared__ BatchShared<NINT, NT> S;
+  __shared__ SweepParams Ps;
+  __shared__ int s_inst, s_cur;
+  __shared__ long long s_local;
+  const int tid = threadIdx.x;
+  const long long total = m.item_ofs[m.n];
+  if (tid == 0) {
+    s_cur = -1;
+    S.inext = S.iend = 0;
+    if (m.timeout_ns) atomicCAS(m.t_start, 0ull, global_ns());
+  }
+  int F = 0;
+  ItemEnv E{};
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      if (S.inext >= S.iend) {
+        const long long b0 = (long long)atomicAdd(m.queue, (unsigned long long)m.chunk);
+        S.inext = b0;
+        S.iend = b0 + m.chunk;
+      }
+      S.item = S.inext++;
+      if (m.timeout_ns && global_ns() - *((volatile unsigned long long*)m.t_start) > m.timeout_ns) {
+        atomicOr(m.err, 128);  // watchdog: stop taking work, report the timeout
+        S.item = total;
+      }
+      if (S.item < total) {
+        const int i = instance_of(m.item_ofs, m.n, S.item);
+        s_inst = i;
+        s_local = S.item - m.item_ofs[i];
+      }
+    }
+    __syncthreads();
+    if (S.item >= total) break;
+    const int inst = s_inst;
+    if (inst != s_cur) {
+      if (tid == 0 && s_cur >= 0) {
+        Ps.tk_cnt[blockIdx.x] = S.tkcnt;
+        Ps.tk_tau[blockIdx.x] = S.tau;
+      }
+      __syncthreads();
+      load_params(Ps, m.ps, inst);
+      __syncthreads();
+      if (tid == 0) {
+        s_cur = inst;
+        S.tkcnt = Ps.tk_cnt[blockIdx.x];
+        S.tau = Ps.tk_tau[blockIdx.x];
+        S.slot = -1;
+      }
+      F = fix_scale(Ps);
+      E = item_env<false>(Ps);
+      __syncthreads();
+    }
+    double* te = Ps.tk_e + (size_t)blockIdx.x * (size_t)Ps.cap;
+    double* ta = Ps.tk_a + (size_t)blockIdx.x * (size_t)Ps.cap;
+    uint64_t* tk = Ps.tk_key + (size_t)blockIdx.x * (size_t)Ps.cap * NW;
+    batch_item<NINT, NT, false, false>(Ps, S, s_local, F, te, ta, tk, E, numer_eri<NT>(Ps), numer_h<NT>(Ps));
+  }
+  __syncthreads();
+  if (tid == 0 && s_cur >= 0) {
+    Ps.tk_cnt[blockIdx.x] = S.tkcnt;
+    Ps.tk_tau[blockIdx.x] = S.tau;
+  }
+}
+
+// After the last wave: CTA buffer blockIdx.x of instance blockIdx.y keeps its
+// k best candidates (as the last wave of a single sweep does).
+template <int NINT, typename NT>
+__global__ void __launch_bounds__(kThreads) compact_multi_kernel(const SweepParams* __restrict__ ps) {
+  constexpr int NW = 2 * NINT;
+  __shared__ BatchShared<NINT, NT> S;
+  const SweepParams& p = ps[blockIdx.y];
+  if (p.k <= 0) return;
+  if (threadIdx.x == 0) {
+    S.tkcnt = p.tk_cnt[blockIdx.x];
+    S.tau = p.tk_tau[blockIdx.x];
+  }
+  compact_selection<NINT, NT>(p, S, p.tk_e + (size_t)blockIdx.x * (size_t)p.cap,
+                              p.tk_a + (size_t)blockIdx.x * (size_t)p.cap,
+                              p.tk_key + (size_t)blockIdx.x * (size_t)p.cap * NW);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    p.tk_cnt[blockIdx.x] = S.tkcnt;
+    p.tk_tau[blockIdx.x] = S.tau;
+  }
+}
+
+// Launch helpers of the multi-instance batch kernels, instantiated for FP64
+// in sweep.cu and for the mixed form in sweep_mixed.cu (the prep kernel is
+// launched from sweep.cu only).
+template <typename NT>
+static cudaError_t multi_wave_launch(int nint, const MultiWave& m, int total_slots, int grid, size_t smem,
+                                     cudaStream_t st) {
+  if (total_slots <= 0) return cudaSuccess;
+  if (nint == 1) {
+    cudaFuncSetAttribute(batch_multi_kernel<1, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    batch_multi_kernel<1, NT><<<grid, kThreads, smem, st>>>(m);
+  } else {
+    cudaFuncSetAttribute(batch_multi_kernel<2, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    batch_multi_kernel<2, NT><<<grid, kThreads, smem, st>>>(m);
+  }
+  return cudaGetLastError();
+}
+
+template <typename NT>
+static cudaError_t multi_compact_launch(int nint, const SweepParams* ps, int n, int grid, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (nint == 1) compact_multi_kernel<1, NT><<<dim3(grid, n), kThreads, 0, st>>>(ps);
+  else compact_multi_kernel<2, NT><<<dim3(grid, n), kThreads, 0, st>>>(ps);
+  return cudaGetLastError();
+}
+
+template <typename NT>
+static int multi_blocks_per_sm(int nint, size_t smem) {
+  int n = 0;
+  if (nint == 1) {
+    cudaFuncSetAttribute(batch_multi_kernel<1, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_multi_kernel<1, NT>, kThreads, smem);
+  } else {
+    cudaFuncSetAttribute(batch_multi_kernel<2, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_multi_kernel<2, NT>, kThreads, smem);
+  }
+  return n;
 }
 
 // Per generator: wH * dH_II + sum_{s,x} wF[s][x] * dF^I_s(x), with

@@ -18,6 +18,17 @@ cudaError_t launch_batch_mixed(int nint, const SweepParams& p, int grid, size_t 
   return cudaGetLastError();
 }
 
+cudaError_t launch_wave_multi_mixed(int nint, const MultiWave& m, int total_slots, int grid, size_t smem,
+                                    cudaStream_t st) {
+  return multi_wave_launch<float>(nint, m, total_slots, grid, smem, st);
+}
+
+cudaError_t launch_compact_multi_mixed(int nint, const SweepParams* ps, int n, int grid, cudaStream_t st) {
+  return multi_compact_launch<float>(nint, ps, n, grid, st);
+}
+
+int batch_multi_blocks_per_sm_mixed(int nint, size_t smem) { return multi_blocks_per_sm<float>(nint, smem); }
+
 int batch_blocks_per_sm_mixed(int nint, size_t smem) {
   int n = 0;
   if (nint == 1) {

@@ -30,6 +30,14 @@ not available; shapes follow the paper's CAS-sized active spaces):
         selection, Sec. "The basic algorithm") are run from them by the
         consumer.
 
+  cfg5seed: the seed spaces of the 64 batched instances
+        (``synthetic.batch_specs``: norb in {24, 32, 48, 64, 96}, 6..12
+        electrons per spin, N_det log-uniform in [1e3, 5e4], Cholesky rank
+        1.5 norb, seeds 1000 + i): per instance HF plus the N_det / 8 - 1
+        single and double substitutions of HF with the lowest diagonal
+        energy, ties by key.  As for cfg3seed, only the determinants are
+        stored and the consumer runs the three doublings.
+
 Files: ``<cfg>_psi0.npz`` (dets, coefs, e0 and metadata) and
 ``<cfg>_expected.npz`` (totals, per-generator arrays by rank, selection).
 """
@@ -59,7 +67,22 @@ CONFIGS = {
     # the seed space (N_det / 8) of the 128-orbital workload's CIPSI growth
     "cfg3seed": dict(norb=128, nalpha=14, nbeta=14, rank=192, seed=2, ndet=12500, final_ndet=100000,
                      doublings=3, grow=False, instance="cfg3seed"),
+    # the seed spaces (N_det / 8 each) of the 64 batched instances
+    "cfg5seed": dict(n=64, seed0=1000, doublings=3, grow=False, instance="cfg5seed"),
 }
+
+
+def make_cfg5seed(name, cfg):
+    t0 = time.time()
+    specs = S.batch_specs(cfg["n"], cfg["seed0"])
+    out = {}
+    for i, sp in enumerate(specs):
+        h, eri = S.hamiltonian_fast(sp["norb"], sp["rank"], sp["seed"])
+        ham = oracle.Hamiltonian(sp["norb"], sp["nalpha"], sp["nbeta"], h, eri)
+        hf = S.hf_det(sp["norb"], sp["nalpha"], sp["nbeta"])
+        out[f"dets_{i}"] = psi0.seed_space(ham, hf, sp["ndet"] // 2 ** cfg["doublings"])
+    log(f"{name}: {len(specs)} seed spaces, {sum(len(v) for v in out.values())} dets in {time.time() - t0:.1f}s")
+    np.savez_compressed(os.path.join(HERE, f"{name}.npz"), meta=json.dumps(dict(cfg, specs=specs)), **out)
 
 
 def make_cfg3r(name, cfg):
@@ -99,6 +122,8 @@ def make(name, mem_budget=12 << 30):
         return make_cfg3r(name, cfg)
     if cfg.get("instance") == "cfg3seed":
         return make_cfg3seed(name, cfg)
+    if cfg.get("instance") == "cfg5seed":
+        return make_cfg5seed(name, cfg)
     t0 = time.time()
     h, eri = S.hamiltonian(cfg["norb"], cfg["rank"], cfg["seed"])
     ham = oracle.Hamiltonian(cfg["norb"], cfg["nalpha"], cfg["nbeta"], h, eri)
