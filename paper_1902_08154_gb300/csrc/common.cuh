@@ -208,6 +208,21 @@ struct SweepParams {
   double* g_wH;                  // [ndet]           weight of dH_II per generator rank
 };
 
+// The batch kernel's view of one wave of several instances: the pieces'
+// parameters travel inside the kernel's parameters (constant bank, read-only
+// and uncontended like a single sweep's), at most kMaxPieces per wave.
+constexpr int kMaxPieces = 16;
+struct MultiWaveInline {
+  SweepParams ps[kMaxPieces];
+  long long item_ofs[kMaxPieces + 1];
+  int n;
+  int chunk;                   // work items per draw from the shared queue
+  unsigned long long* queue;   // the wave's item counter
+  unsigned long long timeout_ns;
+  unsigned long long* t_start;
+  int* err;                    // flag 128: the watchdog stopped the launch
+};
+
 // One wave of several instances' sweeps in one launch: ps[i] holds instance
 // i's parameters for the wave; slot_ofs / item_ofs number the instances'
 // generator slots / work items one instance after the other.

@@ -30,8 +30,8 @@ int batch_blocks_per_sm_states(int nint, size_t smem);
 cudaError_t launch_batch_states(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_reduce_items(const SweepParams& p, cudaStream_t st);
 cudaError_t launch_reduce_items_multi(const SweepParams* ps, int n, int max_slots, cudaStream_t st);
-cudaError_t launch_wave_multi(int nint, int mixed, const MultiWave& m, int total_slots, int grid, size_t smem,
-                              cudaStream_t st);
+cudaError_t launch_wave_multi(int nint, int mixed, const MultiWave& m, const MultiWaveInline& mi, int total_slots,
+                              int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_compact_multi(int nint, int mixed, const SweepParams* ps, int n, int grid, cudaStream_t st);
 int batch_multi_blocks_per_sm(int nint, int mixed, size_t smem);
 }  // namespace qp
@@ -1362,10 +1362,14 @@ struct FusedGroup {
   int nint = 1, mixed = 0;
   std::vector<int> members;  // instance indices, largest work items first
   int grid = 0, nwaves = 0, chunk = 1;
+  int npw = 0;  // the most pieces in a wave (row length of the tables)
   size_t smem = 0;
   unsigned long long timeout_ns = 0;
-  std::vector<int> nact, slots, max_slots;  // per wave
-  SweepParams* d_ps = nullptr;    // [nwaves + 1][nm]: the wave's active instances; row nwaves: all members
+  std::vector<int> nact, slots, max_slots;  // per wave: pieces, slots, most slots of a piece
+  void* pool = nullptr;           // the waves' records and buckets, laid out per wave
+  std::vector<SweepParams> hps;   // host copy of the wave rows of d_ps
+  std::vector<long long> hitem;   // host copy of d_item_ofs
+  SweepParams* d_ps = nullptr;    // [nwaves + 1][nm]: the wave's pieces; row nwaves: all members
   int* d_slot_ofs = nullptr;      // [nwaves][nm + 1]
   long long* d_item_ofs = nullptr;  // [nwaves][nm + 1]
   unsigned long long* d_words = nullptr;  // [nwaves] item counters, then the watchdog's start time
@@ -1395,7 +1399,7 @@ static size_t inst_slot_bytes(const BatchInst& b) {
 
 // Workspaces of instance b: W slots per wave (W_fixed > 0) or as many as
 // wave_budget bytes hold.
-static int plan_instance(BatchInst& b, size_t wave_budget, int64_t W_fixed) {
+static int plan_instance(BatchInst& b, size_t wave_budget, int64_t W_fixed, bool pooled = false) {
   qp_pt2_ctx* x = b.x;
   const int nint = x->nint, nw = 2 * nint;
   const size_t nd = (size_t)b.ndet;
@@ -1426,14 +1430,19 @@ static int plan_instance(BatchInst& b, size_t wave_budget, int64_t W_fixed) {
       (rc = x->hidx2.grow(4 * nd)) || (rc = x->rkey.grow(8 * nd)) || (rc = x->rkey2.grow(8 * nd)) ||
       (rc = x->order.grow(4 * nd)) || (rc = x->rank_of.grow(4 * nd)) || (rc = x->acc.grow(8 * kAccWords)) ||
       (rc = x->cub_tmp.grow(b.tmp1)) || (rc = x->cub_tmp2.grow(b.tmp2 + 256)) || (rc = x->eps.grow(8 * nd)) ||
-      (rc = x->s2.grow(8 * nd)) || (rc = x->na.grow(8 * nd)) || (rc = x->ncon.grow(8 * nd)) ||
-      (rc = x->meta.grow(sizeof(GenMeta) * ws)) || (rc = x->r_words.grow(8 * nd * nw * ws)) ||
+      (rc = x->s2.grow(8 * nd)) || (rc = x->na.grow(8 * nd)) || (rc = x->ncon.grow(8 * nd)))
+    return rc;
+  // the wave's per-slot records and buckets: the instance's own (pooled: in
+  // the batch's pool, laid out per wave)
+  if (!pooled &&
+      ((rc = x->meta.grow(sizeof(GenMeta) * ws)) || (rc = x->r_words.grow(8 * nd * nw * ws)) ||
       (rc = x->r_coef.grow(8 * nd * ws)) || (rc = x->r_hmask.grow(8 * nd * ws)) ||
       (rc = x->r_part.grow(8 * nd * ws)) || (rc = x->r_flag.grow(4 * nd * ws)) ||
       (rc = x->b_ofs.grow(4 * (size_t)(x->nbat + 2) * ws)) || (rc = x->e_hm.grow(8 * (size_t)b.ent_cap * ws)) ||
       (rc = x->e_part.grow(8 * (size_t)b.ent_cap * ws)) || (rc = x->e_rec.grow(4 * (size_t)b.ent_cap * ws)) ||
-      (rc = x->it_sum.grow(16 * (size_t)nper * ws)) ||
-      (rc = x->b_dead.grow(4 * dwords * ws)) || (rc = x->queues.grow(4 * (size_t)(b.nwaves + 1))) ||
+      (rc = x->it_sum.grow(16 * (size_t)nper * ws)) || (rc = x->b_dead.grow(4 * dwords * ws))))
+    return rc;
+  if ((rc = x->queues.grow(4 * (size_t)(b.nwaves + 1))) ||
       (rc = x->tk_e.grow(8 * (size_t)b.cap * grid)) || (rc = x->tk_a.grow(8 * (size_t)b.cap * grid)) ||
       (rc = x->tk_key.grow(8 * (size_t)b.cap * grid * nw)) || (rc = x->tk_cnt.grow(4 * (size_t)grid)) ||
       (rc = x->tk_tau.grow(8 * (size_t)grid)) || (rc = x->res.grow(sizeof(DevResult))) ||
@@ -1549,9 +1558,6 @@ static int enqueue_pre(BatchInst& b, cudaStream_t st) {
   CUDA_TRY(cudaMemsetAsync(x->queues.p, 0, 4 * (size_t)(b.nwaves + 1), st));
   CUDA_TRY(cudaMemsetAsync(x->tk_cnt.p, 0, 4 * (size_t)b.grid, st));
   CUDA_TRY(cudaMemsetAsync(x->tk_tau.p, 0, 8 * (size_t)b.grid, st));
-  // the per-item slots of the first wave (the multi-instance reduction
-  // clears them for the next one)
-  CUDA_TRY(cudaMemsetAsync(x->it_sum.p, 0, 16 * (size_t)b.nper * (size_t)b.W, st));
   return QP_OK;
 }
 
@@ -1564,8 +1570,7 @@ static int enqueue_waves(BatchInst& b, cudaStream_t st) {
     p.wave_slots = (int)((b.ngen - w * b.W) < b.W ? (b.ngen - w * b.W) : b.W);
     p.last_wave = (w == b.nwaves - 1);
     p.queue = x->queues.as<int>() + w;
-    CUDA_TRY(cudaMemsetAsync(p.it_sum, 0, sizeof(double) * (size_t)p.wave_slots * p.nper * p.it_stride, st));
-    CUDA_TRY(launch_prep(x->nint, p, p.wave_slots, st));
+    CUDA_TRY(launch_prep(x->nint, p, p.wave_slots, st));  // it zeroes the wave's per-item sums
     CUDA_TRY(launch_batch(x->nint, p, b.grid, b.smem, st));
     CUDA_TRY(launch_reduce_items(p, st));
   }
@@ -1611,10 +1616,14 @@ static int enqueue_post(BatchInst& b, cudaStream_t st) {
   return QP_OK;
 }
 
-// Fused form: group the instances by word count and precision, size their
-// waves together (the same number of waves for all, wave_budget bytes of
-// records and buckets per wave over all instances), and write each group's
-// per-wave tables of parameters and slot / item offsets to the device.
+// Fused form: group the instances by word count and precision.  A group's
+// waves are filled with pieces (instance, run of generator slots) taken
+// instance after instance, each wave holding at most its share of
+// wave_budget bytes of records and buckets, so that a wave holds one or a few
+// instances (their integrals stay in L2 while the wave runs).  The pieces'
+// records and buckets live in one pool per group, laid out per wave; each
+// group's per-wave tables of parameters and slot / item offsets are written
+// to the device.
 static int plan_fused(qp_pt2_batch* B, const qp_pt2_batch_options& o, size_t wave_budget) {
   const int n = (int)B->inst.size();
   for (int i = 0; i < n; i++) {
@@ -1634,8 +1643,7 @@ static int plan_fused(qp_pt2_batch* B, const qp_pt2_batch_options& o, size_t wav
   }
   double total = 0.0;
   for (auto& b : B->inst) total += (double)inst_slot_bytes(b) * (double)b.ngen;
-  int64_t R = (int64_t)std::ceil(total / (double)wave_budget);
-  if (R < 1) R = 1;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   for (auto& G : B->groups) {
     qp_pt2_ctx* x0 = B->inst[G.members[0]].x;
     G.smem = 0;
@@ -1645,54 +1653,111 @@ static int plan_fused(qp_pt2_batch* B, const qp_pt2_batch_options& o, size_t wav
     if (o.blocks_per_sm > 0 && o.blocks_per_sm < bps) bps = o.blocks_per_sm;
     G.grid = bps * x0->nsm;
     G.chunk = o.work_chunk > 0 ? o.work_chunk : 1;
-    // the instance with the largest work items first: the queue's tail is made
-    // of the smallest items
+    // the instance with the largest work items first: a wave's queue ends
+    // with the smallest items
     std::stable_sort(G.members.begin(), G.members.end(), [&](int a, int c) {
       const BatchInst &ba = B->inst[a], &bc = B->inst[c];
       return ba.max_cells != bc.max_cells ? ba.max_cells > bc.max_cells : ba.ndet > bc.ndet;
     });
-    G.nwaves = 0;
+    double gtot = 0.0;
+    for (int i : G.members) gtot += (double)inst_slot_bytes(B->inst[i]) * (double)B->inst[i].ngen;
+    const size_t budget = (size_t)((double)wave_budget * gtot / total);  // this group's share
+    // pieces: (wave, instance, first slot, slots, pool offset)
+    struct Piece {
+      int wave, inst;
+      int64_t start, slots;
+      size_t off;
+    };
+    std::vector<Piece> pieces;
     G.timeout_ns = 0;
+    int wave = 0, inwave = 0;
+    size_t used = 0, pool_bytes = 0;
     for (int i : G.members) {
       BatchInst& b = B->inst[i];
       b.grid = G.grid;
-      const int64_t W = (b.ndet + R - 1) / R;
-      int rc = plan_instance(b, 0, W);
+      const size_t per = inst_slot_bytes(b) + 12 * 256;  // a slot and the alignment of its arrays
+      int64_t start = 0;
+      while (start < b.ngen) {
+        int64_t fit = (int64_t)((budget > used ? budget - used : 0) / per);
+        if ((fit < 1 && used > 0) || inwave == kMaxPieces) {  // the wave is full: start the next one
+          wave++;
+          used = 0;
+          inwave = 0;
+          continue;
+        }
+        if (fit < 1) fit = 1;
+        const int64_t take = std::min(fit, b.ngen - start);
+        pieces.push_back({wave, i, start, take, used});
+        used += al(per * (size_t)take);
+        pool_bytes = std::max(pool_bytes, used);
+        start += take;
+        inwave++;
+      }
+      int64_t wmax = 1;  // the instance's largest piece
+      for (const Piece& q : pieces)
+        if (q.inst == i) wmax = std::max(wmax, q.slots);
+      int rc = plan_instance(b, 0, wmax, true);
       if (rc) return rc;
       make_params(b);
-      G.nwaves = std::max(G.nwaves, (int)b.nwaves);
       const unsigned long long t = b.p.timeout_ns;
       if (t && (G.timeout_ns == 0 || t < G.timeout_ns)) G.timeout_ns = t;
     }
+    G.nwaves = wave + 1;
+    if (cudaMalloc(&G.pool, pool_bytes) != cudaSuccess)
+      return fail(QP_ENOMEM, "device allocation of the batch's wave pool failed");
     const int nm = (int)G.members.size();
-    std::vector<SweepParams> hp((size_t)(G.nwaves + 1) * nm);
-    std::vector<int> hs((size_t)G.nwaves * (nm + 1), 0);
-    std::vector<long long> hi((size_t)G.nwaves * (nm + 1), 0);
+    int maxp = 0;  // the most pieces in a wave
+    {
+      std::vector<int> cnt(G.nwaves, 0);
+      for (const Piece& q : pieces) maxp = std::max(maxp, ++cnt[q.wave]);
+    }
+    G.npw = maxp;
+    std::vector<SweepParams> hp((size_t)G.nwaves * maxp + nm);
+    std::vector<int> hs((size_t)G.nwaves * (maxp + 1), 0);
+    std::vector<long long> hi((size_t)G.nwaves * (maxp + 1), 0);
     G.nact.assign(G.nwaves, 0);
     G.slots.assign(G.nwaves, 0);
     G.max_slots.assign(G.nwaves, 0);
-    for (int r = 0; r < G.nwaves; r++) {
-      int a = 0;
-      int* so = hs.data() + (size_t)r * (nm + 1);
-      long long* io = hi.data() + (size_t)r * (nm + 1);
-      for (int i : G.members) {
-        const BatchInst& b = B->inst[i];
-        if (r >= b.nwaves) continue;
-        SweepParams p = b.p;
-        p.wave_start = (int)(r * b.W);
-        p.wave_slots = (int)std::min<int64_t>(b.W, b.ngen - r * b.W);
-        p.last_wave = 0;  // compact_multi_kernel keeps the k best after the last wave
-        p.queue = nullptr;
-        hp[(size_t)r * nm + a] = p;
-        so[a + 1] = so[a] + p.wave_slots;
-        io[a + 1] = io[a] + (long long)p.wave_slots * p.nper;
-        G.max_slots[r] = std::max(G.max_slots[r], p.wave_slots);
-        a++;
-      }
-      G.nact[r] = a;
-      G.slots[r] = so[a];
+    unsigned char* base = static_cast<unsigned char*>(G.pool);
+    for (const Piece& q : pieces) {
+      const BatchInst& b = B->inst[q.inst];
+      const qp_pt2_ctx* x = b.x;
+      const size_t nd = (size_t)b.ndet, ws = (size_t)q.slots, nw = 2 * (size_t)x->nint;
+      SweepParams p = b.p;
+      unsigned char* c = base + q.off;
+      auto take = [&](size_t bytes) {
+        unsigned char* r = c;
+        c += al(bytes);
+        return r;
+      };
+      p.meta = reinterpret_cast<GenMeta*>(take(sizeof(GenMeta) * ws));
+      p.r_words = reinterpret_cast<uint64_t*>(take(8 * nd * nw * ws));
+      p.r_coef = reinterpret_cast<double*>(take(8 * nd * ws));
+      p.r_hmask = reinterpret_cast<uint64_t*>(take(8 * nd * ws));
+      p.r_part = reinterpret_cast<uint64_t*>(take(8 * nd * ws));
+      p.r_flag = reinterpret_cast<uint32_t*>(take(4 * nd * ws));
+      p.b_ofs = reinterpret_cast<int*>(take(4 * (size_t)(x->nbat + 2) * ws));
+      p.e_hm = reinterpret_cast<uint64_t*>(take(8 * (size_t)b.ent_cap * ws));
+      p.e_part = reinterpret_cast<uint64_t*>(take(8 * (size_t)b.ent_cap * ws));
+      p.e_rec = reinterpret_cast<uint32_t*>(take(4 * (size_t)b.ent_cap * ws));
+      p.b_dead = reinterpret_cast<uint32_t*>(take(4 * (size_t)((x->nbat + 31) / 32) * ws));
+      p.it_sum = reinterpret_cast<double*>(take(16 * (size_t)b.nper * ws));
+      p.wave_start = (int)q.start;
+      p.wave_slots = (int)q.slots;
+      p.last_wave = 0;  // compact_multi_kernel keeps the k best after the last wave
+      p.queue = nullptr;
+      const int r = q.wave, a = G.nact[r]++;
+      hp[(size_t)r * maxp + a] = p;
+      int* so = hs.data() + (size_t)r * (maxp + 1);
+      long long* io = hi.data() + (size_t)r * (maxp + 1);
+      so[a + 1] = so[a] + p.wave_slots;
+      io[a + 1] = io[a] + (long long)p.wave_slots * p.nper;
+      G.slots[r] = so[a + 1];
+      G.max_slots[r] = std::max(G.max_slots[r], p.wave_slots);
     }
-    for (int m = 0; m < nm; m++) hp[(size_t)G.nwaves * nm + m] = B->inst[G.members[m]].p;
+    for (int m = 0; m < nm; m++) hp[(size_t)G.nwaves * maxp + m] = B->inst[G.members[m]].p;
+    G.hps = hp;
+    G.hitem = hi;
     if (cudaMalloc(&G.d_ps, sizeof(SweepParams) * hp.size()) != cudaSuccess ||
         cudaMalloc(&G.d_slot_ofs, sizeof(int) * hs.size()) != cudaSuccess ||
         cudaMalloc(&G.d_item_ofs, sizeof(long long) * hi.size()) != cudaSuccess ||
@@ -1715,24 +1780,33 @@ static int plan_fused(qp_pt2_batch* B, const qp_pt2_batch_options& o, size_t wav
 // all active instances and the per-generator reduction; then the compaction
 // of the candidate buffers.
 static int enqueue_group(FusedGroup& G) {
-  const int nm = (int)G.members.size();
+  const int nm = (int)G.members.size(), np = G.npw;
   CUDA_TRY(cudaMemsetAsync(G.d_words, 0, sizeof(unsigned long long) * (G.nwaves + 1), G.st));
   CUDA_TRY(cudaMemsetAsync(G.d_err, 0, sizeof(int), G.st));
   for (int r = 0; r < G.nwaves; r++) {
     MultiWave m{};
-    m.ps = G.d_ps + (size_t)r * nm;
-    m.slot_ofs = G.d_slot_ofs + (size_t)r * (nm + 1);
-    m.item_ofs = G.d_item_ofs + (size_t)r * (nm + 1);
+    m.ps = G.d_ps + (size_t)r * np;
+    m.slot_ofs = G.d_slot_ofs + (size_t)r * (np + 1);
+    m.item_ofs = G.d_item_ofs + (size_t)r * (np + 1);
     m.n = G.nact[r];
     m.chunk = G.chunk;
     m.queue = G.d_words + r;
     m.timeout_ns = G.timeout_ns;
     m.t_start = G.d_words + G.nwaves;
     m.err = G.d_err;
-    CUDA_TRY(launch_wave_multi(G.nint, G.mixed, m, G.slots[r], G.grid, G.smem, G.st));
+    MultiWaveInline mi{};
+    for (int a = 0; a < G.nact[r]; a++) mi.ps[a] = G.hps[(size_t)r * np + a];
+    for (int a = 0; a <= G.nact[r]; a++) mi.item_ofs[a] = G.hitem[(size_t)r * (np + 1) + a];
+    mi.n = m.n;
+    mi.chunk = m.chunk;
+    mi.queue = m.queue;
+    mi.timeout_ns = m.timeout_ns;
+    mi.t_start = m.t_start;
+    mi.err = m.err;
+    CUDA_TRY(launch_wave_multi(G.nint, G.mixed, m, mi, G.slots[r], G.grid, G.smem, G.st));
     CUDA_TRY(launch_reduce_items_multi(m.ps, G.nact[r], G.max_slots[r], G.st));
   }
-  CUDA_TRY(launch_compact_multi(G.nint, G.mixed, G.d_ps + (size_t)G.nwaves * nm, nm, G.grid, G.st));
+  CUDA_TRY(launch_compact_multi(G.nint, G.mixed, G.d_ps + (size_t)G.nwaves * np, nm, G.grid, G.st));
   return QP_OK;
 }
 
@@ -1949,6 +2023,7 @@ extern "C" void qp_pt2_batch_destroy(qp_pt2_batch* B) {
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
   for (auto& G : B->groups) {
+    if (G.pool) cudaFree(G.pool);
     if (G.d_ps) cudaFree(G.d_ps);
     if (G.d_slot_ofs) cudaFree(G.d_slot_ofs);
     if (G.d_item_ofs) cudaFree(G.d_item_ofs);

@@ -8,18 +8,15 @@ namespace qp {
 // Per generator of the wave and per state: eps_I and sum A^2/D^2 from the
 // items' slots, added in item order with Neumaier's compensation, so that
 // they are the same bits on every run and every grid size.
-// clear = true: each item's slot is set back to zero once read, so that the
-// next wave starts from zeros without a memset of its own.
-__device__ __forceinline__ void reduce_items(const SweepParams& p, const int t, const bool clear) {
+__device__ __forceinline__ void reduce_items(const SweepParams& p, const int t) {
   const int nst = p.nst > 1 ? p.nst : 1;
   if (t >= p.wave_slots * nst) return;
   const int slot = t / nst, st = t - slot * nst;
   const int g = p.meta[slot].g;
-  double* its = p.it_sum + (size_t)slot * p.nper * p.it_stride + 2 * st;
+  const double* its = p.it_sum + (size_t)slot * p.nper * p.it_stride + 2 * st;
   double se = 0.0, ce = 0.0, ss = 0.0, cs = 0.0;
   for (int j = 0; j < p.nper; j++) {
     const double ve = its[(size_t)j * p.it_stride], vs = its[(size_t)j * p.it_stride + 1];
-    if (clear) its[(size_t)j * p.it_stride] = its[(size_t)j * p.it_stride + 1] = 0.0;
     double u = se + ve;
     ce += (fabs(se) >= fabs(ve)) ? (se - u) + ve : (ve - u) + se;
     se = u;
@@ -33,12 +30,12 @@ __device__ __forceinline__ void reduce_items(const SweepParams& p, const int t, 
 }
 
 __global__ void reduce_items_kernel(const __grid_constant__ SweepParams p) {
-  reduce_items(p, blockIdx.x * blockDim.x + threadIdx.x, false);
+  reduce_items(p, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Instance blockIdx.y of a multi-instance wave.
 __global__ void reduce_items_multi_kernel(const SweepParams* __restrict__ ps) {
-  reduce_items(ps[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x, true);
+  reduce_items(ps[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 cudaError_t launch_reduce_items(const SweepParams& p, cudaStream_t st) {
@@ -54,19 +51,21 @@ cudaError_t launch_reduce_items_multi(const SweepParams* ps, int n, int max_slot
   return cudaGetLastError();
 }
 
-cudaError_t launch_wave_multi_mixed(int nint, const MultiWave& m, int total_slots, int grid, size_t smem,
+cudaError_t launch_wave_multi_mixed(int nint, const MultiWaveInline& m, int total_slots, int grid, size_t smem,
                                     cudaStream_t st);
 cudaError_t launch_compact_multi_mixed(int nint, const SweepParams* ps, int n, int grid, cudaStream_t st);
 int batch_multi_blocks_per_sm_mixed(int nint, size_t smem);
 
-// The prep and batch launches of one wave of several instances.
-cudaError_t launch_wave_multi(int nint, int mixed, const MultiWave& m, int total_slots, int grid, size_t smem,
-                              cudaStream_t st) {
+// The prep and batch launches of one wave of several instances: the prep
+// kernel reads the pieces' parameters from the device table m.ps, the batch
+// kernel from its own parameters mi.
+cudaError_t launch_wave_multi(int nint, int mixed, const MultiWave& m, const MultiWaveInline& mi, int total_slots,
+                              int grid, size_t smem, cudaStream_t st) {
   if (total_slots <= 0) return cudaSuccess;
   if (nint == 1) prep_multi_kernel<1><<<total_slots, kThreads, 0, st>>>(m);
   else prep_multi_kernel<2><<<total_slots, kThreads, 0, st>>>(m);
-  if (mixed) return launch_wave_multi_mixed(nint, m, total_slots, grid, smem, st);
-  return multi_wave_launch<double>(nint, m, total_slots, grid, smem, st);
+  if (mixed) return launch_wave_multi_mixed(nint, mi, total_slots, grid, smem, st);
+  return multi_wave_launch<double>(nint, mi, total_slots, grid, smem, st);
 }
 
 cudaError_t launch_compact_multi(int nint, int mixed, const SweepParams* ps, int n, int grid, cudaStream_t st) {

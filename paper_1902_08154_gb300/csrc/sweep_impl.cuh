@@ -325,6 +325,9 @@ __device__ __forceinline__ void prep_slot(const SweepParams& p, const int slot) 
   const int tid = threadIdx.x;
   const int norb = p.norb, nel = p.nel, nbat = p.nbat;
   GenMeta* M = p.meta + slot;
+  // the slot's per-item sums start from zero (an item that adds nothing
+  // does not write its sums)
+  for (int j = tid; j < p.nper * p.it_stride; j += kThreads) p.it_sum[(size_t)slot * p.nper * p.it_stride + j] = 0.0;
   const long long t = (long long)p.wave_start + slot;
   const long long gg = p.gen_list ? (long long)p.gen_list[t] : p.shard_index + t * (long long)p.shard_count;
   if (gg >= p.ndet) {
@@ -2096,21 +2099,19 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
 // candidate buffers for each CTA of the launch; they are compacted to k
 // entries by compact_multi_kernel after the last wave.
 template <int NINT, typename NT>
-__global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_multi_kernel(const __grid_constant__ MultiWave m) {
+__global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_multi_kernel(const __grid_constant__ MultiWaveInline m) {
   constexpr int NW = 2 * NINT;
   __shared__ BatchShared<NINT, NT> S;
-  __shared__ SweepParams Ps;
-  __shared__ int s_inst, s_cur;
+  __shared__ int s_inst;
   __shared__ long long s_local;
   const int tid = threadIdx.x;
   const long long total = m.item_ofs[m.n];
   if (tid == 0) {
-    s_cur = -1;
     S.inext = S.iend = 0;
     if (m.timeout_ns) atomicCAS(m.t_start, 0ull, global_ns());
   }
+  int cur = -1;  // the instance whose parameters and selection state the CTA holds
   int F = 0;
-  ItemEnv E{};
   for (;;) {
     __syncthreads();
     if (tid == 0) {
@@ -2133,33 +2134,32 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_multi_ker
     __syncthreads();
     if (S.item >= total) break;
     const int inst = s_inst;
-    if (inst != s_cur) {
-      if (tid == 0 && s_cur >= 0) {
-        Ps.tk_cnt[blockIdx.x] = S.tkcnt;
-        Ps.tk_tau[blockIdx.x] = S.tau;
-      }
-      __syncthreads();
-      load_params(Ps, m.ps, inst);
-      __syncthreads();
+    const SweepParams* pp = m.ps + inst;
+    if (inst != cur) {
       if (tid == 0) {
-        s_cur = inst;
-        S.tkcnt = Ps.tk_cnt[blockIdx.x];
-        S.tau = Ps.tk_tau[blockIdx.x];
+        if (cur >= 0) {
+          m.ps[cur].tk_cnt[blockIdx.x] = S.tkcnt;
+          m.ps[cur].tk_tau[blockIdx.x] = S.tau;
+        }
+        S.tkcnt = pp->tk_cnt[blockIdx.x];
+        S.tau = pp->tk_tau[blockIdx.x];
         S.slot = -1;
       }
-      F = fix_scale(Ps);
-      E = item_env<false>(Ps);
+      cur = inst;
+      F = fix_scale(*pp);
       __syncthreads();
     }
-    double* te = Ps.tk_e + (size_t)blockIdx.x * (size_t)Ps.cap;
-    double* ta = Ps.tk_a + (size_t)blockIdx.x * (size_t)Ps.cap;
-    uint64_t* tk = Ps.tk_key + (size_t)blockIdx.x * (size_t)Ps.cap * NW;
-    batch_item<NINT, NT, false, false>(Ps, S, s_local, F, te, ta, tk, E, numer_eri<NT>(Ps), numer_h<NT>(Ps));
+    const SweepParams& p = *pp;
+    double* te = p.tk_e + (size_t)blockIdx.x * (size_t)p.cap;
+    double* ta = p.tk_a + (size_t)blockIdx.x * (size_t)p.cap;
+    uint64_t* tk = p.tk_key + (size_t)blockIdx.x * (size_t)p.cap * NW;
+    batch_item<NINT, NT, false, false>(p, S, s_local, F, te, ta, tk, item_env<false>(p), numer_eri<NT>(p),
+                                       numer_h<NT>(p));
   }
   __syncthreads();
-  if (tid == 0 && s_cur >= 0) {
-    Ps.tk_cnt[blockIdx.x] = S.tkcnt;
-    Ps.tk_tau[blockIdx.x] = S.tau;
+  if (tid == 0 && cur >= 0) {
+    m.ps[cur].tk_cnt[blockIdx.x] = S.tkcnt;
+    m.ps[cur].tk_tau[blockIdx.x] = S.tau;
   }
 }
 
@@ -2189,7 +2189,7 @@ __global__ void __launch_bounds__(kThreads) compact_multi_kernel(const SweepPara
 // in sweep.cu and for the mixed form in sweep_mixed.cu (the prep kernel is
 // launched from sweep.cu only).
 template <typename NT>
-static cudaError_t multi_wave_launch(int nint, const MultiWave& m, int total_slots, int grid, size_t smem,
+static cudaError_t multi_wave_launch(int nint, const MultiWaveInline& m, int total_slots, int grid, size_t smem,
                                      cudaStream_t st) {
   if (total_slots <= 0) return cudaSuccess;
   if (nint == 1) {

@@ -18,7 +18,7 @@ cudaError_t launch_batch_mixed(int nint, const SweepParams& p, int grid, size_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_wave_multi_mixed(int nint, const MultiWave& m, int total_slots, int grid, size_t smem,
+cudaError_t launch_wave_multi_mixed(int nint, const MultiWaveInline& m, int total_slots, int grid, size_t smem,
                                     cudaStream_t st) {
   return multi_wave_launch<float>(nint, m, total_slots, grid, smem, st);
 }
