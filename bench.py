@@ -56,10 +56,11 @@ FP64_OPS_PER_PERTURBER_MIN = 9
 # 2 x 2 x nint XOR+POPC per pair test of the coarse filter (N_det per
 # generator).
 INT_OPS_PER_CONNECTION_PER_WORD = 15
-# DRAM bytes (read + write) of the sweep kernels over one sweep of the bench
-# workload, from one ncu capture of the current kernels (None when the
-# kernels have changed since the capture).
-TRAFFIC_BYTES_PER_SWEEP = None
+# DRAM bytes (read + write) of the sweep kernels (prep and batch, all four
+# waves) over one sweep of the bench workload, from one ncu capture of the
+# current kernels (dram__bytes_read.sum + dram__bytes_write.sum; None when
+# the kernels have changed since the capture).
+TRAFFIC_BYTES_PER_SWEEP = 19.628e9
 
 
 def load_workload(name=WORKLOAD):
