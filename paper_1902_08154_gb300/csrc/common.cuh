@@ -216,8 +216,8 @@ struct MultiWaveInline {
   SweepParams ps[kMaxPieces];
   long long item_ofs[kMaxPieces + 1];
   int n;
-  int chunk;                   // work items per draw from the shared queue
-  unsigned long long* queue;   // the wave's item counter
+  int chunk;                   // work items per draw from a piece's queue
+  unsigned long long* queue;   // [n] the pieces' item counters
   unsigned long long timeout_ns;
   unsigned long long* t_start;
   int* err;                    // flag 128: the watchdog stopped the launch
@@ -231,8 +231,8 @@ struct MultiWave {
   const int* slot_ofs;         // [n + 1]
   const long long* item_ofs;   // [n + 1]
   int n;
-  int chunk;                   // work items per draw from the shared queue
-  unsigned long long* queue;   // the wave's item counter
+  int chunk;                   // work items per draw (batch kernel)
+  unsigned long long* queue;   // the pieces' item counters (batch kernel)
   unsigned long long timeout_ns;
   unsigned long long* t_start;
   int* err;                    // flag 128: the watchdog stopped the launch

@@ -1372,7 +1372,7 @@ struct FusedGroup {
   SweepParams* d_ps = nullptr;    // [nwaves + 1][nm]: the wave's pieces; row nwaves: all members
   int* d_slot_ofs = nullptr;      // [nwaves][nm + 1]
   long long* d_item_ofs = nullptr;  // [nwaves][nm + 1]
-  unsigned long long* d_words = nullptr;  // [nwaves] item counters, then the watchdog's start time
+  unsigned long long* d_words = nullptr;  // [nwaves][npw] pieces' item counters, then the watchdog's start time
   int* d_err = nullptr;
   cudaStream_t st = nullptr;
   cudaEvent_t done = nullptr;
@@ -1761,7 +1761,7 @@ static int plan_fused(qp_pt2_batch* B, const qp_pt2_batch_options& o, size_t wav
     if (cudaMalloc(&G.d_ps, sizeof(SweepParams) * hp.size()) != cudaSuccess ||
         cudaMalloc(&G.d_slot_ofs, sizeof(int) * hs.size()) != cudaSuccess ||
         cudaMalloc(&G.d_item_ofs, sizeof(long long) * hi.size()) != cudaSuccess ||
-        cudaMalloc(&G.d_words, sizeof(unsigned long long) * (G.nwaves + 1)) != cudaSuccess ||
+        cudaMalloc(&G.d_words, sizeof(unsigned long long) * ((size_t)G.nwaves * maxp + 1)) != cudaSuccess ||
         cudaMalloc(&G.d_err, sizeof(int)) != cudaSuccess)
       return fail(QP_ENOMEM, "device allocation of the batch tables failed");
     if (cudaMemcpy(G.d_ps, hp.data(), sizeof(SweepParams) * hp.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1781,7 +1781,7 @@ static int plan_fused(qp_pt2_batch* B, const qp_pt2_batch_options& o, size_t wav
 // of the candidate buffers.
 static int enqueue_group(FusedGroup& G) {
   const int nm = (int)G.members.size(), np = G.npw;
-  CUDA_TRY(cudaMemsetAsync(G.d_words, 0, sizeof(unsigned long long) * (G.nwaves + 1), G.st));
+  CUDA_TRY(cudaMemsetAsync(G.d_words, 0, sizeof(unsigned long long) * ((size_t)G.nwaves * np + 1), G.st));
   CUDA_TRY(cudaMemsetAsync(G.d_err, 0, sizeof(int), G.st));
   for (int r = 0; r < G.nwaves; r++) {
     MultiWave m{};
@@ -1790,9 +1790,9 @@ static int enqueue_group(FusedGroup& G) {
     m.item_ofs = G.d_item_ofs + (size_t)r * (np + 1);
     m.n = G.nact[r];
     m.chunk = G.chunk;
-    m.queue = G.d_words + r;
+    m.queue = G.d_words + (size_t)r * np;  // one item counter per piece
     m.timeout_ns = G.timeout_ns;
-    m.t_start = G.d_words + G.nwaves;
+    m.t_start = G.d_words + (size_t)G.nwaves * np;
     m.err = G.d_err;
     MultiWaveInline mi{};
     for (int a = 0; a < G.nact[r]; a++) mi.ps[a] = G.hps[(size_t)r * np + a];

@@ -2090,76 +2090,66 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
 }
 
 // The work items of one wave of several instances' sweeps (one word count
-// and precision) from one queue: instance after instance, in the order of
-// m.ps, `m.chunk` items per draw.  A CTA that moves to another instance
+// and precision): the wave's pieces (instance, run of generator slots) one
+// after another, each piece's items from its own queue, `m.chunk` per draw.
+// A CTA moves to the next piece when the current one's queue is empty; it
 // stores its selection state (candidate count and threshold) for the
-// instance it leaves, copies the parameters of the one it enters to shared
-// memory and loads that instance's state; the dynamic shared memory is sized
-// for the largest accumulator of the instances.  Every instance has its own
-// candidate buffers for each CTA of the launch; they are compacted to k
-// entries by compact_multi_kernel after the last wave.
+// instance it leaves and loads the state of the one it enters.  The dynamic
+// shared memory is sized for the largest accumulator of the instances.
+// Every instance has its own candidate buffers for each CTA of the launch;
+// they are compacted to k entries by compact_multi_kernel after the last
+// wave.
 template <int NINT, typename NT>
 __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_multi_kernel(const __grid_constant__ MultiWaveInline m) {
   constexpr int NW = 2 * NINT;
   __shared__ BatchShared<NINT, NT> S;
-  __shared__ int s_inst;
-  __shared__ long long s_local;
   const int tid = threadIdx.x;
-  const long long total = m.item_ofs[m.n];
-  if (tid == 0) {
-    S.inext = S.iend = 0;
-    if (m.timeout_ns) atomicCAS(m.t_start, 0ull, global_ns());
-  }
-  int cur = -1;  // the instance whose parameters and selection state the CTA holds
-  int F = 0;
-  for (;;) {
+  if (tid == 0 && m.timeout_ns) atomicCAS(m.t_start, 0ull, global_ns());
+  bool stop = false;
+  // the pieces one after another, each from its own queue: the piece index
+  // is the same in every thread, so its parameters are read like a single
+  // sweep's
+#pragma unroll 1
+  for (int pc = 0; pc < m.n && !stop; pc++) {
+    const SweepParams& p = m.ps[pc];
+    const long long nitems = m.item_ofs[pc + 1] - m.item_ofs[pc];
     __syncthreads();
     if (tid == 0) {
-      if (S.inext >= S.iend) {
-        const long long b0 = (long long)atomicAdd(m.queue, (unsigned long long)m.chunk);
-        S.inext = b0;
-        S.iend = b0 + m.chunk;
-      }
-      S.item = S.inext++;
-      if (m.timeout_ns && global_ns() - *((volatile unsigned long long*)m.t_start) > m.timeout_ns) {
-        atomicOr(m.err, 128);  // watchdog: stop taking work, report the timeout
-        S.item = total;
-      }
-      if (S.item < total) {
-        const int i = instance_of(m.item_ofs, m.n, S.item);
-        s_inst = i;
-        s_local = S.item - m.item_ofs[i];
-      }
+      S.tkcnt = p.tk_cnt[blockIdx.x];
+      S.tau = p.tk_tau[blockIdx.x];
+      S.slot = -1;
+      S.inext = S.iend = 0;
     }
-    __syncthreads();
-    if (S.item >= total) break;
-    const int inst = s_inst;
-    const SweepParams* pp = m.ps + inst;
-    if (inst != cur) {
-      if (tid == 0) {
-        if (cur >= 0) {
-          m.ps[cur].tk_cnt[blockIdx.x] = S.tkcnt;
-          m.ps[cur].tk_tau[blockIdx.x] = S.tau;
-        }
-        S.tkcnt = pp->tk_cnt[blockIdx.x];
-        S.tau = pp->tk_tau[blockIdx.x];
-        S.slot = -1;
-      }
-      cur = inst;
-      F = fix_scale(*pp);
-      __syncthreads();
-    }
-    const SweepParams& p = *pp;
+    const int F = fix_scale(p);
+    const ItemEnv E = item_env<false>(p);
     double* te = p.tk_e + (size_t)blockIdx.x * (size_t)p.cap;
     double* ta = p.tk_a + (size_t)blockIdx.x * (size_t)p.cap;
     uint64_t* tk = p.tk_key + (size_t)blockIdx.x * (size_t)p.cap * NW;
-    batch_item<NINT, NT, false, false>(p, S, s_local, F, te, ta, tk, item_env<false>(p), numer_eri<NT>(p),
-                                       numer_h<NT>(p));
-  }
-  __syncthreads();
-  if (tid == 0 && cur >= 0) {
-    m.ps[cur].tk_cnt[blockIdx.x] = S.tkcnt;
-    m.ps[cur].tk_tau[blockIdx.x] = S.tau;
+    for (;;) {
+      __syncthreads();
+      if (tid == 0) {
+        if (S.inext >= S.iend) {
+          const long long b0 = (long long)atomicAdd(m.queue + pc, (unsigned long long)m.chunk);
+          S.inext = b0;
+          S.iend = b0 + m.chunk;
+        }
+        S.item = S.inext++;
+        if (m.timeout_ns && global_ns() - *((volatile unsigned long long*)m.t_start) > m.timeout_ns) {
+          atomicOr(m.err, 128);  // watchdog: stop taking work, report the timeout
+          S.item = -1;
+        }
+      }
+      __syncthreads();
+      const long long item = S.item;
+      if (item < 0) stop = true;
+      if (item < 0 || item >= nitems) break;
+      batch_item<NINT, NT, false, false>(p, S, item, F, te, ta, tk, E, numer_eri<NT>(p), numer_h<NT>(p));
+    }
+    __syncthreads();
+    if (tid == 0) {
+      p.tk_cnt[blockIdx.x] = S.tkcnt;
+      p.tk_tau[blockIdx.x] = S.tau;
+    }
   }
 }
 
