@@ -159,8 +159,7 @@ struct SweepParams {
   // bucket entries, self-contained so that the batch kernel classifies a
   // bucket by streaming it: the record's hole mask and particle codes, and
   // its index with the rank flag (rank(J) < rank(I)) in bit 31
-  uint64_t* e_hm;                 // [slots][ent_cap]
-  uint64_t* e_part;               // [slots][ent_cap]
+  ulonglong2* e_hp;               // [slots][ent_cap]: hole mask, particles (one 16-byte load)
   uint32_t* e_rec;                // [slots][ent_cap]
   uint32_t* b_dead;               // [slots][(nbat + 31) / 32]  batches banned as a whole
   int64_t ent_cap;

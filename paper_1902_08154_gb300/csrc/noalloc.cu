@@ -258,8 +258,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   uint64_t* r_part = cv.take<uint64_t>(nd * wsl);
   uint32_t* r_flag = cv.take<uint32_t>(nd * wsl);
   int* b_ofs = cv.take<int>((size_t)(nbat + 2) * wsl);
-  uint64_t* e_hm = cv.take<uint64_t>((size_t)ent_cap * wsl);
-  uint64_t* e_part = cv.take<uint64_t>((size_t)ent_cap * wsl);
+  ulonglong2* e_hp = cv.take<ulonglong2>((size_t)ent_cap * wsl);
   uint32_t* e_rec = cv.take<uint32_t>((size_t)ent_cap * wsl);
   double* it_sum = cv.take<double>((size_t)2 * nper * wsl);
   uint32_t* b_dead = cv.take<uint32_t>(dwords * wsl);
@@ -318,8 +317,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   p.hmax_bits = d_hmax;
   p.it_sum = it_sum;
   p.it_stride = 2;
-  p.e_hm = e_hm;
-  p.e_part = e_part;
+  p.e_hp = e_hp;
   p.e_rec = e_rec;
   p.ndet = ndet;
   p.dets = dets;

@@ -313,7 +313,7 @@ struct qp_pt2_ctx {
   // workspace
   Buf in_dets, in_coefs, hkey, hkey2, hidx, hidx2, rkey, rkey2, order, rank_of, cub_tmp;
   Buf eps, s2, na, ncon, acc, res;
-  Buf meta, r_words, r_coef, r_hmask, r_part, r_flag, b_ofs, e_hm, e_part, e_rec, b_dead, queues, it_sum;
+  Buf meta, r_words, r_coef, r_hmask, r_part, r_flag, b_ofs, e_hp, e_rec, b_dead, queues, it_sum;
   Buf tk_e, tk_a, tk_key, tk_cnt, tk_tau, sel_hist, gen_list, gen_out, st_cmax;
   Buf cand_e, cand_a, cand_key, skey, skey2, perm, perm2, cub_tmp2;
   Buf out_sel, out_e, out_num, out_eps, out_na, out_ncon, out_rank;
@@ -509,7 +509,7 @@ extern "C" void qp_pt2_destroy(qp_pt2_ctx* x) {
   Buf* all[] = {&x->in_dets, &x->in_coefs, &x->hkey, &x->hkey2, &x->hidx, &x->hidx2, &x->rkey, &x->rkey2,
                 &x->order, &x->rank_of, &x->cub_tmp, &x->eps, &x->s2, &x->na, &x->ncon, &x->acc,
                 &x->res, &x->meta, &x->r_words, &x->r_coef, &x->r_hmask, &x->r_part, &x->r_flag,
-                &x->b_ofs, &x->e_hm, &x->e_part, &x->e_rec, &x->it_sum, &x->b_dead, &x->queues, &x->tk_e, &x->tk_a, &x->tk_key, &x->tk_cnt, &x->tk_tau, &x->sel_hist, &x->gen_list, &x->gen_out, &x->cand_e, &x->cand_a, &x->cand_key, &x->skey,
+                &x->b_ofs, &x->e_hp, &x->e_rec, &x->it_sum, &x->b_dead, &x->queues, &x->tk_e, &x->tk_a, &x->tk_key, &x->tk_cnt, &x->tk_tau, &x->sel_hist, &x->gen_list, &x->gen_out, &x->cand_e, &x->cand_a, &x->cand_key, &x->skey,
                 &x->skey2, &x->perm, &x->perm2, &x->cub_tmp2, &x->out_sel, &x->out_e, &x->out_num,
                 &x->out_eps, &x->out_na, &x->out_ncon, &x->out_rank, &x->g_dh, &x->g_deri, &x->g_wF, &x->g_wH};
   for (Buf* b : all) b->release();
@@ -769,7 +769,7 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
       (rc = x->r_words.grow(8 * nd * nw * ws)) || (rc = x->r_coef.grow(8 * nd * ws * nsts)) ||
       (rc = x->r_hmask.grow(8 * nd * ws)) || (rc = x->r_part.grow(8 * nd * ws)) ||
       (rc = x->r_flag.grow(4 * nd * ws)) || (rc = x->b_ofs.grow(4 * (size_t)(x->nbat + 2) * ws)) ||
-      (rc = x->e_hm.grow(8 * (size_t)ent_cap * ws)) || (rc = x->e_part.grow(8 * (size_t)ent_cap * ws)) ||
+      (rc = x->e_hp.grow(16 * (size_t)ent_cap * ws)) ||
       (rc = x->e_rec.grow(4 * (size_t)ent_cap * ws)) || (rc = x->it_sum.grow(16 * (size_t)nper * nsts * ws)) ||
       (rc = x->b_dead.grow(4 * dwords * ws)) || (rc = x->queues.grow(4 * (size_t)(nwaves + 1))) ||
       (rc = x->tk_e.grow(8 * (size_t)cap * grid)) || (rc = x->tk_a.grow(8 * (size_t)cap * grid)) ||
@@ -800,8 +800,7 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   p.cmax_bits = acc + kAccCmax;
   p.it_sum = x->it_sum.as<double>();
   p.it_stride = 2;
-  p.e_hm = x->e_hm.as<uint64_t>();
-  p.e_part = x->e_part.as<uint64_t>();
+  p.e_hp = x->e_hp.as<ulonglong2>();
   p.e_rec = x->e_rec.as<uint32_t>();
   p.tgt_on = x->tgt_on;
   p.tgt_max_exc = x->tgt_max_exc;
@@ -1170,7 +1169,7 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
       (rc = x->r_words.grow(8 * nd * nw * wsl)) || (rc = x->r_coef.grow(8 * nd * wsl)) ||
       (rc = x->r_hmask.grow(8 * nd * wsl)) || (rc = x->r_part.grow(8 * nd * wsl)) ||
       (rc = x->r_flag.grow(4 * nd * wsl)) || (rc = x->b_ofs.grow(4 * (size_t)(x->nbat + 2) * wsl)) ||
-      (rc = x->e_hm.grow(8 * (size_t)ent_cap * wsl)) || (rc = x->e_part.grow(8 * (size_t)ent_cap * wsl)) ||
+      (rc = x->e_hp.grow(16 * (size_t)ent_cap * wsl)) ||
       (rc = x->e_rec.grow(4 * (size_t)ent_cap * wsl)) || (rc = x->it_sum.grow(16 * (size_t)nper * wsl)) ||
       (rc = x->b_dead.grow(4 * dwords * wsl)) ||
       (rc = x->queues.grow(4 * (size_t)(nwaves + 1))) || (rc = x->tk_cnt.grow(4 * (size_t)grid)) ||
@@ -1201,8 +1200,7 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
   p.cmax_bits = acc + kAccCmax;
   p.it_sum = x->it_sum.as<double>();
   p.it_stride = 2;
-  p.e_hm = x->e_hm.as<uint64_t>();
-  p.e_part = x->e_part.as<uint64_t>();
+  p.e_hp = x->e_hp.as<ulonglong2>();
   p.e_rec = x->e_rec.as<uint32_t>();
   p.tgt_on = x->tgt_on;
   p.tgt_max_exc = x->tgt_max_exc;
@@ -1438,8 +1436,8 @@ static int plan_instance(BatchInst& b, size_t wave_budget, int64_t W_fixed, bool
       ((rc = x->meta.grow(sizeof(GenMeta) * ws)) || (rc = x->r_words.grow(8 * nd * nw * ws)) ||
       (rc = x->r_coef.grow(8 * nd * ws)) || (rc = x->r_hmask.grow(8 * nd * ws)) ||
       (rc = x->r_part.grow(8 * nd * ws)) || (rc = x->r_flag.grow(4 * nd * ws)) ||
-      (rc = x->b_ofs.grow(4 * (size_t)(x->nbat + 2) * ws)) || (rc = x->e_hm.grow(8 * (size_t)b.ent_cap * ws)) ||
-      (rc = x->e_part.grow(8 * (size_t)b.ent_cap * ws)) || (rc = x->e_rec.grow(4 * (size_t)b.ent_cap * ws)) ||
+      (rc = x->b_ofs.grow(4 * (size_t)(x->nbat + 2) * ws)) || (rc = x->e_hp.grow(16 * (size_t)b.ent_cap * ws)) ||
+      (rc = x->e_rec.grow(4 * (size_t)b.ent_cap * ws)) ||
       (rc = x->it_sum.grow(16 * (size_t)nper * ws)) || (rc = x->b_dead.grow(4 * dwords * ws))))
     return rc;
   if ((rc = x->queues.grow(4 * (size_t)(b.nwaves + 1))) ||
@@ -1473,8 +1471,7 @@ static void make_params(BatchInst& b) {
   p.cmax_bits = acc + kAccCmax;
   p.it_sum = x->it_sum.as<double>();
   p.it_stride = 2;
-  p.e_hm = x->e_hm.as<uint64_t>();
-  p.e_part = x->e_part.as<uint64_t>();
+  p.e_hp = x->e_hp.as<ulonglong2>();
   p.e_rec = x->e_rec.as<uint32_t>();
   p.tgt_on = x->tgt_on;
   p.tgt_max_exc = x->tgt_max_exc;
@@ -1737,8 +1734,7 @@ static int plan_fused(qp_pt2_batch* B, const qp_pt2_batch_options& o, size_t wav
       p.r_part = reinterpret_cast<uint64_t*>(take(8 * nd * ws));
       p.r_flag = reinterpret_cast<uint32_t*>(take(4 * nd * ws));
       p.b_ofs = reinterpret_cast<int*>(take(4 * (size_t)(x->nbat + 2) * ws));
-      p.e_hm = reinterpret_cast<uint64_t*>(take(8 * (size_t)b.ent_cap * ws));
-      p.e_part = reinterpret_cast<uint64_t*>(take(8 * (size_t)b.ent_cap * ws));
+      p.e_hp = reinterpret_cast<ulonglong2*>(take(16 * (size_t)b.ent_cap * ws));
       p.e_rec = reinterpret_cast<uint32_t*>(take(4 * (size_t)b.ent_cap * ws));
       p.b_dead = reinterpret_cast<uint32_t*>(take(4 * (size_t)((x->nbat + 31) / 32) * ws));
       p.it_sum = reinterpret_cast<double*>(take(16 * (size_t)b.nper * ws));

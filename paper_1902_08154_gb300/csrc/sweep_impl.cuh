@@ -56,6 +56,9 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kChunk = 1024;  // bucket entries classified per round
 constexpr int kGroup = 8;     // J reaching every cell, handled together
 constexpr unsigned kFull = 0xffffffffu;
+// Bit of a bucket entry's particle word that flags a J ranked before I (see
+// part_code below).
+constexpr uint64_t kBeforeBit = 1ull << 15;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -400,7 +403,7 @@ __device__ __forceinline__ void prep_slot(const SweepParams& p, const int slot) 
     const int pos = block_scan_flag(keep, s_wsum, &total);
     if (keep) {
       const int r = nrec + pos;
-      uint64_t hmask = 0, part = ~0ull;
+      uint64_t hmask = 0, part = 0x7FFF7FFF7FFF7FFFull;  // four unused fields (kNoPart)
       int npart = 0;
 #pragma unroll
       for (int s = 0; s < 2; s++) {
@@ -457,18 +460,17 @@ __device__ __forceinline__ void prep_slot(const SweepParams& p, const int slot) 
   int* ofs = p.b_ofs + (size_t)slot * (nbat + 2);
   for (int b = tid; b <= nbat + 1; b += kThreads) ofs[b] = s_cnt[b];
   __syncthreads();
-  uint64_t* e_hm = p.e_hm + (size_t)slot * (size_t)p.ent_cap;
-  uint64_t* e_part = p.e_part + (size_t)slot * (size_t)p.ent_cap;
+  ulonglong2* e_hp = p.e_hp + (size_t)slot * (size_t)p.ent_cap;
   uint32_t* e_rec = p.e_rec + (size_t)slot * (size_t)p.ent_cap;
   const long long cap = p.ent_cap;
   for (int r = tid; r < nrec; r += kThreads) {
-    const uint64_t hm = rh[r], pt = rp[r];
-    const uint32_t rec = (uint32_t)r | ((rf[r] & 1u) << 31);
+    const uint32_t before = rf[r] & 1u;
+    const uint64_t hm = rh[r], pt = rp[r] | (before ? kBeforeBit : 0ull);
+    const uint32_t rec = (uint32_t)r | (before << 31);
     for_buckets(hm, nel, nbat, [&](int b) {
       const int o = atomicAdd(&s_cnt[b], 1);
       if (o < cap) {
-        e_hm[o] = hm;
-        e_part[o] = pt;
+        e_hp[o] = make_ulonglong2(hm, pt);
         e_rec[o] = rec;
       }
     });
@@ -605,6 +607,9 @@ struct BatchShared {
     } m;
   } v;
   int gx1[kGroup], gx2[kGroup], gsr[kGroup], gsc[kGroup];
+  // two-hole batches, after loop 1: bit x of frow (fcol) set when row
+  // (column) x of cells is banned as a whole by a J ranked before I
+  uint32_t frow[kMaxOrb / 32], fcol[kMaxOrb / 32];
   int wsum[kWarps];
   // selection
   int tkcnt;
@@ -673,14 +678,22 @@ __device__ __forceinline__ int pair_cell(int x, int y) {  // x != y virtual indi
 // indexed at run time would live in local memory.
 __device__ __forceinline__ int pk(uint32_t v, int i) { return (int)((v >> (8 * i)) & 0xFFu); }
 
+// A bucket entry's particle word: four 16-bit fields, each the spin-orbital
+// code s*norb + q (< 256) of a particle of J outside I, or kNoPart.  Bit 15
+// (the top bit of the first field, which always holds a particle when it is
+// set) flags a J ranked before I, so that one 16-byte load of the entry
+// (hole mask, particle word) is all the classification reads.
+constexpr int kNoPart = 0x7FFF;
+__device__ __forceinline__ int part_code(uint64_t part, int i) { return (int)((part >> (16 * i)) & 0x7FFF); }
+
 // Particles of J outside I, filtered to a spin, as orbitals (packed).
 __device__ __forceinline__ uint32_t particles_of_spin(uint64_t part, int norb, int spin, int* n) {
   uint32_t out = 0;
   int k = 0;
 #pragma unroll
   for (int i = 0; i < 4; i++) {
-    const int c = (int)((part >> (16 * i)) & 0xFFFF);
-    if (c == 0xFFFF) continue;
+    const int c = part_code(part, i);
+    if (c == kNoPart) continue;
     const int s = c >= norb;
     if (s == spin) {
       out |= (uint32_t)(c - s * norb) << (8 * k);
@@ -728,8 +741,30 @@ __device__ __forceinline__ bool subset_live(const Batch& B, const BatchShared<NI
   return live;
 }
 
+__device__ __forceinline__ bool flagged(const uint32_t* f, int x) { return (f[x >> 5] >> (x & 31)) & 1u; }
+
+// True when some row or column of cells that a J with t = 1 reaches (the
+// rows of its particles) is not banned as a whole.  Rows flagged in loop 1
+// hold no live cell, so a J whose rows are all flagged adds nothing: it is
+// dropped at classification (the rows and columns of a J ranked after I are
+// mostly those of earlier J with the same particles).
+template <int NINT, typename NT>
+__device__ __forceinline__ bool row_live(const Batch& B, const BatchShared<NINT, NT>& S, int norb, uint64_t part) {
+  bool live = false;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const int c = part_code(part, i);
+    if (c == kNoPart) continue;
+    const int s = c >= norb, q = c - s * norb;
+    if (B.kind == 2) live |= !flagged(s ? S.fcol : S.frow, S.vidx[s][q]);
+    else if (s == B.sa) live |= !flagged(S.frow, S.vidx[s][q]);
+  }
+  return live;
+}
+
 // Cells touching the particles of J (two-hole batch, t = 1): visited by the
-// 32 lanes of a warp, each cell once.
+// 32 lanes of a warp, each cell once.  Rows and columns banned as a whole are
+// skipped (a cell they share with another row is banned too).
 template <int NINT, typename NT, typename Fn>
 __device__ __forceinline__ void for_row_cells(const Batch& B, const BatchShared<NINT, NT>& S, int norb,
                                               uint64_t part, int lane, Fn&& fn) {
@@ -739,6 +774,7 @@ __device__ __forceinline__ void for_row_cells(const Batch& B, const BatchShared<
     const int nv = S.nv[B.sa];
     for (int i = 0; i < np; i++) {
       const int x = S.vidx[B.sa][pk(P, i)];
+      if (flagged(S.frow, x)) continue;
       for (int y = lane; y < nv; y += 32) {
         if (y == x) continue;
         bool dup = false;  // pair {P[j], P[i]}, j < i, was visited from P[j]
@@ -753,10 +789,12 @@ __device__ __forceinline__ void for_row_cells(const Batch& B, const BatchShared<
     const int nv0 = S.nv[0], nv1 = S.nv[1];
     for (int i = 0; i < na; i++) {
       const int x = S.vidx[0][pk(Pa, i)];
+      if (flagged(S.frow, x)) continue;
       for (int y = lane; y < nv1; y += 32) fn(x * nv1 + y);
     }
     for (int j = 0; j < nb; j++) {
       const int y = S.vidx[1][pk(Pb, j)];
+      if (flagged(S.fcol, y)) continue;
       for (int x = lane; x < nv0; x += 32) {
         bool dup = false;  // rows of Pa were visited above
         for (int i = 0; i < na; i++) dup |= (S.vidx[0][pk(Pa, i)] == x);
@@ -775,8 +813,8 @@ __device__ __forceinline__ void excitation_sets(const Batch& B, const BatchShare
   uint32_t xs = 0, ts = 0;
 #pragma unroll
   for (int i = 0; i < 4; i++) {
-    const uint32_t c = (uint32_t)((part >> (16 * i)) & 0xFFFF);
-    if (c != 0xFFFFu && a < 4) xs |= c << (8 * a++);
+    const int c = part_code(part, i);
+    if (c != kNoPart && a < 4) xs |= (uint32_t)c << (8 * a++);
   }
   if (!((hm >> B.ia) & 1ull) && a < 4) xs |= (uint32_t)B.ca << (8 * a++);
   if (B.h == 2 && !((hm >> B.ib) & 1ull) && a < 4) xs |= (uint32_t)B.cb << (8 * a++);
@@ -1261,8 +1299,7 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
   const uint64_t* rw = p.r_words + rb * NW;
   const double* rc = p.r_coef + rb;
   const size_t eb = (size_t)slot * (size_t)p.ent_cap;
-  const uint64_t* ehm = p.e_hm + eb;
-  const uint64_t* epart = p.e_part + eb;
+  const ulonglong2* ehp = p.e_hp + eb;
   const uint32_t* erec = p.e_rec + eb;
   // position of the i-th entry of this batch in the slot's entry arrays
   auto entry = [&](int i) {
@@ -1368,17 +1405,19 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
   for (int c0 = 0; c0 < total; c0 += kChunk) {
     bool dl = false;
     const int c1 = min(c0 + kChunk, total);
+    // each thread's next entry is loaded while it classifies the current one
+    ulonglong2 enx = (c0 + tid < c1) ? ehp[entry(c0 + tid)] : make_ulonglong2(0ull, 0ull);
     for (int i = c0 + tid; i < c1; i += kThreads) {
-      const int o = entry(i);
-      const uint64_t hm = ehm[o];
+      const ulonglong2 en = enx;
+      if (i + kThreads < c1) enx = ehp[entry(i + kThreads)];
+      const uint64_t hm = en.x, part = en.y;
       if (dup(i, hm)) continue;
       const int t = __popcll(hm & ~B.hm);
       if (t > 2) continue;
-      if (erec[o] >> 31) {
+      if (part & kBeforeBit) {
         if ((B.h == 1 && t <= 1) || (B.h == 2 && t == 0)) {
           dl = true;
         } else if (B.h == 2 && t == 1) {
-          const uint64_t part = epart[o];
           int na_, nb_;
           const uint32_t Pa = particles_of_spin(part, norb, B.kind == 2 ? 0 : B.sa, &na_);
           for (int q = 0; q < na_; q++) S.v.m.rowm[S.vidx[B.kind == 2 ? 0 : B.sa][pk(Pa, q)]] = 1u;
@@ -1387,10 +1426,9 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
             for (int q = 0; q < nb_; q++) S.v.m.colm[S.vidx[1][pk(Pb, q)]] = 1u;
           }
         } else {  // t == 2
-          for_subset_cells<NINT, NT>(B, S, norb, epart[o], [&](int c) { ban_cell(ban, B, c); });
+          for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) { ban_cell(ban, B, c); });
         }
       } else if (t == 0 && hm == B.hm) {  // J = I - H + X with X a cell: alpha is internal
-        const uint64_t part = epart[o];
         int n0, n1, c;
         if (B.kind == 0) {
           const uint32_t P0 = particles_of_spin(part, norb, B.sa, &n0);
@@ -1424,6 +1462,13 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
       const unsigned bw = __ballot_sync(kFull, bn);
       if (lane == 0 && bw) ban[(c0 >> 5) + warp] |= bw;
     }
+    // the flags as bit masks, kept through loop 2 (their storage is reused)
+    static_assert(kWarps >= 2 * (kMaxOrb / 32), "one warp per mask word");
+    if (warp < 2 * (kMaxOrb / 32)) {
+      const int w = warp % (kMaxOrb / 32), x = 32 * w + lane;
+      const unsigned f = __ballot_sync(kFull, (warp < kMaxOrb / 32 ? S.v.m.rowm[x] : S.v.m.colm[x]) != 0u);
+      if (lane == 0) (warp < kMaxOrb / 32 ? S.frow : S.fcol)[w] = f;
+    }
     __syncthreads();
   }
 
@@ -1440,18 +1485,23 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
     }
     __syncthreads();
     const int c1 = min(c0 + kChunk, total);
+    ulonglong2 enx = (c0 + tid < c1) ? ehp[entry(c0 + tid)] : make_ulonglong2(0ull, 0ull);
     for (int i = c0 + tid; i < c1; i += kThreads) {
+      const ulonglong2 en = enx;
       const int o = entry(i);
-      if (erec[o] >> 31) continue;
-      const uint64_t hmr = ehm[o];
+      if (i + kThreads < c1) enx = ehp[entry(i + kThreads)];
+      const uint64_t hmr = en.x, part = en.y;
+      if (part & kBeforeBit) continue;
       if (dup(i, hmr)) continue;
       if (B.h == 2 && hmr == 0ull) continue;  // J = I: added in the cells pass
       const int t = __popcll(hmr & ~B.hm);
       if (t > 2) continue;
       const bool all = (B.h == 1) ? (t <= 1) : (t == 0);
       if (all) S.u.l.L0[atomicAdd(&S.n0, 1)] = o;
-      else if (t == 1) S.u.l.L1[atomicAdd(&S.n1, 1)] = o;
-      else if (subset_live<NINT, NT>(B, S, norb, epart[o], ban)) S.u.l.L2[atomicAdd(&S.n2, 1)] = o;
+      else if (t == 1) {
+        if (row_live<NINT, NT>(B, S, norb, part)) S.u.l.L1[atomicAdd(&S.n1, 1)] = o;
+      }
+      else if (subset_live<NINT, NT>(B, S, norb, part, ban)) S.u.l.L2[atomicAdd(&S.n2, 1)] = o;
     }
     __syncthreads();
     // J reaching every cell: the whole CTA, kGroup of them per pass.
@@ -1472,7 +1522,8 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
           for (int st = 0; st < nst; st++) ms_gc[tid * kMaxStates + st] = rc[st * p.rc_stride + r];
         uint32_t xs, ts;
         int nxs, nts;
-        excitation_sets<NINT, NT>(B, S, epart[o], ehm[o], &xs, &nxs, &ts, &nts);
+        const ulonglong2 en = ehp[o];
+        excitation_sets<NINT, NT>(B, S, en.y, en.x, &xs, &nxs, &ts, &nts);
         S.gX[tid] = xs;
         S.gT[tid] = ts;
         S.gnx[tid] = nxs;
@@ -1548,7 +1599,14 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
               general = false;
             }
           }
-          if (general) v = element<NINT, NT>(eri_n, h_n, norb, S.gJw[j], S.gX[j], S.gnx[j], S.gT[j], S.gnt[j], rcode, scode);
+          if (general) {
+            // two-hole batch: a cell touching the particles of J is a single
+            // substitution of J (or J itself, banned); those cells go by rows
+            // in the row pass below, with every lane of a warp on a cell
+            if (B.h == 2) continue;
+            v = element<NINT, NT>(eri_n, h_n, norb, S.gJw[j], S.gX[j], S.gnx[j], S.gT[j], S.gnt[j], rcode, scode);
+          }
+          con++;
           if constexpr (MS) {
 #pragma unroll
             for (int st = 0; st < kMaxStates; st++)
@@ -1571,21 +1629,21 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
           Alo[cc] = lo;
           Ahi[cc] = hi;
         }
-        con += m;
       }
       __syncthreads();
     }
-    // J reaching a row of cells (one warp each), then J reaching a few
-    // cells (one lane each, 32 per draw), drawn by the warps as they free up
+    // J reaching a row of cells (one warp each; in a two-hole batch the J
+    // reaching every cell come after them, for the cells touching their
+    // particles), then J reaching a few cells (one lane each, 32 per draw),
+    // drawn by the warps as they free up
     {
-      const int n1 = S.n1, n2 = S.n2;
+      const int n1 = S.n1 + (B.h == 2 ? n0 : 0), n2 = S.n2;
       for (;;) {
         int jd = 0;
         if (lane == 0) jd = atomicAdd(&S.cnext, 1);
         jd = __shfl_sync(kFull, jd, 0);
         if (jd < n1) {
-          const int j = jd;
-          const int o = S.u.l.L1[j];
+          const int o = jd < S.n1 ? S.u.l.L1[jd] : S.u.l.L0[jd - S.n1];
           const int r = (int)(erec[o] & 0x7FFFFFFFu);
           const uint64_t* Jw = rw + (size_t)r * NW;
           const NT cj = (NT)rc[r];
@@ -1594,10 +1652,11 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
 #pragma unroll
             for (int st = 0; st < kMaxStates; st++) cjs[st] = st < nst ? rc[st * p.rc_stride + r] : 0.0;
           }
-          const uint64_t part = epart[o];
+          const ulonglong2 en = ehp[o];
+          const uint64_t part = en.y;
           uint32_t X, T;
           int nx, nt;
-          excitation_sets<NINT, NT>(B, S, part, ehm[o], &X, &nx, &T, &nt);
+          excitation_sets<NINT, NT>(B, S, part, en.x, &X, &nx, &T, &nt);
           for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
             const int cc = c - B.clo;
             if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
@@ -1632,10 +1691,11 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
 #pragma unroll
               for (int st = 0; st < kMaxStates; st++) cjs[st] = st < nst ? rc[st * p.rc_stride + r] : 0.0;
             }
-            const uint64_t part = epart[o];
+            const ulonglong2 en = ehp[o];
+          const uint64_t part = en.y;
             uint32_t X, T;
             int nx, nt;
-            excitation_sets<NINT, NT>(B, S, part, ehm[o], &X, &nx, &T, &nt);
+            excitation_sets<NINT, NT>(B, S, part, en.x, &X, &nx, &T, &nt);
             for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
               const int cc = c - B.clo;
               if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
@@ -1917,15 +1977,18 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
       const int c1 = min(c0 + kChunk, total);
       for (int i = c0 + tid; i < c1; i += kThreads) {
         const int o = entry(i);
-        if (erec[o] >> 31) continue;
-        const uint64_t hmr = ehm[o];
+        const ulonglong2 en = ehp[o];
+        const uint64_t hmr = en.x, part = en.y;
+        if (part & kBeforeBit) continue;
         if (dup(i, hmr)) continue;
         const int t = __popcll(hmr & ~B.hm);
         if (t > 2) continue;
         const bool all = (B.h == 1) ? (t <= 1) : (t == 0);
         if (all) S.u.l.L0[atomicAdd(&S.n0, 1)] = o;
-        else if (t == 1) S.u.l.L1[atomicAdd(&S.n1, 1)] = o;
-        else if (subset_live<NINT, NT>(B, S, norb, epart[o], ban)) S.u.l.L2[atomicAdd(&S.n2, 1)] = o;
+        else if (t == 1) {
+          if (row_live<NINT, NT>(B, S, norb, part)) S.u.l.L1[atomicAdd(&S.n1, 1)] = o;
+        }
+        else if (subset_live<NINT, NT>(B, S, norb, part, ban)) S.u.l.L2[atomicAdd(&S.n2, 1)] = o;
       }
       __syncthreads();
       for (int j = 0; j < S.n0; j++) {
@@ -1935,7 +1998,8 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
         const double cj = rc[r];
         uint32_t X, T;
         int nx, nt;
-        excitation_sets<NINT, NT>(B, S, epart[o], ehm[o], &X, &nx, &T, &nt);
+        const ulonglong2 en = ehp[o];
+        excitation_sets<NINT, NT>(B, S, en.y, en.x, &X, &nx, &T, &nt);
         for (int cc = tid; cc < B.nct; cc += kThreads) {
           if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
           int ro, so, x, y;
@@ -1955,10 +2019,11 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
             const int r = (int)(erec[o] & 0x7FFFFFFFu);
             const uint64_t* Jw = rw + (size_t)r * NW;
             const double cj = rc[r];
-            const uint64_t part = epart[o];
+            const ulonglong2 en = ehp[o];
+          const uint64_t part = en.y;
             uint32_t X, T;
             int nx, nt;
-            excitation_sets<NINT, NT>(B, S, part, ehm[o], &X, &nx, &T, &nt);
+            excitation_sets<NINT, NT>(B, S, part, en.x, &X, &nx, &T, &nt);
             for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
               const int cc = c - B.clo;
               if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
@@ -1975,10 +2040,11 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
               const int r = (int)(erec[o] & 0x7FFFFFFFu);
               const uint64_t* Jw = rw + (size_t)r * NW;
               const double cj = rc[r];
-              const uint64_t part = epart[o];
+              const ulonglong2 en = ehp[o];
+          const uint64_t part = en.y;
               uint32_t X, T;
               int nx, nt;
-              excitation_sets<NINT, NT>(B, S, part, ehm[o], &X, &nx, &T, &nt);
+              excitation_sets<NINT, NT>(B, S, part, en.x, &X, &nx, &T, &nt);
               for_subset_cells<NINT, NT>(B, S, norb, part, [&](int c) {
                 const int cc = c - B.clo;
                 if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
