@@ -764,7 +764,9 @@ __device__ __forceinline__ bool row_live(const Batch& B, const BatchShared<NINT,
 
 // Cells touching the particles of J (two-hole batch, t = 1): visited by the
 // 32 lanes of a warp, each cell once.  Rows and columns banned as a whole are
-// skipped (a cell they share with another row is banned too).
+// skipped (a cell they share with another row is banned too).  fn(c, pc, zc)
+// gets the cell index, the spin-orbital code of the particle of J whose row
+// it is and the code of the cell's other orbital.
 template <int NINT, typename NT, typename Fn>
 __device__ __forceinline__ void for_row_cells(const Batch& B, const BatchShared<NINT, NT>& S, int norb,
                                               uint64_t part, int lane, Fn&& fn) {
@@ -779,7 +781,7 @@ __device__ __forceinline__ void for_row_cells(const Batch& B, const BatchShared<
         if (y == x) continue;
         bool dup = false;  // pair {P[j], P[i]}, j < i, was visited from P[j]
         for (int j = 0; j < i; j++) dup |= (S.vidx[B.sa][pk(P, j)] == y);
-        if (!dup) fn(pair_cell(x, y));
+        if (!dup) fn(pair_cell(x, y), B.sa * norb + pk(P, i), B.sa * norb + S.vir[B.sa][y]);
       }
     }
   } else {  // kind 2
@@ -790,7 +792,7 @@ __device__ __forceinline__ void for_row_cells(const Batch& B, const BatchShared<
     for (int i = 0; i < na; i++) {
       const int x = S.vidx[0][pk(Pa, i)];
       if (flagged(S.frow, x)) continue;
-      for (int y = lane; y < nv1; y += 32) fn(x * nv1 + y);
+      for (int y = lane; y < nv1; y += 32) fn(x * nv1 + y, pk(Pa, i), norb + S.vir[1][y]);
     }
     for (int j = 0; j < nb; j++) {
       const int y = S.vidx[1][pk(Pb, j)];
@@ -798,7 +800,7 @@ __device__ __forceinline__ void for_row_cells(const Batch& B, const BatchShared<
       for (int x = lane; x < nv0; x += 32) {
         bool dup = false;  // rows of Pa were visited above
         for (int i = 0; i < na; i++) dup |= (S.vidx[0][pk(Pa, i)] == x);
-        if (!dup) fn(x * nv1 + y);
+        if (!dup) fn(x * nv1 + y, norb + pk(Pb, j), S.vir[0][x]);
       }
     }
   }
@@ -887,6 +889,34 @@ __device__ __noinline__ NT element(const NT* eri, const NT* hh, int norb, const 
   w1[p1 >> 6] |= (1ull << (p1 & 63));
   const int n2 = (s2 == s1) ? count_between<NINT>(w1, h2 < p2 ? h2 : p2, h2 < p2 ? p2 : h2)
                             : count_between<NINT>(Jw + s2 * NINT, h2 < p2 ? h2 : p2, h2 < p2 ? p2 : h2);
+  NT v = eri[eri_index(h1, p1, h2, p2)];
+  if (s1 == s2) v -= eri[eri_index(h1, p2, h2, p1)];
+  return flip_sign(v, (n1 + n2) & 1);
+}
+
+// <J|H|alpha> for a cell of the row pass whose substitution from J is a
+// double: holes u0 < u1 (X without the row's particle), particles q (the
+// hole of J outside the batch) and z (the cell's other orbital, not in X).
+// The same pairing and phases as element(), inline: the row pass evaluates
+// most of its cells here.
+template <int NINT, typename NT>
+__device__ __forceinline__ NT row_double(const NT* eri, int norb, const uint64_t* jw, int u0, int u1, int q, int z) {
+  const int pa0 = q < z ? q : z, pa1 = q < z ? z : q;
+  const int s1 = u0 >= norb, s2 = u1 >= norb;
+  const int h1 = u0 - s1 * norb, p1 = pa0 - s1 * norb;
+  const int h2 = u1 - s2 * norb, p2 = pa1 - s2 * norb;
+  uint64_t w1[NINT];
+#pragma unroll
+  for (int w = 0; w < NINT; w++) w1[w] = s1 ? jw[NINT + w] : jw[w];
+  const int n1 = count_between<NINT>(w1, h1 < p1 ? h1 : p1, h1 < p1 ? p1 : h1);
+  if (s2 == s1) {
+    w1[h1 >> 6] &= ~(1ull << (h1 & 63));
+    w1[p1 >> 6] |= (1ull << (p1 & 63));
+  } else {
+#pragma unroll
+    for (int w = 0; w < NINT; w++) w1[w] = s2 ? jw[NINT + w] : jw[w];
+  }
+  const int n2 = count_between<NINT>(w1, h2 < p2 ? h2 : p2, h2 < p2 ? p2 : h2);
   NT v = eri[eri_index(h1, p1, h2, p2)];
   if (s1 == s2) v -= eri[eri_index(h1, p2, h2, p1)];
   return flip_sign(v, (n1 + n2) & 1);
@@ -1657,22 +1687,37 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
           uint32_t X, T;
           int nx, nt;
           excitation_sets<NINT, NT>(B, S, part, en.x, &X, &nx, &T, &nt);
-          for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
+          for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c, int pc, int zc) {
             const int cc = c - B.clo;
             if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
-            int ro, so, x, y;
-            cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-            const int rcode = B.sa * norb + ro;
-            const int scode = B.sb * norb + so;
+            // holes of the substitution J -> alpha: X without the row's
+            // particle; a double unless the other orbital is in X too or J
+            // reaches every cell (then a single, by the general routine)
+            bool zin = false;
+            int u0 = -1, u1 = -1;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+              if (i >= nx) break;
+              const int xc = pk(X, i);
+              zin |= xc == zc;
+              if (xc != pc) {
+                if (u0 < 0) u0 = xc;
+                else u1 = xc;
+              }
+            }
+            NT v;
+            if (nt == 1 && !zin && u1 >= 0)
+              v = row_double<NINT, NT>(eri_n, norb, Jw, u0 < u1 ? u0 : u1, u0 < u1 ? u1 : u0, pk(T, 0), zc);
+            else
+              v = element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, pc, zc);
             if constexpr (MS) {
-              const double v = (double)element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode);
 #pragma unroll
               for (int st = 0; st < kMaxStates; st++)
-                if (st < nst) atomicAdd(&A[st * mc + cc], cjs[st] * v);
+                if (st < nst) atomicAdd(&A[st * mc + cc], cjs[st] * (double)v);
             } else {
               unsigned long long l;
               int hh;
-              fix_of(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode), F, l, hh);
+              fix_of(cj * v, F, l, hh);
               fix_atomic_add(Alo, Ahi, cc, l, hh);
             }
             con++;
@@ -2024,12 +2069,10 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
             uint32_t X, T;
             int nx, nt;
             excitation_sets<NINT, NT>(B, S, part, en.x, &X, &nx, &T, &nt);
-            for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c) {
+            for_row_cells<NINT, NT>(B, S, norb, part, lane, [&](int c, int pc, int zc) {
               const int cc = c - B.clo;
               if ((unsigned)cc >= (unsigned)B.nct || ((ban[cc >> 5] >> (cc & 31)) & 1u)) return;
-              int ro, so, x, y;
-              cell_orbitals<NINT, NT>(B, S, c, &ro, &so, &x, &y);
-              element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, B.sa * norb + ro, B.sb * norb + so, cj * A[cc]);
+              element_grad<NINT>(p.g_dh, p.g_deri, norb, Jw, X, nx, T, nt, pc, zc, cj * A[cc]);
             });
           } else {
             const int j0 = (jd - n1) * 32;
