@@ -53,7 +53,7 @@ namespace qp {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kChunk = 1024;  // bucket entries classified per round
+constexpr int kChunk = 1536;  // bucket entries classified per round
 constexpr int kGroup = 8;     // J reaching every cell, handled together
 constexpr unsigned kFull = 0xffffffffu;
 // Bit of a bucket entry's particle word that flags a J ranked before I (see
@@ -577,7 +577,9 @@ struct BatchShared {
   // and 3, the selection histogram, the per-thread sums of the reduction
   union {
     struct {
-      int L0[kChunk], L1[kChunk], L2[kChunk];
+      // records of the J reaching every cell; of the J reaching rows (from
+      // the front) and a few cells (from the back)
+      int L0[kChunk], L12[kChunk];
     } l;
     int hist[256];
     double red_t[2][kThreads];  // per-thread e and (A/D)^2 sums of the item
@@ -1328,6 +1330,8 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
   const size_t rb = (size_t)slot * (size_t)p.ndet;
   const uint64_t* rw = p.r_words + rb * NW;
   const double* rc = p.r_coef + rb;
+  const uint64_t* rhm = p.r_hmask + rb;  // hole mask and particle word of each record
+  const uint64_t* rpt = p.r_part + rb;
   const size_t eb = (size_t)slot * (size_t)p.ent_cap;
   const ulonglong2* ehp = p.e_hp + eb;
   const uint32_t* erec = p.e_rec + eb;
@@ -1527,11 +1531,12 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
       const int t = __popcll(hmr & ~B.hm);
       if (t > 2) continue;
       const bool all = (B.h == 1) ? (t <= 1) : (t == 0);
-      if (all) S.u.l.L0[atomicAdd(&S.n0, 1)] = o;
+      const int rec = (int)(erec[o] & 0x7FFFFFFFu);
+      if (all) S.u.l.L0[atomicAdd(&S.n0, 1)] = rec;
       else if (t == 1) {
-        if (row_live<NINT, NT>(B, S, norb, part)) S.u.l.L1[atomicAdd(&S.n1, 1)] = o;
+        if (row_live<NINT, NT>(B, S, norb, part)) S.u.l.L12[atomicAdd(&S.n1, 1)] = rec;
       }
-      else if (subset_live<NINT, NT>(B, S, norb, part, ban)) S.u.l.L2[atomicAdd(&S.n2, 1)] = o;
+      else if (subset_live<NINT, NT>(B, S, norb, part, ban)) S.u.l.L12[kChunk - 1 - atomicAdd(&S.n2, 1)] = rec;
     }
     __syncthreads();
     // J reaching every cell: the whole CTA, kGroup of them per pass.
@@ -1543,8 +1548,7 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
     for (int g0 = 0; g0 < n0; g0 += kGroup) {
       const int m = min(kGroup, n0 - g0);
       if (tid < m) {
-        const int o = S.u.l.L0[g0 + tid];
-        const int r = (int)(erec[o] & 0x7FFFFFFFu);
+        const int r = S.u.l.L0[g0 + tid];
 #pragma unroll
         for (int w = 0; w < NW; w++) S.gJw[tid][w] = rw[(size_t)r * NW + w];
         S.gcj[tid] = (NT)rc[r];
@@ -1552,7 +1556,7 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
           for (int st = 0; st < nst; st++) ms_gc[tid * kMaxStates + st] = rc[st * p.rc_stride + r];
         uint32_t xs, ts;
         int nxs, nts;
-        const ulonglong2 en = ehp[o];
+        const ulonglong2 en = make_ulonglong2(rhm[r], rpt[r]);
         excitation_sets<NINT, NT>(B, S, en.y, en.x, &xs, &nxs, &ts, &nts);
         S.gX[tid] = xs;
         S.gT[tid] = ts;
@@ -1673,8 +1677,7 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
         if (lane == 0) jd = atomicAdd(&S.cnext, 1);
         jd = __shfl_sync(kFull, jd, 0);
         if (jd < n1) {
-          const int o = jd < S.n1 ? S.u.l.L1[jd] : S.u.l.L0[jd - S.n1];
-          const int r = (int)(erec[o] & 0x7FFFFFFFu);
+          const int r = jd < S.n1 ? S.u.l.L12[jd] : S.u.l.L0[jd - S.n1];
           const uint64_t* Jw = rw + (size_t)r * NW;
           const NT cj = (NT)rc[r];
           double cjs[kMaxStates];
@@ -1682,7 +1685,7 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
 #pragma unroll
             for (int st = 0; st < kMaxStates; st++) cjs[st] = st < nst ? rc[st * p.rc_stride + r] : 0.0;
           }
-          const ulonglong2 en = ehp[o];
+          const ulonglong2 en = make_ulonglong2(rhm[r], rpt[r]);
           const uint64_t part = en.y;
           uint32_t X, T;
           int nx, nt;
@@ -1727,8 +1730,7 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
           if (j0 >= n2) break;
           const int j = j0 + lane;
           if (j < n2) {
-            const int o = S.u.l.L2[j];
-          const int r = (int)(erec[o] & 0x7FFFFFFFu);
+            const int r = S.u.l.L12[kChunk - 1 - j];
             const uint64_t* Jw = rw + (size_t)r * NW;
             const NT cj = (NT)rc[r];
             double cjs[kMaxStates];
@@ -1736,7 +1738,7 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
 #pragma unroll
               for (int st = 0; st < kMaxStates; st++) cjs[st] = st < nst ? rc[st * p.rc_stride + r] : 0.0;
             }
-            const ulonglong2 en = ehp[o];
+            const ulonglong2 en = make_ulonglong2(rhm[r], rpt[r]);
           const uint64_t part = en.y;
             uint32_t X, T;
             int nx, nt;
@@ -2029,21 +2031,21 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
         const int t = __popcll(hmr & ~B.hm);
         if (t > 2) continue;
         const bool all = (B.h == 1) ? (t <= 1) : (t == 0);
-        if (all) S.u.l.L0[atomicAdd(&S.n0, 1)] = o;
+        const int rec = (int)(erec[o] & 0x7FFFFFFFu);
+        if (all) S.u.l.L0[atomicAdd(&S.n0, 1)] = rec;
         else if (t == 1) {
-          if (row_live<NINT, NT>(B, S, norb, part)) S.u.l.L1[atomicAdd(&S.n1, 1)] = o;
+          if (row_live<NINT, NT>(B, S, norb, part)) S.u.l.L12[atomicAdd(&S.n1, 1)] = rec;
         }
-        else if (subset_live<NINT, NT>(B, S, norb, part, ban)) S.u.l.L2[atomicAdd(&S.n2, 1)] = o;
+        else if (subset_live<NINT, NT>(B, S, norb, part, ban)) S.u.l.L12[kChunk - 1 - atomicAdd(&S.n2, 1)] = rec;
       }
       __syncthreads();
       for (int j = 0; j < S.n0; j++) {
-        const int o = S.u.l.L0[j];
-        const int r = (int)(erec[o] & 0x7FFFFFFFu);
+        const int r = S.u.l.L0[j];
         const uint64_t* Jw = rw + (size_t)r * NW;
         const double cj = rc[r];
         uint32_t X, T;
         int nx, nt;
-        const ulonglong2 en = ehp[o];
+        const ulonglong2 en = make_ulonglong2(rhm[r], rpt[r]);
         excitation_sets<NINT, NT>(B, S, en.y, en.x, &X, &nx, &T, &nt);
         for (int cc = tid; cc < B.nct; cc += kThreads) {
           if ((ban[cc >> 5] >> (cc & 31)) & 1u) continue;
@@ -2060,11 +2062,10 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
           jd = __shfl_sync(kFull, jd, 0);
           if (jd < n1) {
             const int j = jd;
-            const int o = S.u.l.L1[j];
-            const int r = (int)(erec[o] & 0x7FFFFFFFu);
+            const int r = S.u.l.L12[j];
             const uint64_t* Jw = rw + (size_t)r * NW;
             const double cj = rc[r];
-            const ulonglong2 en = ehp[o];
+            const ulonglong2 en = make_ulonglong2(rhm[r], rpt[r]);
           const uint64_t part = en.y;
             uint32_t X, T;
             int nx, nt;
@@ -2079,11 +2080,10 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
             if (j0 >= n2) break;
             const int j = j0 + lane;
             if (j < n2) {
-              const int o = S.u.l.L2[j];
-              const int r = (int)(erec[o] & 0x7FFFFFFFu);
+              const int r = S.u.l.L12[kChunk - 1 - j];
               const uint64_t* Jw = rw + (size_t)r * NW;
               const double cj = rc[r];
-              const ulonglong2 en = ehp[o];
+              const ulonglong2 en = make_ulonglong2(rhm[r], rpt[r]);
           const uint64_t part = en.y;
               uint32_t X, T;
               int nx, nt;
