@@ -146,6 +146,10 @@ typedef struct {
 
 /* Create a context for norb orbitals and n_alpha + n_beta electrons.
  * Copies h and eri to the device (context-owned).  cfg may be NULL.
+ * Besides the packed copy the context keeps the integrals in a four-index
+ * layout for the sweep's gathers: 8 norb^4 bytes (12 norb^4 with the FP32
+ * copy of the mixed precision), e.g. 134 MB at norb = 64 and 2.1 GB at
+ * norb = 128 in FP64.  QP_ENOMEM when the device cannot hold it.
  * Returns QP_EINVAL for sizes out of range, QP_ESYM if h is not symmetric. */
 int qp_pt2_create(qp_pt2_ctx **out, int norb, int n_alpha, int n_beta, const double *h,
                   const double *eri, const qp_pt2_config *cfg);

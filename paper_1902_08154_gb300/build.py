@@ -15,8 +15,8 @@ OUT = os.path.join(HERE, "_build")
 SO = os.path.join(OUT, "libqp_pt2.so")
 # measured pipe throughput (FP64 FMA, integer XOR/POPC/add) for the roofline
 PEAKS_SO = os.path.join(OUT, "libqp_peaks.so")
-UNITS = ["qp_pt2.cu", "sweep.cu", "sweep_mixed.cu", "sweep_grad.cu", "sweep_states.cu", "noalloc.cu",
-         "davidson.cu"]
+UNITS = ["qp_pt2.cu", "sweep.cu", "sweep_mixed.cu", "sweep_grad.cu", "sweep_states.cu", "sweep_packed.cu",
+         "noalloc.cu", "davidson.cu"]
 HEADERS = ["common.cuh", "sweep_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

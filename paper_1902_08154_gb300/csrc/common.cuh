@@ -34,6 +34,16 @@ __device__ __forceinline__ int eri_index(int p, int q, int r, int s) {
   return tri(tri(p, q), tri(r, s));
 }
 
+// Four-index layout of the integrals for the sweep's numerator gathers:
+// (pq|rs) at ((p * norb + r) * norb + q) * norb + s, so that the integrals
+// (pq|rs) of a fixed pair (p, r) form one norb x norb slab, row q, column s.
+// The cells of a batch vary q and s over the virtual orbitals with (p, r)
+// fixed (two holes, or a J's two particles), so a warp reads consecutive s
+// of one row.  norb^4 entries (below 2^31 for norb <= 128).
+__device__ __forceinline__ int eri4_index(int p, int q, int r, int s, int norb) {
+  return ((p * norb + r) * norb + q) * norb + s;
+}
+
 // Number of set bits of the spin string sw (NINT words) strictly between
 // orbitals lo < hi: the masked popcount that gives a single substitution's
 // phase (Sec. "Internal representation of determinants").
@@ -123,6 +133,8 @@ struct SweepParams {
   const double* eri;      // packed
   const float* h32;       // FP32 copies for the mixed-precision numerator (NULL in FP64 mode)
   const float* eri32;
+  const double* eri4;     // [norb^4] four-index layout (eri4_index) of the batch kernel's gathers
+  const float* eri4_32;   // its FP32 copy (mixed precision; NULL in FP64 mode)
   int mixed;              // 1: numerator gathers and products in FP32
   const double* Jm;       // [norb*norb] (pp|qq)
   const double* Km;       // [norb*norb] (pq|qp)

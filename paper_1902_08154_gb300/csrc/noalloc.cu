@@ -53,9 +53,9 @@ __global__ void select_out_kernel(int n, int nint, const int32_t* perm, const do
                                   const uint64_t* ck, uint64_t* sel, double* se, double* sn);
 namespace qp {
 cudaError_t launch_prep(int nint, const SweepParams& p, int slots, cudaStream_t st);
-cudaError_t launch_batch(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_batch_packed(int nint, const SweepParams& p, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_reduce_items(const SweepParams& p, cudaStream_t st);
-int batch_blocks_per_sm(int nint, int mixed, size_t smem);
+int batch_blocks_per_sm_packed(int nint, size_t smem);
 int report(int code, const char* msg);
 }  // namespace qp
 
@@ -189,7 +189,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
   const int nbat = nel + nel * (nel - 1) / 2;
   const int max_cells = cells_max(norb, n_alpha, n_beta);
   const size_t smem = sweep_smem(max_cells);
-  if (batch_blocks_per_sm(nint, 0, smem) < 1) return nfail(QP_ENOTSUP, "batch accumulator exceeds shared memory");
+  if (batch_blocks_per_sm_packed(nint, smem) < 1) return nfail(QP_ENOTSUP, "batch accumulator exceeds shared memory");
   int nsm = 0;
   NTRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int grid = nsm;  // one CTA per SM keeps the selection buffers small
@@ -365,7 +365,7 @@ extern "C" int qp_pt2_eval_noalloc(int norb, int n_alpha, int n_beta, const doub
     p.queue = queues + w;
     NTRY_Q(cudaMemsetAsync(it_sum, 0, sizeof(double) * 2 * (size_t)nper * p.wave_slots, st));
     NTRY_Q(launch_prep(nint, p, p.wave_slots, st));
-    NTRY_Q(launch_batch(nint, p, grid, smem, st));
+    NTRY_Q(launch_batch_packed(nint, p, grid, smem, st));
     NTRY_Q(launch_reduce_items(p, st));
   }
   finalize_kernel<<<1, 1024, 0, st>>>(ndet, eps, s2, reinterpret_cast<const long long*>(na),

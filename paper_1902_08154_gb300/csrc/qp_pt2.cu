@@ -65,6 +65,18 @@ static const size_t kWaveBudget = (size_t)4 << 30;
 // ---------------------------------------------------------------------------
 // Small kernels
 // ---------------------------------------------------------------------------
+// The integrals in the batch kernel's four-index layout (eri4_index):
+// entry i = ((p * norb + r) * norb + q) * norb + s holds (pq|rs); the FP32
+// copy for the mixed-precision numerator when e4f is set.
+__global__ void eri4_kernel(int norb, const double* eri, double* e4d, float* e4f) {
+  const int64_t n = norb, i = blockIdx.x * 256ll + threadIdx.x;
+  if (i >= n * n * n * n) return;
+  const int s = (int)(i % n), q = (int)((i / n) % n), r = (int)((i / (n * n)) % n), p = (int)(i / (n * n * n));
+  const double v = eri[qp::eri_index(p, q, r, s)];
+  e4d[i] = v;
+  if (e4f) e4f[i] = (float)v;
+}
+
 __global__ void to_f32_kernel(int64_t n, const double* in, float* out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = (float)in[i];
@@ -309,6 +321,8 @@ struct qp_pt2_ctx {
   size_t smem;
   double *d_h = nullptr, *d_eri = nullptr, *d_J = nullptr, *d_K = nullptr;
   float *d_h32 = nullptr, *d_eri32 = nullptr;  // mixed precision only
+  double* d_eri4 = nullptr;                      // four-index layout (eri4_index)
+  float* d_eri4_32 = nullptr;                    // its FP32 copy, mixed precision only
   unsigned long long* d_hmax = nullptr;        // bits of max |h|, max |(pq|rs)|
   // workspace
   Buf in_dets, in_coefs, hkey, hkey2, hidx, hidx2, rkey, rkey2, order, rank_of, cub_tmp;
@@ -462,6 +476,13 @@ extern "C" int qp_pt2_create(qp_pt2_ctx** out, int norb, int n_alpha, int n_beta
     to_f32_kernel<<<(unsigned)((norb * norb + 255) / 256), 256, 0, x->st>>>(norb * norb, x->d_h, x->d_h32);
     to_f32_kernel<<<(unsigned)((P + 255) / 256), 256, 0, x->st>>>(P, x->d_eri, x->d_eri32);
   }
+  {  // the four-index layout of the numerator gathers (12 norb^4 bytes in mixed precision, 8 in FP64)
+    const int64_t n4 = (int64_t)norb * norb * norb * norb;
+    if (cudaMalloc(&x->d_eri4, sizeof(double) * n4) != cudaSuccess ||
+        (c.precision == QP_MIXED && cudaMalloc(&x->d_eri4_32, sizeof(float) * n4) != cudaSuccess))
+      return bail(QP_ENOMEM, "device allocation of the four-index integrals failed");
+    eri4_kernel<<<(unsigned)((n4 + 255) / 256), 256, 0, x->st>>>(norb, x->d_eri, x->d_eri4, x->d_eri4_32);
+  }
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(x->st) != cudaSuccess)
     return bail(QP_ECUDA, "integral tables failed");
   if (c.tile < 0) return bail(QP_EINVAL, "tile must be >= 0");
@@ -503,6 +524,8 @@ extern "C" void qp_pt2_destroy(qp_pt2_ctx* x) {
   cudaFree(x->d_eri);
   cudaFree(x->d_h32);
   cudaFree(x->d_eri32);
+  cudaFree(x->d_eri4);
+  cudaFree(x->d_eri4_32);
   cudaFree(x->d_J);
   cudaFree(x->d_K);
   cudaFree(x->d_hmax);
@@ -818,6 +841,8 @@ static int eval_core(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, const do
   p.eri = x->d_eri;
   p.h32 = x->d_h32;
   p.eri32 = x->d_eri32;
+  p.eri4 = x->d_eri4;
+  p.eri4_32 = x->d_eri4_32;
   p.mixed = x->cfg.precision == QP_MIXED;
   p.Jm = x->d_J;
   p.Km = x->d_K;
@@ -1216,6 +1241,7 @@ extern "C" int qp_pt2_grad(qp_pt2_ctx* x, int64_t ndet, const uint64_t* dets, co
   p.rank_of = x->rank_of.as<int32_t>();
   p.h = x->d_h;
   p.eri = x->d_eri;
+  p.eri4 = x->d_eri4;
   p.Jm = x->d_J;
   p.Km = x->d_K;
   p.e0 = e0;
@@ -1489,6 +1515,8 @@ static void make_params(BatchInst& b) {
   p.eri = x->d_eri;
   p.h32 = x->d_h32;
   p.eri32 = x->d_eri32;
+  p.eri4 = x->d_eri4;
+  p.eri4_32 = x->d_eri4_32;
   p.mixed = x->cfg.precision == QP_MIXED;
   p.Jm = x->d_J;
   p.Km = x->d_K;

@@ -105,12 +105,20 @@ __device__ __forceinline__ int block_scan_flag(bool f, int* wsum, int* total) {
 }
 
 // Integrals in the numerator precision.
-template <typename NT>
-__device__ __forceinline__ const NT* numer_eri(const SweepParams& p);
-template <>
-__device__ __forceinline__ const double* numer_eri<double>(const SweepParams& p) { return p.eri; }
-template <>
-__device__ __forceinline__ const float* numer_eri<float>(const SweepParams& p) { return p.eri32; }
+// E4: the four-index layout of the context (eri4_index); else the packed
+// array (the no-allocation entry point, which has only the caller's copy).
+template <typename NT, bool E4>
+__device__ __forceinline__ const NT* numer_eri(const SweepParams& p) {
+  if constexpr (sizeof(NT) == 8) return reinterpret_cast<const NT*>(E4 ? p.eri4 : p.eri);
+  else return reinterpret_cast<const NT*>(E4 ? p.eri4_32 : p.eri32);
+}
+
+// Position of (pq|rs) in the gather layout.
+template <bool E4>
+__device__ __forceinline__ int gidx(int p, int q, int r, int s, int norb) {
+  if constexpr (E4) return eri4_index(p, q, r, s, norb);
+  else return eri_index(p, q, r, s);
+}
 template <typename NT>
 __device__ __forceinline__ const NT* numer_h(const SweepParams& p);
 template <>
@@ -609,6 +617,9 @@ struct BatchShared {
     } m;
   } v;
   int gx1[kGroup], gx2[kGroup], gsr[kGroup], gsc[kGroup];
+  // four-index layout: the slab of each J's pair (x1, x2) and of the batch's
+  // holes; the pair tables then hold orbitals, not pair indices
+  int gB[kGroup], ibase;
   // two-hole batches, after loop 1: bit x of frow (fcol) set when row
   // (column) x of cells is banned as a whole by a J ranked before I
   uint32_t frow[kMaxOrb / 32], fcol[kMaxOrb / 32];
@@ -840,7 +851,7 @@ __device__ __forceinline__ void excitation_sets(const Batch& B, const BatchShare
 // kernel's code small enough for the instruction cache.
 // Jw points to the record's words in global or shared memory; the sets are
 // packed codes; nothing is passed through local memory.
-template <int NINT, typename NT>
+template <int NINT, typename NT, bool E4>
 __device__ __noinline__ NT element(const NT* eri, const NT* hh, int norb, const uint64_t* Jw, uint32_t X, int nx,
                                    uint32_t T, int nt, int r, int s) {
   int ho[2], pa[2], nh = 0, npp = 0;
@@ -869,8 +880,8 @@ __device__ __noinline__ NT element(const NT* eri, const NT* hh, int norb, const 
         while (bits) {
           const int q = 64 * w + __ffsll((long long)bits) - 1;
           bits &= bits - 1;
-          v += eri[eri_index(a, b, q, q)];
-          if (t == sp) v -= eri[eri_index(a, q, q, b)];
+          v += eri[gidx<E4>(a, b, q, q, norb)];
+          if (t == sp) v -= eri[gidx<E4>(a, q, q, b, norb)];
         }
       }
     }
@@ -891,8 +902,8 @@ __device__ __noinline__ NT element(const NT* eri, const NT* hh, int norb, const 
   w1[p1 >> 6] |= (1ull << (p1 & 63));
   const int n2 = (s2 == s1) ? count_between<NINT>(w1, h2 < p2 ? h2 : p2, h2 < p2 ? p2 : h2)
                             : count_between<NINT>(Jw + s2 * NINT, h2 < p2 ? h2 : p2, h2 < p2 ? p2 : h2);
-  NT v = eri[eri_index(h1, p1, h2, p2)];
-  if (s1 == s2) v -= eri[eri_index(h1, p2, h2, p1)];
+  NT v = eri[gidx<E4>(h1, p1, h2, p2, norb)];
+  if (s1 == s2) v -= eri[gidx<E4>(h1, p2, h2, p1, norb)];
   return flip_sign(v, (n1 + n2) & 1);
 }
 
@@ -901,7 +912,7 @@ __device__ __noinline__ NT element(const NT* eri, const NT* hh, int norb, const 
 // hole of J outside the batch) and z (the cell's other orbital, not in X).
 // The same pairing and phases as element(), inline: the row pass evaluates
 // most of its cells here.
-template <int NINT, typename NT>
+template <int NINT, typename NT, bool E4>
 __device__ __forceinline__ NT row_double(const NT* eri, int norb, const uint64_t* jw, int u0, int u1, int q, int z) {
   const int pa0 = q < z ? q : z, pa1 = q < z ? z : q;
   const int s1 = u0 >= norb, s2 = u1 >= norb;
@@ -919,8 +930,8 @@ __device__ __forceinline__ NT row_double(const NT* eri, int norb, const uint64_t
     for (int w = 0; w < NINT; w++) w1[w] = s2 ? jw[NINT + w] : jw[w];
   }
   const int n2 = count_between<NINT>(w1, h2 < p2 ? h2 : p2, h2 < p2 ? p2 : h2);
-  NT v = eri[eri_index(h1, p1, h2, p2)];
-  if (s1 == s2) v -= eri[eri_index(h1, p2, h2, p1)];
+  NT v = eri[gidx<E4>(h1, p1, h2, p2, norb)];
+  if (s1 == s2) v -= eri[gidx<E4>(h1, p2, h2, p1, norb)];
   return flip_sign(v, (n1 + n2) & 1);
 }
 
@@ -1196,7 +1207,7 @@ __device__ __forceinline__ ItemEnv item_env(const SweepParams& p) {
 // row tile of one): bans, the accumulation of A_alpha, the cells pass and the
 // item's sums.  Used by the kernel of one sweep and by the kernel whose queue
 // spans the waves of several instances.
-template <int NINT, typename NT, bool GRAD, bool MS>
+template <int NINT, typename NT, bool GRAD, bool MS, bool E4>
 __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NINT, NT>& S, const long long item,
                                            const int F, double* te, double* ta, uint64_t* tk, const ItemEnv& E,
                                            const NT* eri_n, const NT* h_n) {
@@ -1384,7 +1395,10 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
           const int s = S.vir[s2][y];
           S.u1[y] = S.F[s2][s] - W(s, s2, B.qa, s1) - W(s, s2, B.qb, s2);
         }
-      if (tid == 0) S.base = S.hii - S.F[s1][B.qa] - S.F[s2][B.qb] + W(B.qa, s1, B.qb, s2);
+      if (tid == 0) {
+        S.base = S.hii - S.F[s1][B.qa] - S.F[s2][B.qb] + W(B.qa, s1, B.qb, s2);
+        S.ibase = (B.qa * norb + B.qb) * norb * norb;
+      }
       // pair tables of J = I: rows tri(qa, r) and columns tri(qb, s) with
       // the phases of qa -> r and qb -> s on I's strings
       const int sl2 = (B.kind == 2) ? 1 : s1;
@@ -1393,7 +1407,7 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
         if (v < nva) {
           const int r = S.vir[s1][v];
           const int par = count_between<NINT>(S.I + s1 * NINT, r < B.qa ? r : B.qa, r < B.qa ? B.qa : r) & 1;
-          S.iRow[v] = tri(B.qa, r) | (par << 31);
+          S.iRow[v] = (E4 ? r : tri(B.qa, r)) | (par << 31);
         } else {
           const int sv = S.vir[sl2][v - nva];
           int par = count_between<NINT>(S.I + sl2 * NINT, sv < B.qb ? sv : B.qb, sv < B.qb ? B.qb : sv) & 1;
@@ -1401,7 +1415,7 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
             const int lo = sv < B.qb ? sv : B.qb, hi = sv < B.qb ? B.qb : sv;
             par ^= (B.qa > lo && B.qa < hi) ? 1 : 0;
           }
-          S.iCol[v - nva] = tri(B.qb, sv) | (par << 31);
+          S.iCol[v - nva] = (E4 ? sv : tri(B.qb, sv)) | (par << 31);
         }
       }
     }
@@ -1570,6 +1584,7 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
           const int s1 = x1 >= norb, s2 = x2 >= norb;
           S.gsr[tid] = S.vidx[s1][x1 - s1 * norb];
           S.gsc[tid] = S.vidx[s2][x2 - s2 * norb];
+          S.gB[tid] = ((x1 - s1 * norb) * norb + (x2 - s2 * norb)) * norb * norb;
         }
       }
       __syncthreads();
@@ -1586,7 +1601,7 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
             const int r = S.vir[sl1][v];
             int par = 0;
             if (r != x1) par = count_between<NINT>(Jw + sl1 * NINT, r < x1 ? r : x1, r < x1 ? x1 : r) & 1;
-            S.v.g.gRow[j][v] = tri(x1, r) | (par << 31);
+            S.v.g.gRow[j][v] = (E4 ? r : tri(x1, r)) | (par << 31);
           } else {
             const int sv = S.vir[sl2][v - nva];
             int par = 0;
@@ -1595,7 +1610,7 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
               const int lo = sv < x2 ? sv : x2, hi = sv < x2 ? x2 : sv;
               par ^= (x1 > lo && x1 < hi) ? 1 : 0;
             }
-            S.v.g.gCol[j][v - nva] = tri(x2, sv) | (par << 31);
+            S.v.g.gCol[j][v - nva] = (E4 ? sv : tri(x2, sv)) | (par << 31);
           }
         }
         __syncthreads();
@@ -1619,13 +1634,17 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
             if (B.kind == 2) {
               if (x != sr && y != sc) {
                 const int rt = S.v.g.gRow[j][x], ct = S.v.g.gCol[j][y];
-                v = flip_sign(eri_n[tri(rt & 0x7fffffff, ct & 0x7fffffff)], (rt ^ ct) < 0);
+                v = flip_sign(eri_n[E4 ? S.gB[j] + (rt & 0x7fffffff) * norb + (ct & 0x7fffffff) : tri(rt & 0x7fffffff, ct & 0x7fffffff)],
+                              (rt ^ ct) < 0);
                 general = false;
               }
             } else if (x != sr && x != sc && y != sr && y != sc) {
               const int a1 = S.v.g.gRow[j][x], b2 = S.v.g.gCol[j][y];
               const int a2 = S.v.g.gRow[j][y], b1 = S.v.g.gCol[j][x];
-              v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
+              if constexpr (E4)
+                v = eri_n[S.gB[j] + (a1 & 0x7fffffff) * norb + (b2 & 0x7fffffff)] - eri_n[S.gB[j] + (b2 & 0x7fffffff) * norb + (a1 & 0x7fffffff)];
+              else
+                v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
               const int x2 = S.gx2[j] - B.sa * norb;
               const int lo = so < x2 ? so : x2, hi = so < x2 ? x2 : so;
               const int par = ((a1 ^ b2) < 0 ? 1 : 0) ^ ((ro > lo && ro < hi) ? 1 : 0);
@@ -1638,7 +1657,7 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
             // substitution of J (or J itself, banned); those cells go by rows
             // in the row pass below, with every lane of a warp on a cell
             if (B.h == 2) continue;
-            v = element<NINT, NT>(eri_n, h_n, norb, S.gJw[j], S.gX[j], S.gnx[j], S.gT[j], S.gnt[j], rcode, scode);
+            v = element<NINT, NT, E4>(eri_n, h_n, norb, S.gJw[j], S.gX[j], S.gnx[j], S.gT[j], S.gnt[j], rcode, scode);
           }
           con++;
           if constexpr (MS) {
@@ -1710,9 +1729,9 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
             }
             NT v;
             if (nt == 1 && !zin && u1 >= 0)
-              v = row_double<NINT, NT>(eri_n, norb, Jw, u0 < u1 ? u0 : u1, u0 < u1 ? u1 : u0, pk(T, 0), zc);
+              v = row_double<NINT, NT, E4>(eri_n, norb, Jw, u0 < u1 ? u0 : u1, u0 < u1 ? u1 : u0, pk(T, 0), zc);
             else
-              v = element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, pc, zc);
+              v = element<NINT, NT, E4>(eri_n, h_n, norb, Jw, X, nx, T, nt, pc, zc);
             if constexpr (MS) {
 #pragma unroll
               for (int st = 0; st < kMaxStates; st++)
@@ -1751,14 +1770,14 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
               const int rcode = B.sa * norb + ro;
               const int scode = (B.h == 2) ? B.sb * norb + so : -1;
               if constexpr (MS) {
-                const double v = (double)element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode);
+                const double v = (double)element<NINT, NT, E4>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode);
 #pragma unroll
                 for (int st = 0; st < kMaxStates; st++)
                   if (st < nst) atomicAdd(&A[st * mc + cc], cjs[st] * v);
               } else {
                 unsigned long long l;
                 int hh;
-                fix_of(cj * element<NINT, NT>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode), F, l, hh);
+                fix_of(cj * element<NINT, NT, E4>(eri_n, h_n, norb, Jw, X, nx, T, nt, rcode, scode), F, l, hh);
                 fix_atomic_add(Alo, Ahi, cc, l, hh);
               }
               con++;
@@ -1801,10 +1820,15 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
       if (B.h == 2) {
         const int a1 = S.iRow[x], b2 = S.iCol[y];
         if (B.kind == 2) {
-          vI = (double)flip_sign(eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)], (a1 ^ b2) < 0);
+          vI = (double)flip_sign(eri_n[E4 ? S.ibase + (a1 & 0x7fffffff) * norb + (b2 & 0x7fffffff) : tri(a1 & 0x7fffffff, b2 & 0x7fffffff)],
+                                 (a1 ^ b2) < 0);
         } else {
           const int a2 = S.iRow[y], b1 = S.iCol[x];
-          NT v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
+          NT v;
+          if constexpr (E4)
+            v = eri_n[S.ibase + (a1 & 0x7fffffff) * norb + (b2 & 0x7fffffff)] - eri_n[S.ibase + (b2 & 0x7fffffff) * norb + (a1 & 0x7fffffff)];
+          else
+            v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
           const int lo = so < B.qb ? so : B.qb, hi = so < B.qb ? B.qb : so;
           vI = (double)flip_sign(v, ((a1 ^ b2) < 0 ? 1 : 0) ^ ((ro > lo && ro < hi) ? 1 : 0));
         }
@@ -1868,10 +1892,13 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
         NT v;
         const int a1 = S.iRow[x], b2 = S.iCol[y];
         if (B.kind == 2) {
-          v = flip_sign(eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)], (a1 ^ b2) < 0);
+          v = flip_sign(eri_n[E4 ? S.ibase + (a1 & 0x7fffffff) * norb + (b2 & 0x7fffffff) : tri(a1 & 0x7fffffff, b2 & 0x7fffffff)], (a1 ^ b2) < 0);
         } else {
           const int a2 = S.iRow[y], b1 = S.iCol[x];
-          v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
+          if constexpr (E4)
+            v = eri_n[S.ibase + (a1 & 0x7fffffff) * norb + (b2 & 0x7fffffff)] - eri_n[S.ibase + (b2 & 0x7fffffff) * norb + (a1 & 0x7fffffff)];
+          else
+            v = eri_n[tri(a1 & 0x7fffffff, b2 & 0x7fffffff)] - eri_n[tri(a2 & 0x7fffffff, b1 & 0x7fffffff)];
           const int lo = so < B.qb ? so : B.qb, hi = so < B.qb ? B.qb : so;
           v = flip_sign(v, ((a1 ^ b2) < 0 ? 1 : 0) ^ ((ro > lo && ro < hi) ? 1 : 0));
         }
@@ -2147,7 +2174,7 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
 // for every state, sums each into its own eps and s2, and offers the
 // determinant to the selection with the criterion sum_s w_s e_s,
 // w_s = 1/max_I c_Is^2 (Sec. "Selected CI", the criterion of Angeli et al.).
-template <int NINT, typename NT, bool GRAD = false, bool MS = false>
+template <int NINT, typename NT, bool GRAD = false, bool MS = false, bool E4 = true>
 __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(const __grid_constant__ SweepParams p) {
   static_assert(!(MS && GRAD), "the gradient is a one-state form");
   static_assert(!MS || sizeof(NT) == 8, "the multi-state form is FP64");
@@ -2159,7 +2186,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
   double* ta = p.tk_a + (size_t)blockIdx.x * (size_t)p.cap;
   uint64_t* tk = p.tk_key + (size_t)blockIdx.x * (size_t)p.cap * NW;
   const ItemEnv E = item_env<MS>(p);
-  const NT* eri_n = numer_eri<NT>(p);
+  const NT* eri_n = numer_eri<NT, E4>(p);
   const NT* h_n = numer_h<NT>(p);
 
   if (tid == 0) {
@@ -2188,7 +2215,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_kernel(co
     __syncthreads();
     const long long item = S.item;
     if (item >= nitems) break;
-    batch_item<NINT, NT, GRAD, MS>(p, S, item, F, te, ta, tk, E, eri_n, h_n);
+    batch_item<NINT, NT, GRAD, MS, E4>(p, S, item, F, te, ta, tk, E, eri_n, h_n);
   }
   if (p.k > 0 && p.last_wave) compact_selection<NINT, NT>(p, S, te, ta, tk);
   __syncthreads();
@@ -2252,7 +2279,7 @@ __global__ void __launch_bounds__(kThreads, (NINT == 1) ? 3 : 2) batch_multi_ker
       const long long item = S.item;
       if (item < 0) stop = true;
       if (item < 0 || item >= nitems) break;
-      batch_item<NINT, NT, false, false>(p, S, item, F, te, ta, tk, E, numer_eri<NT>(p), numer_h<NT>(p));
+      batch_item<NINT, NT, false, false, true>(p, S, item, F, te, ta, tk, E, numer_eri<NT, true>(p), numer_h<NT>(p));
     }
     __syncthreads();
     if (tid == 0) {
