@@ -60,7 +60,7 @@ INT_OPS_PER_CONNECTION_PER_WORD = 15
 # waves) over one sweep of the bench workload, from one ncu capture of the
 # current kernels (dram__bytes_read.sum + dram__bytes_write.sum; None when
 # the kernels have changed since the capture).
-TRAFFIC_BYTES_PER_SWEEP = 18.238e9
+TRAFFIC_BYTES_PER_SWEEP = 18.099e9
 
 
 def load_workload(name=WORKLOAD):
