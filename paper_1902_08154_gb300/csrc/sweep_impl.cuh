@@ -1557,7 +1557,8 @@ __device__ __forceinline__ void batch_item(const SweepParams& p, BatchShared<NIN
     // In a two-hole batch such a J is K + {x1, x2}; for a cell R disjoint
     // from {x1, x2} the element is a double substitution x1 x2 -> R whose
     // pair indices and phase split into a row part and a column part,
-    // precomputed once per J (cells meeting {x1, x2} take the general path).
+    // precomputed once per J; the cells meeting the particles of J are single
+    // substitutions of J and go to the row pass.
     const int n0 = S.n0;
     for (int g0 = 0; g0 < n0; g0 += kGroup) {
       const int m = min(kGroup, n0 - g0);
